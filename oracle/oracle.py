@@ -1,0 +1,442 @@
+"""Python face of the FP64 REBK oracle (TEST INFRASTRUCTURE ONLY).
+
+The iteration itself (Algorithm 1 of Du, Si, Sun, arXiv:2001.04179) runs in
+the plain C file ``rebk_oracle.c`` next to this one, compiled with
+-ffp-contract=off.  The rest is numpy, one library call per mathematical step:
+
+* ``pinv_solve``: A^+ b from the SVD (the paper's target, Section 1).
+* ``mean_closed_form``: E[z^k] and E[x^k] from the proof of Theorem ner
+  (the recursions for E[z^k] and E[x^k - A^+ b]).
+* ``beta_max``: beta^I_max and beta^J_max of Section 2.2 from the exact
+  spectral norms of the block Gram matrices.
+* ``bound_ner`` / ``bound_estz`` / ``bound_main``: right-hand sides of
+  Theorem ner, Lemma estz and Theorem main.
+* ``refine``: the mixed-precision outer loop (a reading of ours, the paper is
+  silent): FP64 residuals f = b - z - A x, g = A^T z, Algorithm 1 on
+  corrections with the reduced-precision matrix, FP64 update of x and z
+  through the duals.
+* ``mlp_forward`` / ``mlp_backward``: the warm-start network in FP64.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+__all__ = [
+    "build_oracle", "lib",
+    "philox", "uniform", "pick",
+    "block_norms", "cdf", "tables",
+    "rebk", "rebk_correction",
+    "pinv_solve", "mean_closed_form", "beta_max",
+    "bound_ner", "bound_estz", "bound_main",
+    "round_fp32", "round_bf16",
+    "dual_residuals", "refine",
+    "mlp_init", "mlp_forward", "mlp_backward", "mlp_loss",
+]
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rebk_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_SO = os.path.join(_BUILD, "liborc.so")
+_lock = threading.Lock()
+_lib = None
+
+_i64p = ctypes.POINTER(ctypes.c_int64)
+_f64p = ctypes.POINTER(ctypes.c_double)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_u64p = ctypes.POINTER(ctypes.c_uint64)
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile rebk_oracle.c with gcc (no FMA contraction) into _build/liborc.so."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
+        tmp = _SO + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
+               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _SO)
+    return _SO
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            so = build_oracle()
+            L = ctypes.CDLL(so)
+            L.orc_philox4x64_10.argtypes = [_u64p, _u64p, _u64p]
+            L.orc_philox4x64_10.restype = None
+            L.orc_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
+            L.orc_uniform.restype = ctypes.c_double
+            L.orc_pick.argtypes = [_f64p, ctypes.c_int64, ctypes.c_double]
+            L.orc_pick.restype = ctypes.c_int64
+            L.orc_block_norms.argtypes = [ctypes.c_int64, ctypes.c_int64, _f64p, ctypes.c_int64,
+                                          ctypes.c_int64, _i64p, ctypes.c_int64, _i64p, _f64p, _f64p]
+            L.orc_block_norms.restype = None
+            L.orc_cdf.argtypes = [_f64p, ctypes.c_int64, _f64p]
+            L.orc_cdf.restype = None
+            L.orc_rebk.argtypes = [ctypes.c_int64, ctypes.c_int64, _f64p, ctypes.c_int64,
+                                   ctypes.c_int64, _i64p, ctypes.c_int64, _i64p,
+                                   _f64p, _f64p, _f64p, _f64p,
+                                   ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                   _f64p, _f64p, _f64p,
+                                   ctypes.c_int64, ctypes.c_int64, _f64p, ctypes.c_double,
+                                   _i32p, _f64p]
+            L.orc_rebk.restype = ctypes.c_int64
+            L.orc_rebk_correction.argtypes = [ctypes.c_int64, ctypes.c_int64, _f64p, ctypes.c_int64,
+                                              ctypes.c_int64, _i64p, ctypes.c_int64, _i64p,
+                                              _f64p, _f64p, _f64p, _f64p,
+                                              ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                              _f64p, _f64p, _f64p, _f64p, _f64p, _f64p,
+                                              ctypes.c_int64, ctypes.c_int64, _f64p, _f64p, ctypes.c_double,
+                                              _i32p, _f64p]
+            L.orc_rebk_correction.restype = ctypes.c_int64
+            _lib = L
+    return _lib
+
+
+def _p(a, t=_f64p):
+    if a is None:
+        return None
+    return a.ctypes.data_as(t)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+# --------------------------------------------------------------------------
+# Sampling (Algorithm 1, "pick j with probability ...")
+# --------------------------------------------------------------------------
+
+def philox(ctr, key) -> np.ndarray:
+    """Philox4x64-10 block for a 4-word counter and 2-word key."""
+    c = np.ascontiguousarray(ctr, dtype=np.uint64)
+    k = np.ascontiguousarray(key, dtype=np.uint64)
+    out = np.zeros(4, dtype=np.uint64)
+    lib().orc_philox4x64_10(_p(c, _u64p), _p(k, _u64p), _p(out, _u64p))
+    return out
+
+
+def uniform(seed: int, stream: int, d: int) -> float:
+    return lib().orc_uniform(seed, stream, d)
+
+
+def pick(cdf_table: np.ndarray, u: float) -> int:
+    c = _f64(cdf_table)
+    return int(lib().orc_pick(_p(c), c.size, u))
+
+
+def block_norms(A: np.ndarray, row_off: np.ndarray, col_off: np.ndarray):
+    """(nr, nc): squared Frobenius norms of the row blocks A_{I_i,:} and of the
+    column blocks A_{:,J_j}."""
+    A = _f64(A)
+    ro = np.ascontiguousarray(row_off, dtype=np.int64)
+    co = np.ascontiguousarray(col_off, dtype=np.int64)
+    s, t = ro.size - 1, co.size - 1
+    nr = np.zeros(s)
+    nc = np.zeros(t)
+    lib().orc_block_norms(A.shape[0], A.shape[1], _p(A), A.shape[1], s, _p(ro, _i64p), t,
+                          _p(co, _i64p), _p(nr), _p(nc))
+    return nr, nc
+
+
+def cdf(w: np.ndarray) -> np.ndarray:
+    w = _f64(w)
+    out = np.zeros_like(w)
+    lib().orc_cdf(_p(w), w.size, _p(out))
+    return out
+
+
+def tables(A, row_off, col_off):
+    nr, nc = block_norms(A, row_off, col_off)
+    return nr, nc, cdf(nr), cdf(nc)
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1
+# --------------------------------------------------------------------------
+
+def rebk(A, b, row_off, col_off, alpha, seed, iters, stream=0, k0=0, z0=None, x0=None,
+         check_every=0, x_ref=None, tol=0.0, record=False, norms=None):
+    """Run iterations k0+1 .. k0+iters of Algorithm 1.
+
+    z0 defaults to b and x0 to 0 (Section 3).  ``norms`` may pass the block
+    norms of another matrix (used for the sampling table and the step sizes);
+    by default they are those of A.  Returns dict(x, z, iters, idx) where idx
+    is an (iters, 2) array of (j_k, i_k) when ``record``.
+    """
+    A = _f64(A)
+    m, n = A.shape
+    ro = np.ascontiguousarray(row_off, dtype=np.int64)
+    co = np.ascontiguousarray(col_off, dtype=np.int64)
+    if norms is None:
+        nr, nc, cr, cc = tables(A, ro, co)
+    else:
+        nr, nc = _f64(norms[0]), _f64(norms[1])
+        cr, cc = cdf(nr), cdf(nc)
+    b = _f64(b)
+    z = _f64(b.copy() if z0 is None else z0).copy()
+    x = np.zeros(n) if x0 is None else _f64(x0).copy()
+    idx = np.zeros((max(iters, 1), 2), dtype=np.int32) if record else None
+    xr = None if x_ref is None else _f64(x_ref)
+    work = np.zeros(max(np.max(np.diff(ro)), np.max(np.diff(co))) + 1)
+    done = lib().orc_rebk(m, n, _p(A), n, ro.size - 1, _p(ro, _i64p), co.size - 1, _p(co, _i64p),
+                          _p(nr), _p(nc), _p(cr), _p(cc), float(alpha), seed, stream, k0,
+                          _p(b), _p(z), _p(x), iters, check_every, _p(xr), float(tol),
+                          _p(idx, _i32p), _p(work))
+    return {"x": x, "z": z, "iters": int(done), "idx": None if idx is None else idx[:done]}
+
+
+def rebk_correction(Alo, f, g, row_off, col_off, norms, alpha, seed, iters, stream=0, k0=0,
+                    state=None, check_every=0, xbase=None, x_ref=None, err_abs=0.0, record=False):
+    """Algorithm 1 on corrections (see rebk_oracle.c): returns dict(dz, dx, s, v, iters, idx)."""
+    Alo = _f64(Alo)
+    m, n = Alo.shape
+    ro = np.ascontiguousarray(row_off, dtype=np.int64)
+    co = np.ascontiguousarray(col_off, dtype=np.int64)
+    nr, nc = _f64(norms[0]), _f64(norms[1])
+    cr, cc = cdf(nr), cdf(nc)
+    f, g = _f64(f), _f64(g)
+    if state is None:
+        dz, dx, s, v = np.zeros(m), np.zeros(n), np.zeros(n), np.zeros(m)
+    else:
+        dz, dx, s, v = (_f64(a).copy() for a in state)
+    idx = np.zeros((max(iters, 1), 2), dtype=np.int32) if record else None
+    work = np.zeros(max(np.max(np.diff(ro)), np.max(np.diff(co))) + 1)
+    xb = None if xbase is None else _f64(xbase)
+    xr = None if x_ref is None else _f64(x_ref)
+    done = lib().orc_rebk_correction(m, n, _p(Alo), n, ro.size - 1, _p(ro, _i64p), co.size - 1,
+                                     _p(co, _i64p), _p(nr), _p(nc), _p(cr), _p(cc), float(alpha),
+                                     seed, stream, k0, _p(f), _p(g), _p(dz), _p(dx), _p(s), _p(v),
+                                     iters, check_every, _p(xb), _p(xr), float(err_abs),
+                                     _p(idx, _i32p), _p(work))
+    return {"dz": dz, "dx": dx, "s": s, "v": v, "iters": int(done),
+            "idx": None if idx is None else idx[:done]}
+
+
+# --------------------------------------------------------------------------
+# Closed forms and bounds (Section 2)
+# --------------------------------------------------------------------------
+
+def pinv_solve(A, b, rcond=1e-12):
+    """A^+ b through the SVD (numpy.linalg.pinv)."""
+    return np.linalg.pinv(_f64(A), rcond=rcond) @ _f64(b)
+
+
+def mean_closed_form(A, b, alpha, k, z0=None, x0=None):
+    """E[z^k] = (I - alpha A A^T/||A||_F^2)^k z^0 and
+    E[x^k] = A^+ b + (I - alpha A^T A/||A||_F^2)^k (x^0 - A^+ b)
+             - alpha k (I - alpha A^T A/||A||_F^2)^k A^T z^0 / ||A||_F^2
+    (proof of Theorem ner)."""
+    A = _f64(A)
+    m, n = A.shape
+    fro2 = float(np.sum(A * A))
+    z0 = _f64(b) if z0 is None else _f64(z0)
+    x0 = np.zeros(n) if x0 is None else _f64(x0)
+    xs = pinv_solve(A, b)
+    Pz = np.linalg.matrix_power(np.eye(m) - alpha * (A @ A.T) / fro2, k)
+    Px = np.linalg.matrix_power(np.eye(n) - alpha * (A.T @ A) / fro2, k)
+    Ez = Pz @ z0
+    Ex = xs + Px @ (x0 - xs) - alpha * k * (Px @ (A.T @ z0)) / fro2
+    return Ex, Ez
+
+
+def beta_max(A, row_off, col_off):
+    """(beta^I_max, beta^J_max) of Section 2.2: the largest ||block||_2^2 /
+    ||block||_F^2 over row blocks and over column blocks, spectral norms from
+    the eigenvalues of the block Gram matrices (numpy.linalg.eigvalsh).
+    Blocks of zero norm are skipped."""
+    A = _f64(A)
+    bi = 0.0
+    for i in range(len(row_off) - 1):
+        B = A[row_off[i]:row_off[i + 1], :]
+        f2 = float(np.sum(B * B))
+        if f2 > 0:
+            bi = max(bi, float(np.linalg.eigvalsh(B @ B.T)[-1]) / f2)
+    bj = 0.0
+    for j in range(len(col_off) - 1):
+        B = A[:, col_off[j]:col_off[j + 1]]
+        f2 = float(np.sum(B * B))
+        if f2 > 0:
+            bj = max(bj, float(np.linalg.eigvalsh(B.T @ B)[-1]) / f2)
+    return bi, bj
+
+
+def _sv(A):
+    s = np.linalg.svd(_f64(A), compute_uv=False)
+    r = int(np.sum(s > s[0] * 1e-12)) if s.size and s[0] > 0 else 0
+    return s[:r]
+
+
+def bound_ner(A, b, alpha, k, z0=None, x0=None):
+    """Theorem ner: delta^k (||x^0 - A^+ b|| + alpha k ||A^T z^0|| / ||A||_F^2)."""
+    A = _f64(A)
+    sv = _sv(A)
+    fro2 = float(np.sum(A * A))
+    delta = float(np.max(np.abs(1.0 - alpha * sv ** 2 / fro2)))
+    z0 = _f64(b) if z0 is None else _f64(z0)
+    x0 = np.zeros(A.shape[1]) if x0 is None else _f64(x0)
+    xs = pinv_solve(A, b)
+    return delta ** k * (np.linalg.norm(x0 - xs) + alpha * k * np.linalg.norm(A.T @ z0) / fro2)
+
+
+def _eta_rho(A, alpha, row_off, col_off):
+    A = _f64(A)
+    sv = _sv(A)
+    fro2 = float(np.sum(A * A))
+    bI, bJ = beta_max(A, row_off, col_off)
+    sr2 = sv[-1] ** 2
+    eta = 1.0 - (2 * alpha - alpha ** 2 * bI) * sr2 / fro2
+    rho = 1.0 - (2 * alpha - alpha ** 2 * bJ) * sr2 / fro2
+    return eta, rho, bI, bJ, fro2
+
+
+def bound_estz(A, b, alpha, k, row_off, col_off, z0=None):
+    """Lemma estz: rho^k ||z^0 - b_perp||^2, b_perp = (I - A A^+) b."""
+    A = _f64(A)
+    eta, rho, bI, bJ, fro2 = _eta_rho(A, alpha, row_off, col_off)
+    z0 = _f64(b) if z0 is None else _f64(z0)
+    bperp = _f64(b) - A @ pinv_solve(A, b)
+    return rho ** k * float(np.sum((z0 - bperp) ** 2))
+
+
+def bound_main(A, b, alpha, k, row_off, col_off, eps=1.0, z0=None, x0=None):
+    """Theorem main: (1+eps)^k eta^k ||x^0 - A^+ b||^2
+    + (1 + 1/eps) alpha^2 beta^I_max ||z^0 - b_perp||^2 / ||A||_F^2
+      * sum_{l<k} rho^{k-l} (1+eps)^l eta^l."""
+    A = _f64(A)
+    eta, rho, bI, bJ, fro2 = _eta_rho(A, alpha, row_off, col_off)
+    z0 = _f64(b) if z0 is None else _f64(z0)
+    x0 = np.zeros(A.shape[1]) if x0 is None else _f64(x0)
+    xs = pinv_solve(A, b)
+    bperp = _f64(b) - A @ xs
+    tail = sum(rho ** (k - l) * (1 + eps) ** l * eta ** l for l in range(k))
+    return ((1 + eps) ** k * eta ** k * float(np.sum((x0 - xs) ** 2))
+            + (1 + 1 / eps) * alpha ** 2 * bI * float(np.sum((z0 - bperp) ** 2)) / fro2 * tail)
+
+
+# --------------------------------------------------------------------------
+# Reduced-precision storage and the refinement loop (our reading)
+# --------------------------------------------------------------------------
+
+def round_fp32(A):
+    """FP64 -> FP32, round to nearest even, as FP64 values."""
+    return _f64(A).astype(np.float32).astype(np.float64)
+
+
+def round_bf16(A):
+    """FP64 -> FP32 -> BF16, each round to nearest even, as FP64 values.
+    (Inf/NaN inputs are not expected.)"""
+    f = _f64(A).astype(np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    lsb = (u >> 16) & 1
+    u = (u + 0x7FFF + lsb) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def dual_residuals(A, b, z, x):
+    """f = b - z - A x and g = A^T z in FP64.  Both vanish exactly at
+    (x, z) = (A^+ b, (I - A A^+) b)."""
+    A = _f64(A)
+    return _f64(b) - _f64(z) - A @ _f64(x), A.T @ _f64(z)
+
+
+def refine(A, b, Alo, row_off, col_off, alpha, seed, inner_iters, outer_max=50,
+           x_ref=None, tol=1e-8, stream=0, x0=None, z0=None, inner_reduction=None):
+    """Mixed-precision REBK with FP64 refinement (our reading; the paper is silent).
+
+    State (x, z) in FP64 with x0 = 0, z0 = b unless given.  Each outer pass:
+      f = b - z - A x, g = A^T z                  (FP64, A)
+      Algorithm 1 on corrections with Alo          (rebk_correction)
+      z <- z - A s,  x <- x + A^T v                (FP64, A)
+    The random stream continues across passes (k0 advances).  A pass ends
+    after ``inner_iters`` iterations, or earlier when x_ref is given and
+    ||x + dx - x_ref|| <= max(tol ||x_ref||, inner_reduction * err_at_pass_start).
+    Stops when ||x - x_ref|| <= tol ||x_ref|| (x_ref given) or after outer_max
+    passes.  Block norms (sampling table, step sizes) are those of FP64 A.
+    Returns dict(x, z, outer, inner_total, history).
+    """
+    A = _f64(A)
+    m, n = A.shape
+    nr, nc = block_norms(A, row_off, col_off)
+    x = np.zeros(n) if x0 is None else _f64(x0).copy()
+    z = _f64(b).copy() if z0 is None else _f64(z0).copy()
+    k0 = 0
+    hist = []
+    xr = None if x_ref is None else _f64(x_ref)
+    refn = None if xr is None else float(np.linalg.norm(xr))
+    for outer in range(1, outer_max + 1):
+        f, g = dual_residuals(A, b, z, x)
+        err_abs = 0.0
+        check = 0
+        if xr is not None:
+            e0 = float(np.linalg.norm(x - xr))
+            if e0 <= tol * refn:
+                return {"x": x, "z": z, "outer": outer - 1, "inner_total": k0, "history": hist}
+            red = inner_reduction if inner_reduction is not None else 0.0
+            err_abs = max(tol * refn, red * e0)
+            check = 10
+        r = rebk_correction(Alo, f, g, row_off, col_off, (nr, nc), alpha, seed, inner_iters,
+                            stream=stream, k0=k0, check_every=check, xbase=x, x_ref=xr,
+                            err_abs=err_abs)
+        k0 += r["iters"]
+        z = z - A @ r["s"]
+        x = x + A.T @ r["v"]
+        hist.append({"outer": outer, "inner": r["iters"],
+                     "err": None if xr is None else float(np.linalg.norm(x - xr) / refn)})
+    return {"x": x, "z": z, "outer": outer_max, "inner_total": k0, "history": hist}
+
+
+# --------------------------------------------------------------------------
+# Learned warm start network (FP64 reference)
+# --------------------------------------------------------------------------
+
+def mlp_init(sizes, seed):
+    """Weights W_l (out x in) with N(0, 2/in) entries (He initialisation)."""
+    rng = np.random.default_rng(seed)
+    return [rng.standard_normal((sizes[i + 1], sizes[i])) * np.sqrt(2.0 / sizes[i])
+            for i in range(len(sizes) - 1)]
+
+
+def mlp_forward(W, Bm):
+    """y = W_L relu(... relu(W_1 b)): columns of Bm are inputs.  Returns
+    (y, cache) with cache = pre-activations and activations per layer."""
+    acts = [_f64(Bm)]
+    pres = []
+    h = acts[0]
+    for l, Wl in enumerate(W):
+        p = Wl @ h
+        pres.append(p)
+        h = p if l == len(W) - 1 else np.maximum(p, 0.0)
+        acts.append(h)
+    return h, (pres, acts)
+
+
+def mlp_loss(W, A, Bm, Xls):
+    """Mean over columns of ||A^T y - x_ls||^2 with y = mlp(b)."""
+    y, _ = mlp_forward(W, Bm)
+    R = _f64(A).T @ y - _f64(Xls)
+    return float(np.sum(R * R)) / Bm.shape[1]
+
+
+def mlp_backward(W, A, Bm, Xls):
+    """Gradients of mlp_loss w.r.t. each W_l by the chain rule:
+    dL/dy = (2/B) A (A^T y - x_ls); back through the linear layers and the
+    ReLU masks (derivative 0 at 0)."""
+    A = _f64(A)
+    y, (pres, acts) = mlp_forward(W, Bm)
+    B = Bm.shape[1]
+    G = (2.0 / B) * (A @ (A.T @ y - _f64(Xls)))
+    grads = [None] * len(W)
+    for l in range(len(W) - 1, -1, -1):
+        if l < len(W) - 1:
+            G = G * (pres[l] > 0)
+        grads[l] = G @ acts[l].T
+        G = W[l].T @ G
+    return grads
