@@ -1,0 +1,200 @@
+/*
+ * rebk.h -- C ABI of the GB300 (sm_103a) solver for the minimum-norm
+ * least-squares solution A^+ b by randomized extended block Kaczmarz (REBK).
+ *
+ * Method: K. Du, W.-T. Si, X.-H. Sun, "Randomized extended block Kaczmarz for
+ * solving least squares", arXiv:2001.04179.  The problem statement (Section 1)
+ * is A x = b with A any real m x n matrix -- consistent or not, over- or
+ * underdetermined, full rank or rank-deficient -- and the target is A^+ b.
+ * The iteration is Algorithm 1 (Section 2); partitions are the contiguous
+ * equal-size blocks of Section 3 (the last block may be shorter).
+ *
+ * Conventions for every call below:
+ *  - Matrices are row-major FP64 with leading dimension lda >= n (elements).
+ *  - "device" pointers are CUDA device addresses on the current device (for
+ *    example torch tensor data_ptr()); "host" pointers are ordinary memory.
+ *  - The caller owns every buffer it passes; the library never frees them and
+ *    keeps no pointer to them after the call returns.  The library owns the
+ *    handle and everything it allocated inside it (released by rebk_destroy).
+ *  - Work is queued on the handle's stream (rebk_options.stream).  Solve calls
+ *    synchronise that stream before returning (they read stopping results).
+ *  - Errors: every call returns a rebk_status; on failure rebk_last_error()
+ *    returns a message for the calling thread.  No C++ exception crosses the
+ *    boundary.  Invalid arguments never reach a kernel.
+ *  - Random draws (not specified by the paper): Philox4x64-10 with key
+ *    (seed, stream_id) and counter (d, 0, 0, 0), d = 2(k-1) for the column
+ *    draw and 2(k-1)+1 for the row draw of iteration k; u = (word0 >> 11) 2^-53;
+ *    the block picked is the smallest index whose cumulative squared norm
+ *    exceeds u ||A||_F^2 (Algorithm 1's sampling probabilities).
+ */
+#ifndef REBK_H
+#define REBK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct rebk_handle_s *rebk_handle;
+
+typedef enum {
+    REBK_OK = 0,
+    REBK_EINVAL = 1,            /* invalid argument; nothing was launched            */
+    REBK_ENOMEM = 2,            /* device or host allocation failed                  */
+    REBK_ECUDA = 3,             /* a CUDA call failed (message in rebk_last_error)   */
+    REBK_MAX_ITER = 4,          /* stopping test not met within max_iter; x is the
+                                   last iterate                                      */
+    REBK_DIVERGED = 5,          /* a reduced block product became Inf/NaN            */
+    REBK_BARRIER_TIMEOUT = 6,   /* a device-wide wait gave up (bounded spin); x and z
+                                   are not updated                                   */
+    REBK_EUNSUPPORTED = 7       /* size or option outside what this build handles    */
+} rebk_status;
+
+/* Storage precision of the matrix copy used by the inner sweeps. */
+typedef enum { REBK_FP64 = 0, REBK_FP32 = 1, REBK_BF16 = 2 } rebk_storage;
+
+typedef struct {
+    int64_t tau_row;       /* row block size tau >= 1 (Section 3 partition of [m])     */
+    int64_t tau_col;       /* column block size >= 1 (partition of [n])                */
+    int32_t storage_mask;  /* extra copies to keep: (1<<REBK_FP32) | (1<<REBK_BF16);
+                              the FP64 copy is always kept                              */
+    int32_t num_ctas;      /* CTAs of the persistent solve kernel; 0 = library choice  */
+    int64_t check_every;   /* iterations between stopping tests; 0 = library default   */
+    void *stream;          /* cudaStream_t for all work; NULL = legacy default stream  */
+} rebk_options;
+
+typedef struct {
+    int64_t iterations;    /* iterations of Algorithm 1 run (all passes for refinement) */
+    int32_t outer;         /* refinement passes (0 for the plain solve)                 */
+    int32_t status;        /* rebk_status of the solve                                  */
+    double rel_err;        /* ||x - x_ref|| / ||x_ref|| at exit if x_ref given, else -1 */
+    double resid_f;        /* ||b - z - A x|| / ||b|| at exit when computed, else -1    */
+    double resid_g;        /* ||A^T z|| / (||A||_F ||b||) at exit when computed, else -1 */
+    double device_ms;      /* device time from the first to the last queued work of the
+                              solve (CUDA events on the handle's stream)                */
+    double kernel_ms;      /* summed CUDA-event time of the persistent REBK launches    */
+    double sweep_ms;       /* summed CUDA-event time of the FP64 sweeps over A          */
+    int64_t launches;      /* kernels of this library launched by the solve             */
+    int64_t grid_launches; /* of which persistent REBK launches                         */
+} rebk_stats;
+
+/* Optional inputs/outputs of a solve.  Zero-initialise and set what you need. */
+typedef struct {
+    const double *x_ref;   /* device, n: stop when ||x - x_ref||_2 <= tol ||x_ref||_2
+                              (the paper's stop rule, Section 3); NULL = residual test  */
+    const double *x0;      /* device, n: initial x (Theorem main needs x0 in range(A^T));
+                              NULL = 0 (Section 3)                                      */
+    const double *z0;      /* device, m: initial z (Theorem main needs z0 in b+range(A));
+                              NULL = b (Section 3)                                      */
+    double *z_out;         /* device, m: final z (NULL = not returned)                  */
+    int32_t *idx_out;      /* device, 2*max_iter int32: (j_k, i_k) per iteration run    */
+    int64_t k0;            /* first iteration is k0+1 (resume a random stream)          */
+    uint64_t stream_id;    /* Philox key word 1                                         */
+} rebk_solve_ext;
+
+/* Options of the mixed-precision solve. */
+typedef struct {
+    int32_t storage;          /* REBK_FP32 or REBK_BF16 (must be in storage_mask)      */
+    int32_t max_outer;        /* refinement passes at most; 0 = 30                      */
+    int64_t inner_iters;      /* iterations per pass at most; 0 = library default       */
+    double inner_reduction;   /* with x_ref: a pass ends once the error is below this
+                                 fraction of its value at the pass start (0 = 1e-4 for
+                                 FP32, 1e-2 for BF16)                                    */
+} rebk_refine_opts;
+
+/*
+ * Creates a solver for the m x n matrix A (row-major, leading dimension lda,
+ * host memory if A_on_device == 0, device memory otherwise; the library copies
+ * it).  Builds the block squared Frobenius norm tables and their prefix sums
+ * (Algorithm 1 sampling) in FP64 on the device, and the reduced-precision
+ * copies named in opt->storage_mask.
+ * alpha > 0 is the step size of Algorithm 1; alpha <= 0 picks 1.75 / beta_max
+ * (Section 3's empirical choice) with beta_max from rebk_beta_max.
+ * Errors: EINVAL (m, n, lda, tau out of range, NULL pointers), ENOMEM, ECUDA.
+ * A matrix of all zeros is accepted (every solve returns x = 0 = A^+ b).
+ */
+rebk_status rebk_create(rebk_handle *out, const double *A, int64_t m, int64_t n, int64_t lda,
+                        int A_on_device, double alpha, const rebk_options *opt);
+
+/* Releases everything the handle owns.  NULL is ignored. */
+void rebk_destroy(rebk_handle h);
+
+/*
+ * Plain FP64 REBK (Algorithm 1) from z0 = b, x0 = 0 (Section 3).
+ * b: device, m.  x: device, n (output).  Stops at the first multiple of
+ * check_every iterations where the residual test holds:
+ *   max(||b - z - A x|| / ||b||, ||A^T z|| / (||A||_F ||b||)) <= tol
+ * (both vanish exactly at x = A^+ b, z = (I - A A^+) b), or after max_iter
+ * iterations (REBK_MAX_ITER).  tol <= 0 runs exactly max_iter iterations.
+ */
+rebk_status rebk_solve(rebk_handle h, const double *b, double *x, double tol, int64_t max_iter,
+                       uint64_t seed, rebk_stats *stats);
+
+/*
+ * As rebk_solve with the optional inputs/outputs of rebk_solve_ext (ext may be
+ * NULL).  With ext->x_ref the stop rule is the relative error (checked every
+ * check_every iterations; x returned is the iterate that passed).  With an
+ * early stop, z_out holds z one iteration past the returned x (the column step
+ * of the next iteration was already applied).  With idx_out, entries for the
+ * iterations run are written.
+ */
+rebk_status rebk_solve_ex(rebk_handle h, const double *b, double *x, double tol, int64_t max_iter,
+                          uint64_t seed, const rebk_solve_ext *ext, rebk_stats *stats);
+
+/*
+ * Mixed precision: Algorithm 1 applied to corrections with the FP32 or BF16
+ * copy of A (FP32 arithmetic), inside an FP64 refinement loop on (x, z):
+ *   f = b - z - A x,  g = A^T z                      (FP64 sweep over A)
+ *   inner: dz <- dz - cJ A_J (A_J^T dz + g_J),  s_J += cJ (A_J^T dz + g_J)
+ *          dx <- dx - cI A_I^T (A_I dx - f_I + dz_I),  v_I -= cI (same residual)
+ *   z <- z - A s,  x <- x + A^T v                     (FP64 sweep over A)
+ * so x stays in range(A^T) and z in b + range(A) to FP64 rounding (the
+ * hypotheses of Theorem main), and A^+ b is a fixed point.  The random stream
+ * continues across passes.  Stop: relative error <= tol with ext->x_ref, else
+ * the residual test of rebk_solve after each pass.  max_iter bounds the total
+ * inner iterations.  Sampling table and step sizes come from FP64 A.
+ */
+rebk_status rebk_solve_refined(rebk_handle h, const double *b, double *x, double tol,
+                               int64_t max_iter, uint64_t seed, const rebk_refine_opts *ropt,
+                               const rebk_solve_ext *ext, rebk_stats *stats);
+
+/*
+ * beta^I_max and beta^J_max of Section 2.2 (largest ||block||_2^2 / ||block||_F^2
+ * over the row blocks and over the column blocks), from FP64 block Gram
+ * matrices and power iteration on the device.  Outputs are host doubles.
+ */
+rebk_status rebk_beta_max(rebk_handle h, double *beta_row, double *beta_col);
+
+/* Step size alpha in use (host double). */
+rebk_status rebk_get_alpha(rebk_handle h, double *alpha);
+
+/* Number of row blocks s and column blocks t (host int64). */
+rebk_status rebk_get_blocks(rebk_handle h, int64_t *s, int64_t *t);
+
+/*
+ * Copies the FP64 block tables to host arrays: nr (s), nc (t) squared
+ * Frobenius norms, cdf_r (s), cdf_c (t) inclusive prefix sums.  Any may be NULL.
+ */
+rebk_status rebk_get_tables(rebk_handle h, double *nr, double *nc, double *cdf_r, double *cdf_c);
+
+/*
+ * Copies the stored copy of A in the given precision to host memory as an
+ * m x n row-major array of that type (8, 4 or 2 bytes per element; BF16 as
+ * raw uint16 bits).  The copy is FP64 -> FP32 -> BF16, each round to nearest
+ * even.
+ */
+rebk_status rebk_export_storage(rebk_handle h, int32_t storage, void *host_out);
+
+/* Message for the last failed call on this thread ("" if none). */
+const char *rebk_last_error(void);
+
+/* Library version string. */
+const char *rebk_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* REBK_H */

@@ -1,0 +1,880 @@
+// rebk_api.cu -- C ABI of the REBK solver (see include/rebk.h).
+//
+// Host logic only: argument checks, device buffers of the handle, the outer
+// loops (stopping tests, chunked launches, the FP64 refinement passes) and the
+// choice of the persistent kernel's CTA count.  Every arithmetic step of the
+// method runs in the kernels of rebk_grid.cu and rebk_setup.cu.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "rebk.h"
+#include "rebk_internal.h"
+
+using namespace rebk;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+rebk_status fail(rebk_status s, const std::string &msg) {
+    g_last_error = msg;
+    return s;
+}
+
+rebk_status cuda_fail(cudaError_t e, const char *what) {
+    g_last_error = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? REBK_ENOMEM : REBK_ECUDA;
+}
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e__ = (call);                                                                  \
+        if (e__ != cudaSuccess) return cuda_fail(e__, #call);                                      \
+    } while (0)
+
+// a call that launches one kernel of this library: counted in the solve stats
+#define LK(h, call)                                                                                \
+    do {                                                                                           \
+        ++(h)->launches;                                                                           \
+        CK(call);                                                                                  \
+    } while (0)
+
+int64_t round_up(int64_t v, int64_t q) { return (v + q - 1) / q * q; }
+
+struct Workspace {
+    unsigned int bar;
+    int status;
+    int64_t iters_done;
+    double small[8];
+};
+
+}  // namespace
+
+struct rebk_handle_s {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    int64_t m = 0, n = 0, lda = 0;
+    int tau_r = 0, tau_c = 0, s = 0, t = 0;
+    double alpha = 0.0, fro2 = 0.0;
+    int fb[2] = {0, 0};
+    double *A64 = nullptr;
+    float *A32 = nullptr;
+    __nv_bfloat16 *A16 = nullptr;
+    double *nr = nullptr, *nc = nullptr, *cdf_r = nullptr, *cdf_c = nullptr;
+    int *d_fallback = nullptr;
+    double *acc = nullptr;
+    int acc_w = 0, acc_r = kAccReplicas;
+    Workspace *ws = nullptr;
+    double *zbuf = nullptr, *f = nullptr, *g = nullptr, *ym = nullptr, *yn = nullptr;
+    float *dz = nullptr, *dx = nullptr, *sd = nullptr, *vd = nullptr;
+    int64_t check_every = 0;
+    int num_ctas_opt = 0;
+    int G[3] = {0, 0, 0};
+    bool beta_done = false;
+    double beta_r = 0.0, beta_c = 0.0;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    int32_t *idxbuf = nullptr;  // sampled block indices of one launch
+    int64_t idx_cap = 0;        // capacity in iterations
+    // per-solve counters (reset at the start of each solve)
+    int64_t launches = 0, grid_launches = 0;
+    double kernel_ms = 0.0;
+    std::vector<cudaEvent_t> sweep_ev;  // start/stop pairs of the FP64 sweeps
+    size_t sweep_used = 0;
+    cudaEvent_t kev0 = nullptr, kev1 = nullptr;
+};
+
+namespace {
+
+void free_handle(rebk_handle h) {
+    if (!h) return;
+    void *ptrs[] = {h->A64, h->A32, h->A16, h->nr, h->nc, h->cdf_r, h->cdf_c, h->d_fallback, h->acc,
+                    h->ws, h->zbuf, h->f, h->g, h->ym, h->yn, h->dz, h->dx, h->sd, h->vd,
+                    h->idxbuf};
+    for (void *p : ptrs)
+        if (p) cudaFree(p);
+    if (h->ev0) cudaEventDestroy(h->ev0);
+    if (h->ev1) cudaEventDestroy(h->ev1);
+    if (h->kev0) cudaEventDestroy(h->kev0);
+    if (h->kev1) cudaEventDestroy(h->kev1);
+    for (cudaEvent_t e : h->sweep_ev) cudaEventDestroy(e);
+    delete h;
+}
+
+int mode_index(Mode m) { return m == Mode::PlainF64 ? 0 : (m == Mode::CorrF32 ? 1 : 2); }
+
+// Fills the parts of GridArgs that depend only on the handle and mode.
+GridArgs base_args(rebk_handle h, Mode mode, int G) {
+    GridArgs a;
+    memset(&a, 0, sizeof(a));
+    a.A = mode == Mode::PlainF64 ? (const void *)h->A64
+                                 : (mode == Mode::CorrF32 ? (const void *)h->A32 : (const void *)h->A16);
+    a.lda = h->lda;
+    a.m = h->m;
+    a.n = h->n;
+    a.tau_r = h->tau_r;
+    a.tau_c = h->tau_c;
+    a.s = h->s;
+    a.t = h->t;
+    a.cdf_r = h->cdf_r;
+    a.cdf_c = h->cdf_c;
+    a.nr = h->nr;
+    a.nc = h->nc;
+    a.fb_r = h->fb[0];
+    a.fb_c = h->fb[1];
+    a.alpha = h->alpha;
+    a.acc = h->acc;
+    a.acc_w = h->acc_w;
+    a.acc_r = h->acc_r;
+    a.nrow_cap = (int)((h->m + G - 1) / G) + 1;
+    const int64_t nu = (h->n + 7) / 8;
+    a.ncol_cap = (int)(8 * ((nu + G - 1) / G)) + 8;
+    a.bar = &h->ws->bar;
+    a.status = &h->ws->status;
+    a.iters_done = &h->ws->iters_done;
+    a.timeout_ns = kBarrierTimeoutNs;
+    return a;
+}
+
+constexpr int64_t kIdxChunkMax = 1 << 20;  // iterations sampled per launch (internal buffer)
+
+// Samples the block indices of iterations k0+1 .. k0+K into `user` (if not
+// NULL) or the handle's buffer; sets a.idx.
+rebk_status sample_into(rebk_handle h, GridArgs &a, int64_t k0, int64_t K, int32_t *user) {
+    int32_t *dst = user;
+    if (!dst) {
+        if (K > h->idx_cap) {
+            if (h->idxbuf) cudaFree(h->idxbuf);
+            h->idxbuf = nullptr;
+            h->idx_cap = 0;
+            const int64_t cap = std::max<int64_t>(K, 65536);
+            CK(cudaMalloc(&h->idxbuf, sizeof(int32_t) * 2 * cap));
+            h->idx_cap = cap;
+        }
+        dst = h->idxbuf;
+    }
+    LK(h, sample_blocks(a.seed, a.stream, k0, K, h->cdf_r, h->s, h->cdf_c, h->t, h->fb[0], h->fb[1],
+                        dst, h->stream));
+    a.idx = dst;
+    a.k0 = k0;
+    a.iters = K;
+    return REBK_OK;
+}
+
+// One launch of the persistent kernel (a.idx, a.k0, a.iters set); returns the
+// device status and the iterations it ran.
+rebk_status run_grid(rebk_handle h, Mode mode, GridArgs a, int G, int *dev_status, int64_t *done,
+                     cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
+    const cudaStream_t st = h->stream;
+    a.nrow_cap = (int)((h->m + G - 1) / G) + 1;
+    const int64_t nu = (h->n + 7) / 8;
+    a.ncol_cap = (int)(8 * ((nu + G - 1) / G)) + 8;
+    CK(cudaMemsetAsync(h->acc, 0, sizeof(double) * 3 * (size_t)h->acc_r * h->acc_w, st));
+    CK(cudaMemsetAsync(h->ws, 0, sizeof(Workspace), st));
+    if (!e0) {
+        e0 = h->kev0;
+        e1 = h->kev1;
+    }
+    CK(cudaEventRecord(e0, st));
+    CK(launch_grid(mode, a, G, st));
+    CK(cudaEventRecord(e1, st));
+    ++h->launches;
+    ++h->grid_launches;
+    Workspace w;
+    CK(cudaMemcpyAsync(&w, h->ws, sizeof(Workspace), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    float kms = 0.f;
+    CK(cudaEventElapsedTime(&kms, e0, e1));
+    h->kernel_ms += kms;
+    *dev_status = w.status;
+    *done = w.iters_done;
+    return REBK_OK;
+}
+
+int pick_ctas(rebk_handle h, Mode mode);
+
+rebk_status check_smem(rebk_handle h, Mode mode, int G) {
+    GridArgs a = base_args(h, mode, G);
+    const size_t smem = grid_smem_bytes(mode, a);
+    if (smem > 200 * 1024)
+        return fail(REBK_EUNSUPPORTED, "problem too large for the persistent kernel's shared memory "
+                                       "(owned slices of m + n per CTA)");
+    return REBK_OK;
+}
+
+// CTA count of the persistent kernel: the caller's, else the fastest of a few
+// candidates on a short timed run over zero data (same work as a real run).
+int pick_ctas(rebk_handle h, Mode mode) {
+    const int mi = mode_index(mode);
+    if (h->G[mi] > 0) return h->G[mi];
+    int maxG = grid_max_ctas(mode, grid_smem_bytes(mode, base_args(h, mode, 16)));
+    if (maxG <= 0) maxG = 1;
+    if (h->num_ctas_opt > 0) {
+        h->G[mi] = std::min(h->num_ctas_opt, maxG);
+        return h->G[mi];
+    }
+    std::vector<int> cands;
+    for (int c : {8, 16, 32, 48, 64, 96, 128}) if (c < maxG) cands.push_back(c);
+    cands.push_back(maxG);
+    // zero state and right-hand side in scratch buffers
+    const cudaStream_t st = h->stream;
+    void *zs = mode == Mode::PlainF64 ? (void *)h->zbuf : (void *)h->dz;
+    void *xs = mode == Mode::PlainF64 ? (void *)h->yn : (void *)h->dx;
+    cudaMemsetAsync(h->ym, 0, sizeof(double) * h->m, st);
+    cudaMemsetAsync(h->g, 0, sizeof(double) * h->n, st);
+    cudaMemsetAsync(zs, 0, (mode == Mode::PlainF64 ? 8 : 4) * h->m, st);
+    cudaMemsetAsync(xs, 0, (mode == Mode::PlainF64 ? 8 : 4) * h->n, st);
+    cudaMemsetAsync(h->sd, 0, 4 * h->n, st);
+    cudaMemsetAsync(h->vd, 0, 4 * h->m, st);
+    const int64_t iters = 48;
+    float best = 1e30f;
+    int bestG = cands.back();
+    for (int G : cands) {
+        if (check_smem(h, mode, G) != REBK_OK) continue;
+        GridArgs a = base_args(h, mode, G);
+        a.seed = 1;
+        if (sample_into(h, a, 0, iters, nullptr) != REBK_OK) break;
+        a.z = zs;
+        a.x = xs;
+        a.beta = h->ym;
+        a.gamma = mode == Mode::PlainF64 ? nullptr : h->g;
+        a.sdual = h->sd;
+        a.vdual = h->vd;
+        float tbest = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            int ds;
+            int64_t done;
+            if (run_grid(h, mode, a, G, &ds, &done, h->ev0, h->ev1) != REBK_OK || ds != 0) {
+                tbest = 1e30f;
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+            tbest = std::min(tbest, ms);
+        }
+        if (tbest < best) {
+            best = tbest;
+            bestG = G;
+        }
+    }
+    cudaGetLastError();
+    h->G[mi] = bestG;
+    return bestG;
+}
+
+void reset_counters(rebk_handle h) {
+    h->launches = 0;
+    h->grid_launches = 0;
+    h->kernel_ms = 0.0;
+    h->sweep_used = 0;
+}
+
+// FP64 sweep with its CUDA-event time recorded for the stats.
+rebk_status timed_sweep(rebk_handle h, const void *p, bool p_f32, const void *q, bool q_f32,
+                        double *ym, double *yn) {
+    if (h->sweep_used + 2 > h->sweep_ev.size()) {
+        for (int i = 0; i < 2; ++i) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            h->sweep_ev.push_back(e);
+        }
+    }
+    cudaEvent_t e0 = h->sweep_ev[h->sweep_used], e1 = h->sweep_ev[h->sweep_used + 1];
+    h->sweep_used += 2;
+    CK(cudaEventRecord(e0, h->stream));
+    LK(h, dual_sweep(h->A64, h->lda, h->m, h->n, p, p_f32, q, q_f32, ym, yn, h->stream));
+    CK(cudaEventRecord(e1, h->stream));
+    return REBK_OK;
+}
+
+double sweep_time(rebk_handle h) {
+    double tot = 0.0;
+    for (size_t i = 0; i + 1 < h->sweep_used; i += 2) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, h->sweep_ev[i], h->sweep_ev[i + 1]) == cudaSuccess) tot += ms;
+    }
+    return tot;
+}
+
+rebk_status fetch_small(rebk_handle h, double *host, int count) {
+    CK(cudaMemcpyAsync(host, h->ws->small, sizeof(double) * count, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return REBK_OK;
+}
+
+// ||b - z - A x|| / ||b|| and ||A^T z|| / (||A||_F ||b||) in FP64.
+rebk_status residuals(rebk_handle h, const double *b, const double *x, const double *z, double *rf,
+                      double *rg) {
+    const cudaStream_t st = h->stream;
+    rebk_status ts = timed_sweep(h, x, false, z, false, h->ym, h->yn);
+    if (ts != REBK_OK) return ts;
+    LK(h, form_f(b, z, h->ym, h->f, h->m, st));
+    LK(h, sum_sq(h->f, h->m, h->ws->small, st));
+    LK(h, sum_sq(h->yn, h->n, h->ws->small + 2, st));
+    LK(h, sum_sq(b, h->m, h->ws->small + 4, st));
+    double v[6];
+    rebk_status s = fetch_small(h, v, 6);
+    if (s != REBK_OK) return s;
+    const double nb = std::sqrt(v[5]);
+    *rf = nb > 0 ? std::sqrt(v[1]) / nb : 0.0;
+    *rg = nb > 0 ? std::sqrt(v[3]) / (std::sqrt(h->fro2) * nb) : 0.0;
+    return REBK_OK;
+}
+
+rebk_status rel_error(rebk_handle h, const double *x, const double *xref, double *rel) {
+    LK(h, err_norms(nullptr, x, xref, h->n, h->ws->small, h->stream));
+    double v[2];
+    rebk_status s = fetch_small(h, v, 2);
+    if (s != REBK_OK) return s;
+    *rel = v[1] > 0 ? std::sqrt(v[0] / v[1]) : std::sqrt(v[0]);
+    return REBK_OK;
+}
+
+void fill_stats(rebk_handle h, rebk_stats *st, int64_t iters, int outer, rebk_status status,
+                double rel, double rf, double rg, double ms) {
+    if (!st) return;
+    st->kernel_ms = h->kernel_ms;
+    st->sweep_ms = sweep_time(h);
+    st->launches = h->launches;
+    st->grid_launches = h->grid_launches;
+    st->iterations = iters;
+    st->outer = outer;
+    st->status = status;
+    st->rel_err = rel;
+    st->resid_f = rf;
+    st->resid_g = rg;
+    st->device_ms = ms;
+}
+
+}  // namespace
+
+// ===========================================================================
+extern "C" {
+
+const char *rebk_last_error(void) { return g_last_error.c_str(); }
+
+const char *rebk_version(void) { return "rebk-gb300 0.1 (sm_103a)"; }
+
+void rebk_destroy(rebk_handle h) { free_handle(h); }
+
+rebk_status rebk_create(rebk_handle *out, const double *A, int64_t m, int64_t n, int64_t lda,
+                        int A_on_device, double alpha, const rebk_options *opt) {
+    g_last_error.clear();
+    if (!out) return fail(REBK_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!A) return fail(REBK_EINVAL, "A is NULL");
+    if (m < 1 || n < 1) return fail(REBK_EINVAL, "m and n must be >= 1");
+    if (lda < n) return fail(REBK_EINVAL, "lda must be >= n");
+    if (m > (int64_t)1 << 30 || n > (int64_t)1 << 30) return fail(REBK_EUNSUPPORTED, "m, n > 2^30");
+    if (!std::isfinite(alpha)) return fail(REBK_EINVAL, "alpha is not finite");
+    rebk_options o;
+    memset(&o, 0, sizeof(o));
+    if (opt) o = *opt;
+    if (o.tau_row < 0 || o.tau_col < 0) return fail(REBK_EINVAL, "tau must be >= 1 (0 = default)");
+    if (o.tau_row == 0) o.tau_row = std::min<int64_t>(m, 64);
+    if (o.tau_col == 0) o.tau_col = std::min<int64_t>(n, 64);
+    o.tau_row = std::min(o.tau_row, m);
+    o.tau_col = std::min(o.tau_col, n);
+    if (o.tau_row > 512 || o.tau_col > 512) return fail(REBK_EUNSUPPORTED, "tau > 512");
+    if (o.check_every < 0) return fail(REBK_EINVAL, "check_every < 0");
+    if (o.num_ctas < 0) return fail(REBK_EINVAL, "num_ctas < 0");
+    if (o.storage_mask & ~((1 << REBK_FP32) | (1 << REBK_BF16) | 1))
+        return fail(REBK_EINVAL, "unknown bits in storage_mask");
+
+    rebk_handle h = new rebk_handle_s();
+    h->stream = static_cast<cudaStream_t>(o.stream);
+    h->m = m;
+    h->n = n;
+    h->lda = round_up(n, 64);
+    h->tau_r = (int)o.tau_row;
+    h->tau_c = (int)o.tau_col;
+    h->s = (int)((m + h->tau_r - 1) / h->tau_r);
+    h->t = (int)((n + h->tau_c - 1) / h->tau_c);
+    h->check_every = o.check_every;
+    h->num_ctas_opt = o.num_ctas;
+    h->acc_w = (int)round_up(h->tau_c + h->tau_r + 1, 32);
+    const cudaStream_t st = h->stream;
+
+#define CKH(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e__ = (call);                                                                  \
+        if (e__ != cudaSuccess) {                                                                  \
+            rebk_status s__ = cuda_fail(e__, #call);                                               \
+            free_handle(h);                                                                        \
+            return s__;                                                                            \
+        }                                                                                          \
+    } while (0)
+
+    CKH(cudaGetDevice(&h->device));
+    CKH(cudaEventCreate(&h->ev0));
+    CKH(cudaEventCreate(&h->ev1));
+    CKH(cudaEventCreate(&h->kev0));
+    CKH(cudaEventCreate(&h->kev1));
+    const size_t nA = (size_t)m * h->lda;
+    CKH(cudaMalloc(&h->A64, nA * sizeof(double)));
+    CKH(cudaMemcpy2DAsync(h->A64, h->lda * sizeof(double), A, lda * sizeof(double), n * sizeof(double),
+                          m, A_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (h->lda > n)
+        CKH(cudaMemset2DAsync(h->A64 + n, h->lda * sizeof(double), 0, (h->lda - n) * sizeof(double), m,
+                              st));
+    if (o.storage_mask & (1 << REBK_FP32)) {
+        CKH(cudaMalloc(&h->A32, nA * sizeof(float)));
+        CKH(convert_storage(h->A64, h->lda, h->A32, h->lda, m, n, 1, st));
+    }
+    if (o.storage_mask & (1 << REBK_BF16)) {
+        CKH(cudaMalloc(&h->A16, nA * sizeof(__nv_bfloat16)));
+        CKH(convert_storage(h->A64, h->lda, h->A16, h->lda, m, n, 2, st));
+    }
+    CKH(cudaMalloc(&h->nr, sizeof(double) * h->s));
+    CKH(cudaMalloc(&h->cdf_r, sizeof(double) * h->s));
+    CKH(cudaMalloc(&h->nc, sizeof(double) * h->t));
+    CKH(cudaMalloc(&h->cdf_c, sizeof(double) * h->t));
+    CKH(cudaMalloc(&h->d_fallback, sizeof(int) * 2));
+    {
+        double *scratch = nullptr;
+        CKH(cudaMalloc(&scratch, sizeof(double) * (size_t)(m + n + 64 * n)));
+        cudaError_t e = block_tables(h->A64, h->lda, m, n, h->tau_r, h->tau_c, h->s, h->t, h->nr, h->nc,
+                                     h->cdf_r, h->cdf_c, h->d_fallback, scratch, st);
+        cudaError_t e2 = cudaStreamSynchronize(st);
+        cudaFree(scratch);
+        CKH(e);
+        CKH(e2);
+    }
+    CKH(cudaMemcpy(h->fb, h->d_fallback, sizeof(int) * 2, cudaMemcpyDeviceToHost));
+    CKH(cudaMemcpy(&h->fro2, h->cdf_r + (h->s - 1), sizeof(double), cudaMemcpyDeviceToHost));
+    CKH(cudaMalloc(&h->acc, sizeof(double) * 3 * (size_t)h->acc_r * h->acc_w));
+    CKH(cudaMalloc(&h->ws, sizeof(Workspace)));
+    CKH(cudaMalloc(&h->zbuf, sizeof(double) * m));
+    CKH(cudaMalloc(&h->f, sizeof(double) * m));
+    CKH(cudaMalloc(&h->ym, sizeof(double) * m));
+    CKH(cudaMalloc(&h->g, sizeof(double) * n));
+    CKH(cudaMalloc(&h->yn, sizeof(double) * n));
+    CKH(cudaMalloc(&h->dz, sizeof(float) * m));
+    CKH(cudaMalloc(&h->vd, sizeof(float) * m));
+    CKH(cudaMalloc(&h->dx, sizeof(float) * n));
+    CKH(cudaMalloc(&h->sd, sizeof(float) * n));
+#undef CKH
+    if (alpha > 0.0) {
+        h->alpha = alpha;
+    } else if (h->fro2 > 0.0) {
+        double br, bc;
+        rebk_status s = rebk_beta_max(h, &br, &bc);
+        if (s != REBK_OK) {
+            free_handle(h);
+            return s;
+        }
+        h->alpha = 1.75 / std::max(br, bc);
+    } else {
+        h->alpha = 1.0;
+    }
+    *out = h;
+    return REBK_OK;
+}
+
+rebk_status rebk_beta_max(rebk_handle h, double *beta_row, double *beta_col) {
+    if (!h) return fail(REBK_EINVAL, "handle is NULL");
+    if (!h->beta_done) {
+        const cudaStream_t st = h->stream;
+        const size_t gsz = std::max((size_t)h->s * h->tau_r * h->tau_r, (size_t)h->t * h->tau_c * h->tau_c);
+        double *gram = nullptr, *br = nullptr, *bc = nullptr;
+        CK(cudaMalloc(&gram, sizeof(double) * gsz));
+        CK(cudaMalloc(&br, sizeof(double) * h->s));
+        CK(cudaMalloc(&bc, sizeof(double) * h->t));
+        cudaError_t e = beta_max_device(h->A64, h->lda, h->m, h->n, h->tau_r, h->tau_c, h->s, h->t, h->nr,
+                                        h->nc, gram, br, bc, st);
+        std::vector<double> hr(h->s), hc(h->t);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hr.data(), br, sizeof(double) * h->s, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), bc, sizeof(double) * h->t, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(gram);
+        cudaFree(br);
+        cudaFree(bc);
+        if (e != cudaSuccess) return cuda_fail(e, "beta_max");
+        h->beta_r = *std::max_element(hr.begin(), hr.end());
+        h->beta_c = *std::max_element(hc.begin(), hc.end());
+        h->beta_done = true;
+    }
+    if (beta_row) *beta_row = h->beta_r;
+    if (beta_col) *beta_col = h->beta_c;
+    return REBK_OK;
+}
+
+rebk_status rebk_get_alpha(rebk_handle h, double *alpha) {
+    if (!h || !alpha) return fail(REBK_EINVAL, "NULL argument");
+    *alpha = h->alpha;
+    return REBK_OK;
+}
+
+rebk_status rebk_get_blocks(rebk_handle h, int64_t *s, int64_t *t) {
+    if (!h) return fail(REBK_EINVAL, "handle is NULL");
+    if (s) *s = h->s;
+    if (t) *t = h->t;
+    return REBK_OK;
+}
+
+rebk_status rebk_get_tables(rebk_handle h, double *nr, double *nc, double *cdf_r, double *cdf_c) {
+    if (!h) return fail(REBK_EINVAL, "handle is NULL");
+    if (nr) CK(cudaMemcpy(nr, h->nr, sizeof(double) * h->s, cudaMemcpyDeviceToHost));
+    if (nc) CK(cudaMemcpy(nc, h->nc, sizeof(double) * h->t, cudaMemcpyDeviceToHost));
+    if (cdf_r) CK(cudaMemcpy(cdf_r, h->cdf_r, sizeof(double) * h->s, cudaMemcpyDeviceToHost));
+    if (cdf_c) CK(cudaMemcpy(cdf_c, h->cdf_c, sizeof(double) * h->t, cudaMemcpyDeviceToHost));
+    return REBK_OK;
+}
+
+rebk_status rebk_export_storage(rebk_handle h, int32_t storage, void *host_out) {
+    if (!h || !host_out) return fail(REBK_EINVAL, "NULL argument");
+    const void *src = storage == REBK_FP64 ? (const void *)h->A64
+                      : storage == REBK_FP32 ? (const void *)h->A32
+                      : storage == REBK_BF16 ? (const void *)h->A16 : nullptr;
+    if (!src) return fail(REBK_EINVAL, "storage not kept by this handle");
+    const size_t es = storage == REBK_FP64 ? 8 : (storage == REBK_FP32 ? 4 : 2);
+    CK(cudaMemcpy2D(host_out, h->n * es, src, h->lda * es, h->n * es, h->m, cudaMemcpyDeviceToHost));
+    return REBK_OK;
+}
+
+rebk_status rebk_solve_ex(rebk_handle h, const double *b, double *x, double tol, int64_t max_iter,
+                          uint64_t seed, const rebk_solve_ext *ext, rebk_stats *stats) {
+    g_last_error.clear();
+    if (!h) return fail(REBK_EINVAL, "handle is NULL");
+    if (!b || !x) return fail(REBK_EINVAL, "b and x must be device pointers");
+    if (max_iter < 0) return fail(REBK_EINVAL, "max_iter < 0");
+    if (!std::isfinite(tol)) return fail(REBK_EINVAL, "tol is not finite");
+    rebk_solve_ext e;
+    memset(&e, 0, sizeof(e));
+    if (ext) e = *ext;
+    if (e.k0 < 0) return fail(REBK_EINVAL, "k0 < 0");
+    const cudaStream_t st = h->stream;
+    double *z = e.z_out ? e.z_out : h->zbuf;
+    const Mode mode = Mode::PlainF64;
+    // the CTA-count choice runs timed launches on scratch buffers: before any state is set
+    const int G = (h->fro2 == 0.0 || max_iter == 0) ? 1 : pick_ctas(h, mode);
+    reset_counters(h);
+
+    CK(cudaEventRecord(h->ev0, st));
+    if (e.z0) {
+        if (e.z0 != z) CK(cudaMemcpyAsync(z, e.z0, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, st));
+    } else {
+        CK(cudaMemcpyAsync(z, b, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, st));
+    }
+    if (e.x0) {
+        if (e.x0 != x) CK(cudaMemcpyAsync(x, e.x0, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, st));
+    } else {
+        CK(cudaMemsetAsync(x, 0, sizeof(double) * h->n, st));
+    }
+    if (h->fro2 == 0.0 || max_iter == 0) {
+        // A = 0: A^+ b = 0 and Algorithm 1 cannot move.
+        CK(cudaStreamSynchronize(st));
+        double rel = -1;
+        if (e.x_ref) {
+            rebk_status s = rel_error(h, x, e.x_ref, &rel);
+            if (s != REBK_OK) return s;
+        }
+        fill_stats(h, stats, 0, 0, REBK_OK, rel, -1, -1, 0.0);
+        return REBK_OK;
+    }
+    rebk_status s = check_smem(h, mode, G);
+    if (s != REBK_OK) return s;
+
+    GridArgs a = base_args(h, mode, G);
+    a.seed = seed;
+    a.stream = e.stream_id;
+    a.z = z;
+    a.x = x;
+    a.beta = b;
+    a.gamma = nullptr;
+
+    double ref2 = 0.0;
+    const bool use_ref = e.x_ref != nullptr;
+    int64_t check = h->check_every;
+    if (use_ref) {
+        LK(h, sum_sq(e.x_ref, h->n, h->ws->small, st));
+        double v[2];
+        s = fetch_small(h, v, 2);
+        if (s != REBK_OK) return s;
+        ref2 = v[1];
+        if (check <= 0) check = 10;
+        a.x_ref = tol > 0 ? e.x_ref : nullptr;
+        a.x_base = nullptr;
+        a.tol2_abs = tol * tol * ref2;
+        a.check_every = check;
+    } else if (tol > 0) {
+        if (check <= 0) {
+            const double per_iter = (double)h->tau_r * h->n + (double)h->tau_c * h->m;
+            check = std::max<int64_t>(50, (int64_t)(20.0 * (double)h->m * h->n / per_iter));
+        }
+    }
+
+    int64_t total = 0;
+    int dev_status = 0;
+    rebk_status result = REBK_MAX_ITER;
+    double rf = -1, rg = -1, rel = -1;
+    int64_t grow = 16384;
+    while (total < max_iter) {
+        int64_t chunk = max_iter - total;
+        if (!use_ref && tol > 0) chunk = std::min(chunk, check);
+        chunk = std::min(chunk, e.idx_out ? kMaxItersPerLaunch : kIdxChunkMax);
+        if (use_ref && tol > 0) {  // early stop likely: sample in growing chunks
+            chunk = std::min(chunk, grow);
+            grow = std::min<int64_t>(grow * 2, kIdxChunkMax);
+        }
+        s = sample_into(h, a, e.k0 + total, chunk, e.idx_out ? e.idx_out + 2 * total : nullptr);
+        if (s != REBK_OK) return s;
+        a.check_offset = total;
+        int64_t done = 0;
+        s = run_grid(h, mode, a, G, &dev_status, &done);
+        if (s != REBK_OK) return s;
+        total += done;
+        if (dev_status == 6) {
+            fill_stats(h, stats, total, 0, REBK_BARRIER_TIMEOUT, -1, -1, -1, 0);
+            return fail(REBK_BARRIER_TIMEOUT, "device-wide barrier timed out");
+        }
+        if (dev_status == 5) {
+            result = REBK_DIVERGED;
+            break;
+        }
+        if (use_ref) {
+            if (done < chunk) {  // stopped by the error test
+                result = REBK_OK;
+                break;
+            }
+            // the kernel does not test the last iterate of a launch: do it here
+            if (tol > 0 && total % check == 0) {
+                s = rel_error(h, x, e.x_ref, &rel);
+                if (s != REBK_OK) return s;
+                if (rel <= tol) {
+                    result = REBK_OK;
+                    break;
+                }
+            }
+        } else if (tol > 0) {
+            s = residuals(h, b, x, z, &rf, &rg);
+            if (s != REBK_OK) return s;
+            if (std::max(rf, rg) <= tol) {
+                result = REBK_OK;
+                break;
+            }
+        }
+    }
+    CK(cudaEventRecord(h->ev1, st));
+    CK(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    if (use_ref) {
+        s = rel_error(h, x, e.x_ref, &rel);
+        if (s != REBK_OK) return s;
+        if (result == REBK_MAX_ITER && tol > 0 && rel <= tol) result = REBK_OK;
+    }
+    if (tol <= 0 && result == REBK_MAX_ITER) result = REBK_OK;
+    fill_stats(h, stats, total, 0, result, rel, rf, rg, ms);
+    if (result == REBK_DIVERGED) return fail(REBK_DIVERGED, "iteration diverged (Inf/NaN)");
+    return result;
+}
+
+rebk_status rebk_solve(rebk_handle h, const double *b, double *x, double tol, int64_t max_iter,
+                       uint64_t seed, rebk_stats *stats) {
+    return rebk_solve_ex(h, b, x, tol, max_iter, seed, nullptr, stats);
+}
+
+rebk_status rebk_solve_refined(rebk_handle h, const double *b, double *x, double tol,
+                               int64_t max_iter, uint64_t seed, const rebk_refine_opts *ropt,
+                               const rebk_solve_ext *ext, rebk_stats *stats) {
+    g_last_error.clear();
+    if (!h) return fail(REBK_EINVAL, "handle is NULL");
+    if (!b || !x) return fail(REBK_EINVAL, "b and x must be device pointers");
+    if (max_iter < 0) return fail(REBK_EINVAL, "max_iter < 0");
+    if (!std::isfinite(tol)) return fail(REBK_EINVAL, "tol is not finite");
+    rebk_refine_opts ro;
+    memset(&ro, 0, sizeof(ro));
+    ro.storage = REBK_FP32;
+    if (ropt) ro = *ropt;
+    Mode mode;
+    if (ro.storage == REBK_FP32) {
+        if (!h->A32) return fail(REBK_EINVAL, "FP32 copy not kept (storage_mask)");
+        mode = Mode::CorrF32;
+    } else if (ro.storage == REBK_BF16) {
+        if (!h->A16) return fail(REBK_EINVAL, "BF16 copy not kept (storage_mask)");
+        mode = Mode::CorrBF16;
+    } else {
+        return fail(REBK_EINVAL, "refinement storage must be REBK_FP32 or REBK_BF16");
+    }
+    if (ro.max_outer < 0 || ro.inner_iters < 0 || ro.inner_reduction < 0)
+        return fail(REBK_EINVAL, "negative refinement option");
+    const int max_outer = ro.max_outer > 0 ? ro.max_outer : 30;
+    const double red = ro.inner_reduction > 0 ? ro.inner_reduction : (mode == Mode::CorrF32 ? 1e-4 : 1e-2);
+    rebk_solve_ext e;
+    memset(&e, 0, sizeof(e));
+    if (ext) e = *ext;
+    if (e.k0 < 0) return fail(REBK_EINVAL, "k0 < 0");
+    const cudaStream_t st = h->stream;
+    double *z = e.z_out ? e.z_out : h->zbuf;
+    const int G = (h->fro2 == 0.0 || max_iter == 0) ? 1 : pick_ctas(h, mode);
+    reset_counters(h);
+
+    CK(cudaEventRecord(h->ev0, st));
+    if (e.z0) {
+        if (e.z0 != z) CK(cudaMemcpyAsync(z, e.z0, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, st));
+    } else {
+        CK(cudaMemcpyAsync(z, b, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, st));
+    }
+    if (e.x0) {
+        if (e.x0 != x) CK(cudaMemcpyAsync(x, e.x0, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, st));
+    } else {
+        CK(cudaMemsetAsync(x, 0, sizeof(double) * h->n, st));
+    }
+    if (h->fro2 == 0.0 || max_iter == 0) {
+        CK(cudaStreamSynchronize(st));
+        double rel = -1;
+        if (e.x_ref) {
+            rebk_status s = rel_error(h, x, e.x_ref, &rel);
+            if (s != REBK_OK) return s;
+        }
+        fill_stats(h, stats, 0, 0, REBK_OK, rel, -1, -1, 0.0);
+        return REBK_OK;
+    }
+    rebk_status s = check_smem(h, mode, G);
+    if (s != REBK_OK) return s;
+
+    const bool use_ref = e.x_ref != nullptr;
+    double refn = 0.0;
+    if (use_ref) {
+        LK(h, sum_sq(e.x_ref, h->n, h->ws->small, st));
+        double v[2];
+        s = fetch_small(h, v, 2);
+        if (s != REBK_OK) return s;
+        refn = std::sqrt(v[1]);
+    }
+    int64_t inner_max = ro.inner_iters;
+    if (inner_max <= 0) {
+        if (use_ref) {
+            inner_max = 1000000;
+        } else {
+            const double per_iter = (double)h->tau_r * h->n + (double)h->tau_c * h->m;
+            inner_max = std::max<int64_t>(200, (int64_t)(40.0 * (double)h->m * h->n / per_iter));
+        }
+    }
+    int64_t check = h->check_every > 0 ? h->check_every : 10;
+
+    GridArgs a = base_args(h, mode, G);
+    a.seed = seed;
+    a.stream = e.stream_id;
+    a.z = h->dz;
+    a.x = h->dx;
+    a.beta = h->f;
+    a.gamma = h->g;
+    a.sdual = h->sd;
+    a.vdual = h->vd;
+
+    int64_t total = 0;
+    int outer = 0;
+    rebk_status result = REBK_MAX_ITER;
+    double rel = -1, rf = -1, rg = -1, prev_res = -1;
+    for (outer = 0; outer < max_outer; ++outer) {
+        // f = b - z - A x, g = A^T z (FP64)
+        s = timed_sweep(h, x, false, z, false, h->ym, h->g);
+        if (s != REBK_OK) return s;
+        LK(h, form_f(b, z, h->ym, h->f, h->m, st));
+        double e0 = 0.0;
+        if (use_ref) {
+            LK(h, err_norms(nullptr, x, e.x_ref, h->n, h->ws->small, st));
+            double v[2];
+            s = fetch_small(h, v, 2);
+            if (s != REBK_OK) return s;
+            e0 = std::sqrt(v[0]);
+            rel = refn > 0 ? e0 / refn : e0;
+            if (rel <= tol) {
+                result = REBK_OK;
+                break;
+            }
+        } else {
+            LK(h, sum_sq(h->f, h->m, h->ws->small, st));
+            LK(h, sum_sq(h->g, h->n, h->ws->small + 2, st));
+            LK(h, sum_sq(b, h->m, h->ws->small + 4, st));
+            double v[6];
+            s = fetch_small(h, v, 6);
+            if (s != REBK_OK) return s;
+            const double nb = std::sqrt(v[5]);
+            rf = nb > 0 ? std::sqrt(v[1]) / nb : 0.0;
+            rg = nb > 0 ? std::sqrt(v[3]) / (std::sqrt(h->fro2) * nb) : 0.0;
+            const double res = std::max(rf, rg);
+            if (res <= tol) {
+                result = REBK_OK;
+                break;
+            }
+            if (prev_res > 0 && res > 0.1 * prev_res) inner_max = std::min<int64_t>(inner_max * 2, 1 << 24);
+            prev_res = res;
+        }
+        if (total >= max_iter) break;
+        // inner sweeps on corrections from zero
+        LK(h, fill_zero_f32(h->dz, h->m, st));
+        LK(h, fill_zero_f32(h->vd, h->m, st));
+        LK(h, fill_zero_f32(h->dx, h->n, st));
+        LK(h, fill_zero_f32(h->sd, h->n, st));
+        const int64_t iters = std::min(inner_max, max_iter - total);
+        int64_t ran = 0;
+        int64_t grow = 16384;
+        while (ran < iters) {
+            int64_t chunk = std::min(iters - ran, e.idx_out ? kMaxItersPerLaunch : kIdxChunkMax);
+            if (use_ref) {
+                chunk = std::min(chunk, grow);
+                grow = std::min<int64_t>(grow * 2, kIdxChunkMax);
+            }
+            s = sample_into(h, a, e.k0 + total + ran, chunk,
+                            e.idx_out ? e.idx_out + 2 * (total + ran) : nullptr);
+            if (s != REBK_OK) return s;
+            a.check_offset = ran;
+            if (use_ref) {
+                const double thr = std::max(tol * refn, red * e0);
+                a.x_ref = e.x_ref;
+                a.x_base = x;
+                a.tol2_abs = thr * thr;
+                a.check_every = check;
+            }
+            int dev_status = 0;
+            int64_t done = 0;
+            s = run_grid(h, mode, a, G, &dev_status, &done);
+            if (s != REBK_OK) return s;
+            ran += done;
+            if (dev_status == 6) {
+                fill_stats(h, stats, total + ran, outer + 1, REBK_BARRIER_TIMEOUT, -1, -1, -1, 0);
+                return fail(REBK_BARRIER_TIMEOUT, "device-wide barrier timed out");
+            }
+            if (dev_status == 5) {
+                fill_stats(h, stats, total + ran, outer + 1, REBK_DIVERGED, -1, -1, -1, 0);
+                return fail(REBK_DIVERGED, "inner iteration diverged (Inf/NaN)");
+            }
+            if (done < chunk) break;  // error test met
+        }
+        total += ran;
+        // z <- z - A s, x <- x + A^T v (FP64 A)
+        s = timed_sweep(h, h->sd, true, h->vd, true, h->ym, h->yn);
+        if (s != REBK_OK) return s;
+        LK(h, apply_update(x, h->yn, h->n, z, h->ym, h->m, st));
+    }
+    if (result != REBK_OK) {
+        // final test after the last pass
+        if (use_ref) {
+            s = rel_error(h, x, e.x_ref, &rel);
+            if (s != REBK_OK) return s;
+            if (rel <= tol) result = REBK_OK;
+        } else {
+            s = residuals(h, b, x, z, &rf, &rg);
+            if (s != REBK_OK) return s;
+            if (std::max(rf, rg) <= tol) result = REBK_OK;
+        }
+    }
+    CK(cudaEventRecord(h->ev1, st));
+    CK(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    fill_stats(h, stats, total, outer, result, rel, rf, rg, ms);
+    return result;
+}
+
+}  // extern "C"

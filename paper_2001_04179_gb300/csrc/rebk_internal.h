@@ -1,0 +1,129 @@
+// rebk_internal.h -- declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+namespace rebk {
+
+constexpr int kThreads = 512;              // threads per CTA of the persistent kernel
+constexpr int kWarps = kThreads / 32;
+constexpr int kRing = 8;                   // block indices kept ahead / behind
+constexpr int kAccReplicas = 8;            // replicated accumulators (atomic contention)
+constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s per wait
+constexpr int64_t kMaxItersPerLaunch = 8000000;                 // barrier counter headroom
+
+// Arguments of the persistent REBK kernel (Algorithm 1 on one system).
+//
+// State arrays z (length m) and x (length n) have the kernel's arithmetic type
+// TS.  In the plain form (CORR = false) they are z and x of Algorithm 1,
+// beta = b and gamma = NULL.  In the correction form (CORR = true) they are
+// the corrections dz, dx, beta = f = b - z - A x, gamma = g = A^T z, and the
+// duals s (length n) and v (length m) are accumulated (see rebk.h).
+struct GridArgs {
+    const void *A;          // stored copy, row-major, leading dimension lda (zero padded)
+    int64_t lda, m, n;
+    int tau_r, tau_c, s, t; // block sizes and counts (Section 3 partition)
+    const double *cdf_r, *cdf_c, *nr, *nc;
+    int fb_r, fb_c;         // fallback picks (last block of nonzero norm)
+    double alpha;
+    uint64_t seed, stream;
+    int64_t k0, iters;      // iterations k0+1 .. k0+iters
+    void *z, *x;            // TS, length m / n
+    const double *beta;     // length m
+    const double *gamma;    // length n (CORR) or NULL
+    void *sdual, *vdual;    // TS, length n / m (CORR)
+    const double *x_ref;    // NULL = no error test
+    const double *x_base;   // CORR: the test uses x_base + x
+    double tol2_abs;        // stop once ||(x_base +) x - x_ref||^2 <= tol2_abs
+    int64_t check_every;    // test x^k when (check_offset + k) % check_every == 0
+    int64_t check_offset;
+    const int32_t *idx;     // 2 * iters entries: (j_k, i_k), from sample_blocks()
+    double *acc;            // [3][acc_r][acc_w] doubles, zeroed before launch
+    int acc_w, acc_r;
+    int nrow_cap, ncol_cap; // shared-memory capacity for the owned slices
+    unsigned int *bar;      // barrier counter, zeroed before launch
+    int *status;            // zeroed before launch
+    int64_t *iters_done;
+    unsigned long long timeout_ns;
+};
+
+enum class Mode { PlainF64, CorrF32, CorrBF16 };
+
+// Shared-memory layout of the persistent kernel (byte offsets, 16-byte aligned).
+struct SmemLayout {
+    size_t zeta, beta, v, xi, s, w, r, red, total;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(int nrow_cap, int ncol_cap, int tau_r, int tau_c,
+                                                  bool corr, int ts, int vec) {
+    auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    SmemLayout L;
+    size_t o = 128;  // block-index ring and flags
+    L.zeta = o; o = al(o + (size_t)nrow_cap * ts);
+    L.beta = o; o = al(o + (size_t)nrow_cap * ts);
+    L.v = o;    if (corr) o = al(o + (size_t)nrow_cap * ts);
+    L.xi = o;   o = al(o + (size_t)ncol_cap * ts);
+    L.s = o;    if (corr) o = al(o + (size_t)ncol_cap * ts);
+    L.w = o;    o = al(o + (size_t)tau_c * ts);
+    L.r = o;    o = al(o + (size_t)tau_r * ts);
+    L.red = o;
+    size_t red = (size_t)kThreads * vec * ts;
+    if (red < (size_t)kWarps * 8) red = (size_t)kWarps * 8;
+    o = al(o + red);
+    L.total = o;
+    return L;
+}
+
+// Owned row / column slices of CTA c of G (rows [r0, r1), columns [c0, c1);
+// column slices are aligned to 8 elements so every 16-byte vector load of a
+// slice starts inside it or in the zero padding).
+inline void host_slices(int64_t m, int64_t n, int G, int c, int64_t *r0, int64_t *r1,
+                        int64_t *c0, int64_t *c1) {
+    const int64_t nu = (n + 7) / 8;
+    *r0 = m * c / G;
+    *r1 = m * (c + 1) / G;
+    int64_t a = 8 * (nu * c / G), b = 8 * (nu * (c + 1) / G);
+    *c0 = a < n ? a : n;
+    *c1 = b < n ? b : n;
+}
+
+size_t grid_smem_bytes(Mode mode, const GridArgs &a);
+// idx[2(k-1)] = j_k, idx[2(k-1)+1] = i_k for k = 1..K (draws of iterations k0+1..k0+K).
+cudaError_t sample_blocks(uint64_t seed, uint64_t stream, int64_t k0, int64_t K, const double *cdf_r,
+                          int s, const double *cdf_c, int t, int fb_r, int fb_c, int32_t *idx,
+                          cudaStream_t st);
+cudaError_t launch_grid(Mode mode, const GridArgs &a, int G, cudaStream_t st);
+int grid_max_ctas(Mode mode, size_t smem);
+
+// Setup and sweep kernels (rebk_setup.cu).
+cudaError_t convert_storage(const double *src, int64_t lds, void *dst, int64_t ldd, int64_t m,
+                            int64_t n, int storage, cudaStream_t st);
+cudaError_t block_tables(const double *A, int64_t lda, int64_t m, int64_t n, int tau_r, int tau_c,
+                         int s, int t, double *nr, double *nc, double *cdf_r, double *cdf_c,
+                         int *fallback /* device int[2] */, double *scratch /* m + n + 64*n */,
+                         cudaStream_t st);
+// y_m = A p (length m), y_n = A^T q (length n); p or q may be NULL (skipped).
+// TP/TQ: double or float inputs.
+cudaError_t dual_sweep(const double *A, int64_t lda, int64_t m, int64_t n, const void *p,
+                       bool p_f32, const void *q, bool q_f32, double *ym, double *yn,
+                       cudaStream_t st);
+cudaError_t beta_max_device(const double *A, int64_t lda, int64_t m, int64_t n, int tau_r, int tau_c,
+                            int s, int t, const double *nr, const double *nc, double *gram_scratch,
+                            double *beta_rows, double *beta_cols, cudaStream_t st);
+// out[0] = sum (a + x - r)^2 over n (a may be NULL), out[1] = sum r^2.
+cudaError_t err_norms(const double *a, const double *x, const double *r, int64_t n, double *out,
+                      cudaStream_t st);
+cudaError_t sum_sq(const double *v, int64_t n, double *out, cudaStream_t st);
+// f = b - z - ym (length m); g = yn copy handled by caller
+cudaError_t form_f(const double *b, const double *z, const double *ym, double *f, int64_t m,
+                   cudaStream_t st);
+// x += yn (n), z -= ym (m)
+cudaError_t apply_update(double *x, const double *yn, int64_t n, double *z, const double *ym,
+                         int64_t m, cudaStream_t st);
+cudaError_t fill_zero_f32(float *p, int64_t n, cudaStream_t st);
+
+}  // namespace rebk

@@ -1,0 +1,166 @@
+"""Python face of the REBK solver: a handle around the C ABI with torch tensors
+for device memory and streams.  Every computation runs in librebk.so."""
+from __future__ import annotations
+
+import ctypes
+from typing import Optional, Sequence
+
+import numpy as np
+
+from . import rebk as _r
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _dptr(t) -> Optional[int]:
+    return None if t is None else t.data_ptr()
+
+
+def _require_cuda_f64(t, n: int, name: str):
+    torch = _torch()
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+            and t.numel() == n):
+        raise ValueError(f"{name} must be a contiguous CUDA float64 tensor of {n} elements")
+
+
+class Solver:
+    """REBK solver for one matrix A (Algorithm 1 of arXiv:2001.04179).
+
+    A: torch CUDA float64 tensor (m x n, row-major) or a numpy float64 array.
+    tau_row / tau_col: block sizes of the contiguous partitions (Section 3).
+    alpha: step size; <= 0 picks 1.75 / beta_max.
+    storage: reduced-precision copies to keep for solve_refined ("fp32", "bf16").
+    """
+
+    def __init__(self, A, tau_row: int, tau_col: int, alpha: float = 0.0,
+                 storage: Sequence[str] = ("fp32",), num_ctas: int = 0, check_every: int = 0,
+                 stream=None):
+        torch = _torch()
+        lib = _r.load()
+        mask = 0
+        for s in storage:
+            mask |= 1 << _r.STORAGE[s]
+        self._stream = stream
+        opt = _r.RebkOptions(tau_row, tau_col, mask, num_ctas, check_every,
+                             None if stream is None else ctypes.c_void_p(stream.cuda_stream))
+        h = ctypes.c_void_p()
+        if isinstance(A, torch.Tensor):
+            if not (A.is_cuda and A.dtype == torch.float64 and A.dim() == 2 and A.stride(1) == 1):
+                raise ValueError("A must be a CUDA float64 matrix with unit column stride")
+            m, n = A.shape
+            st = lib.rebk_create(ctypes.byref(h), ctypes.c_void_p(A.data_ptr()), m, n, A.stride(0), 1,
+                                 float(alpha), ctypes.byref(opt))
+        else:
+            An = np.ascontiguousarray(A, dtype=np.float64)
+            m, n = An.shape
+            st = lib.rebk_create(ctypes.byref(h), An.ctypes.data_as(ctypes.c_void_p), m, n, n, 0,
+                                 float(alpha), ctypes.byref(opt))
+        _r.check(st)
+        self._h = h
+        self.m, self.n = int(m), int(n)
+        self.tau_row, self.tau_col = tau_row, tau_col
+
+    # ------------------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            _r.load().rebk_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ------------------------------------------------------------------
+    @property
+    def alpha(self) -> float:
+        a = ctypes.c_double()
+        _r.check(_r.load().rebk_get_alpha(self._h, ctypes.byref(a)))
+        return a.value
+
+    def blocks(self):
+        s, t = ctypes.c_int64(), ctypes.c_int64()
+        _r.check(_r.load().rebk_get_blocks(self._h, ctypes.byref(s), ctypes.byref(t)))
+        return s.value, t.value
+
+    def tables(self):
+        s, t = self.blocks()
+        nr, nc, cr, cc = np.zeros(s), np.zeros(t), np.zeros(s), np.zeros(t)
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        _r.check(_r.load().rebk_get_tables(self._h, p(nr), p(nc), p(cr), p(cc)))
+        return nr, nc, cr, cc
+
+    def beta_max(self):
+        br, bc = ctypes.c_double(), ctypes.c_double()
+        _r.check(_r.load().rebk_beta_max(self._h, ctypes.byref(br), ctypes.byref(bc)))
+        return br.value, bc.value
+
+    def export_storage(self, storage: str) -> np.ndarray:
+        dt = {"fp64": np.float64, "fp32": np.float32, "bf16": np.uint16}[storage]
+        out = np.zeros((self.m, self.n), dtype=dt)
+        _r.check(_r.load().rebk_export_storage(self._h, _r.STORAGE[storage],
+                                               out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    # ------------------------------------------------------------------
+    def _ext(self, x_ref, x0, z0, z_out, idx_out, k0, stream_id):
+        for t, n, name in [(x_ref, self.n, "x_ref"), (x0, self.n, "x0"), (z0, self.m, "z0"),
+                           (z_out, self.m, "z_out")]:
+            if t is not None:
+                _require_cuda_f64(t, n, name)
+        return _r.RebkSolveExt(_dptr(x_ref), _dptr(x0), _dptr(z0), _dptr(z_out), _dptr(idx_out),
+                               int(k0), int(stream_id))
+
+    def solve(self, b, tol: float = 0.0, max_iter: int = 1000, seed: int = 0, x_ref=None, x0=None,
+              z0=None, k0: int = 0, stream_id: int = 0, record: bool = False, return_z: bool = False,
+              x=None, allow=(_r.REBK_OK, _r.REBK_MAX_ITER)):
+        """Plain FP64 Algorithm 1.  Returns dict(x, stats[, z][, idx])."""
+        torch = _torch()
+        _require_cuda_f64(b, self.m, "b")
+        if x is None:
+            x = torch.empty(self.n, dtype=torch.float64, device=b.device)
+        z = torch.empty(self.m, dtype=torch.float64, device=b.device) if return_z else None
+        idx = torch.zeros(max(2 * max_iter, 2), dtype=torch.int32, device=b.device) if record else None
+        ext = self._ext(x_ref, x0, z0, z, idx, k0, stream_id)
+        stats = _r.RebkStats()
+        st = _r.load().rebk_solve_ex(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                     float(tol), int(max_iter), int(seed), ctypes.byref(ext),
+                                     ctypes.byref(stats))
+        _r.check(st, allow)
+        out = {"x": x, "stats": stats.as_dict(), "status": st}
+        if return_z:
+            out["z"] = z
+        if record:
+            out["idx"] = idx[: 2 * stats.iterations].view(-1, 2)
+        return out
+
+    def solve_refined(self, b, tol: float = 1e-8, max_iter: int = 10**7, seed: int = 0,
+                      storage: str = "fp32", x_ref=None, x0=None, z0=None, k0: int = 0,
+                      stream_id: int = 0, max_outer: int = 0, inner_iters: int = 0,
+                      inner_reduction: float = 0.0, record: bool = False, return_z: bool = False,
+                      x=None, allow=(_r.REBK_OK, _r.REBK_MAX_ITER)):
+        """Mixed precision (FP32/BF16 inner sweeps, FP64 refinement).  Returns dict(x, stats, ...)."""
+        torch = _torch()
+        _require_cuda_f64(b, self.m, "b")
+        if x is None:
+            x = torch.empty(self.n, dtype=torch.float64, device=b.device)
+        z = torch.empty(self.m, dtype=torch.float64, device=b.device) if return_z else None
+        idx = torch.zeros(max(2 * min(max_iter, 10**7), 2), dtype=torch.int32, device=b.device) if record else None
+        ext = self._ext(x_ref, x0, z0, z, idx, k0, stream_id)
+        ro = _r.RebkRefineOpts(_r.STORAGE[storage], int(max_outer), int(inner_iters), float(inner_reduction))
+        stats = _r.RebkStats()
+        st = _r.load().rebk_solve_refined(self._h, ctypes.c_void_p(b.data_ptr()),
+                                          ctypes.c_void_p(x.data_ptr()), float(tol), int(max_iter),
+                                          int(seed), ctypes.byref(ro), ctypes.byref(ext),
+                                          ctypes.byref(stats))
+        _r.check(st, allow)
+        out = {"x": x, "stats": stats.as_dict(), "status": st}
+        if return_z:
+            out["z"] = z
+        if record:
+            out["idx"] = idx[: 2 * stats.iterations].view(-1, 2)
+        return out
