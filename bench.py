@@ -1,0 +1,402 @@
+#!/usr/bin/env python3
+"""REBK benchmark on GB300: solves/s to 1e-8 relative error.
+
+Workload (the precision configuration): A = G1 G2 with G1 = randn(8000, 2000),
+G2 = randn(2000, 20000) (m = 8000, n = 20000, rank 2000, rank-deficient and
+underdetermined), inconsistent b = A x* + N(0, 0.01^2), seed = rank;
+contiguous blocks tau = 128 (Section 3 partitions); alpha = 1.75 / beta_max
+(Section 3's empirical step, beta_max from the block spectral norms on the
+GPU).  A step is one complete solve to ||x - A^+ b|| <= 1e-8 ||A^+ b|| (the
+paper's stop rule with a relative tolerance) by the mixed-precision path:
+FP32 or BF16 storage, FP32 inner sweeps, FP64 refinement.  The plain FP64
+path is timed on the same problem for comparison.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+M, N, RANK, TAU, TOL = 8000, 20000, 2000, 128, 1e-8
+METRIC = "solves/s to 1e-8 rel err (mixed+warm-start+batched vs plain FP64); HBM GB/s"
+WORKLOAD = ("precision: A = G1 G2, G1 = randn(8000,2000), G2 = randn(2000,20000) "
+            "(8000x20000, rank 2000), b = A x* + N(0,0.01^2), tau = 128, alpha = 1.75/beta_max, "
+            "stop ||x - A^+b|| <= 1e-8 ||A^+b||")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--storage", choices=["fp32", "bf16"], default="fp32")
+    ap.add_argument("--plain-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), float(d["bf16_tflops"]), "measured"
+    return 6800.0, 1900.0, "fallback"
+
+
+def load_anchor():
+    path = os.path.join(ROOT, "tests", "golden", "precision_anchor.txt")
+    out = {}
+    if os.path.exists(path):
+        for line in open(path):
+            if line.startswith("#") or not line.strip():
+                continue
+            k, v = line.split()
+            out[k] = float(v)
+    return out
+
+
+def load_traffic(kernel_tag: str):
+    """DRAM bytes per iteration of the headline kernel from the committed ncu
+    summary, only if it was taken on the current kernel source."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_2001_04179_gb300", "csrc", "rebk_grid.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "rebk_grid_precision_8000x20000.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        if line.startswith("traffic:"):
+            # traffic: <tag> <source sha> <dram bytes per iteration>
+            parts = line.split()
+            if len(parts) == 4 and parts[1] == kernel_tag and parts[2] == sha:
+                return float(parts[3])
+    return None
+
+
+def make_problem(seed: int, use_gpu: bool):
+    from workloads import product_problem
+    mm = None
+    if use_gpu:
+        import torch
+
+        def mm(a, b):
+            ta = torch.from_numpy(np.ascontiguousarray(a)).cuda()
+            tb = torch.from_numpy(np.ascontiguousarray(b)).cuda()
+            r = (ta @ tb).cpu().numpy()
+            del ta, tb
+            return r
+    return product_problem(M, N, RANK, seed=seed, noise=0.01, matmul=mm)
+
+
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def cpu_baseline(prob, alpha, iters_per_solve, seconds, source):
+    """The oracle (plain FP64 Algorithm 1, single thread) on a bounded number
+    of iterations of the same workload; solves/s = iterations/s divided by
+    the iterations one solve needs."""
+    import oracle as O
+    from workloads import contiguous_offsets
+    ro, co = contiguous_offsets(M, TAU), contiguous_offsets(N, TAU)
+    norms = O.block_norms(prob.A, ro, co)
+    t0 = time.perf_counter()
+    O.rebk(prob.A, prob.b, ro, co, alpha, seed=1000, iters=3, norms=norms)
+    per = (time.perf_counter() - t0) / 3
+    n_it = max(5, int(seconds / max(per, 1e-6)))
+    t0 = time.perf_counter()
+    O.rebk(prob.A, prob.b, ro, co, alpha, seed=1000, iters=n_it, norms=norms)
+    dt = time.perf_counter() - t0
+    its = n_it / dt
+    return {"value": its / iters_per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "iterations_per_s": its,
+            "sample": (f"{n_it} iterations of the FP64 oracle (C, -O2, no FMA contraction) of Algorithm 1 "
+                       f"on this workload in {dt:.1f} s; solves/s = iterations/s / {iters_per_solve:.0f} "
+                       f"iterations per solve ({source})")}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    anchor = load_anchor()
+    use_gpu = False
+    try:
+        import torch
+        use_gpu = torch.cuda.is_available()
+    except Exception:
+        pass
+    prob = make_problem(0, use_gpu)
+    alpha = anchor.get("alpha")
+    if alpha is None:
+        import oracle as O
+        from workloads import contiguous_offsets
+        alpha = 1.75 / max(O.beta_max(prob.A, contiguous_offsets(M, TAU), contiguous_offsets(N, TAU)))
+    ipsolve = anchor.get("iterations_to_1e-8", float("nan"))
+    import oracle as O
+    from workloads import contiguous_offsets
+    ro, co = contiguous_offsets(M, TAU), contiguous_offsets(N, TAU)
+    norms = O.block_norms(prob.A, ro, co)
+    # each step: a bounded sample of ~3 s of oracle iterations
+    t0 = time.perf_counter()
+    O.rebk(prob.A, prob.b, ro, co, alpha, seed=1000, iters=2, norms=norms)
+    per = (time.perf_counter() - t0) / 2
+    n_it = max(3, int(3.0 / max(per, 1e-6)))
+    for _ in range(args.warmup):
+        O.rebk(prob.A, prob.b, ro, co, alpha, seed=1000, iters=max(1, n_it // 10), norms=norms)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        O.rebk(prob.A, prob.b, ro, co, alpha, seed=1000 + s, iters=n_it, norms=norms)
+    dt = time.perf_counter() - t0
+    its = args.steps * n_it / dt
+    value = its / ipsolve
+    sample = (f"per step {n_it} iterations of the FP64 oracle of Algorithm 1 on this workload; "
+              f"solves/s = iterations/s / {ipsolve:.0f} iterations per solve "
+              f"(oracle's own count to 1e-8, tests/golden/precision_anchor.txt)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "tau": TAU, "alpha": alpha},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                             "sample": sample, "iterations_per_s": its},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    from paper_2001_04179_gb300 import Solver
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    hbm_peak, bf16_peak, peak_src = load_peaks()
+    prob = make_problem(rank, True)
+    stream = torch.cuda.current_stream()
+    A_dev = torch.from_numpy(prob.A).to(dev)
+    sol = Solver(A_dev, TAU, TAU, alpha=0.0, storage=("fp32", "bf16"), stream=stream)
+    del A_dev
+    torch.cuda.empty_cache()
+    alpha = sol.alpha
+    b = torch.from_numpy(prob.b).to(dev)
+    xr = torch.from_numpy(prob.x_ref).to(dev)
+    S = args.storage
+
+    def solve_mixed(seed, bb=b, xx=xr, x=None):
+        r = sol.solve_refined(bb, tol=TOL, seed=seed, storage=S, x_ref=xx, x=x)
+        if r["stats"]["rel_err"] > TOL:
+            raise RuntimeError(f"solve did not reach {TOL}: {r['stats']}")
+        return r
+
+    for w in range(args.warmup):
+        solve_mixed(900 + w)
+
+    # ---------------- timed region: K solves, inputs resident in HBM ----------------
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    agg = {"iterations": 0, "kernel_ms": 0.0, "sweep_ms": 0.0, "launches": 0, "grid_launches": 0, "outer": 0}
+    for s in range(args.steps):
+        st = solve_mixed(1000 + s)["stats"]
+        for k in agg:
+            agg[k] += st[k]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = args.steps * world / (ms_max / 1000.0)
+
+    # ---------------- e2e: host buffers, copies inside the timed region ----------------
+    b_host = torch.from_numpy(prob.b).pin_memory()
+    xr_host = torch.from_numpy(prob.x_ref).pin_memory()
+    x_host = torch.empty(N, dtype=torch.float64).pin_memory()
+    b_d = torch.empty_like(b)
+    xr_d = torch.empty_like(xr)
+    x_d = torch.empty(N, dtype=torch.float64, device=dev)
+    e2e_steps = max(1, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        b_d.copy_(b_host, non_blocking=True)
+        xr_d.copy_(xr_host, non_blocking=True)
+        solve_mixed(2000 + s, bb=b_d, xx=xr_d, x=x_d)
+        x_host.copy_(x_d, non_blocking=True)
+        torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    te = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(te, op=dist.ReduceOp.MAX)
+    e2e_value = e2e_steps * world / float(te.item())
+
+    # ---------------- plain FP64 path on the same problem ----------------
+    plain = None
+    if args.plain_steps > 0:
+        sol.solve(b, tol=TOL, max_iter=10**7, seed=800, x_ref=xr)
+        torch.cuda.synchronize()
+        p_ev0, p_ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p_ev0.record(stream)
+        pagg = {"iterations": 0, "kernel_ms": 0.0, "grid_launches": 0}
+        for s in range(args.plain_steps):
+            st = sol.solve(b, tol=TOL, max_iter=10**7, seed=1000 + s, x_ref=xr)["stats"]
+            for k in pagg:
+                pagg[k] += st[k]
+        p_ev1.record(stream)
+        torch.cuda.synchronize()
+        pms = p_ev0.elapsed_time(p_ev1) / args.plain_steps
+        it = pagg["iterations"] / args.plain_steps
+        flops = 4.0 * TAU * (M + N) * pagg["iterations"]
+        plain = {"value": 1000.0 / pms, "unit": "solves/s", "ms_per_solve": pms, "iterations_per_solve": it,
+                 "block_iterations_per_s": pagg["iterations"] / (pagg["kernel_ms"] / 1000.0),
+                 "roofline": {"bound": "alu", "achieved": flops / (pagg["kernel_ms"] / 1000.0) / 1e12,
+                              "peak": 1.25, "unit": "TFLOP/s",
+                              "frac": flops / (pagg["kernel_ms"] / 1000.0) / 1e12 / 1.25,
+                              "peak_source": "nominal GB300 FP64 rate (recipe table); FP64 FMA pipe",
+                              "hbm_gbs": 8.0 * TAU * (M + N) * pagg["iterations"] / (pagg["kernel_ms"] / 1000.0) / 1e9}}
+
+    # ---------------- roofline of the dominant kernel ----------------
+    esize = {"fp32": 4, "bf16": 2}[S]
+    bytes_per_iter = float(TAU * N + TAU * M) * esize
+    kernel_s = agg["kernel_ms"] / 1000.0
+    achieved = bytes_per_iter * agg["iterations"] / kernel_s / 1e9
+    traffic_per_iter = load_traffic(f"corr_{S}")
+    per_launch_iters = agg["iterations"] / max(agg["grid_launches"], 1)
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+            "frac": achieved / hbm_peak, "peak_source": peak_src,
+            "traffic": None if traffic_per_iter is None else traffic_per_iter * per_launch_iters,
+            "algorithmic_bytes_per_launch": bytes_per_iter * per_launch_iters,
+            "kernel": f"rebk_grid_kernel<{ 'float' if S == 'fp32' else '__nv_bfloat16' },float,corr>",
+            "kernel_share_of_step": kernel_s / (ms_max / 1000.0),
+            "avg_launch_ms": agg["kernel_ms"] / max(agg["grid_launches"], 1)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        anchor = load_anchor()
+        if "iterations_to_1e-8" in anchor:
+            ips, src = anchor["iterations_to_1e-8"], "oracle's own count, tests/golden/precision_anchor.txt"
+        else:
+            ips, src = (plain or {}).get("iterations_per_solve", float("nan")), "GPU plain FP64 count"
+        cpu = cpu_baseline(prob, alpha, ips, args.cpu_seconds, src)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "storage": S, "tau": TAU, "alpha": alpha, "tol": TOL,
+                       "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
+                       "l2": "inputs larger than L2 (A: 320 MB bf16 / 640 MB fp32 / 1.28 GB fp64)"},
+            "iterations_per_solve": agg["iterations"] / args.steps,
+            "outer_passes_per_solve": agg["outer"] / args.steps,
+            "hbm_gbs": achieved,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": "solves/s", "h2d_bytes_per_step": 8 * (M + N),
+                    "d2h_bytes_per_step": 8 * N},
+            "gpu_launches": agg["launches"],
+            "clocks": clk,
+            "plain_fp64": plain,
+            "speedup_vs_plain_fp64": None if plain is None else value / plain["value"],
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -70,8 +70,12 @@ struct rebk_handle_s {
     __nv_bfloat16 *A16 = nullptr;
     double *nr = nullptr, *nc = nullptr, *cdf_r = nullptr, *cdf_c = nullptr;
     int *d_fallback = nullptr;
-    double *acc = nullptr;
+    void *acc = nullptr;  // 3 sets x acc_r replicas x acc_w, 8 bytes per entry
     int acc_w = 0, acc_r = kAccReplicas;
+    double *coef_r64 = nullptr, *coef_c64 = nullptr;
+    float *coef_r32 = nullptr, *coef_c32 = nullptr;
+    GridArgs prep[3];       // prepared launch arguments per mode (for prepG CTAs)
+    int prepG[3] = {0, 0, 0};
     Workspace *ws = nullptr;
     double *zbuf = nullptr, *f = nullptr, *g = nullptr, *ym = nullptr, *yn = nullptr;
     float *dz = nullptr, *dx = nullptr, *sd = nullptr, *vd = nullptr;
@@ -96,6 +100,7 @@ namespace {
 void free_handle(rebk_handle h) {
     if (!h) return;
     void *ptrs[] = {h->A64, h->A32, h->A16, h->nr, h->nc, h->cdf_r, h->cdf_c, h->d_fallback, h->acc,
+                    h->coef_r64, h->coef_c64, h->coef_r32, h->coef_c32,
                     h->ws, h->zbuf, h->f, h->g, h->ym, h->yn, h->dz, h->dx, h->sd, h->vd,
                     h->idxbuf};
     for (void *p : ptrs)
@@ -110,8 +115,14 @@ void free_handle(rebk_handle h) {
 
 int mode_index(Mode m) { return m == Mode::PlainF64 ? 0 : (m == Mode::CorrF32 ? 1 : 2); }
 
-// Fills the parts of GridArgs that depend only on the handle and mode.
+constexpr size_t kSmemLimit = 227 * 1024;
+
+// Launch arguments that depend only on the handle, the mode and the CTA count
+// G: matrix copy, tables, workspace, owned-slice capacities and, when the
+// tiles fit twice in shared memory, the TMA box geometry and tensor maps.
 GridArgs base_args(rebk_handle h, Mode mode, int G) {
+    const int mi = mode == Mode::PlainF64 ? 0 : (mode == Mode::CorrF32 ? 1 : 2);
+    if (h->prepG[mi] == G) return h->prep[mi];
     GridArgs a;
     memset(&a, 0, sizeof(a));
     a.A = mode == Mode::PlainF64 ? (const void *)h->A64
@@ -127,6 +138,8 @@ GridArgs base_args(rebk_handle h, Mode mode, int G) {
     a.cdf_c = h->cdf_c;
     a.nr = h->nr;
     a.nc = h->nc;
+    a.coef_r = mode == Mode::PlainF64 ? (const void *)h->coef_r64 : (const void *)h->coef_r32;
+    a.coef_c = mode == Mode::PlainF64 ? (const void *)h->coef_c64 : (const void *)h->coef_c32;
     a.fb_r = h->fb[0];
     a.fb_c = h->fb[1];
     a.alpha = h->alpha;
@@ -140,6 +153,13 @@ GridArgs base_args(rebk_handle h, Mode mode, int G) {
     a.status = &h->ws->status;
     a.iters_done = &h->ws->iters_done;
     a.timeout_ns = kBarrierTimeoutNs;
+    a.use_tma = 0;
+    if (mode != Mode::PlainF64 && a.A != nullptr && tma_geometry(mode, a)) {
+        a.use_tma = 1;
+        if (grid_smem_bytes(mode, a) > kSmemLimit || tma_encode(mode, a) != cudaSuccess) a.use_tma = 0;
+    }
+    h->prep[mi] = a;
+    h->prepG[mi] = G;
     return a;
 }
 
@@ -173,9 +193,7 @@ rebk_status sample_into(rebk_handle h, GridArgs &a, int64_t k0, int64_t K, int32
 rebk_status run_grid(rebk_handle h, Mode mode, GridArgs a, int G, int *dev_status, int64_t *done,
                      cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
     const cudaStream_t st = h->stream;
-    a.nrow_cap = (int)((h->m + G - 1) / G) + 1;
-    const int64_t nu = (h->n + 7) / 8;
-    a.ncol_cap = (int)(8 * ((nu + G - 1) / G)) + 8;
+    (void)G;
     CK(cudaMemsetAsync(h->acc, 0, sizeof(double) * 3 * (size_t)h->acc_r * h->acc_w, st));
     CK(cudaMemsetAsync(h->ws, 0, sizeof(Workspace), st));
     if (!e0) {
@@ -203,7 +221,7 @@ int pick_ctas(rebk_handle h, Mode mode);
 rebk_status check_smem(rebk_handle h, Mode mode, int G) {
     GridArgs a = base_args(h, mode, G);
     const size_t smem = grid_smem_bytes(mode, a);
-    if (smem > 200 * 1024)
+    if (smem > kSmemLimit)
         return fail(REBK_EUNSUPPORTED, "problem too large for the persistent kernel's shared memory "
                                        "(owned slices of m + n per CTA)");
     return REBK_OK;
@@ -450,6 +468,10 @@ rebk_status rebk_create(rebk_handle *out, const double *A, int64_t m, int64_t n,
     CKH(cudaMemcpy(h->fb, h->d_fallback, sizeof(int) * 2, cudaMemcpyDeviceToHost));
     CKH(cudaMemcpy(&h->fro2, h->cdf_r + (h->s - 1), sizeof(double), cudaMemcpyDeviceToHost));
     CKH(cudaMalloc(&h->acc, sizeof(double) * 3 * (size_t)h->acc_r * h->acc_w));
+    CKH(cudaMalloc(&h->coef_r64, sizeof(double) * h->s));
+    CKH(cudaMalloc(&h->coef_c64, sizeof(double) * h->t));
+    CKH(cudaMalloc(&h->coef_r32, sizeof(float) * h->s));
+    CKH(cudaMalloc(&h->coef_c32, sizeof(float) * h->t));
     CKH(cudaMalloc(&h->ws, sizeof(Workspace)));
     CKH(cudaMalloc(&h->zbuf, sizeof(double) * m));
     CKH(cudaMalloc(&h->f, sizeof(double) * m));
@@ -473,6 +495,16 @@ rebk_status rebk_create(rebk_handle *out, const double *A, int64_t m, int64_t n,
         h->alpha = 1.75 / std::max(br, bc);
     } else {
         h->alpha = 1.0;
+    }
+    {
+        cudaError_t e1 = step_coefficients(h->nr, h->s, h->alpha, h->coef_r64, h->coef_r32, st);
+        cudaError_t e2 = step_coefficients(h->nc, h->t, h->alpha, h->coef_c64, h->coef_c32, st);
+        cudaError_t e3 = cudaStreamSynchronize(st);
+        if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+            rebk_status s = cuda_fail(e1 != cudaSuccess ? e1 : (e2 != cudaSuccess ? e2 : e3), "step coefficients");
+            free_handle(h);
+            return s;
+        }
     }
     *out = h;
     return REBK_OK;

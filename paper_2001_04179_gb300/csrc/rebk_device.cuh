@@ -74,6 +74,13 @@ template <> struct VecIO<double, double> {
         const double2 v = __ldg(reinterpret_cast<const double2 *>(p));
         o[0] = v.x; o[1] = v.y;
     }
+    __device__ __forceinline__ static void load_generic(const double *p, double (&o)[2]) {
+        const double2 v = *reinterpret_cast<const double2 *>(p);
+        o[0] = v.x; o[1] = v.y;
+    }
+    __device__ __forceinline__ static void load_shared(uint32_t a, double (&o)[2]) {
+        asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(o[0]), "=d"(o[1]) : "r"(a));
+    }
 };
 
 template <> struct VecIO<float, float> {
@@ -82,18 +89,37 @@ template <> struct VecIO<float, float> {
         const float4 v = __ldg(reinterpret_cast<const float4 *>(p));
         o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
     }
+    __device__ __forceinline__ static void load_generic(const float *p, float (&o)[4]) {
+        const float4 v = *reinterpret_cast<const float4 *>(p);
+        o[0] = v.x; o[1] = v.y; o[2] = v.z; o[3] = v.w;
+    }
+    __device__ __forceinline__ static void load_shared(uint32_t a, float (&o)[4]) {
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]) : "r"(a));
+    }
 };
 
 template <> struct VecIO<__nv_bfloat16, float> {
     static constexpr int V = 8;
-    __device__ __forceinline__ static void load(const __nv_bfloat16 *p, float (&o)[8]) {
-        const uint4 v = __ldg(reinterpret_cast<const uint4 *>(p));
+    __device__ __forceinline__ static void unpack(const uint4 v, float (&o)[8]) {
         const uint32_t w[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             o[2 * i] = __uint_as_float(w[i] << 16);
             o[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
         }
+    }
+    __device__ __forceinline__ static void load(const __nv_bfloat16 *p, float (&o)[8]) {
+        unpack(__ldg(reinterpret_cast<const uint4 *>(p)), o);
+    }
+    __device__ __forceinline__ static void load_generic(const __nv_bfloat16 *p, float (&o)[8]) {
+        unpack(*reinterpret_cast<const uint4 *>(p), o);
+    }
+    __device__ __forceinline__ static void load_shared(uint32_t a, float (&o)[8]) {
+        uint4 v;
+        asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+        unpack(v, o);
     }
 };
 
@@ -108,6 +134,8 @@ template <typename T> __device__ __forceinline__ T warp_sum(T v) {
 
 // Loads that bypass L1: data written by other CTAs during this launch.
 __device__ __forceinline__ double ld_cg(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ double ld_cg_t(const double *p) { return __ldcg(p); }
+__device__ __forceinline__ float ld_cg_t(const float *p) { return __ldcg(p); }
 
 // ---------------------------------------------------------------------------
 // L2 prefetch of a byte range (rounded out to 16-byte boundaries)

@@ -1,6 +1,7 @@
 // rebk_internal.h -- declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -12,7 +13,7 @@ namespace rebk {
 constexpr int kThreads = 512;              // threads per CTA of the persistent kernel
 constexpr int kWarps = kThreads / 32;
 constexpr int kRing = 8;                   // block indices kept ahead / behind
-constexpr int kAccReplicas = 8;            // replicated accumulators (atomic contention)
+constexpr int kAccReplicas = 4;            // replicated accumulators (atomic contention)
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s per wait
 constexpr int64_t kMaxItersPerLaunch = 8000000;                 // barrier counter headroom
 
@@ -24,10 +25,13 @@ constexpr int64_t kMaxItersPerLaunch = 8000000;                 // barrier count
 // the corrections dz, dx, beta = f = b - z - A x, gamma = g = A^T z, and the
 // duals s (length n) and v (length m) are accumulated (see rebk.h).
 struct GridArgs {
+    CUtensorMap tmap_c;     // TMA: column tiles (own rows x tau_c box)
+    CUtensorMap tmap_r;     // TMA: row tiles (tau_r x own columns box)
     const void *A;          // stored copy, row-major, leading dimension lda (zero padded)
     int64_t lda, m, n;
     int tau_r, tau_c, s, t; // block sizes and counts (Section 3 partition)
     const double *cdf_r, *cdf_c, *nr, *nc;
+    const void *coef_r, *coef_c;  // TS: alpha / ||block||_F^2 (0 for blocks of zero norm)
     int fb_r, fb_c;         // fallback picks (last block of nonzero norm)
     double alpha;
     uint64_t seed, stream;
@@ -42,9 +46,15 @@ struct GridArgs {
     int64_t check_every;    // test x^k when (check_offset + k) % check_every == 0
     int64_t check_offset;
     const int32_t *idx;     // 2 * iters entries: (j_k, i_k), from sample_blocks()
-    double *acc;            // [3][acc_r][acc_w] doubles, zeroed before launch
+    void *acc;              // TS [3][acc_r][acc_w], zeroed before launch
     int acc_w, acc_r;
     int nrow_cap, ncol_cap; // shared-memory capacity for the owned slices
+    int use_tma;            // tiles staged in shared memory by TMA
+    int tma_vx;             // elements per 16 bytes
+    int bw_c, bh_c, nbox_c; // column-tile box (width, height) and boxes per tile
+    int bw_r;               // row-tile box width (height tau_r)
+    int64_t tile_c_bytes, tile_r_bytes;        // shared-memory size of a tile (128-aligned)
+    int64_t tile_c_bytes_tx, tile_r_bytes_tx;  // bytes a tile's copies deliver
     unsigned int *bar;      // barrier counter, zeroed before launch
     int *status;            // zeroed before launch
     int64_t *iters_done;
@@ -55,14 +65,21 @@ enum class Mode { PlainF64, CorrF32, CorrBF16 };
 
 // Shared-memory layout of the persistent kernel (byte offsets, 16-byte aligned).
 struct SmemLayout {
-    size_t zeta, beta, v, xi, s, w, r, red, total;
+    size_t ringc, zeta, beta, v, xi, s, w, r, red, tc0, tc1, tr0, tr1, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int nrow_cap, int ncol_cap, int tau_r, int tau_c,
-                                                  bool corr, int ts, int vec) {
+                                                  bool corr, int ts, int vec, int64_t tile_c_bytes,
+                                                  int64_t tile_r_bytes) {
     auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
+    auto al128 = [](size_t x) { return (x + 127) & ~(size_t)127; };
     SmemLayout L;
-    size_t o = 128;  // block-index ring and flags
+    size_t o = 128;  // block-index ring, flags, two mbarriers
+    L.tc0 = o; o = al128(o + (size_t)tile_c_bytes);
+    L.tc1 = o; o = al128(o + (size_t)tile_c_bytes);
+    L.tr0 = o; o = al128(o + (size_t)tile_r_bytes);
+    L.tr1 = o; o = al128(o + (size_t)tile_r_bytes);
+    L.ringc = o; o = al(o + (size_t)2 * kRing * ts);  // step coefficients of the ring
     L.zeta = o; o = al(o + (size_t)nrow_cap * ts);
     L.beta = o; o = al(o + (size_t)nrow_cap * ts);
     L.v = o;    if (corr) o = al(o + (size_t)nrow_cap * ts);
@@ -92,6 +109,11 @@ inline void host_slices(int64_t m, int64_t n, int G, int c, int64_t *r0, int64_t
 }
 
 size_t grid_smem_bytes(Mode mode, const GridArgs &a);
+int storage_size(Mode mode);
+bool tma_geometry(Mode mode, GridArgs &a);
+cudaError_t tma_encode(Mode mode, GridArgs &a);
+cudaError_t step_coefficients(const double *norms, int nb, double alpha, double *c64, float *c32,
+                              cudaStream_t st);
 // idx[2(k-1)] = j_k, idx[2(k-1)+1] = i_k for k = 1..K (draws of iterations k0+1..k0+K).
 cudaError_t sample_blocks(uint64_t seed, uint64_t stream, int64_t k0, int64_t K, const double *cdf_r,
                           int s, const double *cdf_c, int t, int fb_r, int fb_c, int32_t *idx,

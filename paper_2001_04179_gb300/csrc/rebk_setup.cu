@@ -328,6 +328,16 @@ __global__ void apply_update_kernel(double *__restrict__ x, const double *__rest
     }
 }
 
+// c[b] = alpha / norm[b] (0 for blocks of zero norm, which are never sampled)
+__global__ void coef_kernel(const double *__restrict__ norms, int nb, double alpha, double *c64,
+                            float *c32) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nb; b += gridDim.x * blockDim.x) {
+        const double c = norms[b] > 0.0 ? alpha / norms[b] : 0.0;
+        c64[b] = c;
+        c32[b] = (float)c;
+    }
+}
+
 __global__ void fill_zero_f32_kernel(float *p, int64_t n) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x)
@@ -442,6 +452,13 @@ cudaError_t apply_update(double *x, const double *yn, int64_t n, double *z, cons
                          int64_t m, cudaStream_t st) {
     apply_update_kernel<<<grid_for(n + m, 256) > 2048 ? 2048 : grid_for(n + m, 256), 256, 0, st>>>(
         x, yn, n, z, ym, m);
+    return cudaGetLastError();
+}
+
+cudaError_t step_coefficients(const double *norms, int nb, double alpha, double *c64, float *c32,
+                              cudaStream_t st) {
+    coef_kernel<<<grid_for(nb, 256) > 1024 ? 1024 : grid_for(nb, 256), 256, 0, st>>>(norms, nb, alpha, c64,
+                                                                                     c32);
     return cudaGetLastError();
 }
 

@@ -122,27 +122,39 @@ def test_storage_copies_round_like_the_oracle():
     assert np.array_equal(bits.view(np.float32).astype(np.float64), O.round_bf16(p.A))
 
 
+PASS_SHAPES = [
+    # m, n, rank, tau_r, tau_c, num_ctas
+    (120, 90, 30, 8, 8, 0),        # library's CTA choice, shared-memory tiles
+    (600, 300, 80, 7, 13, 2),      # two TMA boxes per column tile, unaligned tile starts
+    (333, 517, 60, 16, 5, 5),      # ragged blocks, odd column block
+    (4000, 64, 20, 8, 32, 2),      # tiles too large for shared memory: global-load path
+]
+
+
 @pytest.mark.parametrize("storage,lo", [("fp32", O.round_fp32), ("bf16", O.round_bf16)])
-def test_one_refinement_pass_matches_oracle_pass(storage, lo):
+@pytest.mark.parametrize("shape", PASS_SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_one_refinement_pass_matches_oracle_pass(storage, lo, shape):
     """One outer pass (FP64 residuals, K inner iterations on corrections with
     the rounded matrix, FP64 update) against the oracle's pass on the same
     rounded values: the index sequence is identical and the iterate agrees to
     the FP32 arithmetic of the inner sweeps."""
-    p = product_problem(120, 90, 30, seed=4)
-    tr, tc = 8, 8
-    ro, co = contiguous_offsets(120, tr), contiguous_offsets(90, tc)
+    m, n, rank, tr, tc, G = shape
+    p = product_problem(m, n, rank, seed=4)
+    ro, co = contiguous_offsets(m, tr), contiguous_offsets(n, tc)
     alpha = 1.5 / max(O.beta_max(p.A, ro, co))
-    sol = Solver(p.A, tr, tc, alpha=alpha, storage=(storage,))
+    sol = Solver(p.A, tr, tc, alpha=alpha, storage=(storage,), num_ctas=G)
     K = 200
     out = sol.solve_refined(_t(p.b), tol=0.0, max_iter=K, seed=21, storage=storage, max_outer=1,
                             inner_iters=K, record=True, return_z=True)
     ref = O.refine(p.A, p.b, lo(p.A), ro, co, alpha, seed=21, inner_iters=K, outer_max=1)
     assert out["stats"]["iterations"] == K
-    idx_ref = O.rebk_correction(lo(p.A), *O.dual_residuals(p.A, p.b, p.b, np.zeros(90)), ro, co,
+    idx_ref = O.rebk_correction(lo(p.A), *O.dual_residuals(p.A, p.b, p.b, np.zeros(n)), ro, co,
                                 O.block_norms(p.A, ro, co), alpha, seed=21, iters=K, record=True)["idx"]
     assert np.array_equal(out["idx"].cpu().numpy(), idx_ref)
+    # FP32 inner arithmetic: errors of order 1e-6 of the corrections' scale
+    # (||x||, and ||b|| for z = b - A s, which cancels down to a small vector)
     assert _rel(out["x"].cpu().numpy(), ref["x"]) <= 1e-4
-    assert _rel(out["z"].cpu().numpy(), ref["z"]) <= 1e-4
+    assert np.linalg.norm(out["z"].cpu().numpy() - ref["z"]) <= 1e-4 * np.linalg.norm(p.b)
 
 
 @pytest.mark.parametrize("storage", ["fp32", "bf16"])
