@@ -187,6 +187,36 @@ rebk_status rebk_get_tables(rebk_handle h, double *nr, double *nc, double *cdf_r
  */
 rebk_status rebk_export_storage(rebk_handle h, int32_t storage, void *host_out);
 
+/*
+ * Plain FP64 REBK for a fixed number of iterations without allocating any
+ * memory.  The paper has no counterpart to this call; it exists for callers
+ * that must not call cudaMalloc -- code running while a CUDA graph is being
+ * captured, hosts that route every device allocation through their own
+ * allocator, serving loops that must not take the driver's allocation locks.
+ *
+ * A (device, m x n row-major, leading dimension lda), b (device, m) are
+ * inputs; x (device, n) and z (device, m) are outputs: x^iters and z^iters of
+ * Algorithm 1 from z^0 = b, x^0 = 0 with Philox key (seed, 0) -- the same
+ * iterates rebk_solve_ex gives with stream_id 0 and k0 0, up to the
+ * summation order of the device's reductions.  alpha > 0 is required (no
+ * beta_max estimate here).  stream is a cudaStream_t (NULL = legacy default).
+ * The call synchronises the stream before it returns.
+ *
+ * Working memory is one 32 MiB device array inside the library (every GPU that
+ * loads the library holds it until the process exits).  It must hold a
+ * zero-padded copy of A plus the tables: m * ceil(n/64)*64 * 8 bytes plus
+ * about 520 n + 48 (m/tau_row + n/tau_col) bytes; larger problems are
+ * rejected with REBK_EUNSUPPORTED before any GPU work.  The first call on a
+ * device looks up the array's device address (cudaGetSymbolAddress) while
+ * that device is current: make that first call before any stream capture.
+ * All calls share the array and each call overwrites and re-zeroes what it
+ * needs; calls whose GPU work overlaps (other streams, other host threads on
+ * the same device) race on it: serialise them.
+ */
+rebk_status rebk_solve_noalloc(const double *A, int64_t m, int64_t n, int64_t lda, int64_t tau_row,
+                               int64_t tau_col, double alpha, const double *b, double *x, double *z,
+                               int64_t iters, uint64_t seed, void *stream);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *rebk_last_error(void);
 

@@ -373,6 +373,10 @@ void fill_stats(rebk_handle h, rebk_stats *st, int64_t iters, int outer, rebk_st
 
 }  // namespace
 
+namespace rebk {
+void set_last_error(const std::string &msg) { g_last_error = msg; }
+}  // namespace rebk
+
 // ===========================================================================
 extern "C" {
 

@@ -148,4 +148,7 @@ cudaError_t apply_update(double *x, const double *yn, int64_t n, double *z, cons
                          int64_t m, cudaStream_t st);
 cudaError_t fill_zero_f32(float *p, int64_t n, cudaStream_t st);
 
+// Sets the message rebk_last_error() returns on this thread (rebk_api.cu).
+void set_last_error(const std::string &msg);
+
 }  // namespace rebk
