@@ -187,6 +187,79 @@ rebk_status rebk_get_tables(rebk_handle h, double *nr, double *nc, double *cdf_r
  */
 rebk_status rebk_export_storage(rebk_handle h, int32_t storage, void *host_out);
 
+/* ------------------------------------------------------------------------ */
+/* Batches of independent systems                                           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct rebk_batch_s *rebk_batch;
+
+typedef struct {
+    int32_t tau;          /* block size for rows and columns of every system (Section 3
+                             partitions), 1..256; 0 = autotune over {16, 32, 64, 128, 256}
+                             on a sample of the systems at the first solve              */
+    int32_t nrhs;         /* right-hand sides per system, 1..8 (all share one block
+                             sequence per system)                                       */
+    int32_t max_outer;    /* refinement passes at most; 0 = 6                           */
+    int32_t check_every;  /* inner iterations between error tests; 0 = 10               */
+    double inner_reduction; /* a pass ends once every RHS error is below this fraction
+                               of its value at the pass start; 0 = 1e-4                */
+    void *stream;         /* cudaStream_t for all work; NULL = legacy default stream    */
+} rebk_batch_options;
+
+typedef struct {
+    int32_t converged;     /* systems whose every RHS reached the tolerance            */
+    int32_t outer;         /* refinement passes run                                   */
+    int64_t iterations;    /* inner iterations summed over systems                    */
+    int64_t max_iterations;/* largest per-system inner iteration count                */
+    double device_ms;      /* device time of the solve (CUDA events)                  */
+    double inner_ms;       /* summed event time of the persistent batch launches      */
+    double sweep_ms;       /* summed event time of the FP64 sweeps                    */
+    int64_t launches;      /* kernels launched by the solve (graph nodes counted)     */
+    int32_t tau;           /* block size in use                                       */
+    int32_t graph;         /* 1 if the passes ran as one CUDA graph                   */
+} rebk_batch_stats;
+
+/*
+ * Creates a batch of `count` independent systems A_i x = b_i (Section 1 for
+ * each: any shape, rank or consistency).  m[i], n[i] (host arrays) are the
+ * shapes; A[i] (host array of pointers) points to row-major FP64 matrices with
+ * leading dimension n[i], in host memory (A_on_device == 0) or device memory.
+ * The library copies every matrix (FP64 for the refinement sweeps, FP32 for
+ * the inner iterations) and builds each system's block tables.  alpha (host
+ * array, may be NULL) gives each system's step size; NULL or a value <= 0 picks
+ * 1.75 / beta_max of that system (Section 3's empirical choice).
+ * Errors: EINVAL (count < 1, shapes, NULL pointers, options), ENOMEM, ECUDA.
+ */
+rebk_status rebk_batch_create(rebk_batch *out, int32_t count, const int64_t *m, const int64_t *n,
+                              const double *const *A, int A_on_device, const double *alpha,
+                              const rebk_batch_options *opt);
+
+void rebk_batch_destroy(rebk_batch h);
+
+/*
+ * Solves every system of the batch for its nrhs right-hand sides by mixed
+ * precision REBK (the correction form of rebk_solve_refined: FP32 inner
+ * iterations, FP64 refinement of (x, z)), one persistent launch per
+ * refinement pass in which each CTA takes systems from a queue.
+ * B: device, the systems' right-hand sides concatenated, system i occupying
+ *    m[i] rows of nrhs doubles (row-major m[i] x nrhs).
+ * X: device, output, concatenated n[i] x nrhs blocks.
+ * X_ref: device, n[i] x nrhs blocks of the known solutions A_i^+ b_i (the
+ *    paper's stop rule, Section 3); a system stops when every RHS has
+ *    ||x - x_ref|| <= tol ||x_ref||.  NULL: fixed passes (max_outer) of
+ *    inner_iters iterations each, no stopping test.
+ * max_iter bounds each system's inner iterations (systems that need more,
+ * e.g. nearly square Gaussian ones, end unconverged).  Random draws: Philox
+ * key (seed, system index), the same counter layout as rebk_solve.
+ * status_out (device or NULL): int32 per system, REBK_OK or REBK_MAX_ITER.
+ */
+rebk_status rebk_batch_solve(rebk_batch h, const double *B, double *X, const double *X_ref, double tol,
+                             int64_t max_iter, int64_t inner_iters, uint64_t seed, int32_t *status_out,
+                             rebk_batch_stats *stats);
+
+/* Block size in use and the number of systems (host outputs; either may be NULL). */
+rebk_status rebk_batch_info(rebk_batch h, int32_t *tau, int32_t *count);
+
 /*
  * Plain FP64 REBK for a fixed number of iterations without allocating any
  * memory.  The paper has no counterpart to this call; it exists for callers

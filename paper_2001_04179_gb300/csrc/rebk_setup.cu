@@ -245,7 +245,7 @@ __global__ void power_kernel(const double *__restrict__ gram, int tau, int64_t t
     for (int i = tid; i < h; i += blockDim.x) v[i] = 1.0 + 0.01 * (i % 7);
     __syncthreads();
     double lam_prev = 0.0, lam = 0.0;
-    for (int it = 0; it < 20000; ++it) {
+    for (int it = 0; it < 6000; ++it) {
         for (int i = tid; i < h; i += blockDim.x) {
             double s = 0.0;
             for (int j = 0; j < h; ++j) s = fma(G[(int64_t)i * tau + j], v[j], s);
@@ -275,7 +275,7 @@ __global__ void power_kernel(const double *__restrict__ gram, int tau, int64_t t
         const double inv = NN > 0.0 ? rsqrt(NN) : 0.0;
         for (int i = tid; i < h; i += blockDim.x) v[i] = gv[i] * inv;
         __syncthreads();
-        if (it > 50 && fabs(lam - lam_prev) <= 1e-14 * lam) break;
+        if (it > 30 && fabs(lam - lam_prev) <= 1e-13 * lam) break;
         lam_prev = lam;
     }
     if (tid == 0) beta[blk] = lam / fro2[blk];

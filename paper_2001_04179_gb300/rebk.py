@@ -49,6 +49,22 @@ class RebkRefineOpts(ctypes.Structure):
                 ("inner_iters", ctypes.c_int64), ("inner_reduction", ctypes.c_double)]
 
 
+class RebkBatchOptions(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("max_outer", ctypes.c_int32),
+                ("check_every", ctypes.c_int32), ("inner_reduction", ctypes.c_double),
+                ("stream", ctypes.c_void_p)]
+
+
+class RebkBatchStats(ctypes.Structure):
+    _fields_ = [("converged", ctypes.c_int32), ("outer", ctypes.c_int32), ("iterations", ctypes.c_int64),
+                ("max_iterations", ctypes.c_int64), ("device_ms", ctypes.c_double),
+                ("inner_ms", ctypes.c_double), ("sweep_ms", ctypes.c_double), ("launches", ctypes.c_int64),
+                ("tau", ctypes.c_int32), ("graph", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 _lock = threading.Lock()
 _lib: Optional[ctypes.CDLL] = None
 
@@ -69,6 +85,14 @@ _SIGNATURES = {
     "rebk_get_blocks": ([_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "rebk_get_tables": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "rebk_export_storage": ([_P, ctypes.c_int32, _P], ctypes.c_int),
+    "rebk_batch_create": ([ctypes.POINTER(_P), ctypes.c_int32, _P, _P, _P, ctypes.c_int, _P,
+                           ctypes.POINTER(RebkBatchOptions)], ctypes.c_int),
+    "rebk_batch_destroy": ([_P], None),
+    "rebk_batch_solve": ([_P, _P, _P, _P, ctypes.c_double, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
+                          _P, ctypes.POINTER(RebkBatchStats)], ctypes.c_int),
+    "rebk_batch_info": ([_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "rebk_solve_noalloc": ([_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
+                            ctypes.c_double, _P, _P, _P, ctypes.c_int64, ctypes.c_uint64, _P], ctypes.c_int),
     "rebk_last_error": ([], ctypes.c_char_p),
     "rebk_version": ([], ctypes.c_char_p),
 }
