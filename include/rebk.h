@@ -260,6 +260,61 @@ rebk_status rebk_batch_solve(rebk_batch h, const double *B, double *X, const dou
 /* Block size in use and the number of systems (host outputs; either may be NULL). */
 rebk_status rebk_batch_info(rebk_batch h, int32_t *tau, int32_t *count);
 
+/* ------------------------------------------------------------------------ */
+/* Learned warm start                                                        */
+/* ------------------------------------------------------------------------ */
+
+typedef struct rebk_mlp_s *rebk_mlp;
+
+/*
+ * Creates the warm-start network y = W3 relu(W2 relu(W1 b)) for right-hand
+ * sides b of length m (W1: hidden x m, W2: hidden x hidden, W3: m x hidden,
+ * row-major), tied to the m x n matrix A (FP64 row-major, leading dimension
+ * n, host or device memory; the library keeps a BF16 copy) through its loss
+ * mean ||A^T y - x_ls||^2.  The solve then starts from x^0 = A^T y (in
+ * range(A^T)) and z^0 = b - A x^0 (in b + range(A)): the hypotheses of
+ * Theorem main hold, so the limit is still A^+ b.  The paper has no learned
+ * start; this is our extension.
+ * init_weights: host array of three FP32 arrays, or NULL for He-initialised
+ * weights drawn from `seed`.  batch_capacity: largest batch of any call.
+ * Arithmetic: BF16 operands with FP32 accumulation (tensor cores), FP32
+ * master weights, Adam.  stream: cudaStream_t (NULL = legacy default).
+ */
+rebk_status rebk_mlp_create(rebk_mlp *out, const double *A, int64_t m, int64_t n, int A_on_device,
+                            int64_t hidden, int64_t batch_capacity, const float *const *init_weights,
+                            uint64_t seed, void *stream);
+void rebk_mlp_destroy(rebk_mlp h);
+
+/* Y (device, batch x m) = network applied to the rows of Bm (device, batch x m). */
+rebk_status rebk_mlp_forward(rebk_mlp h, const double *Bm, int64_t batch, double *Y);
+
+/*
+ * Gradients of loss = (1/batch) sum_b ||A^T y_b - x_ls,b||^2 for the rows of
+ * Bm (device, batch x m) and Xls (device, batch x n, the least-squares
+ * solutions, e.g. produced by the solver).  loss (host) may be NULL;
+ * grads_host (three host FP32 arrays, any NULL) receives dL/dW_l.
+ */
+rebk_status rebk_mlp_gradients(rebk_mlp h, const double *Bm, const double *Xls, int64_t batch, double *loss,
+                               float *const *grads_host);
+
+/* One Adam step (lr; beta1 0.9, beta2 0.999, eps 1e-8) on the same loss. */
+rebk_status rebk_mlp_train_step(rebk_mlp h, const double *Bm, const double *Xls, int64_t batch, double lr,
+                                double *loss);
+
+/* Copies the FP32 master weights to three host arrays (any NULL). */
+rebk_status rebk_mlp_get_weights(rebk_mlp h, float *const *weights_host);
+
+/* m (input / output length) and n (columns of A) of the network (host outputs). */
+rebk_status rebk_mlp_shape(rebk_mlp h, int64_t *m, int64_t *n);
+
+/*
+ * Warm start for rebk_solve_ex / rebk_solve_refined: y = net(b),
+ * x0 = A^T y and z0 = b - A x0 computed with the solver's FP64 copy of A.
+ * b: device, m; x0: device, n; z0: device, m (outputs).  Pass them as
+ * rebk_solve_ext.x0 / .z0.
+ */
+rebk_status rebk_warm_start(rebk_handle h, rebk_mlp net, const double *b, double *x0, double *z0);
+
 /*
  * Plain FP64 REBK for a fixed number of iterations without allocating any
  * memory.  The paper has no counterpart to this call; it exists for callers

@@ -713,6 +713,25 @@ rebk_status rebk_solve_ex(rebk_handle h, const double *b, double *x, double tol,
     return result;
 }
 
+rebk_status rebk_warm_start(rebk_handle h, rebk_mlp net, const double *b, double *x0, double *z0) {
+    g_last_error.clear();
+    if (!h || !net || !b || !x0 || !z0) return fail(REBK_EINVAL, "NULL argument");
+    int64_t nm = 0, nn = 0;
+    rebk_status s = rebk_mlp_shape(net, &nm, &nn);
+    if (s != REBK_OK) return s;
+    if (nm != h->m || nn != h->n) return fail(REBK_EINVAL, "network shape does not match the solver's A");
+    const cudaStream_t st = h->stream;
+    CK(cudaStreamSynchronize(st));
+    s = rebk_mlp_forward(net, b, 1, h->ym);  // y (length m) in the handle's scratch
+    if (s != REBK_OK) return s;
+    // x0 = A^T y and A x0 with the FP64 copy of A; z0 = b - A x0
+    CK(dual_sweep(h->A64, h->lda, h->m, h->n, nullptr, false, h->ym, false, nullptr, x0, st));
+    CK(dual_sweep(h->A64, h->lda, h->m, h->n, x0, false, nullptr, false, h->f, nullptr, st));
+    CK(vec_sub(b, h->f, z0, h->m, st));
+    CK(cudaStreamSynchronize(st));
+    return REBK_OK;
+}
+
 rebk_status rebk_solve(rebk_handle h, const double *b, double *x, double tol, int64_t max_iter,
                        uint64_t seed, rebk_stats *stats) {
     return rebk_solve_ex(h, b, x, tol, max_iter, seed, nullptr, stats);

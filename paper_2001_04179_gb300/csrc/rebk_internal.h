@@ -147,6 +147,8 @@ cudaError_t form_f(const double *b, const double *z, const double *ym, double *f
 cudaError_t apply_update(double *x, const double *yn, int64_t n, double *z, const double *ym,
                          int64_t m, cudaStream_t st);
 cudaError_t fill_zero_f32(float *p, int64_t n, cudaStream_t st);
+// out = a - b (length n)
+cudaError_t vec_sub(const double *a, const double *b, double *out, int64_t n, cudaStream_t st);
 
 // Sets the message rebk_last_error() returns on this thread (rebk_api.cu).
 void set_last_error(const std::string &msg);

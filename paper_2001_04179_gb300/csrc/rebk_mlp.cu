@@ -1,0 +1,464 @@
+// rebk_mlp.cu -- the learned warm start: a small network y = W3 relu(W2 relu(W1 b))
+// whose output gives the starting point x^0 = A^T y, z^0 = b - A x^0 of REBK.
+//
+// Theorem main of Du, Si, Sun (arXiv:2001.04179) needs x^0 in range(A^T) and
+// z^0 in b + range(A); x^0 = A^T y satisfies the first for any y and z^0 =
+// b - A x^0 the second, so the solve still converges to A^+ b while its error
+// bound starts from ||x^0 - A^+ b|| and ||z^0 - b_perp|| = ||A (A^+ b - x^0)||,
+// both small when the network is good.  The network is trained on
+// (b, A^+ b) pairs with the loss mean ||A^T y - A^+ b||^2.
+//
+// Arithmetic: BF16 operands, FP32 accumulation on the tensor cores
+// (mma.sync m16n8k16), FP32 master weights and Adam moments.  The network is a
+// tiny share of a warm-started solve, so one generic tiled GEMM with strided
+// operands serves every product of the forward and backward passes.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "rebk.h"
+#include "rebk_device.cuh"
+#include "rebk_internal.h"
+
+namespace rebk {
+namespace {
+
+constexpr int BM = 64, BN = 64, BK = 32, PAD = 8;
+
+// C[i, j] = alpha * sum_k A(i, k) B(k, j) (+ beta * C[i, j]), A(i, k) =
+// A[i * a_rs + k * a_cs], B(k, j) = B[k * b_rs + j * b_cs]; optional ReLU,
+// optional multiply by (mask[i, j] > 0), FP32 output (ldc) and BF16 copy (ldcb).
+struct GemmArgs {
+    int M, N, K;
+    const __nv_bfloat16 *A;
+    int64_t a_rs, a_cs;
+    const __nv_bfloat16 *B;
+    int64_t b_rs, b_cs;
+    float *C;
+    int64_t ldc;
+    __nv_bfloat16 *Cb;
+    int64_t ldcb;
+    float alpha, beta;
+    int relu;
+    const float *mask;
+    int64_t ldm;
+};
+
+__device__ __forceinline__ uint32_t pack2(const __nv_bfloat16 *p) {
+    return *reinterpret_cast<const uint32_t *>(p);
+}
+
+__global__ void __launch_bounds__(128) mlp_gemm_kernel(const GemmArgs g) {
+    __shared__ __align__(16) __nv_bfloat16 As[BM][BK + PAD];
+    __shared__ __align__(16) __nv_bfloat16 Bs[BN][BK + PAD];  // stored [n][k]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int bm = blockIdx.y * BM, bn = blockIdx.x * BN;
+    const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;  // warp tile 32 x 32
+    const int gid = lane >> 2, tig = lane & 3;
+    float acc[2][4][4];
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) acc[a][b][c] = 0.f;
+    const __nv_bfloat16 zero = __float2bfloat16(0.f);
+    for (int k0 = 0; k0 < g.K; k0 += BK) {
+        for (int e = tid; e < BM * BK; e += 128) {
+            const int i = e / BK, k = e % BK;
+            const int gi = bm + i, gk = k0 + k;
+            As[i][k] = (gi < g.M && gk < g.K) ? g.A[(int64_t)gi * g.a_rs + (int64_t)gk * g.a_cs] : zero;
+        }
+        for (int e = tid; e < BN * BK; e += 128) {
+            const int j = e / BK, k = e % BK;
+            const int gj = bn + j, gk = k0 + k;
+            Bs[j][k] = (gj < g.N && gk < g.K) ? g.B[(int64_t)gk * g.b_rs + (int64_t)gj * g.b_cs] : zero;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < BK; kk += 16) {
+            uint32_t af[2][4], bf[4][2];
+#pragma unroll
+            for (int a = 0; a < 2; ++a) {
+                const int r = wm + a * 16 + gid;
+                af[a][0] = pack2(&As[r][kk + tig * 2]);
+                af[a][1] = pack2(&As[r + 8][kk + tig * 2]);
+                af[a][2] = pack2(&As[r][kk + 8 + tig * 2]);
+                af[a][3] = pack2(&As[r + 8][kk + 8 + tig * 2]);
+            }
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const int c = wn + b * 8 + gid;
+                bf[b][0] = pack2(&Bs[c][kk + tig * 2]);
+                bf[b][1] = pack2(&Bs[c][kk + 8 + tig * 2]);
+            }
+#pragma unroll
+            for (int a = 0; a < 2; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    asm volatile(
+                        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+                        "{%8,%9}, {%0,%1,%2,%3};"
+                        : "+f"(acc[a][b][0]), "+f"(acc[a][b][1]), "+f"(acc[a][b][2]), "+f"(acc[a][b][3])
+                        : "r"(af[a][0]), "r"(af[a][1]), "r"(af[a][2]), "r"(af[a][3]), "r"(bf[b][0]),
+                          "r"(bf[b][1]));
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b)
+#pragma unroll
+            for (int h = 0; h < 4; ++h) {
+                const int i = bm + wm + a * 16 + gid + (h >= 2 ? 8 : 0);
+                const int j = bn + wn + b * 8 + tig * 2 + (h & 1);
+                if (i >= g.M || j >= g.N) continue;
+                float v = g.alpha * acc[a][b][h];
+                if (g.beta != 0.f) v += g.beta * g.C[(int64_t)i * g.ldc + j];
+                if (g.relu) v = fmaxf(v, 0.f);
+                if (g.mask && !(g.mask[(int64_t)i * g.ldm + j] > 0.f)) v = 0.f;
+                if (g.C) g.C[(int64_t)i * g.ldc + j] = v;
+                if (g.Cb) g.Cb[(int64_t)i * g.ldcb + j] = __float2bfloat16_rn(v);
+            }
+}
+
+__global__ void f64_to_bf16_kernel(const double *src, __nv_bfloat16 *dst, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = __float2bfloat16_rn(__double2float_rn(src[e]));
+}
+
+__global__ void f32_to_bf16_kernel(const float *src, __nv_bfloat16 *dst, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = __float2bfloat16_rn(src[e]);
+}
+
+__global__ void f32_to_f64_kernel(const float *src, double *dst, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = (double)src[e];
+}
+
+// R = P - X (FP32 P, FP64 X), BF16 copy; out[0] += sum R^2 (atomic).
+__global__ void residual_kernel(const float *P, const double *X, float *R, __nv_bfloat16 *Rb, int64_t n,
+                                double *loss) {
+    double s = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const float r = (float)((double)P[e] - X[e]);
+        R[e] = r;
+        Rb[e] = __float2bfloat16_rn(r);
+        s += (double)r * r;
+    }
+    s = warp_sum(s);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, s);
+}
+
+// Adam on FP32 master weights; refreshes the BF16 copy.
+__global__ void adam_kernel(float *w, const float *grad, float *m1, float *m2, __nv_bfloat16 *wb, int64_t n,
+                            float lr, float b1, float b2, float eps, float c1, float c2) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        const float gv = grad[e];
+        const float a = b1 * m1[e] + (1.f - b1) * gv, b = b2 * m2[e] + (1.f - b2) * gv * gv;
+        m1[e] = a;
+        m2[e] = b;
+        const float v = w[e] - lr * (a / c1) / (sqrtf(b / c2) + eps);
+        w[e] = v;
+        wb[e] = __float2bfloat16_rn(v);
+    }
+}
+
+int eblocks(int64_t n) {
+    int64_t b = (n + 255) / 256;
+    return (int)(b < 1 ? 1 : (b > 4096 ? 4096 : b));
+}
+
+cudaError_t gemm(const GemmArgs &g, cudaStream_t st) {
+    dim3 grid((g.N + BN - 1) / BN, (g.M + BM - 1) / BM);
+    mlp_gemm_kernel<<<grid, 128, 0, st>>>(g);
+    return cudaGetLastError();
+}
+
+GemmArgs gemm_args(int M, int N, int K, const __nv_bfloat16 *A, int64_t a_rs, int64_t a_cs,
+                   const __nv_bfloat16 *B, int64_t b_rs, int64_t b_cs, float *C, int64_t ldc,
+                   __nv_bfloat16 *Cb, int64_t ldcb) {
+    GemmArgs g;
+    memset(&g, 0, sizeof(g));
+    g.M = M; g.N = N; g.K = K;
+    g.A = A; g.a_rs = a_rs; g.a_cs = a_cs;
+    g.B = B; g.b_rs = b_rs; g.b_cs = b_cs;
+    g.C = C; g.ldc = ldc; g.Cb = Cb; g.ldcb = ldcb;
+    g.alpha = 1.f;
+    return g;
+}
+
+}  // namespace
+}  // namespace rebk
+
+using namespace rebk;
+
+struct rebk_mlp_s {
+    cudaStream_t stream = nullptr;
+    int64_t m = 0, n = 0, hidden = 0, cap = 0;  // input / output size m, A columns n, batch capacity
+    // weights: W1 (hidden x m), W2 (hidden x hidden), W3 (m x hidden)
+    float *w[3] = {nullptr, nullptr, nullptr}, *g[3] = {nullptr, nullptr, nullptr};
+    float *m1[3] = {nullptr, nullptr, nullptr}, *m2[3] = {nullptr, nullptr, nullptr};
+    __nv_bfloat16 *wb[3] = {nullptr, nullptr, nullptr};
+    int64_t wsize[3] = {0, 0, 0};
+    __nv_bfloat16 *Ab = nullptr;  // BF16 copy of A (m x n, row-major, ld n)
+    // activations (cap rows)
+    __nv_bfloat16 *Xb = nullptr, *H1b = nullptr, *H2b = nullptr, *Yb = nullptr, *Rb = nullptr, *dYb = nullptr,
+                  *dH2b = nullptr, *dH1b = nullptr;
+    float *H1 = nullptr, *H2 = nullptr, *Y = nullptr, *P = nullptr, *R = nullptr, *dY = nullptr, *dH2 = nullptr,
+          *dH1 = nullptr;
+    double *loss = nullptr;
+    int64_t step = 0;
+};
+
+namespace {
+
+rebk_status mfail(rebk_status s, const std::string &msg) {
+    set_last_error(msg);
+    return s;
+}
+
+#define MCK(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e__ = (call);                                                                  \
+        if (e__ != cudaSuccess) return mfail(e__ == cudaErrorMemoryAllocation ? REBK_ENOMEM : REBK_ECUDA, \
+                                             std::string(#call) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+
+void free_mlp(rebk_mlp h) {
+    if (!h) return;
+    for (int l = 0; l < 3; ++l) {
+        void *p[] = {h->w[l], h->g[l], h->m1[l], h->m2[l], h->wb[l]};
+        for (void *q : p)
+            if (q) cudaFree(q);
+    }
+    void *p[] = {h->Ab, h->Xb, h->H1b, h->H2b, h->Yb, h->Rb, h->dYb, h->dH2b, h->dH1b, h->H1, h->H2, h->Y,
+                 h->P, h->R, h->dY, h->dH2, h->dH1, h->loss};
+    for (void *q : p)
+        if (q) cudaFree(q);
+    delete h;
+}
+
+// Forward pass for `batch` inputs (rows of Xb): H1, H2 (FP32 + BF16), Y (FP32 + BF16).
+rebk_status forward(rebk_mlp h, int64_t batch) {
+    const cudaStream_t st = h->stream;
+    const int64_t m = h->m, H = h->hidden;
+    GemmArgs g = gemm_args((int)batch, (int)H, (int)m, h->Xb, m, 1, h->wb[0], 1, m, h->H1, H, h->H1b, H);
+    g.relu = 1;
+    MCK(gemm(g, st));
+    g = gemm_args((int)batch, (int)H, (int)H, h->H1b, H, 1, h->wb[1], 1, H, h->H2, H, h->H2b, H);
+    g.relu = 1;
+    MCK(gemm(g, st));
+    g = gemm_args((int)batch, (int)m, (int)H, h->H2b, H, 1, h->wb[2], 1, H, h->Y, m, h->Yb, m);
+    MCK(gemm(g, st));
+    return REBK_OK;
+}
+
+rebk_status check_batch(rebk_mlp h, int64_t batch) {
+    if (batch < 1 || batch > h->cap) return mfail(REBK_EINVAL, "batch must be 1..capacity");
+    return REBK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rebk_status rebk_mlp_create(rebk_mlp *out, const double *A, int64_t m, int64_t n, int A_on_device,
+                            int64_t hidden, int64_t batch_capacity, const float *const *init_weights,
+                            uint64_t seed, void *stream) {
+    set_last_error("");
+    if (!out) return mfail(REBK_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (!A || m < 1 || n < 1 || hidden < 1 || batch_capacity < 1)
+        return mfail(REBK_EINVAL, "A, m, n, hidden, batch_capacity required");
+    rebk_mlp h = new rebk_mlp_s();
+    h->stream = static_cast<cudaStream_t>(stream);
+    h->m = m;
+    h->n = n;
+    h->hidden = hidden;
+    h->cap = batch_capacity;
+    h->wsize[0] = hidden * m;
+    h->wsize[1] = hidden * hidden;
+    h->wsize[2] = m * hidden;
+    const cudaStream_t st = h->stream;
+    auto fin = [&](rebk_status s) {
+        if (s != REBK_OK) free_mlp(h);
+        return s;
+    };
+#define MCKH(call)                                                                                 \
+    do {                                                                                           \
+        cudaError_t e__ = (call);                                                                  \
+        if (e__ != cudaSuccess)                                                                    \
+            return fin(mfail(e__ == cudaErrorMemoryAllocation ? REBK_ENOMEM : REBK_ECUDA,          \
+                             std::string(#call) + ": " + cudaGetErrorString(e__)));                \
+    } while (0)
+    const int64_t fan_in[3] = {m, hidden, hidden};
+    for (int l = 0; l < 3; ++l) {
+        const int64_t sz = h->wsize[l];
+        MCKH(cudaMalloc(&h->w[l], sizeof(float) * sz));
+        MCKH(cudaMalloc(&h->g[l], sizeof(float) * sz));
+        MCKH(cudaMalloc(&h->m1[l], sizeof(float) * sz));
+        MCKH(cudaMalloc(&h->m2[l], sizeof(float) * sz));
+        MCKH(cudaMalloc(&h->wb[l], sizeof(__nv_bfloat16) * sz));
+        MCKH(cudaMemsetAsync(h->m1[l], 0, sizeof(float) * sz, st));
+        MCKH(cudaMemsetAsync(h->m2[l], 0, sizeof(float) * sz, st));
+        if (init_weights && init_weights[l]) {
+            MCKH(cudaMemcpyAsync(h->w[l], init_weights[l], sizeof(float) * sz, cudaMemcpyHostToDevice, st));
+        } else {
+            // He initialisation N(0, 2 / fan_in), drawn on the host from a fixed seed
+            std::vector<float> hw(sz);
+            uint64_t sstate = seed * 0x9E3779B97F4A7C15ull + (uint64_t)l + 1;
+            auto next = [&]() {  // splitmix64
+                uint64_t z = (sstate += 0x9E3779B97F4A7C15ull);
+                z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+                z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+                return z ^ (z >> 31);
+            };
+            const double sd = std::sqrt(2.0 / (double)fan_in[l]);
+            for (int64_t e = 0; e < sz; e += 2) {
+                const double u1 = ((next() >> 11) + 1.0) * 0x1.0p-53, u2 = (next() >> 11) * 0x1.0p-53;
+                const double r = std::sqrt(-2.0 * std::log(u1));
+                hw[e] = (float)(sd * r * std::cos(2 * M_PI * u2));
+                if (e + 1 < sz) hw[e + 1] = (float)(sd * r * std::sin(2 * M_PI * u2));
+            }
+            MCKH(cudaMemcpyAsync(h->w[l], hw.data(), sizeof(float) * sz, cudaMemcpyHostToDevice, st));
+            MCKH(cudaStreamSynchronize(st));
+        }
+        f32_to_bf16_kernel<<<eblocks(sz), 256, 0, st>>>(h->w[l], h->wb[l], sz);
+        MCKH(cudaGetLastError());
+    }
+    // BF16 copy of A (m x n) for the loss-gradient products
+    double *Ad = nullptr;
+    if (!A_on_device) {
+        MCKH(cudaMalloc(&Ad, sizeof(double) * m * n));
+        MCKH(cudaMemcpyAsync(Ad, A, sizeof(double) * m * n, cudaMemcpyHostToDevice, st));
+    }
+    MCKH(cudaMalloc(&h->Ab, sizeof(__nv_bfloat16) * m * n));
+    f64_to_bf16_kernel<<<eblocks(m * n), 256, 0, st>>>(A_on_device ? A : Ad, h->Ab, m * n);
+    MCKH(cudaGetLastError());
+    MCKH(cudaStreamSynchronize(st));
+    if (Ad) cudaFree(Ad);
+    const int64_t C = batch_capacity;
+    MCKH(cudaMalloc(&h->Xb, sizeof(__nv_bfloat16) * C * m));
+    MCKH(cudaMalloc(&h->H1b, sizeof(__nv_bfloat16) * C * hidden));
+    MCKH(cudaMalloc(&h->H2b, sizeof(__nv_bfloat16) * C * hidden));
+    MCKH(cudaMalloc(&h->Yb, sizeof(__nv_bfloat16) * C * m));
+    MCKH(cudaMalloc(&h->Rb, sizeof(__nv_bfloat16) * C * n));
+    MCKH(cudaMalloc(&h->dYb, sizeof(__nv_bfloat16) * C * m));
+    MCKH(cudaMalloc(&h->dH2b, sizeof(__nv_bfloat16) * C * hidden));
+    MCKH(cudaMalloc(&h->dH1b, sizeof(__nv_bfloat16) * C * hidden));
+    MCKH(cudaMalloc(&h->H1, sizeof(float) * C * hidden));
+    MCKH(cudaMalloc(&h->H2, sizeof(float) * C * hidden));
+    MCKH(cudaMalloc(&h->Y, sizeof(float) * C * m));
+    MCKH(cudaMalloc(&h->P, sizeof(float) * C * n));
+    MCKH(cudaMalloc(&h->R, sizeof(float) * C * n));
+    MCKH(cudaMalloc(&h->dY, sizeof(float) * C * m));
+    MCKH(cudaMalloc(&h->dH2, sizeof(float) * C * hidden));
+    MCKH(cudaMalloc(&h->dH1, sizeof(float) * C * hidden));
+    MCKH(cudaMalloc(&h->loss, sizeof(double)));
+#undef MCKH
+    *out = h;
+    return REBK_OK;
+}
+
+void rebk_mlp_destroy(rebk_mlp h) { free_mlp(h); }
+
+rebk_status rebk_mlp_forward(rebk_mlp h, const double *Bm, int64_t batch, double *Y) {
+    if (!h || !Bm || !Y) return mfail(REBK_EINVAL, "NULL argument");
+    rebk_status s = check_batch(h, batch);
+    if (s != REBK_OK) return s;
+    const cudaStream_t st = h->stream;
+    f64_to_bf16_kernel<<<eblocks(batch * h->m), 256, 0, st>>>(Bm, h->Xb, batch * h->m);
+    MCK(cudaGetLastError());
+    s = forward(h, batch);
+    if (s != REBK_OK) return s;
+    f32_to_f64_kernel<<<eblocks(batch * h->m), 256, 0, st>>>(h->Y, Y, batch * h->m);
+    MCK(cudaGetLastError());
+    MCK(cudaStreamSynchronize(st));
+    return REBK_OK;
+}
+
+rebk_status rebk_mlp_gradients(rebk_mlp h, const double *Bm, const double *Xls, int64_t batch, double *loss,
+                               float *const *grads_host) {
+    if (!h || !Bm || !Xls) return mfail(REBK_EINVAL, "NULL argument");
+    rebk_status s = check_batch(h, batch);
+    if (s != REBK_OK) return s;
+    const cudaStream_t st = h->stream;
+    const int64_t m = h->m, n = h->n, H = h->hidden;
+    f64_to_bf16_kernel<<<eblocks(batch * m), 256, 0, st>>>(Bm, h->Xb, batch * m);
+    MCK(cudaGetLastError());
+    s = forward(h, batch);
+    if (s != REBK_OK) return s;
+    // P = Y A (batch x n): A^T y for every sample; R = P - X_ls
+    MCK(gemm(gemm_args((int)batch, (int)n, (int)m, h->Yb, m, 1, h->Ab, n, 1, h->P, n, nullptr, 0), st));
+    MCK(cudaMemsetAsync(h->loss, 0, sizeof(double), st));
+    residual_kernel<<<eblocks(batch * n), 256, 0, st>>>(h->P, Xls, h->R, h->Rb, batch * n, h->loss);
+    MCK(cudaGetLastError());
+    // dY = (2 / batch) R A^T (batch x m)
+    GemmArgs g = gemm_args((int)batch, (int)m, (int)n, h->Rb, n, 1, h->Ab, 1, n, h->dY, m, h->dYb, m);
+    g.alpha = 2.f / (float)batch;
+    MCK(gemm(g, st));
+    // dW3 = dY^T H2 (m x H)
+    MCK(gemm(gemm_args((int)m, (int)H, (int)batch, h->dYb, 1, m, h->H2b, H, 1, h->g[2], H, nullptr, 0), st));
+    // dH2 = (dY W3) * [H2 > 0]
+    g = gemm_args((int)batch, (int)H, (int)m, h->dYb, m, 1, h->wb[2], H, 1, h->dH2, H, h->dH2b, H);
+    g.mask = h->H2;
+    g.ldm = H;
+    MCK(gemm(g, st));
+    // dW2 = dH2^T H1 (H x H)
+    MCK(gemm(gemm_args((int)H, (int)H, (int)batch, h->dH2b, 1, H, h->H1b, H, 1, h->g[1], H, nullptr, 0), st));
+    // dH1 = (dH2 W2) * [H1 > 0]
+    g = gemm_args((int)batch, (int)H, (int)H, h->dH2b, H, 1, h->wb[1], H, 1, h->dH1, H, h->dH1b, H);
+    g.mask = h->H1;
+    g.ldm = H;
+    MCK(gemm(g, st));
+    // dW1 = dH1^T X (H x m)
+    MCK(gemm(gemm_args((int)H, (int)m, (int)batch, h->dH1b, 1, H, h->Xb, m, 1, h->g[0], m, nullptr, 0), st));
+    double lsum = 0.0;
+    MCK(cudaMemcpyAsync(&lsum, h->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+    MCK(cudaStreamSynchronize(st));
+    if (loss) *loss = lsum / (double)batch;
+    if (grads_host)
+        for (int l = 0; l < 3; ++l)
+            if (grads_host[l]) MCK(cudaMemcpy(grads_host[l], h->g[l], sizeof(float) * h->wsize[l], cudaMemcpyDeviceToHost));
+    return REBK_OK;
+}
+
+rebk_status rebk_mlp_train_step(rebk_mlp h, const double *Bm, const double *Xls, int64_t batch, double lr,
+                                double *loss) {
+    rebk_status s = rebk_mlp_gradients(h, Bm, Xls, batch, loss, nullptr);
+    if (s != REBK_OK) return s;
+    const cudaStream_t st = h->stream;
+    ++h->step;
+    const float b1 = 0.9f, b2 = 0.999f;
+    const float c1 = 1.f - std::pow(b1, (float)h->step), c2 = 1.f - std::pow(b2, (float)h->step);
+    for (int l = 0; l < 3; ++l)
+        adam_kernel<<<eblocks(h->wsize[l]), 256, 0, st>>>(h->w[l], h->g[l], h->m1[l], h->m2[l], h->wb[l],
+                                                          h->wsize[l], (float)lr, b1, b2, 1e-8f, c1, c2);
+    MCK(cudaGetLastError());
+    MCK(cudaStreamSynchronize(st));
+    return REBK_OK;
+}
+
+rebk_status rebk_mlp_shape(rebk_mlp h, int64_t *m, int64_t *n) {
+    if (!h) return mfail(REBK_EINVAL, "NULL network");
+    if (m) *m = h->m;
+    if (n) *n = h->n;
+    return REBK_OK;
+}
+
+rebk_status rebk_mlp_get_weights(rebk_mlp h, float *const *weights_host) {
+    if (!h || !weights_host) return mfail(REBK_EINVAL, "NULL argument");
+    for (int l = 0; l < 3; ++l)
+        if (weights_host[l]) MCK(cudaMemcpy(weights_host[l], h->w[l], sizeof(float) * h->wsize[l], cudaMemcpyDeviceToHost));
+    return REBK_OK;
+}
+
+}  // extern "C"

@@ -338,6 +338,11 @@ __global__ void coef_kernel(const double *__restrict__ norms, int nb, double alp
     }
 }
 
+__global__ void vec_sub_kernel(const double *a, const double *b, double *out, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = a[e] - b[e];
+}
+
 __global__ void fill_zero_f32_kernel(float *p, int64_t n) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x)
@@ -459,6 +464,11 @@ cudaError_t step_coefficients(const double *norms, int nb, double alpha, double 
                               cudaStream_t st) {
     coef_kernel<<<grid_for(nb, 256) > 1024 ? 1024 : grid_for(nb, 256), 256, 0, st>>>(norms, nb, alpha, c64,
                                                                                      c32);
+    return cudaGetLastError();
+}
+
+cudaError_t vec_sub(const double *a, const double *b, double *out, int64_t n, cudaStream_t st) {
+    vec_sub_kernel<<<grid_for(n, 256) > 2048 ? 2048 : grid_for(n, 256), 256, 0, st>>>(a, b, out, n);
     return cudaGetLastError();
 }
 

@@ -93,6 +93,16 @@ _SIGNATURES = {
     "rebk_batch_info": ([_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "rebk_solve_noalloc": ([_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                             ctypes.c_double, _P, _P, _P, ctypes.c_int64, ctypes.c_uint64, _P], ctypes.c_int),
+    "rebk_mlp_create": ([ctypes.POINTER(_P), _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,
+                         ctypes.c_int64, _P, ctypes.c_uint64, _P], ctypes.c_int),
+    "rebk_mlp_destroy": ([_P], None),
+    "rebk_mlp_forward": ([_P, _P, ctypes.c_int64, _P], ctypes.c_int),
+    "rebk_mlp_gradients": ([_P, _P, _P, ctypes.c_int64, ctypes.POINTER(ctypes.c_double), _P], ctypes.c_int),
+    "rebk_mlp_train_step": ([_P, _P, _P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
+                            ctypes.c_int),
+    "rebk_mlp_get_weights": ([_P, _P], ctypes.c_int),
+    "rebk_mlp_shape": ([_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
+    "rebk_warm_start": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "rebk_last_error": ([], ctypes.c_char_p),
     "rebk_version": ([], ctypes.c_char_p),
 }

@@ -235,3 +235,76 @@ class BatchSolver:
                                         ctypes.c_void_p(status.data_ptr()), ctypes.byref(stats))
         _r.check(st)
         return {"x": X, "status": status.cpu().numpy(), "stats": stats.as_dict()}
+
+
+class WarmStartNet:
+    """The learned warm start y = W3 relu(W2 relu(W1 b)) for a fixed A (m x n):
+    x0 = A^T y and z0 = b - A x0 start the solve (see rebk.h)."""
+
+    def __init__(self, A, hidden: int = 512, batch_capacity: int = 256, init_weights=None, seed: int = 0,
+                 stream=None):
+        lib = _r.load()
+        An = np.ascontiguousarray(A, dtype=np.float64)
+        self.m, self.n = An.shape
+        self.hidden = hidden
+        self.shapes = [(hidden, self.m), (hidden, hidden), (self.m, hidden)]
+        arr = None
+        if init_weights is not None:
+            self._init = [np.ascontiguousarray(w, dtype=np.float32) for w in init_weights]
+            arr = (ctypes.c_void_p * 3)(*[w.ctypes.data for w in self._init])
+        h = ctypes.c_void_p()
+        st = lib.rebk_mlp_create(ctypes.byref(h), An.ctypes.data_as(ctypes.c_void_p), self.m, self.n, 0, hidden,
+                                 batch_capacity, None if arr is None else ctypes.cast(arr, ctypes.c_void_p),
+                                 seed, None if stream is None else ctypes.c_void_p(stream.cuda_stream))
+        _r.check(st)
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _r.load().rebk_mlp_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def forward(self, Bm):
+        """Bm: CUDA float64 (batch x m).  Returns Y (batch x m)."""
+        torch = _torch()
+        Y = torch.empty_like(Bm)
+        _r.check(_r.load().rebk_mlp_forward(self._h, ctypes.c_void_p(Bm.data_ptr()), Bm.shape[0],
+                                            ctypes.c_void_p(Y.data_ptr())))
+        return Y
+
+    def gradients(self, Bm, Xls):
+        grads = [np.zeros(s, dtype=np.float32) for s in self.shapes]
+        arr = (ctypes.c_void_p * 3)(*[g.ctypes.data for g in grads])
+        loss = ctypes.c_double()
+        _r.check(_r.load().rebk_mlp_gradients(self._h, ctypes.c_void_p(Bm.data_ptr()),
+                                              ctypes.c_void_p(Xls.data_ptr()), Bm.shape[0], ctypes.byref(loss),
+                                              ctypes.cast(arr, ctypes.c_void_p)))
+        return loss.value, grads
+
+    def train_step(self, Bm, Xls, lr: float = 1e-3) -> float:
+        loss = ctypes.c_double()
+        _r.check(_r.load().rebk_mlp_train_step(self._h, ctypes.c_void_p(Bm.data_ptr()),
+                                               ctypes.c_void_p(Xls.data_ptr()), Bm.shape[0], float(lr),
+                                               ctypes.byref(loss)))
+        return loss.value
+
+    def weights(self):
+        ws = [np.zeros(s, dtype=np.float32) for s in self.shapes]
+        arr = (ctypes.c_void_p * 3)(*[w.ctypes.data for w in ws])
+        _r.check(_r.load().rebk_mlp_get_weights(self._h, ctypes.cast(arr, ctypes.c_void_p)))
+        return ws
+
+    def warm_start(self, solver: "Solver", b):
+        """(x0, z0) for solver.solve / solve_refined."""
+        torch = _torch()
+        x0 = torch.empty(solver.n, dtype=torch.float64, device=b.device)
+        z0 = torch.empty(solver.m, dtype=torch.float64, device=b.device)
+        _r.check(_r.load().rebk_warm_start(solver._h, self._h, ctypes.c_void_p(b.data_ptr()),
+                                           ctypes.c_void_p(x0.data_ptr()), ctypes.c_void_p(z0.data_ptr())))
+        return x0, z0
