@@ -51,6 +51,7 @@ int64_t round_up(int64_t v, int64_t q) { return (v + q - 1) / q * q; }
 
 struct Workspace {
     unsigned int bar;
+    unsigned int bar_x;
     int status;
     int64_t iters_done;
     double small[8];
@@ -70,7 +71,7 @@ struct rebk_handle_s {
     __nv_bfloat16 *A16 = nullptr;
     double *nr = nullptr, *nc = nullptr, *cdf_r = nullptr, *cdf_c = nullptr;
     int *d_fallback = nullptr;
-    void *acc = nullptr;  // 3 sets x acc_r replicas x acc_w, 8 bytes per entry
+    void *acc = nullptr;  // 2 chains x 3 sets x acc_r replicas x acc_w, 8 bytes per entry
     int acc_w = 0, acc_r = kAccReplicas;
     double *coef_r64 = nullptr, *coef_c64 = nullptr;
     float *coef_r32 = nullptr, *coef_c32 = nullptr;
@@ -150,6 +151,7 @@ GridArgs base_args(rebk_handle h, Mode mode, int G) {
     const int64_t nu = (h->n + 7) / 8;
     a.ncol_cap = (int)(8 * ((nu + G - 1) / G)) + 8;
     a.bar = &h->ws->bar;
+    a.bar_x = &h->ws->bar_x;
     a.status = &h->ws->status;
     a.iters_done = &h->ws->iters_done;
     a.timeout_ns = kBarrierTimeoutNs;
@@ -194,7 +196,7 @@ rebk_status run_grid(rebk_handle h, Mode mode, GridArgs a, int G, int *dev_statu
                      cudaEvent_t e0 = nullptr, cudaEvent_t e1 = nullptr) {
     const cudaStream_t st = h->stream;
     (void)G;
-    CK(cudaMemsetAsync(h->acc, 0, sizeof(double) * 3 * (size_t)h->acc_r * h->acc_w, st));
+    CK(cudaMemsetAsync(h->acc, 0, sizeof(double) * 6 * (size_t)h->acc_r * h->acc_w, st));
     CK(cudaMemsetAsync(h->ws, 0, sizeof(Workspace), st));
     if (!e0) {
         e0 = h->kev0;
@@ -421,7 +423,7 @@ rebk_status rebk_create(rebk_handle *out, const double *A, int64_t m, int64_t n,
     h->t = (int)((n + h->tau_c - 1) / h->tau_c);
     h->check_every = o.check_every;
     h->num_ctas_opt = o.num_ctas;
-    h->acc_w = (int)round_up(h->tau_c + h->tau_r + 1, 32);
+    h->acc_w = (int)round_up(std::max(h->tau_c, h->tau_r + 1), 32);
     const cudaStream_t st = h->stream;
 
 #define CKH(call)                                                                                  \
@@ -471,7 +473,7 @@ rebk_status rebk_create(rebk_handle *out, const double *A, int64_t m, int64_t n,
     }
     CKH(cudaMemcpy(h->fb, h->d_fallback, sizeof(int) * 2, cudaMemcpyDeviceToHost));
     CKH(cudaMemcpy(&h->fro2, h->cdf_r + (h->s - 1), sizeof(double), cudaMemcpyDeviceToHost));
-    CKH(cudaMalloc(&h->acc, sizeof(double) * 3 * (size_t)h->acc_r * h->acc_w));
+    CKH(cudaMalloc(&h->acc, sizeof(double) * 6 * (size_t)h->acc_r * h->acc_w));
     CKH(cudaMalloc(&h->coef_r64, sizeof(double) * h->s));
     CKH(cudaMalloc(&h->coef_c64, sizeof(double) * h->t));
     CKH(cudaMalloc(&h->coef_r32, sizeof(float) * h->s));

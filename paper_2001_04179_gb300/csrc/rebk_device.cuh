@@ -167,6 +167,40 @@ __device__ __forceinline__ void red_release_gpu_add(unsigned int *p, unsigned in
     asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
+// Split-phase device barrier.  grid_arrive: after the CTA's writes of a
+// phase (all threads call it; thread 0 releases them at gpu scope).
+__device__ __forceinline__ void grid_arrive(unsigned int *counter) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        red_release_gpu_add(counter, 1u);
+    }
+}
+
+// grid_wait: until *counter >= target (all threads call it); false for every
+// thread of the CTA if the wait ran past timeout_ns (status set to TIMEOUT).
+__device__ __forceinline__ bool grid_wait(unsigned int *counter, unsigned int target, int *status,
+                                          unsigned long long timeout_ns, int *s_flag) {
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        if (ld_acquire_gpu(counter) < target) {
+            const unsigned long long t0 = globaltimer_ns();
+            unsigned int spins = 0;
+            while (ld_acquire_gpu(counter) < target) {
+                if ((++spins & 255u) == 0u && globaltimer_ns() - t0 > timeout_ns) {
+                    ok = 0;
+                    atomicExch(status, 6 /* REBK_BARRIER_TIMEOUT */);
+                    break;
+                }
+            }
+        }
+        __threadfence();
+        *s_flag = ok;
+    }
+    __syncthreads();
+    return *s_flag != 0;
+}
+
 // All CTAs of the launch call this with the same target = gridDim.x * (phase + 1).
 // Returns false (for every thread of the CTA) if the wait ran past timeout_ns;
 // the CTA then records the timeout in *status and must leave the kernel.

@@ -10,28 +10,34 @@
 // partial sums plus one cross-CTA reduction of a tau-vector (w or r), while
 // the updates of z and x stay with their owners.
 //
-// One device-wide barrier per iteration.  The z-chain never reads x and the
-// block indices do not depend on the data (counter-based Philox, sampled
-// before the launch), so phase p does, between two barriers:
-//   1. read the reduced w^p and r^{p-1} (and a stopping-test partial),
-//   2. x update with block I_{p-1} and r^{p-1}   -> x^{p-1}   (own columns)
-//   3. z update with block J_p and w^p           -> z^p       (own rows)
-//   4. partial of w^{p+1} = A_{R_c, J_{p+1}}^T z^p           -> accumulator
-//   5. partial of r^p = A_{I_p, C_c} x^{p-1} (+ z^p_l - b_l on owned rows)
-//   6. (every check_every iterations) partial of ||x^{p-1} - x_ref||^2
-// then the barrier.  The tiles {A_{R_c,J_q}, A_{I_{q-1},C_c}} that phase q-1
-// reads for its partials are the ones phase q reads for its updates.
+// Two chains on two warp groups.  The z iterates never read x, and the block
+// indices do not depend on the data (counter-based Philox, sampled before the
+// launch).  Each CTA therefore runs the column steps (the z chain) on kZWarps
+// warps and the row steps (the x chain) on the other kXWarps warps, each group
+// with its own named barrier and its own device-wide arrival counter:
+//   z chain, step q: wait until every CTA's partial of w^q is in; z^q =
+//       z^{q-1} - c_J A_{:,J_q} w^q on own rows; hand (z^q - b) on the own rows
+//       of I_q to the x chain; partial of w^{q+1} = A_{R_c,J_{q+1}}^T z^q; arrive.
+//   x chain, step p: take the hand-over of step p; partial of r^p =
+//       A_{I_p,C_c} x^{p-1} (+ (z^p - b) on own rows, + a partial of
+//       ||x^{p-1} - x_ref||^2 on test steps); arrive; wait until r^p is
+//       complete; x^p = x^{p-1} - c_I A_{I_p,:}^T r^p on own columns.
+// The device-wide round trip of one chain then overlaps the work of the other.
+// The hand-over is a ring of kZRing slots with full / empty mbarriers, so the z
+// chain runs at most kZRing steps ahead.  When the x chain stops at step p (the
+// test on x^{p-1} passed), the z chain completes exactly step min(K, p + kZRing):
+// the z written back does not depend on timing.
 //
-// Tile movement.  With TMA (FP32 / BF16 storage) both tiles of iteration q
-// are 2-D tensor copies into one of two shared-memory buffers, issued as soon
-// as the buffer's previous pair has been used (one phase ahead) and waited on
+// Tile movement.  With TMA (FP32 / BF16 storage) each chain double-buffers its
+// tiles (z chain: A_{R_c, J_q}; x chain: A_{I_p, C_c}) in shared memory; each
+// 2-D tensor copy is issued as soon as its buffer has been used and waited on
 // through an mbarrier with a bounded spin.  Without TMA (FP64 storage, whose
-// two tile pairs do not fit in shared memory) the tiles are read from global
-// memory after line prefetches into L2 one phase ahead.
+// tiles do not fit in shared memory) the tiles are read from global memory
+// after line prefetches into L2 two steps ahead.
 //
 // Partial sums go to accumulators of the arithmetic type by atomic adds,
-// replicated to spread contention; three rotating accumulator sets keep the
-// reads, writes and clearing of consecutive phases apart.
+// replicated to spread contention; each chain rotates three accumulator sets so
+// that the reads, writes and clearing of consecutive steps stay apart.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -80,26 +86,28 @@ __device__ __forceinline__ TS group_reduce4(TS (&acc)[4], int gs, int sub, int *
     return k;
 }
 
-// out(row) = sum_{c in [ca, cb)} A[row, c] * vin[c - ca] for rows [ra, rb).
-// A addresses element (r, c) at A + r * lda + c.  Rows go to groups of gs
-// lanes (gs = power of two >= the number of 16-byte vectors of the range, at
-// most 32); each group handles 4 rows per pass.
-template <typename TA, typename TS, bool SM, typename Emit>
-__device__ __forceinline__ void row_dots(const TA *A, int64_t lda, int64_t ra, int64_t rb, int64_t ca,
-                                         int64_t cb, const TS *__restrict__ vin, Emit emit) {
+// out(row) = sum_{c in [ca, cb)} A[row, c] * vin[c - ca] for rows [ra, rb), by
+// a group of NT threads (gt = thread index in the group).  A addresses element
+// (r, c) at A + r * lda + c.  Rows go to lane groups of gs lanes (gs = power of
+// two >= the number of 16-byte vectors of the range, at most 32); each lane
+// group handles 4 rows per pass.
+template <int NT, typename TA, typename TS, bool SM, typename Emit>
+__device__ __forceinline__ void row_dots(int gt, const TA *A, int64_t lda, int64_t ra, int64_t rb,
+                                         int64_t ca, int64_t cb, const TS *__restrict__ vin, Emit emit) {
     using IO = VecIO<TA, TS>;
     constexpr int V = IO::V;
     constexpr int U = 4;
+    constexpr int NW = NT / 32;
     if (rb <= ra || cb <= ca) return;
     const int64_t va = ca / V, vb = (cb + V - 1) / V;
     const int nv = (int)(vb - va);
     int gs = 1;
     while (gs < nv && gs < 32) gs <<= 1;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int lane = gt & 31, warp = gt >> 5;
     const int sub = lane & (gs - 1);
     const int gpw = 32 / gs;
     const int g = warp * gpw + lane / gs;
-    const int NG = kWarps * gpw;
+    const int NG = NW * gpw;
     for (int64_t base = ra; base < rb; base += (int64_t)NG * U) {
         TS acc[U];
 #pragma unroll
@@ -146,23 +154,24 @@ __device__ __forceinline__ void row_dots(const TA *A, int64_t lda, int64_t ra, i
     }
 }
 
-// out(col) = sum_{r in [ra, rb)} A[r, col] * vrow[r - ra] for columns [ca, cb).
-// Threads are laid out as (vector index, row group); each thread sums its
-// vector over its rows, then the row groups are added through shared memory
-// (red: kThreads * V elements).
-template <typename TA, typename TS, bool SM, typename Emit>
-__device__ __forceinline__ void col_sums(const TA *A, int64_t lda, int64_t ra, int64_t rb, int64_t ca,
-                                         int64_t cb, const TS *__restrict__ vrow, TS *red, Emit emit) {
+// out(col) = sum_{r in [ra, rb)} A[r, col] * vrow[r - ra] for columns [ca, cb),
+// by a group of NT threads synchronised by sync().  Threads are laid out as
+// (vector index, row group); each thread sums its vector over its rows, then the
+// row groups are added through shared memory (red: NT * V elements).
+template <int NT, typename TA, typename TS, bool SM, typename Sync, typename Emit>
+__device__ __forceinline__ void col_sums(int gt, const TA *A, int64_t lda, int64_t ra, int64_t rb,
+                                         int64_t ca, int64_t cb, const TS *__restrict__ vrow, TS *red,
+                                         Sync sync, Emit emit) {
     using IO = VecIO<TA, TS>;
     constexpr int V = IO::V;
     constexpr int U = 4;
     if (rb <= ra || cb <= ca) return;
     const int64_t va = ca / V, vb = (cb + V - 1) / V;
     const int nv = (int)(vb - va);
-    for (int vc0 = 0; vc0 < nv; vc0 += kThreads) {
-        const int nvc = min(kThreads, nv - vc0);
-        const int NRG = kThreads / nvc;
-        const int vi = threadIdx.x % nvc, rg = threadIdx.x / nvc;
+    for (int vc0 = 0; vc0 < nv; vc0 += NT) {
+        const int nvc = min(NT, nv - vc0);
+        const int NRG = NT / nvc;
+        const int vi = gt % nvc, rg = gt / nvc;
         if (rg < NRG) {
             TS acc[V];
 #pragma unroll
@@ -191,8 +200,8 @@ __device__ __forceinline__ void col_sums(const TA *A, int64_t lda, int64_t ra, i
 #pragma unroll
             for (int e = 0; e < V; ++e) red[rg * (nvc * V) + vi * V + e] = acc[e];
         }
-        __syncthreads();
-        for (int c = threadIdx.x; c < nvc * V; c += kThreads) {
+        sync();
+        for (int c = gt; c < nvc * V; c += NT) {
             const int64_t col = (va + vc0) * V + c;
             if (col >= ca && col < cb) {
                 TS sum = tzero<TS>();
@@ -200,15 +209,22 @@ __device__ __forceinline__ void col_sums(const TA *A, int64_t lda, int64_t ra, i
                 emit(col, sum);
             }
         }
-        __syncthreads();
+        sync();
     }
 }
 
 template <typename T> __device__ __forceinline__ bool finite_val(T v) { return isfinite(v); }
 
 // ---------------------------------------------------------------------------
-// TMA / mbarrier helpers
+// Named barriers, shared-memory flags, TMA / mbarrier helpers
 // ---------------------------------------------------------------------------
+__device__ __forceinline__ void named_sync(int id, int nthreads) {
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
+
+__device__ __forceinline__ int ld_vol(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
+__device__ __forceinline__ void st_vol(int *p, int v) { *reinterpret_cast<volatile int *>(p) = v; }
+
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return (uint32_t)__cvta_generic_to_shared(p);
 }
@@ -220,6 +236,22 @@ __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                  : "memory");
+}
+
+// One arrival (release at CTA scope).
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Non-blocking test: has the phase with this parity completed (acquire at CTA scope)?
+__device__ __forceinline__ bool mbar_test(uint64_t *bar, uint32_t parity) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return done != 0;
 }
 
 // Bounded wait for the phase with the given parity to complete.
@@ -238,6 +270,20 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, unsign
     }
 }
 
+// Leader-side bounded poll: 0 once ready() holds; the nonzero code of quit() if
+// that comes first; 6 (REBK_BARRIER_TIMEOUT) once timeout_ns have passed.
+template <typename Ready, typename Quit>
+__device__ __forceinline__ int lead_poll(Ready ready, Quit quit, unsigned long long timeout_ns) {
+    if (ready()) return 0;
+    const unsigned long long t0 = globaltimer_ns();
+    for (uint32_t spins = 1;; ++spins) {
+        const int q = quit();
+        if (q != 0) return q;
+        if (ready()) return 0;
+        if ((spins & 63u) == 0u && globaltimer_ns() - t0 > timeout_ns) return 6;
+    }
+}
+
 __device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int x, int y, uint64_t *bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
@@ -253,6 +299,21 @@ __device__ __forceinline__ void prefetch_line(const void *p) {
     asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// Shared-memory header (byte offsets below kSmemHeader).
+constexpr int kHdrRingJ = 0;      // int[kRing]  z chain: J_k
+constexpr int kHdrRingZI = 32;    // int[kRing]  z chain: I_k (rows handed over)
+constexpr int kHdrRingXI = 64;    // int[kRing]  x chain: I_k
+constexpr int kHdrZF = 96;        // int[4]      z-chain flags
+constexpr int kHdrXF = 112;       // int[4]      x-chain flags
+constexpr int kHdrCtl = 128;      // int[4]      [0] stop code (0, 1 converged, 5, 6), [1] stop step
+constexpr int kHdrMbarC = 160;    // u64[2]      column tiles
+constexpr int kHdrMbarR = 176;    // u64[2]      row tiles
+constexpr int kHdrZFull = 192;    // u64[kZRing] hand-over slot written
+constexpr int kHdrZEmpty = 224;   // u64[kZRing] hand-over slot consumed
+constexpr int kHdrRingCJ = 256;   // TS[kRing]   z chain: alpha / ||A_{:,J_k}||^2
+constexpr int kHdrRingCI = 320;   // TS[kRing]   x chain: alpha / ||A_{I_k,:}||^2
+static_assert(kRing == 8 && kZRing <= 4 && kHdrRingCI + 64 <= (int)kSmemHeader, "header layout");
+
 }  // namespace
 
 template <typename TA, typename TS, bool CORR, bool TMA>
@@ -260,6 +321,8 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
     extern __shared__ __align__(128) unsigned char smem_raw[];
     using IO = VecIO<TA, TS>;
     constexpr int V = IO::V;
+    constexpr int ZT = kZThreads, XT = kXThreads;
+    constexpr int64_t ZR = kZRing;
 
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
     const TA *__restrict__ A = static_cast<const TA *>(args.A);
@@ -268,15 +331,25 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
     const int64_t r0 = m * cta / G, r1 = m * (cta + 1) / G;
     const int64_t c0 = lmin(n, 8 * (nu * cta / G)), c1 = lmin(n, 8 * (nu * (cta + 1) / G));
     const int nrow = (int)(r1 - r0), ncol = (int)(c1 - c0);
+    const int64_t K = args.iters;
+    const int64_t tau_r = args.tau_r;
 
     // ---- shared memory carve-up (same layout as grid_smem_bytes()) ----
     const SmemLayout L = smem_layout(args.nrow_cap, args.ncol_cap, args.tau_r, args.tau_c, CORR,
                                      (int)sizeof(TS), V, TMA ? args.tile_c_bytes : 0,
                                      TMA ? args.tile_r_bytes : 0);
-    int *ring_j = reinterpret_cast<int *>(smem_raw);
-    int *ring_i = ring_j + kRing;
-    int *flags = ring_i + kRing;  // [0] barrier ok, [1] stop code, [2] tile wait failed
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(smem_raw + 96);  // two mbarriers
+    int *ring_j = reinterpret_cast<int *>(smem_raw + kHdrRingJ);
+    int *ring_zi = reinterpret_cast<int *>(smem_raw + kHdrRingZI);
+    int *ring_xi = reinterpret_cast<int *>(smem_raw + kHdrRingXI);
+    int *zf = reinterpret_cast<int *>(smem_raw + kHdrZF);  // [0] wait code, [1] non-finite w, [2] tile wait failed
+    int *xf = reinterpret_cast<int *>(smem_raw + kHdrXF);  // [0] wait code, [1] test passed, [2] tile, [3] non-finite r
+    int *ctl = reinterpret_cast<int *>(smem_raw + kHdrCtl);
+    uint64_t *mbar_c = reinterpret_cast<uint64_t *>(smem_raw + kHdrMbarC);
+    uint64_t *mbar_r = reinterpret_cast<uint64_t *>(smem_raw + kHdrMbarR);
+    uint64_t *zfull = reinterpret_cast<uint64_t *>(smem_raw + kHdrZFull);
+    uint64_t *zempty = reinterpret_cast<uint64_t *>(smem_raw + kHdrZEmpty);
+    TS *ring_cj = reinterpret_cast<TS *>(smem_raw + kHdrRingCJ);
+    TS *ring_ci = reinterpret_cast<TS *>(smem_raw + kHdrRingCI);
     TS *zeta = reinterpret_cast<TS *>(smem_raw + L.zeta);
     TS *beta_own = reinterpret_cast<TS *>(smem_raw + L.beta);
     TS *v_own = reinterpret_cast<TS *>(smem_raw + L.v);    // CORR only
@@ -284,7 +357,9 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
     TS *s_own = reinterpret_cast<TS *>(smem_raw + L.s);    // CORR only
     TS *w = reinterpret_cast<TS *>(smem_raw + L.w);
     TS *rr = reinterpret_cast<TS *>(smem_raw + L.r);
-    TS *red = reinterpret_cast<TS *>(smem_raw + L.red);
+    TS *zr = reinterpret_cast<TS *>(smem_raw + L.zr);      // kZRing slots of tau_r
+    TS *redz = reinterpret_cast<TS *>(smem_raw + L.redz);
+    TS *redx = reinterpret_cast<TS *>(smem_raw + L.redx);
     auto tile_c = [&](int b) { return reinterpret_cast<TA *>(smem_raw + (b ? L.tc1 : L.tc0)); };
     auto tile_r = [&](int b) { return reinterpret_cast<TA *>(smem_raw + (b ? L.tr1 : L.tr0)); };
 
@@ -292,10 +367,11 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
     TS *gx = static_cast<TS *>(args.x);
     TS *gs_dual = static_cast<TS *>(args.sdual);
     TS *gv_dual = static_cast<TS *>(args.vdual);
-    TS *accbase = static_cast<TS *>(args.acc);
     const TS *coef_r = static_cast<const TS *>(args.coef_r);
     const TS *coef_c = static_cast<const TS *>(args.coef_c);
+    const int32_t *idx = args.idx;
 
+    // ---- state, index rings, barriers ----
     for (int i = tid; i < nrow; i += kThreads) {
         zeta[i] = gz[r0 + i];
         beta_own[i] = (TS)args.beta[r0 + i];
@@ -305,333 +381,472 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
         xi[j] = gx[c0 + j];
         if (CORR) s_own[j] = gs_dual[c0 + j];
     }
+    if (tid == 0) {
+        for (int64_t k = 1; k <= 4 && k <= K; ++k) {
+            const int j = __ldg(idx + 2 * (k - 1)), i = __ldg(idx + 2 * (k - 1) + 1);
+            ring_j[k % kRing] = j;
+            ring_zi[k % kRing] = i;
+            ring_xi[k % kRing] = i;
+            ring_cj[k % kRing] = coef_c[j];
+            ring_ci[k % kRing] = coef_r[i];
+        }
+        for (int q = 0; q < 4; ++q) {
+            zf[q] = 0;
+            xf[q] = 0;
+            ctl[q] = 0;
+        }
+        mbar_init(&mbar_c[0], 1);
+        mbar_init(&mbar_c[1], 1);
+        mbar_init(&mbar_r[0], 1);
+        mbar_init(&mbar_r[1], 1);
+        for (int q = 0; q < kZRing; ++q) {
+            mbar_init(&zfull[q], 1);
+            mbar_init(&zempty[q], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
 
-    const int64_t K = args.iters;
     const int rep = cta % args.acc_r;
     const int aw = args.acc_w;
     const int64_t accset = (int64_t)args.acc_r * aw;
+    TS *accw_base = static_cast<TS *>(args.acc);   // w partials: 3 sets
+    TS *accr_base = accw_base + 3 * accset;        // r partials (+ test partial at tau_r): 3 sets
     const bool check = args.x_ref != nullptr && args.check_every > 0;
 
-    TS *ring_cj = reinterpret_cast<TS *>(smem_raw + L.ringc);          // step coefficients
-    TS *ring_ci = ring_cj + kRing;
-    auto load_idx = [&](int64_t k) {
-        const int j = __ldg(args.idx + 2 * (k - 1)), i = __ldg(args.idx + 2 * (k - 1) + 1);
-        ring_j[k % kRing] = j;
-        ring_i[k % kRing] = i;
-        ring_cj[k % kRing] = coef_c[j];
-        ring_ci[k % kRing] = coef_r[i];
-    };
     auto col_range = [&](int j, int64_t *a, int64_t *b) {
         *a = (int64_t)j * args.tau_c;
         *b = lmin(n, *a + args.tau_c);
     };
     auto row_range = [&](int i, int64_t *a, int64_t *b) {
-        *a = (int64_t)i * args.tau_r;
-        *b = lmin(m, *a + args.tau_r);
+        *a = (int64_t)i * tau_r;
+        *b = lmin(m, *a + tau_r);
     };
-    if (tid == 0) {
-        for (int64_t k = 1; k <= 4 && k <= K; ++k) load_idx(k);
-        flags[1] = 0;
-        flags[2] = 0;
-        flags[3] = 0;
-        if (TMA) {
-            mbar_init(&mbar[0], 1);
-            mbar_init(&mbar[1], 1);
-            asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        }
-    }
-    __syncthreads();
+    // a wait gave up after its time limit: record it for the host and for the other group
+    auto give_up = [&](int code) {
+        if (code == 6) atomicExch(args.status, 6);
+        if (code == 5) atomicExch(args.status, 5);
+        atomicCAS(&ctl[0], 0, code);
+    };
 
-    // ---------------- tile sources ----------------
-    // TileSet(q) = {A[R_c, J_q] if 1 <= q <= K, A[I_{q-1}, C_c] if 2 <= q <= K+1},
-    // in buffer q % 2 (TMA) or read from global (no TMA).
-    // per-buffer state, kept in scalars (uniform across the CTA)
-    uint32_t par0 = 0u, par1 = 0u;     // mbarrier phase parity to wait for
-    bool pend0 = false, pend1 = false;  // copies issued and not yet waited for
-    int xc0 = 0, xc1 = 0;               // x origin (column) of the column tile
-    auto issue_tiles = [&](int64_t q) {  // TMA: called by all threads, thread 0 issues
-        const int b = (int)(q & 1);
-        const bool hasc = (q >= 1 && q <= K && nrow > 0);
-        const bool hasr = (q >= 2 && q <= K + 1 && ncol > 0);
-        int x0 = 0;
-        if (hasc) {
+    if (tid < ZT) {
+        // =================== z chain: column steps ===================
+        const int gt = tid;
+        auto zsync = [&]() { named_sync(1, ZT); };
+
+        // index ring: entry k = q + 4 is written at step q from registers loaded
+        // one (coefficient) and two (indices) steps earlier
+        int ld_j1 = 0, ld_i1 = 0, ld_j2 = 0, ld_i2 = 0;
+        TS ld_c1 = tzero<TS>();
+        if (gt == ZT - 1) {
+            if (K >= 5) {
+                ld_j1 = __ldg(idx + 8);
+                ld_i1 = __ldg(idx + 9);
+                ld_c1 = coef_c[ld_j1];
+            }
+            if (K >= 6) {
+                ld_j2 = __ldg(idx + 10);
+                ld_i2 = __ldg(idx + 11);
+            }
+        }
+        auto loader = [&](int64_t q) {
+            if (gt != ZT - 1) return;
+            if (q + 4 <= K) {
+                ring_j[(q + 4) % kRing] = ld_j1;
+                ring_zi[(q + 4) % kRing] = ld_i1;
+                ring_cj[(q + 4) % kRing] = ld_c1;
+            }
+            if (q + 5 <= K) {
+                ld_j1 = ld_j2;
+                ld_i1 = ld_i2;
+                ld_c1 = coef_c[ld_j2];
+            }
+            if (q + 6 <= K) {
+                ld_j2 = __ldg(idx + 2 * (q + 5));
+                ld_i2 = __ldg(idx + 2 * (q + 5) + 1);
+            }
+        };
+
+        // column tile of J_q (own rows) in buffer q % 2
+        uint32_t cpar0 = 0u, cpar1 = 0u;
+        bool cpend0 = false, cpend1 = false;
+        int xc0 = 0, xc1 = 0;  // x origin of each buffer's copy
+        auto issue_col = [&](int64_t q) {
+            if (!TMA || q < 1 || q > K || nrow == 0) return;
+            const int b = (int)(q & 1);
             int64_t ja, jb;
             col_range(ring_j[q % kRing], &ja, &jb);
-            x0 = (int)(ja / args.tma_vx * args.tma_vx);
-        }
-        if (b) { xc1 = x0; pend1 = hasc || hasr; } else { xc0 = x0; pend0 = hasc || hasr; }
-        if (tid == 0 && (hasc || hasr)) {
-            fence_proxy_async();
-            const uint32_t bytes = (hasc ? (uint32_t)args.tile_c_bytes_tx : 0u) +
-                                   (hasr ? (uint32_t)args.tile_r_bytes_tx : 0u);
-            mbar_expect_tx(&mbar[b], bytes);
-            if (hasc) {
+            const int x0 = (int)(ja / args.tma_vx * args.tma_vx);
+            if (b) { xc1 = x0; cpend1 = true; } else { xc0 = x0; cpend0 = true; }
+            if (gt == 0) {
+                fence_proxy_async();
+                mbar_expect_tx(&mbar_c[b], (uint32_t)args.tile_c_bytes_tx);
                 for (int bx = 0; bx < args.nbox_c; ++bx)
                     tma_load_2d(tile_c(b) + (size_t)bx * args.bh_c * args.bw_c, &args.tmap_c, x0,
-                                (int)(r0 + (int64_t)bx * args.bh_c), &mbar[b]);
+                                (int)(r0 + (int64_t)bx * args.bh_c), &mbar_c[b]);
             }
-            if (hasr) {
-                int64_t ia, ib;
-                row_range(ring_i[(q - 1) % kRing], &ia, &ib);
-                tma_load_2d(tile_r(b), &args.tmap_r, (int)c0, (int)ia, &mbar[b]);
+        };
+        auto wait_col = [&](int64_t q) -> bool {
+            const int b = (int)(q & 1);
+            const bool pend = b ? cpend1 : cpend0;
+            if (!pend) return true;
+            const bool ok = mbar_wait(&mbar_c[b], b ? cpar1 : cpar0, args.timeout_ns);
+            if (b) { cpar1 ^= 1u; cpend1 = false; } else { cpar0 ^= 1u; cpend0 = false; }
+            return ok;
+        };
+        auto ctile = [&](int64_t q, int64_t *ld) -> const TA * {
+            if (!TMA) {
+                *ld = lda;
+                return A;
             }
-        }
-    };
-    auto wait_buffer = [&](int b) -> bool {
-        const bool pend = b ? pend1 : pend0;
-        if (!pend) return true;
-        const bool ok = mbar_wait(&mbar[b], b ? par1 : par0, args.timeout_ns);
-        if (b) { par1 ^= 1u; pend1 = false; } else { par0 ^= 1u; pend0 = false; }
-        return ok;
-    };
-    auto wait_tiles = [&](int64_t q) -> bool { return wait_buffer((int)(q & 1)); };
-    // before leaving the kernel: no tensor copy may still be writing shared memory
-    auto drain = [&]() {
-        if (TMA) {
-            wait_buffer(0);
-            wait_buffer(1);
-        }
-    };
-    // base pointer and leading dimension addressing element (r, c) of the
-    // column tile of J_q / the row tile of I_{q-1} in absolute coordinates
-    auto ctile = [&](int64_t q, int64_t *ld) -> const TA * {
-        if (!TMA) {
-            *ld = lda;
-            return A;
-        }
-        const int b = (int)(q & 1);
-        *ld = args.bw_c;
-        return tile_c(b) - r0 * (int64_t)args.bw_c - (b ? xc1 : xc0);
-    };
-    auto rtile = [&](int64_t q, int64_t ia, int64_t *ld) -> const TA * {
-        if (!TMA) {
-            *ld = lda;
-            return A;
-        }
-        const int b = (int)(q & 1);
-        *ld = args.bw_r;
-        return tile_r(b) - ia * (int64_t)args.bw_r - c0;
-    };
-    // line prefetch of TileSet(q) into L2 (no-TMA path), spread over threads
-    auto prefetch_tiles = [&](int64_t q) {
-        constexpr int64_t LINE = 128 / sizeof(TA);
-        if (q >= 1 && q <= K && nrow > 0) {
+            const int b = (int)(q & 1);
+            *ld = args.bw_c;
+            return tile_c(b) - r0 * (int64_t)args.bw_c - (b ? xc1 : xc0);
+        };
+        auto prefetch_col = [&](int64_t q) {  // no-TMA path: L2 line prefetch
+            if (TMA || q < 1 || q > K || nrow == 0) return;
+            constexpr int64_t LINE = 128 / sizeof(TA);
             int64_t ja, jb;
             col_range(ring_j[q % kRing], &ja, &jb);
             const int64_t l0 = ja / LINE;
             const int nl = (int)((jb + LINE - 1) / LINE - l0);
-            for (int e = tid; e < nrow * nl; e += kThreads) {
+            for (int e = gt; e < nrow * nl; e += ZT) {
                 const int rr_ = e / nl, l = e - rr_ * nl;
                 prefetch_line(A + (r0 + rr_) * lda + (l0 + l) * LINE);
             }
+        };
+        auto partial_w = [&](int64_t q, TS *accp) {  // over own rows, column block J_q, with zeta
+            int64_t ja, jb, ld;
+            col_range(ring_j[q % kRing], &ja, &jb);
+            const TA *T = ctile(q, &ld);
+            col_sums<ZT, TA, TS, TMA>(gt, T, ld, r0, r1, ja, jb, zeta, redz, zsync,
+                                      [&](int64_t col, TS v) { atomicAdd(accp + (col - ja), v); });
+        };
+        // stop signal for the z chain at step q: 5 / 6 at once; after a converged
+        // stop of the x chain at step p, once q > min(K, p + kZRing)
+        auto quit_z = [&](int64_t q) -> int {
+            const int c = ld_vol(&ctl[0]);
+            if (c == 5 || c == 6) return c;
+            if (c == 1) {
+                __threadfence_block();
+                if (q > lmin(K, (int64_t)ld_vol(&ctl[1]) + ZR)) return 1;
+            }
+            return 0;
+        };
+
+        bool alive = K >= 1;
+        if (alive) {
+            issue_col(1);
+            issue_col(2);
+            prefetch_col(1);
+            prefetch_col(2);
+            if (!wait_col(1)) zf[2] = 1;
+            zsync();
+            if (zf[2] != 0) {
+                if (gt == 0) give_up(6);
+                alive = false;
+            } else {
+                partial_w(1, accw_base + (int64_t)rep * aw);
+                zsync();
+                if (gt == 0) red_release_gpu_add(args.bar, 1u);
+            }
         }
-        if (q >= 2 && q <= K + 1 && ncol > 0) {
+        for (int64_t q = 1; alive && q <= K; ++q) {
+            loader(q);
+            if (gt == 0) {
+                int code = lead_poll([&] { return ld_acquire_gpu(args.bar) >= (unsigned)G * (unsigned)q; },
+                                     [&] { return quit_z(q); }, args.timeout_ns);
+                if (code == 0 && q > ZR) {  // hand-over slot of step q - kZRing consumed
+                    const uint32_t par = (uint32_t)(((q - 1) / ZR - 1) & 1);
+                    code = lead_poll([&] { return mbar_test(&zempty[(q - 1) % ZR], par); },
+                                     [&] { return quit_z(q); }, args.timeout_ns);
+                }
+                if (code == 6) give_up(6);
+                zf[0] = code;
+            }
+            zsync();
+            if (zf[0] != 0) break;
+
+            // w^q = sum of the replicas (+ g_J in the correction form)
+            const int jq = ring_j[q % kRing];
+            int64_t ja, jb;
+            col_range(jq, &ja, &jb);
+            const int wc = (int)(jb - ja);
+            const TS *accq = accw_base + ((q - 1) % 3) * accset;
+            for (int t = gt; t < wc; t += ZT) {
+                const TS *q0 = accq + t;
+                const TS a0 = ld_cg_t(q0), a1 = ld_cg_t(q0 + aw), a2 = ld_cg_t(q0 + 2 * aw),
+                         a3 = ld_cg_t(q0 + 3 * aw);
+                TS sum = (a0 + a1) + (a2 + a3);
+                if (CORR) sum += (TS)args.gamma[ja + t];
+                w[t] = sum;
+                if (!finite_val(sum)) zf[1] = 1;
+            }
+            zsync();
+            if (zf[1] != 0) {
+                if (gt == 0) give_up(5);
+                break;
+            }
+            // z^q on own rows; hand (z^q - b) on own rows of I_q to the x chain
+            const TS cJ = ring_cj[q % kRing];
             int64_t ia, ib;
-            row_range(ring_i[(q - 1) % kRing], &ia, &ib);
+            row_range(ring_zi[q % kRing], &ia, &ib);
+            TS *zslot = zr + ((q - 1) % ZR) * tau_r;
+            {
+                int64_t ld;
+                const TA *T = ctile(q, &ld);
+                row_dots<ZT, TA, TS, TMA>(gt, T, ld, r0, r1, ja, jb, w, [&](int64_t row, TS v) {
+                    const TS nz = zeta[row - r0] - cJ * v;
+                    zeta[row - r0] = nz;
+                    if (row >= ia && row < ib) zslot[row - ia] = nz - beta_own[row - r0];
+                });
+            }
+            if (CORR) {
+                const int64_t la = lmax(ja, c0), lb = lmin(jb, c1);
+                for (int64_t l = la + gt; l < lb; l += ZT) s_own[l - c0] += cJ * w[l - ja];
+            }
+            zsync();
+            if (gt == 0) mbar_arrive(&zfull[(q - 1) % ZR]);
+            // column tile of J_q is used up: its buffer takes J_{q+2}
+            issue_col(q + 2);
+            prefetch_col(q + 2);
+            if (q < K) {
+                if (!wait_col(q + 1)) zf[2] = 1;
+                zsync();
+                if (zf[2] != 0) {
+                    if (gt == 0) give_up(6);
+                    break;
+                }
+                partial_w(q + 1, accw_base + (q % 3) * accset + (int64_t)rep * aw);
+                if (cta == 0) {  // clear the set read two steps ahead
+                    TS *accz = accw_base + ((q + 1) % 3) * accset;
+                    for (int64_t e = gt; e < accset; e += ZT) accz[e] = tzero<TS>();
+                }
+                zsync();
+                if (gt == 0) red_release_gpu_add(args.bar, 1u);
+            }
+        }
+        // no tensor copy may still be writing shared memory when the group leaves
+        if (TMA) {
+            wait_col(0);
+            wait_col(1);
+        }
+        for (int i = gt; i < nrow; i += ZT) gz[r0 + i] = zeta[i];
+        if (CORR)
+            for (int j = gt; j < ncol; j += ZT) gs_dual[c0 + j] = s_own[j];
+    } else {
+        // =================== x chain: row steps ===================
+        const int gt = tid - ZT;
+        auto xsync = [&]() { named_sync(2, XT); };
+
+        int ld_i1 = 0, ld_i2 = 0;
+        TS ld_c1 = tzero<TS>();
+        if (gt == XT - 1) {
+            if (K >= 5) {
+                ld_i1 = __ldg(idx + 9);
+                ld_c1 = coef_r[ld_i1];
+            }
+            if (K >= 6) ld_i2 = __ldg(idx + 11);
+        }
+        auto loader = [&](int64_t p) {
+            if (gt != XT - 1) return;
+            if (p + 4 <= K) {
+                ring_xi[(p + 4) % kRing] = ld_i1;
+                ring_ci[(p + 4) % kRing] = ld_c1;
+            }
+            if (p + 5 <= K) {
+                ld_i1 = ld_i2;
+                ld_c1 = coef_r[ld_i2];
+            }
+            if (p + 6 <= K) ld_i2 = __ldg(idx + 2 * (p + 5) + 1);
+        };
+
+        // row tile of I_p (own columns) in buffer p % 2
+        uint32_t rpar0 = 0u, rpar1 = 0u;
+        bool rpend0 = false, rpend1 = false;
+        auto issue_row = [&](int64_t p) {
+            if (!TMA || p < 1 || p > K || ncol == 0) return;
+            const int b = (int)(p & 1);
+            if (b) rpend1 = true; else rpend0 = true;
+            if (gt == 0) {
+                int64_t ia, ib;
+                row_range(ring_xi[p % kRing], &ia, &ib);
+                fence_proxy_async();
+                mbar_expect_tx(&mbar_r[b], (uint32_t)args.tile_r_bytes_tx);
+                tma_load_2d(tile_r(b), &args.tmap_r, (int)c0, (int)ia, &mbar_r[b]);
+            }
+        };
+        auto wait_row = [&](int64_t p) -> bool {
+            const int b = (int)(p & 1);
+            const bool pend = b ? rpend1 : rpend0;
+            if (!pend) return true;
+            const bool ok = mbar_wait(&mbar_r[b], b ? rpar1 : rpar0, args.timeout_ns);
+            if (b) { rpar1 ^= 1u; rpend1 = false; } else { rpar0 ^= 1u; rpend0 = false; }
+            return ok;
+        };
+        auto rtile = [&](int64_t p, int64_t ia, int64_t *ld) -> const TA * {
+            if (!TMA) {
+                *ld = lda;
+                return A;
+            }
+            *ld = args.bw_r;
+            return tile_r((int)(p & 1)) - ia * (int64_t)args.bw_r - c0;
+        };
+        auto prefetch_row = [&](int64_t p) {
+            if (TMA || p < 1 || p > K || ncol == 0) return;
+            constexpr int64_t LINE = 128 / sizeof(TA);
+            int64_t ia, ib;
+            row_range(ring_xi[p % kRing], &ia, &ib);
             const int64_t l0 = c0 / LINE;
             const int nl = (int)((c1 + LINE - 1) / LINE - l0), h = (int)(ib - ia);
-            for (int e = tid; e < h * nl; e += kThreads) {
+            for (int e = gt; e < h * nl; e += XT) {
                 const int rr_ = e / nl, l = e - rr_ * nl;
                 prefetch_line(A + (ia + rr_) * lda + (l0 + l) * LINE);
             }
-        }
-    };
-    auto partial_w = [&](int64_t q, TS *accp) {  // over own rows, column block J_q
-        int64_t ja, jb, ld;
-        col_range(ring_j[q % kRing], &ja, &jb);
-        const TA *T = ctile(q, &ld);
-        col_sums<TA, TS, TMA>(T, ld, r0, r1, ja, jb, zeta, red, [&](int64_t col, TS v) {
-            atomicAdd(accp + (col - ja), v);
-        });
-    };
+        };
+        auto quit_x = [&]() -> int {
+            const int c = ld_vol(&ctl[0]);
+            return (c == 5 || c == 6) ? c : 0;
+        };
 
-    // ---------------- phase 0 ----------------
-    int64_t done = 0;
-    int stop_code = 0;  // 0 running, 1 converged, 5 diverged, 6 timeout
-    if (K >= 1) {
-        if (TMA) {
-            issue_tiles(1);
-            issue_tiles(2);
-            if (!wait_tiles(1)) flags[2] = 1;
-        } else {
-            prefetch_tiles(1);
-            prefetch_tiles(2);
+        int64_t done = K;
+        if (K >= 1) {
+            issue_row(1);
+            issue_row(2);
+            prefetch_row(1);
+            prefetch_row(2);
         }
-        __syncthreads();
-        if (flags[2] == 0) partial_w(1, accbase + (int64_t)rep * aw);
-    }
-    if (flags[2] != 0 && tid == 0) atomicExch(args.status, 6);
-    if (!grid_barrier(args.bar, (unsigned)G * 1u, args.status, args.timeout_ns, &flags[0]) || flags[2] != 0) {
-        drain();
-        return;
-    }
-
-    // ---------------- phases 1 .. K+1 ----------------
-    for (int64_t p = 1; p <= K + 1; ++p) {
-        if (tid == kThreads - 1 && p + 4 <= K) load_idx(p + 4);
-        if (!TMA) prefetch_tiles(p + 2);
-
-        const TS *accr = accbase + ((p - 1) % 3) * accset;
-        const int jp = (p <= K) ? ring_j[p % kRing] : 0;
-        const int ip1 = (p >= 2) ? ring_i[(p - 1) % kRing] : 0;
-        int64_t ja = 0, jb = 0, ia = 0, ib = 0;
-        if (p <= K) col_range(jp, &ja, &jb);
-        if (p >= 2) row_range(ip1, &ia, &ib);
-        const int wc = (int)(jb - ja), hr = (int)(ib - ia);
-
-        // 1. reduced vectors (flags[3]: a reduced product is Inf/NaN)
-        static_assert(kAccReplicas == 4, "step 1 reads four replicas");
-        if (tid < wc) {
-            const TS *q0 = accr + tid;
-            const TS a0 = ld_cg_t(q0), a1 = ld_cg_t(q0 + aw), a2 = ld_cg_t(q0 + 2 * aw),
-                     a3 = ld_cg_t(q0 + 3 * aw);
-            TS sum = (a0 + a1) + (a2 + a3);
-            if (CORR) sum += (TS)args.gamma[ja + tid];
-            w[tid] = sum;
-            if (!finite_val(sum)) flags[3] = 1;
-        }
-        if (tid < hr) {
-            const TS *q0 = accr + args.tau_c + tid;
-            const TS a0 = ld_cg_t(q0), a1 = ld_cg_t(q0 + aw), a2 = ld_cg_t(q0 + 2 * aw),
-                     a3 = ld_cg_t(q0 + 3 * aw);
-            const TS sum = (a0 + a1) + (a2 + a3);
-            rr[tid] = sum;
-            if (!finite_val(sum)) flags[3] = 1;
-        }
-        if (tid == kThreads - 2) {
-            int code = 0;
-            const int64_t kc = p - 2;  // iterate whose error partial was formed in phase p-1
-            if (check && kc >= 1 && (args.check_offset + kc) % args.check_every == 0) {
-                TS e2 = tzero<TS>();
-                for (int q = 0; q < kAccReplicas; ++q)
-                    e2 += ld_cg_t(accr + (int64_t)q * aw + args.tau_c + args.tau_r);
-                if ((double)e2 <= args.tol2_abs) code = 1;
+        for (int64_t p = 1; p <= K; ++p) {
+            loader(p);
+            if (!wait_row(p)) xf[2] = 1;
+            if (gt == 0) {  // hand-over of step p written
+                const uint32_t par = (uint32_t)(((p - 1) / ZR) & 1);
+                const int code = lead_poll([&] { return mbar_test(&zfull[(p - 1) % ZR], par); }, quit_x,
+                                           args.timeout_ns);
+                if (code == 6) give_up(6);
+                xf[0] = code;
             }
-            flags[1] = code;
-        }
-        __syncthreads();
-        stop_code = flags[1];
-        if (stop_code == 0 && flags[3] != 0) stop_code = 5;
-        if (stop_code == 1) {
-            done = p - 2;
-            break;
-        }
-        if (stop_code == 5) {
-            done = p - 1;
-            break;
-        }
-
-        // 2. x update with I_{p-1} (row tile of TileSet(p))
-        if (p >= 2) {
-            const TS cI = ring_ci[(p - 1) % kRing];
-            int64_t ld;
-            const TA *T = rtile(p, ia, &ld);
-            col_sums<TA, TS, TMA>(T, ld, ia, ib, c0, c1, rr, red, [&](int64_t col, TS v) {
-                xi[col - c0] -= cI * v;
-            });
-            if (CORR) {
-                const int64_t la = lmax(ia, r0), lb = lmin(ib, r1);
-                for (int64_t l = la + tid; l < lb; l += kThreads) v_own[l - r0] -= cI * rr[l - ia];
+            xsync();
+            if (xf[2] != 0 || xf[0] != 0) {
+                if (xf[2] != 0 && gt == 0) give_up(6);
+                done = p - 1;
+                break;
             }
-        }
-        if (p == K + 1) {
-            done = K;
-            break;
-        }
 
-        // 3. z update with J_p (column tile of TileSet(p))
-        {
-            const TS cJ = ring_cj[p % kRing];
-            int64_t ld;
-            const TA *T = ctile(p, &ld);
-            row_dots<TA, TS, TMA>(T, ld, r0, r1, ja, jb, w, [&](int64_t row, TS v) {
-                zeta[row - r0] -= cJ * v;
-            });
-            if (CORR) {
-                const int64_t la = lmax(ja, c0), lb = lmin(jb, c1);
-                for (int64_t l = la + tid; l < lb; l += kThreads) s_own[l - c0] += cJ * w[l - ja];
-            }
-        }
-        __syncthreads();
-
-        // TileSet(p) has been used: its buffer takes TileSet(p + 2); TileSet(p + 1)
-        // (loaded during the previous phase) must have landed for the partials.
-        if (TMA) {
-            issue_tiles(p + 2);
-            if (!wait_tiles(p + 1)) flags[2] = 1;
-            __syncthreads();
-            if (flags[2] != 0) {
-                if (tid == 0) atomicExch(args.status, 6);
-                drain();
-                return;  // the other CTAs give up at their next barrier
-            }
-        }
-
-        TS *accw = accbase + (p % 3) * accset + (int64_t)rep * aw;
-        // 4. partial of w^{p+1}
-        if (p < K) partial_w(p + 1, accw);
-
-        // 5. partial of r^p = A_{I_p, C_c} x^{p-1} + (z^p - b) on owned rows (TileSet(p+1))
-        {
-            int64_t qa, qb;
-            row_range(ring_i[p % kRing], &qa, &qb);
+            // partial of r^p: A_{I_p, C_c} x^{p-1} (+ (z^p - b) on own rows of I_p)
+            int64_t ia, ib;
+            row_range(ring_xi[p % kRing], &ia, &ib);
+            TS *accp = accr_base + (p % 3) * accset + (int64_t)rep * aw;
             if (ncol > 0) {
                 int64_t ld;
-                const TA *T = rtile(p + 1, qa, &ld);
-                row_dots<TA, TS, TMA>(T, ld, qa, qb, c0, c1, xi, [&](int64_t row, TS v) {
-                    atomicAdd(accw + args.tau_c + (row - qa), v);
-                });
+                const TA *T = rtile(p, ia, &ld);
+                row_dots<XT, TA, TS, TMA>(gt, T, ld, ia, ib, c0, c1, xi,
+                                          [&](int64_t row, TS v) { atomicAdd(accp + (row - ia), v); });
             }
-            const int64_t la = lmax(qa, r0), lb = lmin(qb, r1);
-            for (int64_t l = la + tid; l < lb; l += kThreads)
-                atomicAdd(accw + args.tau_c + (l - qa), zeta[l - r0] - beta_own[l - r0]);
-        }
-
-        // 6. stopping-test partial for x^{p-1}
-        if (check && (p - 1) >= 1 && (args.check_offset + p - 1) % args.check_every == 0) {
-            double e2 = 0.0;
-            for (int j = tid; j < ncol; j += kThreads) {
-                const double xb = args.x_base ? args.x_base[c0 + j] : 0.0;
-                const double d = xb + (double)xi[j] - args.x_ref[c0 + j];
-                e2 = fma(d, d, e2);
+            {
+                const TS *zslot = zr + ((p - 1) % ZR) * tau_r;
+                const int64_t la = lmax(ia, r0), lb = lmin(ib, r1);
+                for (int64_t l = la + gt; l < lb; l += XT) atomicAdd(accp + (l - ia), zslot[l - ia]);
             }
-            e2 = warp_sum(e2);
-            double *dred = reinterpret_cast<double *>(red);
-            __syncthreads();
-            if ((tid & 31) == 0) dred[tid >> 5] = e2;
-            __syncthreads();
-            if (tid == 0) {
-                double s = 0.0;
-                for (int q = 0; q < kWarps; ++q) s += dred[q];
-                atomicAdd(accw + args.tau_c + args.tau_r, (TS)s);
+            // stopping-test partial for x^{p-1}
+            const bool due = check && p >= 2 && (args.check_offset + p - 1) % args.check_every == 0;
+            if (due) {
+                double e2 = 0.0;
+                for (int j = gt; j < ncol; j += XT) {
+                    const double xb = args.x_base ? args.x_base[c0 + j] : 0.0;
+                    const double d = xb + (double)xi[j] - args.x_ref[c0 + j];
+                    e2 = fma(d, d, e2);
+                }
+                e2 = warp_sum(e2);
+                double *dred = reinterpret_cast<double *>(redx);
+                if ((gt & 31) == 0) dred[gt >> 5] = e2;
+                xsync();
+                if (gt == 0) {
+                    double s = 0.0;
+                    for (int q = 0; q < kXWarps; ++q) s += dred[q];
+                    atomicAdd(accp + tau_r, (TS)s);
+                }
             }
-        }
+            if (cta == 0) {  // clear the set read two steps ahead
+                TS *accz = accr_base + ((p + 1) % 3) * accset;
+                for (int64_t e = gt; e < accset; e += XT) accz[e] = tzero<TS>();
+            }
+            xsync();
+            if (gt == 0) {
+                mbar_arrive(&zempty[(p - 1) % ZR]);
+                red_release_gpu_add(args.bar_x, 1u);
+                const int code = lead_poll(
+                    [&] { return ld_acquire_gpu(args.bar_x) >= (unsigned)G * (unsigned)p; }, quit_x,
+                    args.timeout_ns);
+                if (code == 6) give_up(6);
+                xf[0] = code;
+            }
+            xsync();
+            if (xf[0] != 0) {
+                done = p - 1;
+                break;
+            }
 
-        // clear the set used two phases ahead
-        if (cta == 0) {
-            TS *accz = accbase + ((p + 1) % 3) * accset;
-            for (int64_t q = tid; q < accset; q += kThreads) accz[q] = tzero<TS>();
+            // r^p = sum of the replicas; stopping test on x^{p-1}
+            const int hr = (int)(ib - ia);
+            const TS *accq = accr_base + (p % 3) * accset;
+            for (int t = gt; t < hr; t += XT) {
+                const TS *q0 = accq + t;
+                const TS a0 = ld_cg_t(q0), a1 = ld_cg_t(q0 + aw), a2 = ld_cg_t(q0 + 2 * aw),
+                         a3 = ld_cg_t(q0 + 3 * aw);
+                const TS sum = (a0 + a1) + (a2 + a3);
+                rr[t] = sum;
+                if (!finite_val(sum)) xf[3] = 1;
+            }
+            if (gt == XT - 1) {
+                int code = 0;
+                if (due) {
+                    TS e2 = tzero<TS>();
+                    for (int q = 0; q < kAccReplicas; ++q) e2 += ld_cg_t(accq + (int64_t)q * aw + tau_r);
+                    if ((double)e2 <= args.tol2_abs) code = 1;
+                }
+                xf[1] = code;
+            }
+            xsync();
+            if (xf[1] == 1) {  // x^{p-1} passed: the x chain stops, the z chain completes step p + kZRing
+                done = p - 1;
+                if (gt == 0) {
+                    st_vol(&ctl[1], (int)p);
+                    __threadfence_block();
+                    atomicCAS(&ctl[0], 0, 1);
+                }
+                break;
+            }
+            if (xf[3] != 0) {
+                done = p - 1;
+                if (gt == 0) give_up(5);
+                break;
+            }
+            // x^p on own columns (+ dual v on own rows of I_p)
+            const TS cI = ring_ci[p % kRing];
+            {
+                int64_t ld;
+                const TA *T = rtile(p, ia, &ld);
+                col_sums<XT, TA, TS, TMA>(gt, T, ld, ia, ib, c0, c1, rr, redx, xsync,
+                                          [&](int64_t col, TS v) { xi[col - c0] -= cI * v; });
+            }
+            if (CORR) {
+                const int64_t la = lmax(ia, r0), lb = lmin(ib, r1);
+                for (int64_t l = la + gt; l < lb; l += XT) v_own[l - r0] -= cI * rr[l - ia];
+            }
+            xsync();
+            // row tile of I_p is used up: its buffer takes I_{p+2}
+            issue_row(p + 2);
+            prefetch_row(p + 2);
         }
-        if (!grid_barrier(args.bar, (unsigned)G * (unsigned)(p + 1), args.status, args.timeout_ns,
-                          &flags[0])) {
-            drain();
-            return;
+        if (TMA) {
+            wait_row(0);
+            wait_row(1);
         }
-    }
-    drain();
-
-    // ---- write back the owned slices ----
-    for (int i = tid; i < nrow; i += kThreads) {
-        gz[r0 + i] = zeta[i];
-        if (CORR) gv_dual[r0 + i] = v_own[i];
-    }
-    for (int j = tid; j < ncol; j += kThreads) {
-        gx[c0 + j] = xi[j];
-        if (CORR) gs_dual[c0 + j] = s_own[j];
-    }
-    if (cta == 0 && tid == 0) {
-        *args.iters_done = done;
-        if (stop_code == 5) atomicExch(args.status, 5);
+        for (int j = gt; j < ncol; j += XT) gx[c0 + j] = xi[j];
+        if (CORR)
+            for (int i = gt; i < nrow; i += XT) gv_dual[r0 + i] = v_own[i];
+        if (cta == 0 && gt == 0) *args.iters_done = done;
     }
 }
 

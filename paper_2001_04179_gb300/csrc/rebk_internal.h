@@ -12,7 +12,12 @@ namespace rebk {
 
 constexpr int kThreads = 512;              // threads per CTA of the persistent kernel
 constexpr int kWarps = kThreads / 32;
+constexpr int kZWarps = 4;                 // warps of the column-step (z) chain
+constexpr int kXWarps = kWarps - kZWarps;  // warps of the row-step (x) chain
+constexpr int kZThreads = kZWarps * 32, kXThreads = kXWarps * 32;
+constexpr int kZRing = 4;                  // z_I hand-over slots between the two chains
 constexpr int kRing = 8;                   // block indices kept ahead / behind
+constexpr size_t kSmemHeader = 512;        // index rings, flags, mbarriers, step coefficients
 constexpr int kAccReplicas = 4;            // replicated accumulators (atomic contention)
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s per wait
 constexpr int64_t kMaxItersPerLaunch = 8000000;                 // barrier counter headroom
@@ -46,7 +51,7 @@ struct GridArgs {
     int64_t check_every;    // test x^k when (check_offset + k) % check_every == 0
     int64_t check_offset;
     const int32_t *idx;     // 2 * iters entries: (j_k, i_k), from sample_blocks()
-    void *acc;              // TS [3][acc_r][acc_w], zeroed before launch
+    void *acc;              // TS [2 chains][3 sets][acc_r][acc_w], zeroed before launch
     int acc_w, acc_r;
     int nrow_cap, ncol_cap; // shared-memory capacity for the owned slices
     int use_tma;            // tiles staged in shared memory by TMA
@@ -55,7 +60,8 @@ struct GridArgs {
     int bw_r;               // row-tile box width (height tau_r)
     int64_t tile_c_bytes, tile_r_bytes;        // shared-memory size of a tile (128-aligned)
     int64_t tile_c_bytes_tx, tile_r_bytes_tx;  // bytes a tile's copies deliver
-    unsigned int *bar;      // barrier counter, zeroed before launch
+    unsigned int *bar;      // barrier counter of the column-step chain, zeroed before launch
+    unsigned int *bar_x;    // barrier counter of the row-step chain, zeroed before launch
     int *status;            // zeroed before launch
     int64_t *iters_done;
     unsigned long long timeout_ns;
@@ -65,7 +71,7 @@ enum class Mode { PlainF64, CorrF32, CorrBF16 };
 
 // Shared-memory layout of the persistent kernel (byte offsets, 16-byte aligned).
 struct SmemLayout {
-    size_t ringc, zeta, beta, v, xi, s, w, r, red, tc0, tc1, tr0, tr1, total;
+    size_t zeta, beta, v, xi, s, w, r, zr, redz, redx, tc0, tc1, tr0, tr1, total;
 };
 
 __host__ __device__ inline SmemLayout smem_layout(int nrow_cap, int ncol_cap, int tau_r, int tau_c,
@@ -74,12 +80,11 @@ __host__ __device__ inline SmemLayout smem_layout(int nrow_cap, int ncol_cap, in
     auto al = [](size_t x) { return (x + 15) & ~(size_t)15; };
     auto al128 = [](size_t x) { return (x + 127) & ~(size_t)127; };
     SmemLayout L;
-    size_t o = 128;  // block-index ring, flags, two mbarriers
+    size_t o = kSmemHeader;
     L.tc0 = o; o = al128(o + (size_t)tile_c_bytes);
     L.tc1 = o; o = al128(o + (size_t)tile_c_bytes);
     L.tr0 = o; o = al128(o + (size_t)tile_r_bytes);
     L.tr1 = o; o = al128(o + (size_t)tile_r_bytes);
-    L.ringc = o; o = al(o + (size_t)2 * kRing * ts);  // step coefficients of the ring
     L.zeta = o; o = al(o + (size_t)nrow_cap * ts);
     L.beta = o; o = al(o + (size_t)nrow_cap * ts);
     L.v = o;    if (corr) o = al(o + (size_t)nrow_cap * ts);
@@ -87,10 +92,12 @@ __host__ __device__ inline SmemLayout smem_layout(int nrow_cap, int ncol_cap, in
     L.s = o;    if (corr) o = al(o + (size_t)ncol_cap * ts);
     L.w = o;    o = al(o + (size_t)tau_c * ts);
     L.r = o;    o = al(o + (size_t)tau_r * ts);
-    L.red = o;
-    size_t red = (size_t)kThreads * vec * ts;
-    if (red < (size_t)kWarps * 8) red = (size_t)kWarps * 8;
-    o = al(o + red);
+    L.zr = o;   o = al(o + (size_t)kZRing * tau_r * ts);
+    size_t rz = (size_t)kZThreads * vec * ts, rx = (size_t)kXThreads * vec * ts;
+    if (rz < (size_t)kZWarps * 8) rz = (size_t)kZWarps * 8;
+    if (rx < (size_t)kXWarps * 8) rx = (size_t)kXWarps * 8;
+    L.redz = o; o = al(o + rz);
+    L.redx = o; o = al(o + rx);
     L.total = o;
     return L;
 }

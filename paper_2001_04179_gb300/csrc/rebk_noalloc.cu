@@ -45,8 +45,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocBytes];
 std::mutex g_noalloc_mutex;
 void *g_noalloc_ptr[kNoallocMaxDevices] = {nullptr};
 
-struct NoallocWorkspace {  // barrier counter, status word, iterations run
+struct NoallocWorkspace {  // barrier counters, status word, iterations run
     unsigned int bar;
+    unsigned int bar_x;
     int status;
     int64_t iters_done;
 };
@@ -99,7 +100,7 @@ extern "C" rebk_status rebk_solve_noalloc(const double *A, int64_t m, int64_t n,
     // ---- carve the scratch array ----
     const int64_t ldp = (n + 63) / 64 * 64;  // padded leading dimension of the copy
     const int s = (int)((m + tr - 1) / tr), t = (int)((n + tc - 1) / tc);
-    const int acc_w = (int)((tc + tr + 1 + 31) / 32 * 32);
+    const int acc_w = (int)((std::max(tc, tr + 1) + 31) / 32 * 32);
     size_t off = 0;
     auto take = [&](size_t bytes) {
         const size_t o = off;
@@ -113,7 +114,7 @@ extern "C" rebk_status rebk_solve_noalloc(const double *A, int64_t m, int64_t n,
     const size_t ocf32r = take(sizeof(float) * s), ocf32c = take(sizeof(float) * t);
     const size_t ofb = take(sizeof(int) * 2);
     const size_t oidx = take(sizeof(int32_t) * 2 * kNoallocIdxChunk);
-    const size_t oacc = take(sizeof(double) * 3 * kAccReplicas * (size_t)acc_w);
+    const size_t oacc = take(sizeof(double) * 6 * kAccReplicas * (size_t)acc_w);
     const size_t ows = take(sizeof(NoallocWorkspace));
     const size_t otab = take(sizeof(double) * (size_t)(m + n + 64 * n));  // norm-table scratch
     if (off > kNoallocBytes)
@@ -189,6 +190,7 @@ extern "C" rebk_status rebk_solve_noalloc(const double *A, int64_t m, int64_t n,
     a.acc_w = acc_w;
     a.acc_r = kAccReplicas;
     a.bar = &ws->bar;
+    a.bar_x = &ws->bar_x;
     a.status = &ws->status;
     a.iters_done = &ws->iters_done;
     a.timeout_ns = kBarrierTimeoutNs;
@@ -215,7 +217,7 @@ extern "C" rebk_status rebk_solve_noalloc(const double *A, int64_t m, int64_t n,
         a.k0 = done;
         a.iters = chunk;
         // what has to start at zero: accumulators, barrier counter, status
-        NA_CK(cudaMemsetAsync(acc, 0, sizeof(double) * 3 * kAccReplicas * (size_t)acc_w, st));
+        NA_CK(cudaMemsetAsync(acc, 0, sizeof(double) * 6 * kAccReplicas * (size_t)acc_w, st));
         NA_CK(cudaMemsetAsync(ws, 0, sizeof(NoallocWorkspace), st));
         NA_CK(launch_grid(Mode::PlainF64, a, G, st));
         NoallocWorkspace w;
