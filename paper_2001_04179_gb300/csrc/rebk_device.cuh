@@ -81,6 +81,9 @@ template <> struct VecIO<double, double> {
     __device__ __forceinline__ static void load_shared(uint32_t a, double (&o)[2]) {
         asm volatile("ld.shared.v2.f64 {%0, %1}, [%2];" : "=d"(o[0]), "=d"(o[1]) : "r"(a));
     }
+    // the V arithmetic-type values that pair with one stored vector
+    __device__ __forceinline__ static void load_shared_ts(uint32_t a, double (&o)[2]) { load_shared(a, o); }
+    __device__ __forceinline__ static void zero(double (&o)[2]) { o[0] = o[1] = 0.0; }
 };
 
 template <> struct VecIO<float, float> {
@@ -97,6 +100,8 @@ template <> struct VecIO<float, float> {
         asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
                      : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]) : "r"(a));
     }
+    __device__ __forceinline__ static void load_shared_ts(uint32_t a, float (&o)[4]) { load_shared(a, o); }
+    __device__ __forceinline__ static void zero(float (&o)[4]) { o[0] = o[1] = o[2] = o[3] = 0.f; }
 };
 
 template <> struct VecIO<__nv_bfloat16, float> {
@@ -120,6 +125,16 @@ template <> struct VecIO<__nv_bfloat16, float> {
         asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
                      : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
         unpack(v, o);
+    }
+    __device__ __forceinline__ static void load_shared_ts(uint32_t a, float (&o)[8]) {
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]) : "r"(a));
+        asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                     : "=f"(o[4]), "=f"(o[5]), "=f"(o[6]), "=f"(o[7]) : "r"(a + 16u));
+    }
+    __device__ __forceinline__ static void zero(float (&o)[8]) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) o[i] = 0.f;
     }
 };
 

@@ -86,14 +86,63 @@ __device__ __forceinline__ TS group_reduce4(TS (&acc)[4], int gs, int sub, int *
     return k;
 }
 
+// Vector loads of V arithmetic-type values from shared memory (16-byte aligned).
+__device__ __forceinline__ void lds_vec(const float *p, float (&t)[4]) {
+    const float4 f = *reinterpret_cast<const float4 *>(p);
+    t[0] = f.x; t[1] = f.y; t[2] = f.z; t[3] = f.w;
+}
+__device__ __forceinline__ void lds_vec(const float *p, float (&t)[8]) {
+    const float4 f = *reinterpret_cast<const float4 *>(p), g = *reinterpret_cast<const float4 *>(p + 4);
+    t[0] = f.x; t[1] = f.y; t[2] = f.z; t[3] = f.w;
+    t[4] = g.x; t[5] = g.y; t[6] = g.z; t[7] = g.w;
+}
+__device__ __forceinline__ void lds_vec(const double *p, double (&t)[2]) {
+    const double2 f = *reinterpret_cast<const double2 *>(p);
+    t[0] = f.x; t[1] = f.y;
+}
+
+// Four consecutive atomic adds into global memory: one vector reduction when the
+// address is 16-byte aligned (FP32), else four scalar ones.
+__device__ __forceinline__ void red_add4(float *p, float a, float b, float c, float d) {
+    if ((reinterpret_cast<uintptr_t>(p) & 15u) == 0u) {
+        asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+                     : "memory");
+    } else {
+        atomicAdd(p, a);
+        atomicAdd(p + 1, b);
+        atomicAdd(p + 2, c);
+        atomicAdd(p + 3, d);
+    }
+}
+__device__ __forceinline__ void red_add4(double *p, double a, double b, double c, double d) {
+    atomicAdd(p, a);
+    atomicAdd(p + 1, b);
+    atomicAdd(p + 2, c);
+    atomicAdd(p + 3, d);
+}
+
+// Sum of the kAccReplicas replicas of one accumulator entry (fixed pairwise order).
+template <typename TS> __device__ __forceinline__ TS sum_replicas(const TS *p, int aw) {
+    TS v[kAccReplicas];
+#pragma unroll
+    for (int q = 0; q < kAccReplicas; ++q) v[q] = ld_cg_t(p + (int64_t)q * aw);
+#pragma unroll
+    for (int h = kAccReplicas / 2; h > 0; h >>= 1)
+#pragma unroll
+        for (int q = 0; q < h; ++q) v[q] += v[q + h];
+    return v[0];
+}
+
 // out(row) = sum_{c in [ca, cb)} A[row, c] * vin[c - ca] for rows [ra, rb), by
 // a group of NT threads (gt = thread index in the group).  A addresses element
-// (r, c) at A + r * lda + c.  Rows go to lane groups of gs lanes (gs = power of
-// two >= the number of 16-byte vectors of the range, at most 32); each lane
-// group handles 4 rows per pass.
-template <int NT, typename TA, typename TS, bool SM, typename Emit>
+// (r, c) at A + r * lda + c.  Rows go to lane groups of gs lanes (gs in 4..32,
+// chosen to minimise passes x vector loads per lane, then passes); each lane
+// group handles 4 consecutive rows per pass and hands them to emit4(r, v0..v3)
+// from one lane (emit(r, v) for the rows of an incomplete quad).
+template <int NT, typename TA, typename TS, bool SM, typename Emit, typename Emit4>
 __device__ __forceinline__ void row_dots(int gt, const TA *A, int64_t lda, int64_t ra, int64_t rb,
-                                         int64_t ca, int64_t cb, const TS *__restrict__ vin, Emit emit) {
+                                         int64_t ca, int64_t cb, const TS *__restrict__ vin, Emit emit,
+                                         Emit4 emit4) {
     using IO = VecIO<TA, TS>;
     constexpr int V = IO::V;
     constexpr int U = 4;
@@ -101,14 +150,29 @@ __device__ __forceinline__ void row_dots(int gt, const TA *A, int64_t lda, int64
     if (rb <= ra || cb <= ca) return;
     const int64_t va = ca / V, vb = (cb + V - 1) / V;
     const int nv = (int)(vb - va);
-    int gs = 1;
-    while (gs < nv && gs < 32) gs <<= 1;
+    const int nr = (int)(rb - ra);
+    int gs = 4;
+    {
+        int best = 0x7fffffff;
+#pragma unroll
+        for (int lc = 2; lc <= 5; ++lc) {  // gs = 1 << lc; divisions by constants only
+            const int c = 1 << lc;
+            const int rows_per_pass = NW * (32 >> lc) * U;
+            const int passes = (nr + rows_per_pass - 1) / rows_per_pass;
+            const int cost = passes * (((nv + c - 1) >> lc) * 8 + 1);
+            if (cost < best) {
+                best = cost;
+                gs = c;
+            }
+        }
+    }
     const int lane = gt & 31, warp = gt >> 5;
     const int sub = lane & (gs - 1);
     const int gpw = 32 / gs;
     const int g = warp * gpw + lane / gs;
     const int NG = NW * gpw;
     for (int64_t base = ra; base < rb; base += (int64_t)NG * U) {
+        const int64_t rq = base + (int64_t)U * g;  // this lane group's quad
         TS acc[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) acc[u] = tzero<TS>();
@@ -124,7 +188,7 @@ __device__ __forceinline__ void row_dots(int gt, const TA *A, int64_t lda, int64
             TS a[U][V];
 #pragma unroll
             for (int u = 0; u < U; ++u) {
-                const int64_t r = base + g + (int64_t)u * NG;
+                const int64_t r = rq + u;
                 if (vi < nv && r < rb) {
                     vload<TA, TS, SM>(A + r * lda + col0, a[u]);
                 } else {
@@ -137,18 +201,22 @@ __device__ __forceinline__ void row_dots(int gt, const TA *A, int64_t lda, int64
 #pragma unroll
                 for (int e = 0; e < V; ++e) acc[u] = fma(a[u][e], xv[e], acc[u]);
         }
-        if (gs >= 4) {
+        {
             int ru = 0;
             const TS v = group_reduce4<TS>(acc, gs, sub, &ru);
-            const int64_t r = base + g + (int64_t)ru * NG;
-            if ((sub & ((gs >> 2) - 1)) == 0 && r < rb) emit(r, v);
-        } else {
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                TS v = acc[u];
-                for (int o = gs >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-                const int64_t r = base + g + (int64_t)u * NG;
-                if (sub == 0 && r < rb) emit(r, v);
+            // lanes sub = 0, gs/4, gs/2, 3gs/4 hold rows rq + 0, 1, 2, 3
+            const int q4 = gs >> 2;
+            const TS v1 = __shfl_down_sync(0xffffffffu, v, q4);
+            const TS v2 = __shfl_down_sync(0xffffffffu, v, 2 * q4);
+            const TS v3 = __shfl_down_sync(0xffffffffu, v, 3 * q4);
+            if (sub == 0) {
+                if (rq + 3 < rb) {
+                    emit4(rq, v, v1, v2, v3);
+                } else {
+                    if (rq < rb) emit(rq, v);
+                    if (rq + 1 < rb) emit(rq + 1, v1);
+                    if (rq + 2 < rb) emit(rq + 2, v2);
+                }
             }
         }
     }
@@ -157,11 +225,13 @@ __device__ __forceinline__ void row_dots(int gt, const TA *A, int64_t lda, int64
 // out(col) = sum_{r in [ra, rb)} A[r, col] * vrow[r - ra] for columns [ca, cb),
 // by a group of NT threads synchronised by sync().  Threads are laid out as
 // (vector index, row group); each thread sums its vector over its rows, then the
-// row groups are added through shared memory (red: NT * V elements).
-template <int NT, typename TA, typename TS, bool SM, typename Sync, typename Emit>
+// row groups are added through shared memory (red: NT * V elements), one thread
+// per vector, which hands each quad of columns inside [ca, cb) to
+// emit4(col, v0..v3) and the other columns to emit(col, v).
+template <int NT, typename TA, typename TS, bool SM, typename Sync, typename Emit, typename Emit4>
 __device__ __forceinline__ void col_sums(int gt, const TA *A, int64_t lda, int64_t ra, int64_t rb,
                                          int64_t ca, int64_t cb, const TS *__restrict__ vrow, TS *red,
-                                         Sync sync, Emit emit) {
+                                         Sync sync, Emit emit, Emit4 emit4) {
     using IO = VecIO<TA, TS>;
     constexpr int V = IO::V;
     constexpr int U = 4;
@@ -201,13 +271,164 @@ __device__ __forceinline__ void col_sums(int gt, const TA *A, int64_t lda, int64
             for (int e = 0; e < V; ++e) red[rg * (nvc * V) + vi * V + e] = acc[e];
         }
         sync();
-        for (int c = gt; c < nvc * V; c += NT) {
-            const int64_t col = (va + vc0) * V + c;
-            if (col >= ca && col < cb) {
-                TS sum = tzero<TS>();
-                for (int q = 0; q < NRG; ++q) sum += red[q * (nvc * V) + c];
-                emit(col, sum);
+        for (int c = gt; c < nvc; c += NT) {
+            TS sum[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e) sum[e] = tzero<TS>();
+            for (int q = 0; q < NRG; ++q) {
+                TS t[V];
+                lds_vec(red + q * (nvc * V) + c * V, t);
+#pragma unroll
+                for (int e = 0; e < V; ++e) sum[e] += t[e];
             }
+            const int64_t col0 = (va + vc0 + c) * V;
+#pragma unroll
+            for (int e4 = 0; e4 < V; e4 += 4) {
+                if (V >= 4 && col0 + e4 >= ca && col0 + e4 + 3 < cb) {
+                    emit4(col0 + e4, sum[e4], sum[(e4 + 1) % V], sum[(e4 + 2) % V], sum[(e4 + 3) % V]);
+                } else {
+#pragma unroll
+                    for (int e = e4; e < e4 + 4 && e < V; ++e) {
+                        const int64_t col = col0 + e;
+                        if (col >= ca && col < cb) emit(col, sum[e]);
+                    }
+                }
+            }
+        }
+        sync();
+    }
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+// ---------------------------------------------------------------------------
+// Shared-memory tile products (TMA path).  T: rows of ld elements, 16-byte
+// aligned, nvec 16-byte vectors per row; 32-bit shared addresses throughout.
+// ---------------------------------------------------------------------------
+
+// out(l) = sum_{t < nvec * V} T[l * ld + t] * vin[t] for rows l in [0, rows);
+// vin holds nvec * V values (zero where the tile has no column of the range).
+// Lane groups of gs lanes take 4 consecutive rows; emit4(l, v0..v3) for full
+// quads, emit(l, v) for the rows of the last, incomplete one.
+template <int NT, typename TA, typename TS, typename Emit, typename Emit4>
+__device__ __forceinline__ void tile_rowdot(int gt, const TA *T, int ld, int rows, int nvec,
+                                            const TS *vin, Emit emit, Emit4 emit4) {
+    using IO = VecIO<TA, TS>;
+    constexpr int V = IO::V;
+    constexpr int NW = NT / 32;
+    if (rows <= 0 || nvec <= 0) return;
+    int gs = 4;
+    {
+        int best = 0x7fffffff;
+#pragma unroll
+        for (int lc = 2; lc <= 5; ++lc) {
+            const int rows_per_pass = NW * (32 >> lc) * 4;
+            const int passes = (rows + rows_per_pass - 1) / rows_per_pass;
+            const int cost = passes * ((((nvec + (1 << lc) - 1) >> lc)) * 8 + 1);
+            if (cost < best) {
+                best = cost;
+                gs = 1 << lc;
+            }
+        }
+    }
+    const int lane = gt & 31, warp = gt >> 5;
+    const int sub = lane & (gs - 1);
+    const int g = warp * (32 / gs) + lane / gs;
+    const int NG = NW * (32 / gs);
+    const uint32_t row_bytes = (uint32_t)ld * (uint32_t)sizeof(TA);
+    const uint32_t tb = smem_u32(T), vb = smem_u32(vin);
+    // the pass loop is uniform over the warp (every lane takes part in the shuffles)
+    for (int base = 0; base < rows; base += 4 * NG) {
+        const int rq = base + 4 * g;
+        const bool ok0 = rq < rows, ok1 = rq + 1 < rows, ok2 = rq + 2 < rows, ok3 = rq + 3 < rows;
+        TS acc0 = tzero<TS>(), acc1 = tzero<TS>(), acc2 = tzero<TS>(), acc3 = tzero<TS>();
+        uint32_t a = tb + (uint32_t)rq * row_bytes + (uint32_t)sub * 16u;
+        uint32_t xa = vb + (uint32_t)sub * (uint32_t)(V * sizeof(TS));
+#pragma unroll 2
+        for (int vi = ok0 ? sub : nvec; vi < nvec; vi += gs) {
+            TS xv[V], t0[V], t1[V], t2[V], t3[V];
+            IO::load_shared_ts(xa, xv);
+            IO::load_shared(a, t0);
+            if (ok1) IO::load_shared(a + row_bytes, t1); else IO::zero(t1);
+            if (ok2) IO::load_shared(a + 2 * row_bytes, t2); else IO::zero(t2);
+            if (ok3) IO::load_shared(a + 3 * row_bytes, t3); else IO::zero(t3);
+#pragma unroll
+            for (int e = 0; e < V; ++e) {
+                acc0 = fma(t0[e], xv[e], acc0);
+                acc1 = fma(t1[e], xv[e], acc1);
+                acc2 = fma(t2[e], xv[e], acc2);
+                acc3 = fma(t3[e], xv[e], acc3);
+            }
+            a += (uint32_t)gs * 16u;
+            xa += (uint32_t)(gs * V * sizeof(TS));
+        }
+        TS acc[4] = {acc0, acc1, acc2, acc3};
+        int ru = 0;
+        const TS v = group_reduce4<TS>(acc, gs, sub, &ru);
+        const int q4 = gs >> 2;
+        const TS v1 = __shfl_down_sync(0xffffffffu, v, q4);
+        const TS v2 = __shfl_down_sync(0xffffffffu, v, 2 * q4);
+        const TS v3 = __shfl_down_sync(0xffffffffu, v, 3 * q4);
+        if (sub == 0 && ok0) {
+            if (ok3) {
+                emit4(rq, v, v1, v2, v3);
+            } else {
+                emit(rq, v);
+                if (ok1) emit(rq + 1, v1);
+                if (ok2) emit(rq + 2, v2);
+            }
+        }
+    }
+}
+
+// out(vector t) = sum_{l < rows} T[l * ld + t * V + e] * vrow[l], e < V, for the
+// nvec vectors t of a row, by a group of NT threads synchronised by sync();
+// threads are (vector, row group) pairs whose partial sums meet in red (NT * V
+// values).  emitv(t, sum[V]) once per vector.
+template <int NT, typename TA, typename TS, typename Sync, typename EmitV>
+__device__ __forceinline__ void tile_colsum(int gt, const TA *T, int ld, int rows, int nvec,
+                                            const TS *vrow, TS *red, Sync sync, EmitV emitv) {
+    using IO = VecIO<TA, TS>;
+    constexpr int V = IO::V;
+    if (rows <= 0 || nvec <= 0) return;
+    const uint32_t row_bytes = (uint32_t)ld * (uint32_t)sizeof(TA);
+    const uint32_t tb = smem_u32(T);
+    for (int vc0 = 0; vc0 < nvec; vc0 += NT) {
+        const int nvc = min(NT, nvec - vc0);
+        const int NRG = NT / nvc;
+        const int vi = gt % nvc, rg = gt / nvc;
+        if (rg < NRG) {
+            TS acc[V];
+#pragma unroll
+            for (int e = 0; e < V; ++e) acc[e] = tzero<TS>();
+            uint32_t a = tb + (uint32_t)rg * row_bytes + (uint32_t)(vc0 + vi) * 16u;
+            const uint32_t step = (uint32_t)NRG * row_bytes;
+#pragma unroll 4
+            for (int l = rg; l < rows; l += NRG) {
+                TS t[V];
+                IO::load_shared(a, t);
+                const TS xr = vrow[l];
+#pragma unroll
+                for (int e = 0; e < V; ++e) acc[e] = fma(t[e], xr, acc[e]);
+                a += step;
+            }
+            TS *dst = red + (rg * nvc + vi) * V;
+#pragma unroll
+            for (int e = 0; e < V; ++e) dst[e] = acc[e];
+        }
+        sync();
+        for (int c = gt; c < nvc; c += NT) {
+            TS sum[V];
+            lds_vec(red + c * V, sum);
+            for (int q = 1; q < NRG; ++q) {
+                TS t[V];
+                lds_vec(red + (q * nvc + c) * V, t);
+#pragma unroll
+                for (int e = 0; e < V; ++e) sum[e] += t[e];
+            }
+            emitv(vc0 + c, sum);
         }
         sync();
     }
@@ -224,10 +445,6 @@ __device__ __forceinline__ void named_sync(int id, int nthreads) {
 
 __device__ __forceinline__ int ld_vol(const int *p) { return *reinterpret_cast<const volatile int *>(p); }
 __device__ __forceinline__ void st_vol(int *p, int v) { *reinterpret_cast<volatile int *>(p) = v; }
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
 
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -381,6 +598,9 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
         xi[j] = gx[c0 + j];
         if (CORR) s_own[j] = gs_dual[c0 + j];
     }
+    // x is read over whole row-tile rows: zero beyond the owned columns
+    const int xpad = (args.ncol_cap + 7) / 8 * 8;
+    for (int j = ncol + tid; j < xpad; j += kThreads) xi[j] = tzero<TS>();
     if (tid == 0) {
         for (int64_t k = 1; k <= 4 && k <= K; ++k) {
             const int j = __ldg(idx + 2 * (k - 1)), i = __ldg(idx + 2 * (k - 1) + 1);
@@ -413,6 +633,13 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
     TS *accw_base = static_cast<TS *>(args.acc);   // w partials: 3 sets
     TS *accr_base = accw_base + 3 * accset;        // r partials (+ test partial at tau_r): 3 sets
     const bool check = args.x_ref != nullptr && args.check_every > 0;
+    // column tiles start exactly at their block (tau_c a multiple of the 16-byte vector)
+    const bool fast_c = TMA && args.bw_c == args.tau_c;
+    const int wpad = (args.tau_c + 7) / 8 * 8;
+    // Any CTA past the arrivals of step q may clear a set that step q + 1 fills:
+    // every CTA has read it (step q - 1) before arriving, and nobody adds to it
+    // before every CTA has arrived once more.  Each CTA clears a 1/G share.
+    const int64_t clr0 = accset * cta / G, clr1 = accset * (cta + 1) / G;
 
     auto col_range = [&](int j, int64_t *a, int64_t *b) {
         *a = (int64_t)j * args.tau_c;
@@ -476,7 +703,7 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
             const int b = (int)(q & 1);
             int64_t ja, jb;
             col_range(ring_j[q % kRing], &ja, &jb);
-            const int x0 = (int)(ja / args.tma_vx * args.tma_vx);
+            const int x0 = (int)(ja & ~(int64_t)(args.tma_vx - 1));  // tma_vx is 4 or 8
             if (b) { xc1 = x0; cpend1 = true; } else { xc0 = x0; cpend0 = true; }
             if (gt == 0) {
                 fence_proxy_async();
@@ -518,9 +745,31 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
         auto partial_w = [&](int64_t q, TS *accp) {  // over own rows, column block J_q, with zeta
             int64_t ja, jb, ld;
             col_range(ring_j[q % kRing], &ja, &jb);
+            if constexpr (TMA) {
+                if (fast_c) {
+                    const int wc = (int)(jb - ja);
+                    tile_colsum<ZT, TA, TS>(gt, tile_c((int)(q & 1)), args.bw_c, nrow, args.bw_c / V, zeta, redz,
+                                            zsync, [&](int t, const TS(&sum)[V]) {
+#pragma unroll
+                                                for (int e4 = 0; e4 < V; e4 += 4) {
+                                                    const int c = t * V + e4;
+                                                    if (c + 3 < wc) {
+                                                        red_add4(accp + c, sum[e4], sum[e4 + 1], sum[e4 + 2],
+                                                                 sum[e4 + 3]);
+                                                    } else {
+                                                        for (int e = 0; e < 4; ++e)
+                                                            if (c + e < wc) atomicAdd(accp + c + e, sum[e4 + e]);
+                                                    }
+                                                }
+                                            });
+                    return;
+                }
+            }
             const TA *T = ctile(q, &ld);
-            col_sums<ZT, TA, TS, TMA>(gt, T, ld, r0, r1, ja, jb, zeta, redz, zsync,
-                                      [&](int64_t col, TS v) { atomicAdd(accp + (col - ja), v); });
+            col_sums<ZT, TA, TS, TMA>(
+                gt, T, ld, r0, r1, ja, jb, zeta, redz, zsync,
+                [&](int64_t col, TS v) { atomicAdd(accp + (col - ja), v); },
+                [&](int64_t col, TS v0, TS v1, TS v2, TS v3) { red_add4(accp + (col - ja), v0, v1, v2, v3); });
         };
         // stop signal for the z chain at step q: 5 / 6 at once; after a converged
         // stop of the x chain at step p, once q > min(K, p + kZRing)
@@ -573,11 +822,12 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
             col_range(jq, &ja, &jb);
             const int wc = (int)(jb - ja);
             const TS *accq = accw_base + ((q - 1) % 3) * accset;
-            for (int t = gt; t < wc; t += ZT) {
-                const TS *q0 = accq + t;
-                const TS a0 = ld_cg_t(q0), a1 = ld_cg_t(q0 + aw), a2 = ld_cg_t(q0 + 2 * aw),
-                         a3 = ld_cg_t(q0 + 3 * aw);
-                TS sum = (a0 + a1) + (a2 + a3);
+            for (int t = gt; t < wpad; t += ZT) {
+                if (t >= wc) {  // the z update reads w over whole tile rows
+                    w[t] = tzero<TS>();
+                    continue;
+                }
+                TS sum = sum_replicas(accq + t, aw);
                 if (CORR) sum += (TS)args.gamma[ja + t];
                 w[t] = sum;
                 if (!finite_val(sum)) zf[1] = 1;
@@ -593,13 +843,32 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
             row_range(ring_zi[q % kRing], &ia, &ib);
             TS *zslot = zr + ((q - 1) % ZR) * tau_r;
             {
-                int64_t ld;
-                const TA *T = ctile(q, &ld);
-                row_dots<ZT, TA, TS, TMA>(gt, T, ld, r0, r1, ja, jb, w, [&](int64_t row, TS v) {
+                auto upd = [&](int64_t row, TS v) {
                     const TS nz = zeta[row - r0] - cJ * v;
                     zeta[row - r0] = nz;
                     if (row >= ia && row < ib) zslot[row - ia] = nz - beta_own[row - r0];
-                });
+                };
+                auto upd4 = [&](int64_t row, TS v0, TS v1, TS v2, TS v3) {
+                    upd(row, v0);
+                    upd(row + 1, v1);
+                    upd(row + 2, v2);
+                    upd(row + 3, v3);
+                };
+                bool done_fast = false;
+                if constexpr (TMA) {
+                    if (fast_c) {
+                        tile_rowdot<ZT, TA, TS>(
+                            gt, tile_c((int)(q & 1)), args.bw_c, nrow, args.bw_c / V, w,
+                            [&](int l, TS v) { upd(r0 + l, v); },
+                            [&](int l, TS v0, TS v1, TS v2, TS v3) { upd4(r0 + l, v0, v1, v2, v3); });
+                        done_fast = true;
+                    }
+                }
+                if (!done_fast) {
+                    int64_t ld;
+                    const TA *T = ctile(q, &ld);
+                    row_dots<ZT, TA, TS, TMA>(gt, T, ld, r0, r1, ja, jb, w, upd, upd4);
+                }
             }
             if (CORR) {
                 const int64_t la = lmax(ja, c0), lb = lmin(jb, c1);
@@ -618,9 +887,9 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
                     break;
                 }
                 partial_w(q + 1, accw_base + (q % 3) * accset + (int64_t)rep * aw);
-                if (cta == 0) {  // clear the set read two steps ahead
+                {  // clear this CTA's share of the set read two steps ahead
                     TS *accz = accw_base + ((q + 1) % 3) * accset;
-                    for (int64_t e = gt; e < accset; e += ZT) accz[e] = tzero<TS>();
+                    for (int64_t e = clr0 + gt; e < clr1; e += ZT) accz[e] = tzero<TS>();
                 }
                 zsync();
                 if (gt == 0) red_release_gpu_add(args.bar, 1u);
@@ -710,6 +979,12 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
         };
 
         int64_t done = K;
+        // steps p whose partial carries the test of x^{p-1}: (check_offset + p - 1) % check_every == 0
+        int64_t to_test = 0;
+        if (check) {
+            const int64_t r = (args.check_offset + 1) % args.check_every;  // residue at p = 2
+            to_test = r == 0 ? 0 : args.check_every - r;                  // steps until the next test, from p = 2
+        }
         if (K >= 1) {
             issue_row(1);
             issue_row(2);
@@ -738,10 +1013,20 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
             row_range(ring_xi[p % kRing], &ia, &ib);
             TS *accp = accr_base + (p % 3) * accset + (int64_t)rep * aw;
             if (ncol > 0) {
-                int64_t ld;
-                const TA *T = rtile(p, ia, &ld);
-                row_dots<XT, TA, TS, TMA>(gt, T, ld, ia, ib, c0, c1, xi,
-                                          [&](int64_t row, TS v) { atomicAdd(accp + (row - ia), v); });
+                if constexpr (TMA) {
+                    tile_rowdot<XT, TA, TS>(
+                        gt, tile_r((int)(p & 1)), args.bw_r, (int)(ib - ia), args.bw_r / V, xi,
+                        [&](int l, TS v) { atomicAdd(accp + l, v); },
+                        [&](int l, TS v0, TS v1, TS v2, TS v3) { red_add4(accp + l, v0, v1, v2, v3); });
+                } else {
+                    int64_t ld;
+                    const TA *T = rtile(p, ia, &ld);
+                    row_dots<XT, TA, TS, TMA>(
+                        gt, T, ld, ia, ib, c0, c1, xi, [&](int64_t row, TS v) { atomicAdd(accp + (row - ia), v); },
+                        [&](int64_t row, TS v0, TS v1, TS v2, TS v3) {
+                            red_add4(accp + (row - ia), v0, v1, v2, v3);
+                        });
+                }
             }
             {
                 const TS *zslot = zr + ((p - 1) % ZR) * tau_r;
@@ -749,7 +1034,11 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
                 for (int64_t l = la + gt; l < lb; l += XT) atomicAdd(accp + (l - ia), zslot[l - ia]);
             }
             // stopping-test partial for x^{p-1}
-            const bool due = check && p >= 2 && (args.check_offset + p - 1) % args.check_every == 0;
+            bool due = false;
+            if (check && p >= 2) {
+                due = to_test == 0;
+                to_test = due ? args.check_every - 1 : to_test - 1;
+            }
             if (due) {
                 double e2 = 0.0;
                 for (int j = gt; j < ncol; j += XT) {
@@ -767,9 +1056,9 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
                     atomicAdd(accp + tau_r, (TS)s);
                 }
             }
-            if (cta == 0) {  // clear the set read two steps ahead
+            {  // clear this CTA's share of the set read two steps ahead
                 TS *accz = accr_base + ((p + 1) % 3) * accset;
-                for (int64_t e = gt; e < accset; e += XT) accz[e] = tzero<TS>();
+                for (int64_t e = clr0 + gt; e < clr1; e += XT) accz[e] = tzero<TS>();
             }
             xsync();
             if (gt == 0) {
@@ -791,18 +1080,14 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
             const int hr = (int)(ib - ia);
             const TS *accq = accr_base + (p % 3) * accset;
             for (int t = gt; t < hr; t += XT) {
-                const TS *q0 = accq + t;
-                const TS a0 = ld_cg_t(q0), a1 = ld_cg_t(q0 + aw), a2 = ld_cg_t(q0 + 2 * aw),
-                         a3 = ld_cg_t(q0 + 3 * aw);
-                const TS sum = (a0 + a1) + (a2 + a3);
+                const TS sum = sum_replicas(accq + t, aw);
                 rr[t] = sum;
                 if (!finite_val(sum)) xf[3] = 1;
             }
             if (gt == XT - 1) {
                 int code = 0;
                 if (due) {
-                    TS e2 = tzero<TS>();
-                    for (int q = 0; q < kAccReplicas; ++q) e2 += ld_cg_t(accq + (int64_t)q * aw + tau_r);
+                    const TS e2 = sum_replicas(accq + tau_r, aw);
                     if ((double)e2 <= args.tol2_abs) code = 1;
                 }
                 xf[1] = code;
@@ -824,11 +1109,26 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
             }
             // x^p on own columns (+ dual v on own rows of I_p)
             const TS cI = ring_ci[p % kRing];
-            {
+            if constexpr (TMA) {
+                tile_colsum<XT, TA, TS>(gt, tile_r((int)(p & 1)), args.bw_r, hr, args.bw_r / V, rr, redx, xsync,
+                                        [&](int t, const TS(&sum)[V]) {
+#pragma unroll
+                                            for (int e = 0; e < V; ++e) {
+                                                const int c = t * V + e;
+                                                if (c < ncol) xi[c] -= cI * sum[e];
+                                            }
+                                        });
+            } else {
                 int64_t ld;
                 const TA *T = rtile(p, ia, &ld);
-                col_sums<XT, TA, TS, TMA>(gt, T, ld, ia, ib, c0, c1, rr, redx, xsync,
-                                          [&](int64_t col, TS v) { xi[col - c0] -= cI * v; });
+                auto upd = [&](int64_t col, TS v) { xi[col - c0] -= cI * v; };
+                col_sums<XT, TA, TS, TMA>(gt, T, ld, ia, ib, c0, c1, rr, redx, xsync, upd,
+                                          [&](int64_t col, TS v0, TS v1, TS v2, TS v3) {
+                                              upd(col, v0);
+                                              upd(col + 1, v1);
+                                              upd(col + 2, v2);
+                                              upd(col + 3, v3);
+                                          });
             }
             if (CORR) {
                 const int64_t la = lmax(ia, r0), lb = lmin(ib, r1);

@@ -18,7 +18,7 @@ constexpr int kZThreads = kZWarps * 32, kXThreads = kXWarps * 32;
 constexpr int kZRing = 4;                  // z_I hand-over slots between the two chains
 constexpr int kRing = 8;                   // block indices kept ahead / behind
 constexpr size_t kSmemHeader = 512;        // index rings, flags, mbarriers, step coefficients
-constexpr int kAccReplicas = 4;            // replicated accumulators (atomic contention)
+constexpr int kAccReplicas = 16;           // replicated accumulators (atomic contention)
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s per wait
 constexpr int64_t kMaxItersPerLaunch = 8000000;                 // barrier counter headroom
 
@@ -88,9 +88,10 @@ __host__ __device__ inline SmemLayout smem_layout(int nrow_cap, int ncol_cap, in
     L.zeta = o; o = al(o + (size_t)nrow_cap * ts);
     L.beta = o; o = al(o + (size_t)nrow_cap * ts);
     L.v = o;    if (corr) o = al(o + (size_t)nrow_cap * ts);
-    L.xi = o;   o = al(o + (size_t)ncol_cap * ts);
+    // x and w are read over whole tile rows: room for the zero padding up to a multiple of 8
+    L.xi = o;   o = al(o + (size_t)((ncol_cap + 7) / 8 * 8) * ts);
     L.s = o;    if (corr) o = al(o + (size_t)ncol_cap * ts);
-    L.w = o;    o = al(o + (size_t)tau_c * ts);
+    L.w = o;    o = al(o + (size_t)((tau_c + 7) / 8 * 8) * ts);
     L.r = o;    o = al(o + (size_t)tau_r * ts);
     L.zr = o;   o = al(o + (size_t)kZRing * tau_r * ts);
     size_t rz = (size_t)kZThreads * vec * ts, rx = (size_t)kXThreads * vec * ts;
