@@ -9,6 +9,8 @@
 //   form f = b - z - A x, g = A^T z and to apply z -= A s, x += A^T v.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "rebk_device.cuh"
@@ -122,9 +124,38 @@ __global__ void tables_kernel(const double *__restrict__ rowsq, const double *__
 // ---------------------------------------------------------------------------
 // Dual sweep: ym = A p, yn = A^T q over FP64 A, 2-D tiles, FP64 atomics.
 // ---------------------------------------------------------------------------
-constexpr int kSweepRows = 32;    // tile rows
 constexpr int kSweepCols = 1024;  // tile columns (4 per thread, 256 threads)
 
+// Sum over the 32 lanes of 8 per-lane values v[0..7] (a transposed butterfly:
+// every add is a useful one).  Afterwards lane L holds the total of value
+// ((L >> 4) & 1) * 4 + ((L >> 3) & 1) * 2 + ((L >> 2) & 1).
+__device__ __forceinline__ double warp_sum8(double (&v)[8], int lane) {
+    const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0, h2 = (lane & 4) != 0;
+    double a[4], b[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const double keep = h4 ? v[i + 4] : v[i], send = h4 ? v[i] : v[i + 4];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const double keep = h3 ? a[i + 2] : a[i], send = h3 ? a[i] : a[i + 2];
+        b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    double c = (h2 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, h2 ? b[0] : b[1], 4);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
+}
+
+// y_m = A p and y_n = A^T q in one pass over the FP64 matrix.  CTA (x, y) takes
+// the kSweepCols-column stripe x over the y-th of gridDim.y row ranges (one wave
+// of CTAs in all); a thread owns 4 columns (two 16-byte vectors) and issues the
+// loads of 8 rows at a time, so that many loads are in flight.  The 8 row
+// partials of A p are reduced across the warp with one transposed butterfly and
+// kept per warp in shared memory (rowpart: rows of the range x 8 warps); the
+// column partials of A^T q stay in registers.  Both leave by FP64 atomic adds
+// once per CTA (y zeroed by the caller).
 template <typename TP, typename TQ>
 __global__ void __launch_bounds__(256) dual_sweep_kernel(const double *__restrict__ A, int64_t lda,
                                                          int64_t m, int64_t n,
@@ -132,11 +163,13 @@ __global__ void __launch_bounds__(256) dual_sweep_kernel(const double *__restric
                                                          const TQ *__restrict__ q,
                                                          double *__restrict__ ym,
                                                          double *__restrict__ yn) {
-    __shared__ double rowpart[kSweepRows][8];
-    const int64_t ra = (int64_t)blockIdx.y * kSweepRows;
+    constexpr int RU = 8;
+    extern __shared__ double rowpart[];  // [rows of the range][8]
+    const int64_t ra = m * blockIdx.y / gridDim.y, rb = m * (blockIdx.y + 1) / gridDim.y;
     const int64_t cbase = (int64_t)blockIdx.x * kSweepCols;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t col = cbase + tid * 2;  // this thread: columns col, col+1 and col+512, col+513
+    const bool in0 = col < lda, in1 = col + 512 < lda;  // the padded row keeps a vector in bounds
     double pv[4] = {0, 0, 0, 0};
     const int64_t cols[4] = {col, col + 1, col + 512, col + 513};
     if (p) {
@@ -144,30 +177,48 @@ __global__ void __launch_bounds__(256) dual_sweep_kernel(const double *__restric
         for (int e = 0; e < 4; ++e) pv[e] = cols[e] < n ? (double)p[cols[e]] : 0.0;
     }
     double cs[4] = {0, 0, 0, 0};
-    const int64_t rb = lmin(m, ra + kSweepRows);
-    for (int64_t i = ra; i < rb; ++i) {
-        const double *row = A + i * lda;
-        double a[4];
-        // two 16-byte loads per thread; the padded row keeps them in bounds
-        if (col < lda) {
-            const double2 v = __ldg(reinterpret_cast<const double2 *>(row + col));
-            a[0] = v.x; a[1] = v.y;
-        } else { a[0] = a[1] = 0.0; }
-        if (col + 512 < lda) {
-            const double2 v = __ldg(reinterpret_cast<const double2 *>(row + col + 512));
-            a[2] = v.x; a[3] = v.y;
-        } else { a[2] = a[3] = 0.0; }
-        if (q) {
-            const double qi = (double)q[i];
+    for (int64_t i0 = ra; i0 < rb; i0 += RU) {
+        double a[RU][4];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) cs[e] = fma(a[e], qi, cs[e]);
+        for (int u = 0; u < RU; ++u) {
+            const int64_t i = i0 + u;
+            const double *row = A + i * lda;
+            const bool ok = i < rb;
+            if (ok && in0) {
+                const double2 v = __ldg(reinterpret_cast<const double2 *>(row + col));
+                a[u][0] = v.x; a[u][1] = v.y;
+            } else {
+                a[u][0] = a[u][1] = 0.0;
+            }
+            if (ok && in1) {
+                const double2 v = __ldg(reinterpret_cast<const double2 *>(row + col + 512));
+                a[u][2] = v.x; a[u][3] = v.y;
+            } else {
+                a[u][2] = a[u][3] = 0.0;
+            }
+        }
+        if (q) {
+#pragma unroll
+            for (int u = 0; u < RU; ++u) {
+                const int64_t i = i0 + u;
+                const double qi = i < rb ? (double)q[i] : 0.0;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) cs[e] = fma(a[u][e], qi, cs[e]);
+            }
         }
         if (p) {
-            double r = 0.0;
+            double r[RU];
 #pragma unroll
-            for (int e = 0; e < 4; ++e) r = fma(a[e], pv[e], r);
-            r = warp_sum(r);
-            if (lane == 0) rowpart[i - ra][warp] = r;
+            for (int u = 0; u < RU; ++u) {
+                r[u] = 0.0;
+#pragma unroll
+                for (int e = 0; e < 4; ++e) r[u] = fma(a[u][e], pv[e], r[u]);
+            }
+            const double t = warp_sum8(r, lane);
+            if ((lane & 3) == 0) {
+                const int u = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                if (i0 + u < rb) rowpart[(i0 + u - ra) * 8 + warp] = t;
+            }
         }
     }
     if (q) {
@@ -177,10 +228,11 @@ __global__ void __launch_bounds__(256) dual_sweep_kernel(const double *__restric
     }
     if (p) {
         __syncthreads();
-        if (tid < rb - ra) {
+        for (int64_t r = tid; r < rb - ra; r += blockDim.x) {
             double s = 0.0;
-            for (int w = 0; w < 8; ++w) s += rowpart[tid][w];
-            atomicAdd(ym + ra + tid, s);
+#pragma unroll
+            for (int w = 0; w < 8; ++w) s += rowpart[r * 8 + w];
+            atomicAdd(ym + ra + r, s);
         }
     }
 }
@@ -392,11 +444,22 @@ cudaError_t dual_sweep(const double *A, int64_t lda, int64_t m, int64_t n, const
                        cudaStream_t st) {
     if (p) cudaMemsetAsync(ym, 0, sizeof(double) * m, st);
     if (q) cudaMemsetAsync(yn, 0, sizeof(double) * n, st);
-    dim3 g((unsigned)((n + kSweepCols - 1) / kSweepCols), (unsigned)((m + kSweepRows - 1) / kSweepRows));
-    if (g.y > 65535u) return cudaErrorInvalidConfiguration;
+    // one wave of CTAs (two per SM): stripes x row ranges, each range short
+    // enough for its row partials to fit in 48 KB of shared memory
+    int dev = 0, sms = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t stripes = (n + kSweepCols - 1) / kSweepCols;
+    constexpr int64_t kMaxRangeRows = 768;  // 768 x 8 doubles = 48 KB
+    int64_t ranges = std::max<int64_t>(1, (2 * (int64_t)sms) / stripes);
+    ranges = std::max(ranges, (m + kMaxRangeRows - 1) / kMaxRangeRows);
+    ranges = std::min(ranges, std::max<int64_t>(1, (m + 7) / 8));
+    if (ranges > 65535) return cudaErrorInvalidConfiguration;
+    const size_t smem = sizeof(double) * 8 * (size_t)((m + ranges - 1) / ranges);  // rows of a range <= 768
+    dim3 g((unsigned)stripes, (unsigned)ranges);
 #define REBK_SWEEP(TP, TQ)                                                                         \
-    dual_sweep_kernel<TP, TQ><<<g, 256, 0, st>>>(A, lda, m, n, static_cast<const TP *>(p),         \
-                                                 static_cast<const TQ *>(q), ym, yn)
+    dual_sweep_kernel<TP, TQ><<<g, 256, smem, st>>>(A, lda, m, n, static_cast<const TP *>(p),      \
+                                                    static_cast<const TQ *>(q), ym, yn)
     if (!p_f32 && !q_f32) REBK_SWEEP(double, double);
     else if (p_f32 && q_f32) REBK_SWEEP(float, float);
     else if (p_f32) REBK_SWEEP(float, double);
