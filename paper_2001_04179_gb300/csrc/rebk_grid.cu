@@ -304,16 +304,17 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p) {
 }
 
 // ---------------------------------------------------------------------------
-// Shared-memory tile products (TMA path).  T: rows of ld elements, 16-byte
-// aligned, nvec 16-byte vectors per row; 32-bit shared addresses throughout.
+// Tile products.  T: rows of ld elements, nvec 16-byte vectors per row, either a
+// TMA-staged tile in shared memory (SM: 32-bit shared addresses) or a strided
+// view of A in global memory (read-only path, more loads in flight).
 // ---------------------------------------------------------------------------
 
 // out(l) = sum_{t < nvec * V} T[l * ld + t] * vin[t] for rows l in [0, rows);
-// vin holds nvec * V values (zero where the tile has no column of the range).
+// vin (shared memory) holds nvec * V values, zero where the range has no column.
 // Lane groups of gs lanes take 4 consecutive rows; emit4(l, v0..v3) for full
 // quads, emit(l, v) for the rows of the last, incomplete one.
-template <int NT, typename TA, typename TS, typename Emit, typename Emit4>
-__device__ __forceinline__ void tile_rowdot(int gt, const TA *T, int ld, int rows, int nvec,
+template <int NT, bool SM, typename TA, typename TS, typename Emit, typename Emit4>
+__device__ __forceinline__ void tile_rowdot(int gt, const TA *T, int64_t ld, int rows, int nvec,
                                             const TS *vin, Emit emit, Emit4 emit4) {
     using IO = VecIO<TA, TS>;
     constexpr int V = IO::V;
@@ -337,23 +338,15 @@ __device__ __forceinline__ void tile_rowdot(int gt, const TA *T, int ld, int row
     const int sub = lane & (gs - 1);
     const int g = warp * (32 / gs) + lane / gs;
     const int NG = NW * (32 / gs);
-    const uint32_t row_bytes = (uint32_t)ld * (uint32_t)sizeof(TA);
-    const uint32_t tb = smem_u32(T), vb = smem_u32(vin);
+    const uint32_t vb = smem_u32(vin);
     // the pass loop is uniform over the warp (every lane takes part in the shuffles)
     for (int base = 0; base < rows; base += 4 * NG) {
         const int rq = base + 4 * g;
         const bool ok0 = rq < rows, ok1 = rq + 1 < rows, ok2 = rq + 2 < rows, ok3 = rq + 3 < rows;
         TS acc0 = tzero<TS>(), acc1 = tzero<TS>(), acc2 = tzero<TS>(), acc3 = tzero<TS>();
-        uint32_t a = tb + (uint32_t)rq * row_bytes + (uint32_t)sub * 16u;
         uint32_t xa = vb + (uint32_t)sub * (uint32_t)(V * sizeof(TS));
-#pragma unroll 2
-        for (int vi = ok0 ? sub : nvec; vi < nvec; vi += gs) {
-            TS xv[V], t0[V], t1[V], t2[V], t3[V];
-            IO::load_shared_ts(xa, xv);
-            IO::load_shared(a, t0);
-            if (ok1) IO::load_shared(a + row_bytes, t1); else IO::zero(t1);
-            if (ok2) IO::load_shared(a + 2 * row_bytes, t2); else IO::zero(t2);
-            if (ok3) IO::load_shared(a + 3 * row_bytes, t3); else IO::zero(t3);
+        auto body = [&](const TS (&xv)[V], const TS (&t0)[V], const TS (&t1)[V], const TS (&t2)[V],
+                        const TS (&t3)[V]) {
 #pragma unroll
             for (int e = 0; e < V; ++e) {
                 acc0 = fma(t0[e], xv[e], acc0);
@@ -361,8 +354,37 @@ __device__ __forceinline__ void tile_rowdot(int gt, const TA *T, int ld, int row
                 acc2 = fma(t2[e], xv[e], acc2);
                 acc3 = fma(t3[e], xv[e], acc3);
             }
-            a += (uint32_t)gs * 16u;
-            xa += (uint32_t)(gs * V * sizeof(TS));
+        };
+        if constexpr (SM) {
+            const uint32_t row_bytes = (uint32_t)ld * (uint32_t)sizeof(TA);
+            uint32_t a = smem_u32(T) + (uint32_t)rq * row_bytes + (uint32_t)sub * 16u;
+#pragma unroll 2
+            for (int vi = ok0 ? sub : nvec; vi < nvec; vi += gs) {
+                TS xv[V], t0[V], t1[V], t2[V], t3[V];
+                IO::load_shared_ts(xa, xv);
+                IO::load_shared(a, t0);
+                if (ok1) IO::load_shared(a + row_bytes, t1); else IO::zero(t1);
+                if (ok2) IO::load_shared(a + 2 * row_bytes, t2); else IO::zero(t2);
+                if (ok3) IO::load_shared(a + 3 * row_bytes, t3); else IO::zero(t3);
+                body(xv, t0, t1, t2, t3);
+                a += (uint32_t)gs * 16u;
+                xa += (uint32_t)(gs * V * sizeof(TS));
+            }
+        } else {
+            const TA *a = T + (int64_t)rq * ld + (int64_t)sub * V;
+            constexpr int UR = V == 2 ? 3 : 1;  // chunks of loads in flight (register budget)
+#pragma unroll UR
+            for (int vi = ok0 ? sub : nvec; vi < nvec; vi += gs) {
+                TS xv[V], t0[V], t1[V], t2[V], t3[V];
+                IO::load(a, t0);
+                if (ok1) IO::load(a + ld, t1); else IO::zero(t1);
+                if (ok2) IO::load(a + 2 * ld, t2); else IO::zero(t2);
+                if (ok3) IO::load(a + 3 * ld, t3); else IO::zero(t3);
+                IO::load_shared_ts(xa, xv);
+                body(xv, t0, t1, t2, t3);
+                a += (int64_t)gs * V;
+                xa += (uint32_t)(gs * V * sizeof(TS));
+            }
         }
         TS acc[4] = {acc0, acc1, acc2, acc3};
         int ru = 0;
@@ -387,14 +409,12 @@ __device__ __forceinline__ void tile_rowdot(int gt, const TA *T, int ld, int row
 // nvec vectors t of a row, by a group of NT threads synchronised by sync();
 // threads are (vector, row group) pairs whose partial sums meet in red (NT * V
 // values).  emitv(t, sum[V]) once per vector.
-template <int NT, typename TA, typename TS, typename Sync, typename EmitV>
-__device__ __forceinline__ void tile_colsum(int gt, const TA *T, int ld, int rows, int nvec,
+template <int NT, bool SM, typename TA, typename TS, typename Sync, typename EmitV>
+__device__ __forceinline__ void tile_colsum(int gt, const TA *T, int64_t ld, int rows, int nvec,
                                             const TS *vrow, TS *red, Sync sync, EmitV emitv) {
     using IO = VecIO<TA, TS>;
     constexpr int V = IO::V;
     if (rows <= 0 || nvec <= 0) return;
-    const uint32_t row_bytes = (uint32_t)ld * (uint32_t)sizeof(TA);
-    const uint32_t tb = smem_u32(T);
     for (int vc0 = 0; vc0 < nvec; vc0 += NT) {
         const int nvc = min(NT, nvec - vc0);
         const int NRG = NT / nvc;
@@ -403,16 +423,32 @@ __device__ __forceinline__ void tile_colsum(int gt, const TA *T, int ld, int row
             TS acc[V];
 #pragma unroll
             for (int e = 0; e < V; ++e) acc[e] = tzero<TS>();
-            uint32_t a = tb + (uint32_t)rg * row_bytes + (uint32_t)(vc0 + vi) * 16u;
-            const uint32_t step = (uint32_t)NRG * row_bytes;
+            if constexpr (SM) {
+                const uint32_t row_bytes = (uint32_t)ld * (uint32_t)sizeof(TA);
+                uint32_t a = smem_u32(T) + (uint32_t)rg * row_bytes + (uint32_t)(vc0 + vi) * 16u;
+                const uint32_t step = (uint32_t)NRG * row_bytes;
 #pragma unroll 4
-            for (int l = rg; l < rows; l += NRG) {
-                TS t[V];
-                IO::load_shared(a, t);
-                const TS xr = vrow[l];
+                for (int l = rg; l < rows; l += NRG) {
+                    TS t[V];
+                    IO::load_shared(a, t);
+                    const TS xr = vrow[l];
 #pragma unroll
-                for (int e = 0; e < V; ++e) acc[e] = fma(t[e], xr, acc[e]);
-                a += step;
+                    for (int e = 0; e < V; ++e) acc[e] = fma(t[e], xr, acc[e]);
+                    a += step;
+                }
+            } else {
+                const TA *a = T + (int64_t)rg * ld + (int64_t)(vc0 + vi) * V;
+                const int64_t step = (int64_t)NRG * ld;
+                constexpr int UR = V == 2 ? 8 : 4;
+#pragma unroll UR
+                for (int l = rg; l < rows; l += NRG) {
+                    TS t[V];
+                    IO::load(a, t);
+                    const TS xr = vrow[l];
+#pragma unroll
+                    for (int e = 0; e < V; ++e) acc[e] = fma(t[e], xr, acc[e]);
+                    a += step;
+                }
             }
             TS *dst = red + (rg * nvc + vi) * V;
 #pragma unroll
@@ -635,6 +671,8 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
     const bool check = args.x_ref != nullptr && args.check_every > 0;
     // column tiles start exactly at their block (tau_c a multiple of the 16-byte vector)
     const bool fast_c = TMA && args.bw_c == args.tau_c;
+    // global-memory column views start on a 16-byte vector (rows are 16-byte aligned)
+    const bool fast_g = !TMA && args.tau_c % V == 0;
     const int wpad = (args.tau_c + 7) / 8 * 8;
     // Any CTA past the arrivals of step q may clear a set that step q + 1 fills:
     // every CTA has read it (step q - 1) before arriving, and nobody adds to it
@@ -745,23 +783,35 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
         auto partial_w = [&](int64_t q, TS *accp) {  // over own rows, column block J_q, with zeta
             int64_t ja, jb, ld;
             col_range(ring_j[q % kRing], &ja, &jb);
+            const int wc = (int)(jb - ja);
+            auto emitv = [&](int t, const TS(&sum)[V]) {
+                if constexpr (V >= 4) {
+#pragma unroll
+                    for (int e4 = 0; e4 < V; e4 += 4) {
+                        const int c = t * V + e4;
+                        if (c + 3 < wc) {
+                            red_add4(accp + c, sum[e4], sum[e4 + 1], sum[e4 + 2], sum[e4 + 3]);
+                        } else {
+                            for (int e = 0; e < 4; ++e)
+                                if (c + e < wc) atomicAdd(accp + c + e, sum[e4 + e]);
+                        }
+                    }
+                } else {
+#pragma unroll
+                    for (int e = 0; e < V; ++e)
+                        if (t * V + e < wc) atomicAdd(accp + t * V + e, sum[e]);
+                }
+            };
             if constexpr (TMA) {
                 if (fast_c) {
-                    const int wc = (int)(jb - ja);
-                    tile_colsum<ZT, TA, TS>(gt, tile_c((int)(q & 1)), args.bw_c, nrow, args.bw_c / V, zeta, redz,
-                                            zsync, [&](int t, const TS(&sum)[V]) {
-#pragma unroll
-                                                for (int e4 = 0; e4 < V; e4 += 4) {
-                                                    const int c = t * V + e4;
-                                                    if (c + 3 < wc) {
-                                                        red_add4(accp + c, sum[e4], sum[e4 + 1], sum[e4 + 2],
-                                                                 sum[e4 + 3]);
-                                                    } else {
-                                                        for (int e = 0; e < 4; ++e)
-                                                            if (c + e < wc) atomicAdd(accp + c + e, sum[e4 + e]);
-                                                    }
-                                                }
-                                            });
+                    tile_colsum<ZT, true, TA, TS>(gt, tile_c((int)(q & 1)), args.bw_c, nrow, args.bw_c / V, zeta,
+                                                  redz, zsync, emitv);
+                    return;
+                }
+            } else {
+                if (fast_g) {
+                    tile_colsum<ZT, false, TA, TS>(gt, A + r0 * lda + ja, lda, nrow, (wc + V - 1) / V, zeta, redz,
+                                                   zsync, emitv);
                     return;
                 }
             }
@@ -855,12 +905,17 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
                     upd(row + 3, v3);
                 };
                 bool done_fast = false;
+                auto e1 = [&](int l, TS v) { upd(r0 + l, v); };
+                auto e4 = [&](int l, TS v0, TS v1, TS v2, TS v3) { upd4(r0 + l, v0, v1, v2, v3); };
                 if constexpr (TMA) {
                     if (fast_c) {
-                        tile_rowdot<ZT, TA, TS>(
-                            gt, tile_c((int)(q & 1)), args.bw_c, nrow, args.bw_c / V, w,
-                            [&](int l, TS v) { upd(r0 + l, v); },
-                            [&](int l, TS v0, TS v1, TS v2, TS v3) { upd4(r0 + l, v0, v1, v2, v3); });
+                        tile_rowdot<ZT, true, TA, TS>(gt, tile_c((int)(q & 1)), args.bw_c, nrow, args.bw_c / V, w, e1,
+                                                      e4);
+                        done_fast = true;
+                    }
+                } else {
+                    if (fast_g) {  // w is zero from wc up to a multiple of 8
+                        tile_rowdot<ZT, false, TA, TS>(gt, A + r0 * lda + ja, lda, nrow, (wc + V - 1) / V, w, e1, e4);
                         done_fast = true;
                     }
                 }
@@ -1013,19 +1068,14 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
             row_range(ring_xi[p % kRing], &ia, &ib);
             TS *accp = accr_base + (p % 3) * accset + (int64_t)rep * aw;
             if (ncol > 0) {
+                auto e1 = [&](int l, TS v) { atomicAdd(accp + l, v); };
+                auto e4 = [&](int l, TS v0, TS v1, TS v2, TS v3) { red_add4(accp + l, v0, v1, v2, v3); };
                 if constexpr (TMA) {
-                    tile_rowdot<XT, TA, TS>(
-                        gt, tile_r((int)(p & 1)), args.bw_r, (int)(ib - ia), args.bw_r / V, xi,
-                        [&](int l, TS v) { atomicAdd(accp + l, v); },
-                        [&](int l, TS v0, TS v1, TS v2, TS v3) { red_add4(accp + l, v0, v1, v2, v3); });
-                } else {
-                    int64_t ld;
-                    const TA *T = rtile(p, ia, &ld);
-                    row_dots<XT, TA, TS, TMA>(
-                        gt, T, ld, ia, ib, c0, c1, xi, [&](int64_t row, TS v) { atomicAdd(accp + (row - ia), v); },
-                        [&](int64_t row, TS v0, TS v1, TS v2, TS v3) {
-                            red_add4(accp + (row - ia), v0, v1, v2, v3);
-                        });
+                    tile_rowdot<XT, true, TA, TS>(gt, tile_r((int)(p & 1)), args.bw_r, (int)(ib - ia), args.bw_r / V,
+                                                  xi, e1, e4);
+                } else {  // x is zero beyond the owned columns
+                    tile_rowdot<XT, false, TA, TS>(gt, A + ia * lda + c0, lda, (int)(ib - ia), (ncol + V - 1) / V, xi,
+                                                   e1, e4);
                 }
             }
             {
@@ -1109,26 +1159,21 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
             }
             // x^p on own columns (+ dual v on own rows of I_p)
             const TS cI = ring_ci[p % kRing];
-            if constexpr (TMA) {
-                tile_colsum<XT, TA, TS>(gt, tile_r((int)(p & 1)), args.bw_r, hr, args.bw_r / V, rr, redx, xsync,
-                                        [&](int t, const TS(&sum)[V]) {
+            {
+                auto emitv = [&](int t, const TS(&sum)[V]) {
 #pragma unroll
-                                            for (int e = 0; e < V; ++e) {
-                                                const int c = t * V + e;
-                                                if (c < ncol) xi[c] -= cI * sum[e];
-                                            }
-                                        });
-            } else {
-                int64_t ld;
-                const TA *T = rtile(p, ia, &ld);
-                auto upd = [&](int64_t col, TS v) { xi[col - c0] -= cI * v; };
-                col_sums<XT, TA, TS, TMA>(gt, T, ld, ia, ib, c0, c1, rr, redx, xsync, upd,
-                                          [&](int64_t col, TS v0, TS v1, TS v2, TS v3) {
-                                              upd(col, v0);
-                                              upd(col + 1, v1);
-                                              upd(col + 2, v2);
-                                              upd(col + 3, v3);
-                                          });
+                    for (int e = 0; e < V; ++e) {
+                        const int c = t * V + e;
+                        if (c < ncol) xi[c] -= cI * sum[e];
+                    }
+                };
+                if constexpr (TMA) {
+                    tile_colsum<XT, true, TA, TS>(gt, tile_r((int)(p & 1)), args.bw_r, hr, args.bw_r / V, rr, redx,
+                                                  xsync, emitv);
+                } else if (ncol > 0) {
+                    tile_colsum<XT, false, TA, TS>(gt, A + ia * lda + c0, lda, hr, (ncol + V - 1) / V, rr, redx, xsync,
+                                                   emitv);
+                }
             }
             if (CORR) {
                 const int64_t la = lmax(ia, r0), lb = lmin(ib, r1);
