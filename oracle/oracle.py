@@ -404,35 +404,51 @@ def mlp_init(sizes, seed):
             for i in range(len(sizes) - 1)]
 
 
-def mlp_forward(W, Bm):
-    """y = W_L relu(... relu(W_1 b)): columns of Bm are inputs.  Returns
-    (y, cache) with cache = pre-activations and activations per layer."""
+def mlp_forward(W, Bm, out_scale=1.0):
+    """y = s W_L relu(... relu(W_1 b)) with output scale s: columns of Bm are
+    inputs.  Returns (y, cache) with cache = pre-activations and activations
+    per layer (the last pre-activation unscaled)."""
     acts = [_f64(Bm)]
     pres = []
     h = acts[0]
     for l, Wl in enumerate(W):
         p = Wl @ h
         pres.append(p)
-        h = p if l == len(W) - 1 else np.maximum(p, 0.0)
+        h = out_scale * p if l == len(W) - 1 else np.maximum(p, 0.0)
         acts.append(h)
     return h, (pres, acts)
 
 
-def mlp_loss(W, A, Bm, Xls):
-    """Mean over columns of ||A^T y - x_ls||^2 with y = mlp(b)."""
-    y, _ = mlp_forward(W, Bm)
-    R = _f64(A).T @ y - _f64(Xls)
-    return float(np.sum(R * R)) / Bm.shape[1]
+def mlp_loss(W, A, Bm, T, loss="x", out_scale=1.0):
+    """Mean over columns of the training loss of the warm start x^0 = A^T y:
+    loss "x": ||A^T y - x_ls||^2 (T = x_ls, n x B);
+    loss "y_rel": ||y - y*||^2 / ||y*||^2 (T = y* = (A^T)^+ x_ls, m x B)."""
+    y, _ = mlp_forward(W, Bm, out_scale)
+    if loss == "x":
+        R = _f64(A).T @ y - _f64(T)
+        return float(np.sum(R * R)) / Bm.shape[1]
+    T = _f64(T)
+    nt = np.sum(T * T, axis=0)
+    d = np.sum((y - T) ** 2, axis=0)
+    return float(np.sum(np.where(nt > 0, d / np.where(nt > 0, nt, 1.0), 0.0))) / Bm.shape[1]
 
 
-def mlp_backward(W, A, Bm, Xls):
-    """Gradients of mlp_loss w.r.t. each W_l by the chain rule:
-    dL/dy = (2/B) A (A^T y - x_ls); back through the linear layers and the
-    ReLU masks (derivative 0 at 0)."""
-    A = _f64(A)
-    y, (pres, acts) = mlp_forward(W, Bm)
+def mlp_backward(W, A, Bm, T, loss="x", out_scale=1.0):
+    """Gradients of mlp_loss w.r.t. each W_l by the chain rule.  dL/dy:
+    loss "x": (2/B) A (A^T y - x_ls); loss "y_rel": (2/B) (y - y*) / ||y*||^2
+    per column (0 for a zero target).  The output scale s multiplies the
+    signal entering the last layer; then back through the linear layers and
+    the ReLU masks (derivative 0 at 0)."""
+    y, (pres, acts) = mlp_forward(W, Bm, out_scale)
     B = Bm.shape[1]
-    G = (2.0 / B) * (A @ (A.T @ y - _f64(Xls)))
+    if loss == "x":
+        A = _f64(A)
+        G = (2.0 / B) * (A @ (A.T @ y - _f64(T)))
+    else:
+        T = _f64(T)
+        nt = np.sum(T * T, axis=0)
+        G = (2.0 / B) * (y - T) * np.where(nt > 0, 1.0 / np.where(nt > 0, nt, 1.0), 0.0)
+    G = out_scale * G
     grads = [None] * len(W)
     for l in range(len(W) - 1, -1, -1):
         if l < len(W) - 1:
