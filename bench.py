@@ -47,6 +47,13 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", choices=["precision", "warm"], default="precision",
+                    help="precision: the headline solve (default); warm: the learned warm start "
+                         "on the 8192 x 2048 spectrum workload (targets, training, warm vs cold)")
+    ap.add_argument("--warm-train", type=int, default=2048)
+    ap.add_argument("--warm-eval", type=int, default=32)
+    ap.add_argument("--warm-batch-systems", type=int, default=152)
+    ap.add_argument("--warm-steps", type=int, default=4000)
     ap.add_argument("--profile-pass", type=int, default=0, metavar="K",
                     help="run one K-iteration refinement pass of the workload twice and exit "
                          "(the case the ncu summaries under profiles/ capture)")
@@ -241,10 +248,168 @@ def run_reference(args):
     return 0
 
 
+def run_warm(args):
+    """Learned warm start on the 8192 x 2048 workload: A = U diag(i^-1/2) V^T,
+    b = A (M c) + N(0, 1e-3^2), M = randn(2048, 32), c ~ N(0, I).  Training
+    pairs come from the solver: x_ls = A^+ b from batched systems sharing A
+    (8 right-hand sides each), y* = (A^T)^+ x_ls from batched systems sharing
+    A^T; the network 8192 -> 512 -> 512 -> 8192 (BF16 tensor-core GEMMs) is
+    trained with the y-space loss; then mixed-precision solves of held-out
+    right-hand sides to 1e-8 from the cold start and from x0 = A^T y.  The warm
+    solves' timed region includes the network and the x0 / z0 products."""
+    import torch
+
+    from paper_2001_04179_gb300 import BatchSolver, Solver, WarmStartNet
+    from workloads import spectrum_problem
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    m5, n5, ntr, nev = 8192, 2048, args.warm_train, args.warm_eval
+    ntr = max(256, ntr // 256 * 256)
+    nbs = max(1, args.warm_batch_systems)
+    nbe = 8 * nbs  # held-out right-hand sides of the batched legs
+    t0 = time.perf_counter()
+    p = spectrum_problem(m5, n5, seed=rank, latent=32, noise=1e-3, nrhs=ntr + nev + nbe)
+    gen_s = time.perf_counter() - t0
+    A = p.A
+    At = np.ascontiguousarray(A.T)
+    sol = Solver(A, TAU, TAU, alpha=0.0, storage=("fp32", "bf16"))
+    alpha = sol.alpha  # blocks of A^T are the transposes of A's: the same beta_max
+    ns = ntr // 8
+
+    def batched(mat, rhs_rows, rows_out):
+        bs = BatchSolver([mat] * ns, nrhs=8, tau=TAU, alpha=[alpha] * ns, max_outer=2)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        out = bs.solve(rhs_rows, X_ref=None, tol=0.0, max_iter=0, inner_iters=25000, seed=3)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t1
+        bs.close()
+        return out["x"], dt, out["stats"]
+
+    # 1. x_ls for the training right-hand sides (system i holds RHS 8i..8i+7)
+    B_sys = torch.from_numpy(np.ascontiguousarray(
+        np.concatenate([p.b[:, 8 * i:8 * i + 8] for i in range(ns)], axis=0))).to(dev)
+    Xs, tx, stx = batched(A, B_sys, n5)
+    # 2. y* = (A^T)^+ x_ls: the x_ls rows are already laid out as the A^T systems' right-hand sides
+    Ys, ty, sty = batched(At, Xs, m5)
+    Xtr = Xs.view(ns, n5, 8).permute(0, 2, 1).reshape(ntr, n5)
+    Ytr = Ys.view(ns, m5, 8).permute(0, 2, 1).reshape(ntr, m5).contiguous()
+    xr_tr = torch.from_numpy(np.ascontiguousarray(p.x_ref[:, :ntr].T)).to(dev)
+    x_err = float(((Xtr - xr_tr).norm(dim=1) / xr_tr.norm(dim=1)).max())
+    # 3. training
+    Btr = torch.from_numpy(np.ascontiguousarray(p.b[:, :ntr].T)).to(dev)
+    net = WarmStartNet(A, hidden=512, batch_capacity=256, seed=1)
+    out_scale = 0.1 * float(torch.sqrt((Ytr * Ytr).sum(1).mean() / (Btr * Btr).sum(1).mean()))
+    net.set_loss("y_rel", out_scale)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    losses = net.fit(Btr, Ytr, steps=args.warm_steps, lr=1e-3, batch=256)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    # 4. held-out solves, cold vs warm
+    stream = torch.cuda.current_stream()
+    res = {}
+    for S in ("fp32", "bf16"):
+        row = {}
+        for mode in ("cold", "warm"):
+            its, e0s = [], []
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for i in range(ntr, ntr + nev):
+                b = torch.from_numpy(np.ascontiguousarray(p.b[:, i])).to(dev)
+                xr = torch.from_numpy(np.ascontiguousarray(p.x_ref[:, i])).to(dev)
+                if mode == "warm":
+                    x0, z0 = net.warm_start(sol, b)
+                    r = sol.solve_refined(b, tol=TOL, seed=7, storage=S, x_ref=xr, x0=x0, z0=z0)
+                    e0s.append(float((x0 - xr).norm() / xr.norm()))
+                else:
+                    r = sol.solve_refined(b, tol=TOL, seed=7, storage=S, x_ref=xr)
+                if r["stats"]["rel_err"] > TOL:
+                    raise RuntimeError(f"{mode} {S} solve did not reach {TOL}: {r['stats']}")
+                its.append(r["stats"]["iterations"])
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            row[mode] = {"solves_per_s": nev / (ms / 1000.0), "iterations_mean": float(np.mean(its))}
+            if e0s:
+                row[mode]["x0_rel_err_median"] = float(np.median(e0s))
+        row["speedup"] = row["warm"]["solves_per_s"] / row["cold"]["solves_per_s"]
+        res[S] = row
+    # plain FP64 (Algorithm 1 as printed) on the same held-out right-hand sides
+    nplain = min(nev, 16)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    its = []
+    ev0.record(stream)
+    for i in range(ntr, ntr + nplain):
+        b = torch.from_numpy(np.ascontiguousarray(p.b[:, i])).to(dev)
+        xr = torch.from_numpy(np.ascontiguousarray(p.x_ref[:, i])).to(dev)
+        r = sol.solve(b, tol=TOL, max_iter=10**7, seed=7, x_ref=xr)
+        if r["stats"]["rel_err"] > TOL:
+            raise RuntimeError(f"plain FP64 solve did not reach {TOL}: {r['stats']}")
+        its.append(r["stats"]["iterations"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    plain = {"solves_per_s": nplain / (ev0.elapsed_time(ev1) / 1000.0), "iterations_mean": float(np.mean(its)),
+             "rhs": nplain}
+    # batched FP32 mixed: nbs systems of 8 right-hand sides sharing A, cold and warm
+    c0 = ntr + nev
+    Bb = torch.from_numpy(np.ascontiguousarray(
+        np.concatenate([p.b[:, c0 + 8 * i:c0 + 8 * i + 8] for i in range(nbs)], axis=0))).to(dev)
+    Xrb = torch.from_numpy(np.ascontiguousarray(
+        np.concatenate([p.x_ref[:, c0 + 8 * i:c0 + 8 * i + 8] for i in range(nbs)], axis=0))).to(dev)
+    bsv = BatchSolver([A] * nbs, nrhs=8, tau=TAU, alpha=[alpha] * nbs)
+    batched_res = {}
+    for mode in ("cold", "warm"):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        X0 = Z0 = None
+        if mode == "warm":  # the network and the x0 / z0 products are inside the timed region
+            X0 = torch.empty(nbs * n5, 8, dtype=torch.float64, device=dev)
+            Z0 = torch.empty(nbs * m5, 8, dtype=torch.float64, device=dev)
+            for i in range(nbs):
+                for r_ in range(8):
+                    b = Bb[i * m5:(i + 1) * m5, r_].contiguous()
+                    x0, z0 = net.warm_start(sol, b)
+                    X0[i * n5:(i + 1) * n5, r_] = x0
+                    Z0[i * m5:(i + 1) * m5, r_] = z0
+        out = bsv.solve(Bb, X_ref=Xrb, tol=TOL, max_iter=400000, seed=11, X0=X0, Z0=Z0)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        st_ = out["stats"]
+        if st_["converged"] != nbs:
+            raise RuntimeError(f"batched {mode}: {st_['converged']} of {nbs} systems converged")
+        batched_res[mode] = {"solves_per_s": nbe / (ev0.elapsed_time(ev1) / 1000.0),
+                             "iterations_mean_per_system": st_["iterations"] / nbs, "rhs": nbe,
+                             "systems": nbs}
+    bsv.close()
+    res["batched_fp32"] = batched_res
+    res["plain_fp64"] = plain
+    res["speedup_mixed_warm_batched_vs_plain_fp64"] = batched_res["warm"]["solves_per_s"] / plain["solves_per_s"]
+    if rank == 0:
+        print(json.dumps({
+            "workload": "warm start: A = U diag(i^-1/2) V^T 8192x2048, b = A(Mc) + N(0,1e-3^2), latent 32; "
+                        "MLP 8192-512-512-8192 (BF16 GEMMs), x0 = A^T y, z0 = b - A x0; tau = 128; tol 1e-8",
+            "metric": "solves/s to 1e-8 rel err, warm vs cold (mixed precision)", "unit": "solves/s",
+            "train_rhs": ntr, "eval_rhs": nev, "problem_gen_s": gen_s,
+            "targets": {"x_ls_batch_s": tx, "y_star_batch_s": ty, "x_ls_max_rel_err": x_err,
+                        "systems": ns, "rhs_per_system": 8, "passes": 2, "iterations_per_pass": 25000},
+            "training": {"steps": args.warm_steps, "seconds": train_s, "loss_first": losses[0],
+                         "loss_last": float(np.mean(losses[-20:])), "out_scale": out_scale,
+                         "loss": "mean ||y - y*||^2 / ||y*||^2", "lr": "1e-3 cosine", "batch": 256},
+            "fp32": res["fp32"], "bf16": res["bf16"], "plain_fp64": res["plain_fp64"],
+            "batched_fp32": res["batched_fp32"],
+            "speedup_mixed_warm_batched_vs_plain_fp64": res["speedup_mixed_warm_batched_vs_plain_fp64"]}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "warm":
+        return run_warm(args)
     import torch
     import torch.distributed as dist
 

@@ -225,7 +225,10 @@ typedef struct {
  * shapes; A[i] (host array of pointers) points to row-major FP64 matrices with
  * leading dimension n[i], in host memory (A_on_device == 0) or device memory.
  * The library copies every matrix (FP64 for the refinement sweeps, FP32 for
- * the inner iterations) and builds each system's block tables.  alpha (host
+ * the inner iterations) and builds each system's block tables; systems given
+ * the same pointer with the same shape share one stored copy (a stream of
+ * right-hand-side groups for one matrix: each system then holds up to eight
+ * right-hand sides and its own block sequence).  alpha (host
  * array, may be NULL) gives each system's step size; NULL or a value <= 0 picks
  * 1.75 / beta_max of that system (Section 3's empirical choice).
  * Errors: EINVAL (count < 1, shapes, NULL pointers, options), ENOMEM, ECUDA.
@@ -257,6 +260,18 @@ rebk_status rebk_batch_solve(rebk_batch h, const double *B, double *X, const dou
                              int64_t max_iter, int64_t inner_iters, uint64_t seed, int32_t *status_out,
                              rebk_batch_stats *stats);
 
+/*
+ * rebk_batch_solve from given starting points: X0 (device, n[i] x nrhs
+ * blocks like X, or NULL for x^0 = 0) and Z0 (device, m[i] x nrhs blocks like
+ * B, or NULL for z^0 = b).  Theorem main's hypotheses are x^0 in range(A_i^T)
+ * and z^0 in b + range(A_i) for every right-hand side (the learned warm start
+ * x^0 = A^T y, z^0 = b - A x^0 meets both); the limit is then A_i^+ b.
+ */
+rebk_status rebk_batch_solve_ex(rebk_batch h, const double *B, double *X, const double *X_ref,
+                                const double *X0, const double *Z0, double tol, int64_t max_iter,
+                                int64_t inner_iters, uint64_t seed, int32_t *status_out,
+                                rebk_batch_stats *stats);
+
 /* Block size in use and the number of systems (host outputs; either may be NULL). */
 rebk_status rebk_batch_info(rebk_batch h, int32_t *tau, int32_t *count);
 
@@ -285,13 +300,31 @@ rebk_status rebk_mlp_create(rebk_mlp *out, const double *A, int64_t m, int64_t n
                             uint64_t seed, void *stream);
 void rebk_mlp_destroy(rebk_mlp h);
 
+/* Training losses of the network (rebk_mlp_set_loss). */
+enum { REBK_MLP_LOSS_X = 0, REBK_MLP_LOSS_Y_REL = 1 };
+
+/*
+ * Selects the loss of rebk_mlp_gradients / rebk_mlp_train_step and the output
+ * scale s of the network, y = s W3 relu(W2 relu(W1 b)):
+ *   REBK_MLP_LOSS_X (default, s = 1): mean ||A^T y - x_ls||^2, targets x_ls
+ *     (batch x n);
+ *   REBK_MLP_LOSS_Y_REL: mean ||y - y*||^2 / ||y*||^2, targets y* = (A^T)^+ x_ls
+ *     (batch x m; the minimum-norm solution of A^T y = x_ls, a REBK solve with
+ *     the matrix A^T).  It weighs the error of x^0 = A^T y along singular value
+ *     sigma by 1 / sigma^2: the directions Theorem main's rate makes slowest.
+ * s (> 0) lets the output reach ||y*|| without huge last-layer weights.
+ * Errors: EINVAL (NULL network, unknown loss, s not positive and finite).
+ */
+rebk_status rebk_mlp_set_loss(rebk_mlp h, int32_t loss, double out_scale);
+
 /* Y (device, batch x m) = network applied to the rows of Bm (device, batch x m). */
 rebk_status rebk_mlp_forward(rebk_mlp h, const double *Bm, int64_t batch, double *Y);
 
 /*
- * Gradients of loss = (1/batch) sum_b ||A^T y_b - x_ls,b||^2 for the rows of
- * Bm (device, batch x m) and Xls (device, batch x n, the least-squares
- * solutions, e.g. produced by the solver).  loss (host) may be NULL;
+ * Gradients of the selected loss (rebk_mlp_set_loss; default (1/batch)
+ * sum_b ||A^T y_b - x_ls,b||^2) for the rows of Bm (device, batch x m) and the
+ * targets Xls (device: x_ls, batch x n, for REBK_MLP_LOSS_X; y*, batch x m, for
+ * REBK_MLP_LOSS_Y_REL; e.g. produced by the solver).  loss (host) may be NULL;
  * grads_host (three host FP32 arrays, any NULL) receives dL/dW_l.
  */
 rebk_status rebk_mlp_gradients(rebk_mlp h, const double *Bm, const double *Xls, int64_t batch, double *loss,

@@ -875,12 +875,20 @@ rebk_status rebk_solve_refined(rebk_handle h, const double *b, double *x, double
         LK(h, fill_zero_f32(h->sd, h->n, st));
         const int64_t iters = std::min(inner_max, max_iter - total);
         int64_t ran = 0;
-        int64_t grow = 16384;
+        int64_t grow = 2048;  // chunks of 2048, 2048, 4096, 8192, ... iterations
+        int chunks = 0;
+        // A pass ends when its error test passes, or (with a reference) when its
+        // error stops falling: after a chunk without the test, the error of
+        // x + dx is measured; a chunk that did not lower it, or whose rate
+        // (log-reduction per iteration) fell below a tenth of the previous
+        // chunk's, means the inner iteration reached the floor that the rounded
+        // matrix sets, and a new FP64 residual is the way on.
+        double e_prev = e0, rate_prev = -1.0;
         while (ran < iters) {
             int64_t chunk = std::min(iters - ran, e.idx_out ? kMaxItersPerLaunch : kIdxChunkMax);
             if (use_ref) {
                 chunk = std::min(chunk, grow);
-                grow = std::min<int64_t>(grow * 2, kIdxChunkMax);
+                if (++chunks >= 2) grow = std::min<int64_t>(grow * 2, kIdxChunkMax);
             }
             s = sample_into(h, a, e.k0 + total + ran, chunk,
                             e.idx_out ? e.idx_out + 2 * (total + ran) : nullptr);
@@ -907,6 +915,18 @@ rebk_status rebk_solve_refined(rebk_handle h, const double *b, double *x, double
                 return fail(REBK_DIVERGED, "inner iteration diverged (Inf/NaN)");
             }
             if (done < chunk) break;  // error test met
+            if (use_ref && ran < iters) {
+                LK(h, err_norms_f32(x, h->dx, e.x_ref, h->n, h->ws->small, st));
+                double v[2];
+                s = fetch_small(h, v, 2);
+                if (s != REBK_OK) return s;
+                const double e_now = std::sqrt(v[0]);
+                if (!(e_now < e_prev)) break;
+                const double rate = std::log(e_prev / e_now) / (double)done;
+                if (rate_prev > 0.0 && rate < 0.1 * rate_prev) break;
+                rate_prev = rate;
+                e_prev = e_now;
+            }
         }
         total += ran;
         // z <- z - A s, x <- x + A^T v (FP64 A)

@@ -524,6 +524,8 @@ struct rebk_batch_s {
     // state (rows of kR)
     double *Z = nullptr, *F = nullptr, *YM = nullptr, *G = nullptr, *YN = nullptr, *Xi = nullptr, *Bi = nullptr,
            *Xr = nullptr;
+    double *X0i = nullptr, *Z0i = nullptr;  // starting points (warm start), allocated on first use
+    bool warm_x = false, warm_z = false;    // start from X0i / Z0i instead of x = 0 / z = b
     float *F32 = nullptr, *G32 = nullptr, *dZ = nullptr, *dX = nullptr, *S = nullptr, *Vd = nullptr;
     // per system
     int64_t *iters_done = nullptr, *iter_cap = nullptr;
@@ -554,7 +556,7 @@ void free_batch(rebk_batch h) {
     void *ptrs[] = {h->A64, h->A32, h->nr, h->nc, h->cdf_r, h->cdf_c, h->c64r, h->c64c, h->c32r, h->c32c,
                     h->d_sys, h->d_order, h->Z, h->F, h->YM, h->G, h->YN, h->Xi, h->Bi, h->Xr, h->F32,
                     h->G32, h->dZ, h->dX, h->S, h->Vd, h->iters_done, h->iter_cap, h->active, h->status,
-                    h->counters, h->thr2, h->e2, h->r2, h->items};
+                    h->counters, h->thr2, h->e2, h->r2, h->items, h->X0i, h->Z0i};
     for (void *p : ptrs)
         if (p) cudaFree(p);
     if (h->ev0) cudaEventDestroy(h->ev0);
@@ -810,13 +812,20 @@ rebk_status rebk_batch_create(rebk_batch *out, int32_t count, const int64_t *m, 
     if (alpha)
         for (int i = 0; i < count; ++i) h->alpha_given[i] = alpha[i];
     int64_t mo = 0, no = 0, ao = 0;
+    std::vector<int> first(count);  // first system holding the same matrix (equal pointer and shape)
     for (int i = 0; i < count; ++i) {
         const int64_t ld = (n[i] + 63) / 64 * 64;
+        first[i] = i;
+        for (int k = 0; k < i; ++k)
+            if (first[k] == k && A[k] == A[i] && m[k] == m[i] && n[k] == n[i]) {
+                first[i] = k;
+                break;
+            }
         h->lda.push_back(ld);
-        h->a_off.push_back(ao);
+        h->a_off.push_back(first[i] == i ? ao : h->a_off[first[i]]);
         h->mrow.push_back(mo);
         h->nrow.push_back(no);
-        ao += m[i] * ld;
+        if (first[i] == i) ao += m[i] * ld;
         mo += m[i];
         no += n[i];
     }
@@ -844,6 +853,7 @@ rebk_status rebk_batch_create(rebk_batch *out, int32_t count, const int64_t *m, 
     BCKH(cudaMalloc(&h->A64, sizeof(double) * ao));
     BCKH(cudaMalloc(&h->A32, sizeof(float) * ao));
     for (int i = 0; i < count; ++i) {
+        if (first[i] != i) continue;  // stored once
         BCKH(cudaMemcpy2DAsync(h->A64 + h->a_off[i], h->lda[i] * sizeof(double), A[i], n[i] * sizeof(double),
                                n[i] * sizeof(double), m[i],
                                A_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
@@ -914,9 +924,10 @@ rebk_status run_batch(rebk_batch h, int tau, double tol, int64_t max_iter, int64
         rebk_status ts = build_tables(h, tau, only);
         if (ts != REBK_OK) return ts;
     }
-    // x0 = 0, z0 = b; counters
-    BCK(cudaMemsetAsync(h->Xi, 0, sizeof(double) * NR, st));
-    BCK(cudaMemcpyAsync(h->Z, h->Bi, sizeof(double) * MR, cudaMemcpyDeviceToDevice, st));
+    // x0 = 0, z0 = b (or the caller's starting points); counters
+    if (h->warm_x) BCK(cudaMemcpyAsync(h->Xi, h->X0i, sizeof(double) * NR, cudaMemcpyDeviceToDevice, st));
+    else BCK(cudaMemsetAsync(h->Xi, 0, sizeof(double) * NR, st));
+    BCK(cudaMemcpyAsync(h->Z, h->warm_z ? h->Z0i : h->Bi, sizeof(double) * MR, cudaMemcpyDeviceToDevice, st));
     BCK(cudaMemsetAsync(h->iters_done, 0, sizeof(int64_t) * h->count, st));
     std::vector<int64_t> cap(h->count, max_iter);
     std::vector<int> ones(h->count, 1), fours(h->count, REBK_MAX_ITER);
@@ -990,9 +1001,10 @@ rebk_status run_batch(rebk_batch h, int tau, double tol, int64_t max_iter, int64
 
 }  // namespace
 
-extern "C" rebk_status rebk_batch_solve(rebk_batch h, const double *B, double *X, const double *X_ref,
-                                        double tol, int64_t max_iter, int64_t inner_iters, uint64_t seed,
-                                        int32_t *status_out, rebk_batch_stats *stats) {
+extern "C" rebk_status rebk_batch_solve_ex(rebk_batch h, const double *B, double *X, const double *X_ref,
+                                           const double *X0, const double *Z0, double tol, int64_t max_iter,
+                                           int64_t inner_iters, uint64_t seed, int32_t *status_out,
+                                           rebk_batch_stats *stats) {
     set_last_error("");
     if (!h) return bfail(REBK_EINVAL, "NULL handle");
     if (!B || !X) return bfail(REBK_EINVAL, "B and X must be device pointers");
@@ -1001,6 +1013,16 @@ extern "C" rebk_status rebk_batch_solve(rebk_batch h, const double *B, double *X
     if (h->own_stream) {  // order after the caller's work on the legacy default stream
         BCK(cudaEventRecord(h->ev0, 0));
         BCK(cudaStreamWaitEvent(st, h->ev0, 0));
+    }
+    h->warm_x = X0 != nullptr;
+    h->warm_z = Z0 != nullptr;
+    if (X0) {
+        if (!h->X0i) BCK(cudaMalloc(&h->X0i, sizeof(double) * (size_t)h->Nrows * kR));
+        batch_pack_kernel<<<blocks_for(h->Nrows * kR, 256), 256, 0, st>>>(h->Nrows, h->nrhs, X0, h->X0i);
+    }
+    if (Z0) {
+        if (!h->Z0i) BCK(cudaMalloc(&h->Z0i, sizeof(double) * (size_t)h->Mrows * kR));
+        batch_pack_kernel<<<blocks_for(h->Mrows * kR, 256), 256, 0, st>>>(h->Mrows, h->nrhs, Z0, h->Z0i);
     }
     const bool use_ref = X_ref != nullptr;
     if (inner_iters <= 0) inner_iters = use_ref ? max_iter : 2000;
@@ -1044,4 +1066,11 @@ extern "C" rebk_status rebk_batch_solve(rebk_batch h, const double *B, double *X
     if (status_out) BCK(cudaMemcpyAsync(status_out, h->status, sizeof(int) * h->count, cudaMemcpyDeviceToDevice, st));
     BCK(cudaStreamSynchronize(st));
     return REBK_OK;
+}
+
+extern "C" rebk_status rebk_batch_solve(rebk_batch h, const double *B, double *X, const double *X_ref,
+                                        double tol, int64_t max_iter, int64_t inner_iters, uint64_t seed,
+                                        int32_t *status_out, rebk_batch_stats *stats) {
+    return rebk_batch_solve_ex(h, B, X, X_ref, nullptr, nullptr, tol, max_iter, inner_iters, seed, status_out,
+                               stats);
 }

@@ -147,6 +147,9 @@ cudaError_t beta_max_device(const double *A, int64_t lda, int64_t m, int64_t n, 
 // out[0] = sum (a + x - r)^2 over n (a may be NULL), out[1] = sum r^2.
 cudaError_t err_norms(const double *a, const double *x, const double *r, int64_t n, double *out,
                       cudaStream_t st);
+// the same with an FP32 x (a correction): out[0] = sum (a + x - r)^2, out[1] = sum r^2.
+cudaError_t err_norms_f32(const double *a, const float *x, const double *r, int64_t n, double *out,
+                          cudaStream_t st);
 cudaError_t sum_sq(const double *v, int64_t n, double *out, cudaStream_t st);
 // f = b - z - ym (length m); g = yn copy handled by caller
 cudaError_t form_f(const double *b, const double *z, const double *ym, double *f, int64_t m,

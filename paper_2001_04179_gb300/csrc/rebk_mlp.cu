@@ -1,12 +1,18 @@
 // rebk_mlp.cu -- the learned warm start: a small network y = W3 relu(W2 relu(W1 b))
-// whose output gives the starting point x^0 = A^T y, z^0 = b - A x^0 of REBK.
+// (output scale s: y = s W3 relu(W2 relu(W1 b))) whose output gives the starting
+// point x^0 = A^T y, z^0 = b - A x^0 of REBK.
 //
 // Theorem main of Du, Si, Sun (arXiv:2001.04179) needs x^0 in range(A^T) and
 // z^0 in b + range(A); x^0 = A^T y satisfies the first for any y and z^0 =
 // b - A x^0 the second, so the solve still converges to A^+ b while its error
 // bound starts from ||x^0 - A^+ b|| and ||z^0 - b_perp|| = ||A (A^+ b - x^0)||,
 // both small when the network is good.  The network is trained on
-// (b, A^+ b) pairs with the loss mean ||A^T y - A^+ b||^2.
+// solver-generated pairs with either the loss mean ||A^T y - A^+ b||^2 or the
+// y-space loss mean ||y - y*||^2 / ||y*||^2, y* = (A^T)^+ A^+ b (the minimum-norm
+// solution of A^T y = A^+ b, also a solver output).  The y-space loss weighs the
+// error of x^0 in the direction of singular value sigma by 1 / sigma^2, the
+// directions the iteration converges slowest in; the x-space loss shrinks their
+// gradient by sigma^2 instead.
 //
 // Arithmetic: BF16 operands, FP32 accumulation on the tensor cores
 // (mma.sync m16n8k16), FP32 master weights and Adam moments.  The network is a
@@ -157,6 +163,40 @@ __global__ void residual_kernel(const float *P, const double *X, float *R, __nv_
     if ((threadIdx.x & 31) == 0) atomicAdd(loss, s);
 }
 
+// y-space relative loss, one CTA (256 threads) per batch row b:
+// dY[b] = coef (Y[b] - T[b]) / ||T[b]||^2 (0 for a zero target), BF16 copy;
+// loss[0] += ||Y[b] - T[b]||^2 / ||T[b]||^2.
+__global__ void __launch_bounds__(256) yrel_kernel(const float *Y, const double *T, int64_t m, double coef,
+                                                   float *dY, __nv_bfloat16 *dYb, double *loss) {
+    __shared__ double red[2][8];
+    const int64_t off = (int64_t)blockIdx.x * m;
+    double st = 0.0, sd = 0.0;
+    for (int64_t e = threadIdx.x; e < m; e += blockDim.x) {
+        const double tv = T[off + e], d = (double)Y[off + e] - tv;
+        st += tv * tv;
+        sd += d * d;
+    }
+    st = warp_sum(st);
+    sd = warp_sum(sd);
+    if ((threadIdx.x & 31) == 0) {
+        red[0][threadIdx.x >> 5] = st;
+        red[1][threadIdx.x >> 5] = sd;
+    }
+    __syncthreads();
+    double nt = 0.0, nd = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        nt += red[0][w];
+        nd += red[1][w];
+    }
+    const double inv = nt > 0.0 ? 1.0 / nt : 0.0;
+    for (int64_t e = threadIdx.x; e < m; e += blockDim.x) {
+        const float g = (float)(coef * ((double)Y[off + e] - T[off + e]) * inv);
+        dY[off + e] = g;
+        dYb[off + e] = __float2bfloat16_rn(g);
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, nd * inv);
+}
+
 // Adam on FP32 master weights; refreshes the BF16 copy.
 __global__ void adam_kernel(float *w, const float *grad, float *m1, float *m2, __nv_bfloat16 *wb, int64_t n,
                             float lr, float b1, float b2, float eps, float c1, float c2) {
@@ -216,6 +256,8 @@ struct rebk_mlp_s {
           *dH1 = nullptr;
     double *loss = nullptr;
     int64_t step = 0;
+    int32_t loss_kind = REBK_MLP_LOSS_X;
+    float out_scale = 1.f;  // y = out_scale * W3 relu(W2 relu(W1 b))
 };
 
 namespace {
@@ -257,6 +299,7 @@ rebk_status forward(rebk_mlp h, int64_t batch) {
     g.relu = 1;
     MCK(gemm(g, st));
     g = gemm_args((int)batch, (int)m, (int)H, h->H2b, H, 1, h->wb[2], 1, H, h->Y, m, h->Yb, m);
+    g.alpha = h->out_scale;
     MCK(gemm(g, st));
     return REBK_OK;
 }
@@ -396,15 +439,24 @@ rebk_status rebk_mlp_gradients(rebk_mlp h, const double *Bm, const double *Xls, 
     MCK(cudaGetLastError());
     s = forward(h, batch);
     if (s != REBK_OK) return s;
-    // P = Y A (batch x n): A^T y for every sample; R = P - X_ls
-    MCK(gemm(gemm_args((int)batch, (int)n, (int)m, h->Yb, m, 1, h->Ab, n, 1, h->P, n, nullptr, 0), st));
     MCK(cudaMemsetAsync(h->loss, 0, sizeof(double), st));
-    residual_kernel<<<eblocks(batch * n), 256, 0, st>>>(h->P, Xls, h->R, h->Rb, batch * n, h->loss);
-    MCK(cudaGetLastError());
-    // dY = (2 / batch) R A^T (batch x m)
-    GemmArgs g = gemm_args((int)batch, (int)m, (int)n, h->Rb, n, 1, h->Ab, 1, n, h->dY, m, h->dYb, m);
-    g.alpha = 2.f / (float)batch;
-    MCK(gemm(g, st));
+    // dY: gradient w.r.t. the last layer's unscaled output (the loss gradient in y times out_scale)
+    GemmArgs g;
+    if (h->loss_kind == REBK_MLP_LOSS_X) {
+        // P = Y A (batch x n): A^T y for every sample; R = P - X_ls
+        MCK(gemm(gemm_args((int)batch, (int)n, (int)m, h->Yb, m, 1, h->Ab, n, 1, h->P, n, nullptr, 0), st));
+        residual_kernel<<<eblocks(batch * n), 256, 0, st>>>(h->P, Xls, h->R, h->Rb, batch * n, h->loss);
+        MCK(cudaGetLastError());
+        // dY = (2 s / batch) R A^T (batch x m)
+        g = gemm_args((int)batch, (int)m, (int)n, h->Rb, n, 1, h->Ab, 1, n, h->dY, m, h->dYb, m);
+        g.alpha = 2.f * h->out_scale / (float)batch;
+        MCK(gemm(g, st));
+    } else {
+        // dY = (2 s / batch) (Y - Y*) / ||Y*||^2 per row
+        yrel_kernel<<<(unsigned)batch, 256, 0, st>>>(h->Y, Xls, m, 2.0 * h->out_scale / (double)batch, h->dY,
+                                                     h->dYb, h->loss);
+        MCK(cudaGetLastError());
+    }
     // dW3 = dY^T H2 (m x H)
     MCK(gemm(gemm_args((int)m, (int)H, (int)batch, h->dYb, 1, m, h->H2b, H, 1, h->g[2], H, nullptr, 0), st));
     // dH2 = (dY W3) * [H2 > 0]
@@ -444,6 +496,15 @@ rebk_status rebk_mlp_train_step(rebk_mlp h, const double *Bm, const double *Xls,
                                                           h->wsize[l], (float)lr, b1, b2, 1e-8f, c1, c2);
     MCK(cudaGetLastError());
     MCK(cudaStreamSynchronize(st));
+    return REBK_OK;
+}
+
+rebk_status rebk_mlp_set_loss(rebk_mlp h, int32_t loss, double out_scale) {
+    if (!h) return mfail(REBK_EINVAL, "NULL network");
+    if (loss != REBK_MLP_LOSS_X && loss != REBK_MLP_LOSS_Y_REL) return mfail(REBK_EINVAL, "unknown loss");
+    if (!(out_scale > 0.0) || !std::isfinite(out_scale)) return mfail(REBK_EINVAL, "out_scale must be > 0");
+    h->loss_kind = loss;
+    h->out_scale = (float)out_scale;
     return REBK_OK;
 }
 

@@ -336,12 +336,13 @@ __global__ void power_kernel(const double *__restrict__ gram, int tau, int64_t t
 // ---------------------------------------------------------------------------
 // Small vector kernels
 // ---------------------------------------------------------------------------
-__global__ void err_norms_kernel(const double *__restrict__ a, const double *__restrict__ x,
+template <typename TX>
+__global__ void err_norms_kernel(const double *__restrict__ a, const TX *__restrict__ x,
                                  const double *__restrict__ r, int64_t n, double *out) {
     __shared__ double s1[32], s2[32];
     double e2 = 0.0, r2 = 0.0;
     for (int64_t j = threadIdx.x; j < n; j += blockDim.x) {
-        const double d = (a ? a[j] : 0.0) + x[j] - r[j];
+        const double d = (a ? a[j] : 0.0) + (double)x[j] - r[j];
         e2 = fma(d, d, e2);
         r2 = fma(r[j], r[j], r2);
     }
@@ -499,14 +500,20 @@ cudaError_t beta_max_device(const double *A, int64_t lda, int64_t m, int64_t n, 
 
 cudaError_t err_norms(const double *a, const double *x, const double *r, int64_t n, double *out,
                       cudaStream_t st) {
-    err_norms_kernel<<<1, 1024, 0, st>>>(a, x, r, n, out);
+    err_norms_kernel<double><<<1, 1024, 0, st>>>(a, x, r, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t err_norms_f32(const double *a, const float *x, const double *r, int64_t n, double *out,
+                          cudaStream_t st) {
+    err_norms_kernel<float><<<1, 1024, 0, st>>>(a, x, r, n, out);
     return cudaGetLastError();
 }
 
 cudaError_t sum_sq(const double *v, int64_t n, double *out, cudaStream_t st) {
     // sum v^2 = err_norms with a = NULL, x = v, r = 0 would need a zero vector;
     // reuse the kernel with r = v (out[1] = sum v^2).
-    err_norms_kernel<<<1, 1024, 0, st>>>(nullptr, v, v, n, out);
+    err_norms_kernel<double><<<1, 1024, 0, st>>>(nullptr, v, v, n, out);
     return cudaGetLastError();
 }
 

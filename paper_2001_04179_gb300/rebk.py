@@ -90,6 +90,8 @@ _SIGNATURES = {
     "rebk_batch_destroy": ([_P], None),
     "rebk_batch_solve": ([_P, _P, _P, _P, ctypes.c_double, ctypes.c_int64, ctypes.c_int64, ctypes.c_uint64,
                           _P, ctypes.POINTER(RebkBatchStats)], ctypes.c_int),
+    "rebk_batch_solve_ex": ([_P, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
+                             ctypes.c_uint64, _P, ctypes.POINTER(RebkBatchStats)], ctypes.c_int),
     "rebk_batch_info": ([_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "rebk_solve_noalloc": ([_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                             ctypes.c_double, _P, _P, _P, ctypes.c_int64, ctypes.c_uint64, _P], ctypes.c_int),
@@ -101,6 +103,7 @@ _SIGNATURES = {
     "rebk_mlp_train_step": ([_P, _P, _P, ctypes.c_int64, ctypes.c_double, ctypes.POINTER(ctypes.c_double)],
                             ctypes.c_int),
     "rebk_mlp_get_weights": ([_P, _P], ctypes.c_int),
+    "rebk_mlp_set_loss": ([_P, ctypes.c_int32, ctypes.c_double], ctypes.c_int),
     "rebk_mlp_shape": ([_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "rebk_warm_start": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "rebk_last_error": ([], ctypes.c_char_p),

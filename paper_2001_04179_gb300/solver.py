@@ -3,6 +3,7 @@ for device memory and streams.  Every computation runs in librebk.so."""
 from __future__ import annotations
 
 import ctypes
+import math
 from typing import Optional, Sequence
 
 import numpy as np
@@ -222,17 +223,18 @@ class BatchSolver:
         return [Xn[self.nrow[i]:self.nrow[i + 1]] for i in range(self.count)]
 
     def solve(self, B, X_ref=None, tol: float = 1e-8, max_iter: int = 200000, inner_iters: int = 0,
-              seed: int = 0):
-        """B: CUDA float64 (sum m_i) x nrhs; X_ref: (sum n_i) x nrhs or None.
+              seed: int = 0, X0=None, Z0=None):
+        """B: CUDA float64 (sum m_i) x nrhs; X_ref: (sum n_i) x nrhs or None;
+        X0 / Z0: starting points laid out like X / B, or None (x = 0, z = b).
         Returns dict(x, status (per system), stats)."""
         torch = _torch()
         X = torch.empty((int(self.nrow[-1]), self.nrhs), dtype=torch.float64, device=B.device)
         status = torch.zeros(self.count, dtype=torch.int32, device=B.device)
         stats = _r.RebkBatchStats()
-        st = _r.load().rebk_batch_solve(self._h, ctypes.c_void_p(B.data_ptr()), ctypes.c_void_p(X.data_ptr()),
-                                        None if X_ref is None else ctypes.c_void_p(X_ref.data_ptr()),
-                                        float(tol), int(max_iter), int(inner_iters), int(seed),
-                                        ctypes.c_void_p(status.data_ptr()), ctypes.byref(stats))
+        ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
+        st = _r.load().rebk_batch_solve_ex(self._h, ptr(B), ptr(X), ptr(X_ref), ptr(X0), ptr(Z0),
+                                           float(tol), int(max_iter), int(inner_iters), int(seed),
+                                           ctypes.c_void_p(status.data_ptr()), ctypes.byref(stats))
         _r.check(st)
         return {"x": X, "status": status.cpu().numpy(), "stats": stats.as_dict()}
 
@@ -277,6 +279,31 @@ class WarmStartNet:
         _r.check(_r.load().rebk_mlp_forward(self._h, ctypes.c_void_p(Bm.data_ptr()), Bm.shape[0],
                                             ctypes.c_void_p(Y.data_ptr())))
         return Y
+
+    LOSSES = {"x": 0, "y_rel": 1}
+
+    def set_loss(self, loss: str = "x", out_scale: float = 1.0):
+        """loss "x": mean ||A^T y - x_ls||^2 (targets x_ls, N x n); "y_rel": mean
+        ||y - y*||^2 / ||y*||^2 (targets y* = (A^T)^+ x_ls, N x m).  out_scale
+        multiplies the network output (see rebk_mlp_set_loss)."""
+        _r.check(_r.load().rebk_mlp_set_loss(self._h, self.LOSSES[loss], float(out_scale)))
+        self.loss, self.out_scale = loss, float(out_scale)
+
+    def fit(self, Bm, T, steps: int, lr: float = 1e-3, batch: int = 256) -> list:
+        """Adam over `steps` minibatches of `batch` consecutive rows of Bm (CUDA,
+        N x m) and T (the targets of the selected loss), cycling through the
+        rows in the caller's order, with the learning rate on a cosine schedule
+        from lr to 0.  Returns the minibatch losses."""
+        N = int(Bm.shape[0])
+        if N < batch:
+            raise ValueError("fewer training rows than one minibatch")
+        nb = N // batch
+        losses = []
+        for k in range(steps):
+            i = (k % nb) * batch
+            lr_k = lr * 0.5 * (1.0 + math.cos(math.pi * k / steps))
+            losses.append(self.train_step(Bm[i:i + batch], T[i:i + batch], lr=lr_k))
+        return losses
 
     def gradients(self, Bm, Xls):
         grads = [np.zeros(s, dtype=np.float32) for s in self.shapes]

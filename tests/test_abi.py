@@ -65,3 +65,10 @@ def test_package_has_no_cpu_fallback():
     for path in glob.glob(os.path.join(pkg, "*.py")):
         src = open(path).read()
         assert "import oracle" not in src and "from oracle" not in src, path
+
+
+def test_network_loss_selection_rejects_bad_arguments_on_the_host():
+    from paper_2001_04179_gb300 import rebk as R
+    lib = R.load()
+    assert lib.rebk_mlp_set_loss(None, 0, 1.0) == R.REBK_EINVAL
+    assert lib.rebk_batch_solve_ex(None, None, None, None, None, None, 0.0, 0, 0, 0, None, None) == R.REBK_EINVAL
