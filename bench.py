@@ -366,14 +366,7 @@ def run_warm(args):
         ev0.record(stream)
         X0 = Z0 = None
         if mode == "warm":  # the network and the x0 / z0 products are inside the timed region
-            X0 = torch.empty(nbs * n5, 8, dtype=torch.float64, device=dev)
-            Z0 = torch.empty(nbs * m5, 8, dtype=torch.float64, device=dev)
-            for i in range(nbs):
-                for r_ in range(8):
-                    b = Bb[i * m5:(i + 1) * m5, r_].contiguous()
-                    x0, z0 = net.warm_start(sol, b)
-                    X0[i * n5:(i + 1) * n5, r_] = x0
-                    Z0[i * m5:(i + 1) * m5, r_] = z0
+            X0, Z0 = net.warm_start_batch(sol, Bb, nbe, group=8)
         out = bsv.solve(Bb, X_ref=Xrb, tol=TOL, max_iter=400000, seed=11, X0=X0, Z0=Z0)
         ev1.record(stream)
         torch.cuda.synchronize()

@@ -349,6 +349,19 @@ rebk_status rebk_mlp_shape(rebk_mlp h, int64_t *m, int64_t *n);
 rebk_status rebk_warm_start(rebk_handle h, rebk_mlp net, const double *b, double *x0, double *z0);
 
 /*
+ * rebk_warm_start for `count` right-hand sides at once (the network runs on
+ * batches of up to its capacity).  Grouped layout: right-hand side j is column
+ * j % group of block j / group, each block row-major (length x group) -- the
+ * layout rebk_batch_solve_ex uses for systems sharing A with group = nrhs;
+ * group = 1 is one right-hand side per row.  B: device, count / group blocks of
+ * m x group; X0, Z0: device outputs, blocks of n x group and m x group.
+ * Errors: EINVAL (NULL pointers, count not a positive multiple of group, shape
+ * mismatch), ENOMEM (scratch of 2 x capacity x m doubles), ECUDA.
+ */
+rebk_status rebk_warm_start_batch(rebk_handle h, rebk_mlp net, const double *B, int64_t count, int32_t group,
+                                  double *X0, double *Z0);
+
+/*
  * Plain FP64 REBK for a fixed number of iterations without allocating any
  * memory.  The paper has no counterpart to this call; it exists for callers
  * that must not call cudaMalloc -- code running while a CUDA graph is being

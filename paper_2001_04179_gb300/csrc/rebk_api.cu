@@ -734,6 +734,51 @@ rebk_status rebk_warm_start(rebk_handle h, rebk_mlp net, const double *b, double
     return REBK_OK;
 }
 
+rebk_status rebk_warm_start_batch(rebk_handle h, rebk_mlp net, const double *B, int64_t count, int32_t group,
+                                  double *X0, double *Z0) {
+    g_last_error.clear();
+    if (!h || !net || !B || !X0 || !Z0) return fail(REBK_EINVAL, "NULL argument");
+    if (count < 1 || group < 1 || count % group != 0) return fail(REBK_EINVAL, "count must be a positive multiple of group");
+    int64_t nm = 0, nn = 0;
+    rebk_status s = rebk_mlp_shape(net, &nm, &nn);
+    if (s != REBK_OK) return s;
+    if (nm != h->m || nn != h->n) return fail(REBK_EINVAL, "network shape does not match the solver's A");
+    const int64_t cap = mlp_batch_capacity(net);
+    const cudaStream_t st = h->stream;
+    const int64_t chunk = std::min<int64_t>(cap, count);
+    double *Bc = nullptr, *Yc = nullptr;
+    cudaError_t ae = cudaMalloc(&Bc, sizeof(double) * chunk * h->m);
+    if (ae == cudaSuccess) ae = cudaMalloc(&Yc, sizeof(double) * chunk * h->m);
+    auto release = [&]() {
+        if (Bc) cudaFree(Bc);
+        if (Yc) cudaFree(Yc);
+    };
+    if (ae != cudaSuccess) {
+        release();
+        return fail(ae == cudaErrorMemoryAllocation ? REBK_ENOMEM : REBK_ECUDA, cudaGetErrorString(ae));
+    }
+    rebk_status out = REBK_OK;
+    for (int64_t j0 = 0; j0 < count && out == REBK_OK; j0 += chunk) {
+        const int64_t cnt = std::min(chunk, count - j0);
+        cudaError_t e = group_gather(B, j0, cnt, group, h->m, Bc, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the network may run on another stream
+        if (e == cudaSuccess) {
+            out = rebk_mlp_forward(net, Bc, cnt, Yc);  // y for the chunk (rows of m)
+            if (out != REBK_OK) break;
+        }
+        for (int64_t c = 0; c < cnt && e == cudaSuccess; ++c) {
+            // x0 = A^T y and A x0 with the FP64 copy of A; z0 = b - A x0
+            e = dual_sweep(h->A64, h->lda, h->m, h->n, nullptr, false, Yc + c * h->m, false, nullptr, h->yn, st);
+            if (e == cudaSuccess) e = dual_sweep(h->A64, h->lda, h->m, h->n, h->yn, false, nullptr, false, h->f, nullptr, st);
+            if (e == cudaSuccess) e = group_store_xz(h->yn, h->n, Bc + c * h->m, h->f, h->m, j0 + c, group, X0, Z0, st);
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) out = fail(REBK_ECUDA, cudaGetErrorString(e));
+    }
+    release();
+    return out;
+}
+
 rebk_status rebk_solve(rebk_handle h, const double *b, double *x, double tol, int64_t max_iter,
                        uint64_t seed, rebk_stats *stats) {
     return rebk_solve_ex(h, b, x, tol, max_iter, seed, nullptr, stats);

@@ -8,6 +8,8 @@
 
 #include <string>
 
+struct rebk_mlp_s;  // the warm-start network (rebk_mlp.cu)
+
 namespace rebk {
 
 constexpr int kThreads = 512;              // threads per CTA of the persistent kernel
@@ -147,6 +149,15 @@ cudaError_t beta_max_device(const double *A, int64_t lda, int64_t m, int64_t n, 
 // out[0] = sum (a + x - r)^2 over n (a may be NULL), out[1] = sum r^2.
 cudaError_t err_norms(const double *a, const double *x, const double *r, int64_t n, double *out,
                       cudaStream_t st);
+// Grouped right-hand-side layout (right-hand side j = column j % g of block j / g,
+// each block len x g row-major): gather cnt of them from j0 into rows of len;
+// store x (n) and b - ax (m) of right-hand side j.
+cudaError_t group_gather(const double *src, int64_t j0, int64_t cnt, int g, int64_t len, double *dst,
+                         cudaStream_t st);
+cudaError_t group_store_xz(const double *x, int64_t n, const double *b, const double *ax, int64_t m, int64_t j, int g,
+                           double *X0, double *Z0, cudaStream_t st);
+// batch capacity of a warm-start network (rebk_mlp.cu)
+int64_t mlp_batch_capacity(::rebk_mlp_s *h);
 // the same with an FP32 x (a correction): out[0] = sum (a + x - r)^2, out[1] = sum r^2.
 cudaError_t err_norms_f32(const double *a, const float *x, const double *r, int64_t n, double *out,
                           cudaStream_t st);

@@ -260,6 +260,10 @@ struct rebk_mlp_s {
     float out_scale = 1.f;  // y = out_scale * W3 relu(W2 relu(W1 b))
 };
 
+namespace rebk {
+int64_t mlp_batch_capacity(::rebk_mlp_s *h) { return h ? h->cap : 0; }
+}  // namespace rebk
+
 namespace {
 
 rebk_status mfail(rebk_status s, const std::string &msg) {

@@ -504,6 +504,48 @@ cudaError_t err_norms(const double *a, const double *x, const double *r, int64_t
     return cudaGetLastError();
 }
 
+// Grouped layout: right-hand side j is column j % g of the row-major (len x g)
+// block j / g.  dst[c * len + k] = entry k of right-hand side j0 + c.
+__global__ void group_gather_kernel(const double *__restrict__ src, int64_t j0, int64_t cnt, int g, int64_t len,
+                                    double *__restrict__ dst) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < cnt * len;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / len, k = e - c * len, j = j0 + c;
+        dst[e] = src[((j / g) * len + k) * g + (j % g)];
+    }
+}
+
+// x0 and z0 = b - ax of right-hand side j into the grouped layouts.
+__global__ void group_store_xz_kernel(const double *__restrict__ x, int64_t n, const double *__restrict__ b,
+                                      const double *__restrict__ ax, int64_t m, int64_t j, int g,
+                                      double *__restrict__ X0, double *__restrict__ Z0) {
+    const int64_t gb = j / g, col = j % g;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n + m;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        if (e < n) X0[(gb * n + e) * g + col] = x[e];
+        else {
+            const int64_t k = e - n;
+            Z0[(gb * m + k) * g + col] = b[k] - ax[k];
+        }
+    }
+}
+
+cudaError_t group_gather(const double *src, int64_t j0, int64_t cnt, int g, int64_t len, double *dst,
+                         cudaStream_t st) {
+    const int64_t tot = cnt * len;
+    group_gather_kernel<<<grid_for(tot, 256) > 4096 ? 4096 : grid_for(tot, 256), 256, 0, st>>>(src, j0, cnt, g, len,
+                                                                                                  dst);
+    return cudaGetLastError();
+}
+
+cudaError_t group_store_xz(const double *x, int64_t n, const double *b, const double *ax, int64_t m, int64_t j, int g,
+                           double *X0, double *Z0, cudaStream_t st) {
+    const int64_t tot = n + m;
+    group_store_xz_kernel<<<grid_for(tot, 256) > 1024 ? 1024 : grid_for(tot, 256), 256, 0, st>>>(x, n, b, ax, m, j,
+                                                                                                    g, X0, Z0);
+    return cudaGetLastError();
+}
+
 cudaError_t err_norms_f32(const double *a, const float *x, const double *r, int64_t n, double *out,
                           cudaStream_t st) {
     err_norms_kernel<float><<<1, 1024, 0, st>>>(a, x, r, n, out);

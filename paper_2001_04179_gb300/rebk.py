@@ -106,6 +106,7 @@ _SIGNATURES = {
     "rebk_mlp_set_loss": ([_P, ctypes.c_int32, ctypes.c_double], ctypes.c_int),
     "rebk_mlp_shape": ([_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "rebk_warm_start": ([_P, _P, _P, _P, _P], ctypes.c_int),
+    "rebk_warm_start_batch": ([_P, _P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P], ctypes.c_int),
     "rebk_last_error": ([], ctypes.c_char_p),
     "rebk_version": ([], ctypes.c_char_p),
 }

@@ -327,6 +327,18 @@ class WarmStartNet:
         _r.check(_r.load().rebk_mlp_get_weights(self._h, ctypes.cast(arr, ctypes.c_void_p)))
         return ws
 
+    def warm_start_batch(self, solver: "Solver", B, count: int, group: int = 1):
+        """(X0, Z0) for `count` right-hand sides in the grouped layout of B
+        (CUDA float64; right-hand side j = column j % group of block j // group,
+        blocks of m x group), e.g. BatchSolver.solve's X0 / Z0 for systems sharing A."""
+        torch = _torch()
+        X0 = torch.empty((count // group * self.n, group), dtype=torch.float64, device=B.device)
+        Z0 = torch.empty((count // group * self.m, group), dtype=torch.float64, device=B.device)
+        _r.check(_r.load().rebk_warm_start_batch(solver._h, self._h, ctypes.c_void_p(B.data_ptr()), int(count),
+                                                 int(group), ctypes.c_void_p(X0.data_ptr()),
+                                                 ctypes.c_void_p(Z0.data_ptr())))
+        return X0, Z0
+
     def warm_start(self, solver: "Solver", b):
         """(x0, z0) for solver.solve / solve_refined."""
         torch = _torch()

@@ -169,3 +169,23 @@ def test_y_space_training_on_batched_solver_targets_cuts_iterations():
             assert np.mean(warm) < 0.85 * np.mean(cold), (st, np.mean(warm), np.mean(cold))
         else:  # BF16: bounded by the refinement's stagnation rule, no runaway pass
             assert np.mean(warm) < 2.0 * np.mean(cold), (st, np.mean(warm), np.mean(cold))
+
+
+def test_batched_warm_start_matches_single_right_hand_sides():
+    rng = np.random.default_rng(3)
+    m, n = 200, 60
+    A = rng.standard_normal((m, n))
+    net = WarmStartNet(A, hidden=64, batch_capacity=16, seed=2)
+    sol = Solver(A, 8, 8, alpha=0.0, storage=("fp32",))
+    count, g = 40, 8  # three network batches (16, 16, 8)
+    Bg = rng.standard_normal((count // g * m, g))
+    X0, Z0 = net.warm_start_batch(sol, _t(Bg), count, group=g)
+    X0, Z0 = X0.cpu().numpy(), Z0.cpu().numpy()
+    for j in range(count):
+        blk, col = divmod(j, g)
+        b = Bg[blk * m:(blk + 1) * m, col]
+        x0, z0 = net.warm_start(sol, _t(b))
+        assert _rel(X0[blk * n:(blk + 1) * n, col], x0.cpu().numpy()) <= 1e-12
+        assert _rel(Z0[blk * m:(blk + 1) * m, col], z0.cpu().numpy()) <= 1e-12
+    with pytest.raises(R.RebkError):
+        net.warm_start_batch(sol, _t(Bg), count - 1, group=g)
