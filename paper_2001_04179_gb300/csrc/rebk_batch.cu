@@ -127,7 +127,57 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                 const int64_t j0 = (int64_t)j * a.tau;
                 const int wc = (int)((j0 + a.tau <= n ? a.tau : n - j0));
                 const float cJ = a.coef_c[d.tc + j];
-                {
+                // full, 16-byte aligned blocks of 16..128 columns: tau/4 lanes per row, one
+                // 16-byte load per lane, 32/(tau/4) rows per warp instruction
+                const bool fast = wc == a.tau && (j0 & 3) == 0 && wc >= 16 && wc <= 128 && (wc & (wc - 1)) == 0;
+                const int lpr = wc >> 2, rpw = fast ? 32 / lpr : 1, sub = lane % lpr, rrow = lane / lpr;
+                if (fast) {
+                    constexpr int UR = 2;
+                    float acc[4][kR];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e)
+#pragma unroll
+                        for (int r = 0; r < kR; ++r) acc[e][r] = 0.f;
+                    for (int64_t row0 = (int64_t)warp * rpw * UR; row0 < m; row0 += (int64_t)kBW * rpw * UR) {
+                        float4 av[UR];
+                        float z[UR][kR];
+#pragma unroll
+                        for (int u = 0; u < UR; ++u) {
+                            const int64_t row = row0 + (int64_t)u * rpw + rrow;
+                            if (row < m) {
+                                av[u] = __ldg(reinterpret_cast<const float4 *>(A + row * lda + j0) + sub);
+                                load8(dZ + row * kR, z[u]);
+                            } else {
+                                av[u] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                                for (int r = 0; r < kR; ++r) z[u][r] = 0.f;
+                            }
+                        }
+#pragma unroll
+                        for (int u = 0; u < UR; ++u) {
+                            const float ae[4] = {av[u].x, av[u].y, av[u].z, av[u].w};
+#pragma unroll
+                            for (int e = 0; e < 4; ++e)
+#pragma unroll
+                                for (int r = 0; r < kR; ++r) acc[e][r] = fmaf(ae[e], z[u][r], acc[e][r]);
+                        }
+                    }
+                    // add the warp's row lanes (same sub), then one lane per column quad writes
+                    for (int o = lpr; o < 32; o <<= 1)
+#pragma unroll
+                        for (int e = 0; e < 4; ++e)
+#pragma unroll
+                            for (int r = 0; r < kR; ++r) acc[e][r] += __shfl_xor_sync(0xffffffffu, acc[e][r], o);
+                    if (rrow == 0) {
+#pragma unroll
+                        for (int e = 0; e < 4; ++e) {
+                            float *dst = Wpart + ((size_t)warp * 32 * CPL + 4 * sub + e) * kR;
+                            *reinterpret_cast<float4 *>(dst) = make_float4(acc[e][0], acc[e][1], acc[e][2], acc[e][3]);
+                            *reinterpret_cast<float4 *>(dst + 4) =
+                                make_float4(acc[e][4], acc[e][5], acc[e][6], acc[e][7]);
+                        }
+                    }
+                } else {
                     constexpr int UR = CPL >= 8 ? 1 : (CPL >= 4 ? 2 : 4);  // rows in flight per warp
                     float acc[CPL][kR];
 #pragma unroll
@@ -176,8 +226,46 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                     S[(j0 + e / kR) * kR + e % kR] += cJ * sum;
                 }
                 __syncthreads();
+                if (fast) {
+                    // z update: the lane's 4 columns of W stay in registers; each row's dot is
+                    // added over its tau/4 lanes
+                    constexpr int UR = 2;
+                    float wv[4][kR];
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) load8(W + (4 * sub + e) * kR, wv[e]);
+                    for (int64_t row0 = (int64_t)warp * rpw * UR; row0 < m; row0 += (int64_t)kBW * rpw * UR) {
+                        float4 av[UR];
+#pragma unroll
+                        for (int u = 0; u < UR; ++u) {
+                            const int64_t row = row0 + (int64_t)u * rpw + rrow;
+                            av[u] = row < m ? __ldg(reinterpret_cast<const float4 *>(A + row * lda + j0) + sub)
+                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+                        }
+#pragma unroll
+                        for (int u = 0; u < UR; ++u) {
+                            const float ae[4] = {av[u].x, av[u].y, av[u].z, av[u].w};
+                            float t8[kR];
+#pragma unroll
+                            for (int r = 0; r < kR; ++r) {
+                                float t = 0.f;
+#pragma unroll
+                                for (int e = 0; e < 4; ++e) t = fmaf(ae[e], wv[e][r], t);
+                                t8[r] = t;
+                            }
+                            for (int o = 1; o < lpr; o <<= 1)
+#pragma unroll
+                                for (int r = 0; r < kR; ++r) t8[r] += __shfl_xor_sync(0xffffffffu, t8[r], o);
+                            const int64_t row = row0 + (int64_t)u * rpw + rrow;
+                            if (sub == 0 && row < m) {
+                                float *zr = dZ + row * kR;
+#pragma unroll
+                                for (int r = 0; r < kR; ++r) zr[r] -= cJ * t8[r];
+                            }
+                        }
+                    }
+                }
                 const bool vec4 = ((j0 & 3) == 0) && ((wc & 3) == 0);
-                for (int64_t row = tid; row < m; row += kBT) {
+                for (int64_t row = fast ? m : tid; row < m; row += kBT) {
                     float t8[kR] = {0, 0, 0, 0, 0, 0, 0, 0};
                     const float *Ar = A + row * lda + j0;
                     if (vec4) {
