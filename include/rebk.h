@@ -391,6 +391,57 @@ rebk_status rebk_solve_noalloc(const double *A, int64_t m, int64_t n, int64_t ld
                                int64_t tau_col, double alpha, const double *b, double *x, double *z,
                                int64_t iters, uint64_t seed, void *stream);
 
+/* ------------------------------------------------------------------------ */
+/* Sparse matrices                                                           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct rebk_sparse_s *rebk_sparse;
+
+typedef struct {
+    int32_t num_ctas;      /* persistent grid size; 0 = one CTA per SM                 */
+    int32_t check_every;   /* stopping-test period in iterations; 0 = 10               */
+    int32_t power_iters;   /* power iterations per block for beta_max; 0 = 100         */
+    void *stream;          /* cudaStream_t for all work; NULL = legacy default stream  */
+} rebk_sparse_options;
+
+/*
+ * Creates a solver for a sparse m x n matrix A in CSR form (host arrays:
+ * row_ptr[m + 1] int64 with row_ptr[0] = 0, col_idx[nnz] int32 strictly
+ * increasing within each row, val[nnz] FP64).  Algorithm 1 of Du, Si, Sun
+ * (arXiv:2001.04179) with row blocks of tau_row consecutive rows and column
+ * blocks of tau_col consecutive columns (the Section 3 partition), sampled by
+ * their squared Frobenius norms (sums of squared values, FP64) through the same
+ * Philox counter layout and tables as rebk_solve: on the same matrix stored
+ * densely the two draw the same blocks.  The library keeps CSR (row blocks) and
+ * a CSC copy built at creation (column blocks) on the device.  alpha <= 0
+ * picks 1.75 / beta_max (Section 3's empirical step), beta_max = the largest
+ * ||block||_2^2 / ||block||_F^2 over all blocks, ||block||_2 from power
+ * iterations (host, FP64).
+ * Errors: EINVAL (shapes, NULL pointers, indices out of range or unsorted),
+ * ENOMEM, ECUDA.
+ */
+rebk_status rebk_sparse_create(rebk_sparse *out, int64_t m, int64_t n, const int64_t *row_ptr,
+                               const int32_t *col_idx, const double *val, int64_t tau_row, int64_t tau_col,
+                               double alpha, const rebk_sparse_options *opt);
+void rebk_sparse_destroy(rebk_sparse h);
+
+/*
+ * Plain FP64 Algorithm 1 on the sparse matrix, as rebk_solve_ex: b (device, m),
+ * x (device, n, output), ext optional (x_ref stop rule checked every
+ * check_every iterations, x0, z0, z_out, idx_out, k0, stream_id).  Without
+ * x_ref the solve runs max_iter iterations.  One persistent launch runs many
+ * iterations: per iteration a column gather, a z scatter and a row gather,
+ * separated by device-wide barriers (a row scatter needs none before the next
+ * column gather, which reads z only).  Results match the dense solve of the
+ * same matrix up to summation order (FP64 atomic adds).
+ */
+rebk_status rebk_sparse_solve(rebk_sparse h, const double *b, double *x, double tol, int64_t max_iter,
+                              uint64_t seed, const rebk_solve_ext *ext, rebk_stats *stats);
+
+/* alpha in use, the beta_max estimate and the block counts (host outputs, any NULL). */
+rebk_status rebk_sparse_info(rebk_sparse h, double *alpha, double *beta_max, int32_t *row_blocks,
+                             int32_t *col_blocks);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *rebk_last_error(void);
 

@@ -1,0 +1,568 @@
+// rebk_sparse.cu -- Algorithm 1 of Du, Si, Sun (arXiv:2001.04179) on a sparse
+// matrix: CSR for the row blocks, a CSC copy for the column blocks.
+//
+// One persistent cooperative launch runs many iterations.  Iteration k (block
+// indices sampled before the launch, as in the dense path):
+//   A. w_c = A_{:,c}^T z for the columns c of J_k: each column belongs to one CTA
+//      (columns strided over the CTAs), whose threads gather over the column's
+//      entries and add up by a block reduction;                      barrier
+//   B. z -= c_J A_{:,J} w: the same CTA scatters its columns' entries into z by
+//      FP64 atomic adds;                                              barrier
+//   C. r_l = A_{l,:} x - b_l + z_l for the rows l of I_k (rows strided over the
+//      CTAs, block reductions), and every check_every iterations each CTA's
+//      share of ||x^{k-1} - x_ref||^2;                                barrier
+//   D. x -= c_I A_{I,:}^T r: scatter of the rows' entries into x.
+// No barrier follows D: the next gather A reads z only, and every CTA finishes
+// D before it reaches the next barrier, which C waits behind.  Gathers read
+// state that no CTA writes until the following barrier, so each step sees the
+// previous iterate exactly.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "rebk.h"
+#include "rebk_device.cuh"
+#include "rebk_internal.h"
+
+namespace rebk {
+namespace {
+
+constexpr int kST = 512;                     // threads per CTA
+constexpr int kSW = kST / 32;
+constexpr int kOwnMax = 512;                 // columns / rows of a block one CTA may own
+constexpr int64_t kSparseChunk = 1 << 20;    // iterations sampled per launch
+constexpr int64_t kSparseLaunchMax = 4000000;  // 3 barriers per iteration: counter headroom
+
+struct SparseArgs {
+    int64_t m, n;
+    int tau_r, tau_c;
+    const int64_t *rp;   // CSR row pointers (m + 1)
+    const int32_t *ci;   // CSR column indices
+    const double *rv;    // CSR values
+    const int64_t *cp;   // CSC column pointers (n + 1)
+    const int32_t *ri;   // CSC row indices
+    const double *cv;    // CSC values
+    const double *coef_r, *coef_c;  // alpha / ||block||_F^2 (0 for zero blocks)
+    const int32_t *idx;  // 2 * iters: (j_k, i_k)
+    int64_t iters;
+    double *z, *x;
+    const double *b;
+    const double *x_ref;  // NULL = no test
+    double tol2_abs;
+    int64_t check_every, check_offset;
+    double *acc;          // [3] rotating error accumulators, zeroed before launch
+    int *bad;             // non-finite reduction seen, zeroed before launch
+    unsigned int *bar;
+    int *status;
+    int64_t *iters_done;
+    unsigned long long timeout_ns;
+};
+
+__device__ __forceinline__ double block_sum(double v, double *red) {
+    v = warp_sum(v);
+    __syncthreads();  // red free (its last readers are past this point)
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+    __syncthreads();
+    double t = 0.0;
+#pragma unroll
+    for (int w = 0; w < kSW; ++w) t += red[w];
+    return t;
+}
+
+__global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_constant__ SparseArgs a) {
+    __shared__ double red[kSW];
+    __shared__ double own[kOwnMax];  // w_c of the CTA's columns, then r_l of its rows
+    __shared__ int s_flag;
+    const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+    const int64_t K = a.iters;
+    const bool check = a.x_ref != nullptr && a.check_every > 0;
+    const int64_t xs0 = a.n * cta / G, xs1 = a.n * (cta + 1) / G;  // this CTA's share of the test
+    unsigned int phase = 0;
+    auto barrier = [&]() -> bool {
+        ++phase;
+        return grid_barrier(a.bar, (unsigned)G * phase, a.status, a.timeout_ns, &s_flag);
+    };
+    int64_t done = K;
+    int stop = 0;
+    for (int64_t k = 1; k <= K; ++k) {
+        const int j = __ldg(a.idx + 2 * (k - 1)), i = __ldg(a.idx + 2 * (k - 1) + 1);
+        const int64_t ja = (int64_t)j * a.tau_c, jb = ja + a.tau_c < a.n ? ja + a.tau_c : a.n;
+        const int64_t ia = (int64_t)i * a.tau_r, ib = ia + a.tau_r < a.m ? ia + a.tau_r : a.m;
+        const double cJ = a.coef_c[j], cI = a.coef_r[i];
+        // ---- A: w_c = A_{:,c}^T z^{k-1} for the CTA's columns ----
+        int q = 0;
+        for (int64_t c = ja + cta; c < jb; c += G, ++q) {
+            double v = 0.0;
+            for (int64_t e = a.cp[c] + tid; e < a.cp[c + 1]; e += kST) v = fma(a.cv[e], a.z[a.ri[e]], v);
+            const double w = block_sum(v, red);
+            if (tid == 0) {
+                own[q] = w;
+                if (!isfinite(w)) atomicExch(a.bad, 1);
+            }
+        }
+        if (!barrier()) return;
+        // ---- B: z^k = z^{k-1} - c_J A_{:,J} w ----
+        q = 0;
+        for (int64_t c = ja + cta; c < jb; c += G, ++q) {
+            const double wc = own[q];
+            for (int64_t e = a.cp[c] + tid; e < a.cp[c + 1]; e += kST) atomicAdd(a.z + a.ri[e], -cJ * a.cv[e] * wc);
+        }
+        if (!barrier()) return;
+        // ---- C: r_l = A_{l,:} x^{k-1} - b_l + z^k_l; test partial of x^{k-1} ----
+        q = 0;
+        for (int64_t l = ia + cta; l < ib; l += G, ++q) {
+            double v = 0.0;
+            for (int64_t e = a.rp[l] + tid; e < a.rp[l + 1]; e += kST) v = fma(a.rv[e], a.x[a.ci[e]], v);
+            const double r = block_sum(v, red);
+            if (tid == 0) {
+                const double rl = r - a.b[l] + a.z[l];
+                own[q] = rl;
+                if (!isfinite(rl)) atomicExch(a.bad, 1);
+            }
+        }
+        const bool due = check && k >= 2 && (a.check_offset + k - 1) % a.check_every == 0;
+        if (due) {
+            double e2 = 0.0;
+            for (int64_t c = xs0 + tid; c < xs1; c += kST) {
+                const double d = a.x[c] - a.x_ref[c];
+                e2 = fma(d, d, e2);
+            }
+            e2 = block_sum(e2, red);
+            if (tid == 0) atomicAdd(a.acc + k % 3, e2);
+        }
+        if (cta == 0 && tid == 0) a.acc[(k + 1) % 3] = 0.0;  // the slot two tests ahead
+        if (!barrier()) return;
+        if (*reinterpret_cast<volatile int *>(a.bad) != 0) {
+            stop = 5;
+            done = k - 1;
+            break;
+        }
+        if (due && __ldcg(a.acc + k % 3) <= a.tol2_abs) {  // every CTA reads the same sum
+            stop = 1;
+            done = k - 1;
+            break;
+        }
+        // ---- D: x^k = x^{k-1} - c_I A_{I,:}^T r ----
+        q = 0;
+        for (int64_t l = ia + cta; l < ib; l += G, ++q) {
+            const double rl = own[q];
+            for (int64_t e = a.rp[l] + tid; e < a.rp[l + 1]; e += kST) atomicAdd(a.x + a.ci[e], -cI * a.rv[e] * rl);
+        }
+        __syncthreads();  // own[] is rewritten by the next gather
+    }
+    if (cta == 0 && tid == 0) {
+        *a.iters_done = done;
+        if (stop == 5) atomicExch(a.status, 5);
+    }
+}
+
+// Host-side power iterations (FP64) for the spectral norms of the blocks.
+double block_spectral_sq(const std::vector<int64_t> &ptr, const std::vector<int32_t> &idx,
+                         const std::vector<double> &val, int64_t l0, int64_t l1, int64_t other, int iters) {
+    // ||B||_2^2 for B = the lines l0..l1-1 of the compressed matrix (rows of CSR or
+    // columns of CSC) by power iterations on B^T B; entries index the other dimension.
+    std::vector<int32_t> cols;
+    for (int64_t l = l0; l < l1; ++l)
+        for (int64_t e = ptr[l]; e < ptr[l + 1]; ++e) cols.push_back(idx[e]);
+    std::sort(cols.begin(), cols.end());
+    cols.erase(std::unique(cols.begin(), cols.end()), cols.end());
+    if (cols.empty()) return 0.0;
+    std::vector<int32_t> pos;  // entry -> position in cols
+    pos.reserve(ptr[l1] - ptr[l0]);
+    for (int64_t e = ptr[l0]; e < ptr[l1]; ++e)
+        pos.push_back((int32_t)(std::lower_bound(cols.begin(), cols.end(), idx[e]) - cols.begin()));
+    (void)other;
+    const int64_t nc = (int64_t)cols.size(), nl = l1 - l0;
+    std::vector<double> v(nc), u(nl), w(nc);
+    for (int64_t c = 0; c < nc; ++c) v[c] = 1.0 + 0.5 * std::sin(0.37 * (double)(c + 1));  // fixed start
+    double lam = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        double nv = 0.0;
+        for (double t : v) nv += t * t;
+        nv = std::sqrt(nv);
+        if (nv == 0.0) return 0.0;
+        for (double &t : v) t /= nv;
+        for (int64_t l = 0; l < nl; ++l) {
+            double s = 0.0;
+            for (int64_t e = ptr[l0 + l]; e < ptr[l0 + l + 1]; ++e) s += val[e] * v[pos[e - ptr[l0]]];
+            u[l] = s;
+        }
+        std::fill(w.begin(), w.end(), 0.0);
+        for (int64_t l = 0; l < nl; ++l)
+            for (int64_t e = ptr[l0 + l]; e < ptr[l0 + l + 1]; ++e) w[pos[e - ptr[l0]]] += val[e] * u[l];
+        double rq = 0.0;
+        for (int64_t c = 0; c < nc; ++c) rq += v[c] * w[c];
+        lam = rq;
+        v.swap(w);
+    }
+    return lam;
+}
+
+}  // namespace
+}  // namespace rebk
+
+using namespace rebk;
+
+struct rebk_sparse_s {
+    int64_t m = 0, n = 0, nnz = 0;
+    int tau_r = 1, tau_c = 1, s = 0, t = 0, fb_r = 0, fb_c = 0;
+    double alpha = 0.0, beta = 0.0, fro2 = 0.0;
+    int G = 0, check_every = 10;
+    cudaStream_t stream = nullptr;
+    int64_t *rp = nullptr, *cp = nullptr;
+    int32_t *ci = nullptr, *ri = nullptr, *idx = nullptr;
+    double *rv = nullptr, *cv = nullptr, *cdf_r = nullptr, *cdf_c = nullptr, *coef_r = nullptr, *coef_c = nullptr;
+    double *zbuf = nullptr, *acc = nullptr, *small = nullptr;
+    int *bad = nullptr, *status = nullptr;
+    unsigned int *bar = nullptr;
+    int64_t *iters_done = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, k0 = nullptr, k1 = nullptr;
+};
+
+namespace {
+
+rebk_status sfail(rebk_status s, const std::string &msg) {
+    set_last_error(msg);
+    return s;
+}
+
+#define SCK(call)                                                                                  \
+    do {                                                                                           \
+        cudaError_t e__ = (call);                                                                  \
+        if (e__ != cudaSuccess) return sfail(e__ == cudaErrorMemoryAllocation ? REBK_ENOMEM : REBK_ECUDA, \
+                                             std::string(#call) + ": " + cudaGetErrorString(e__)); \
+    } while (0)
+
+void free_sparse(rebk_sparse h) {
+    if (!h) return;
+    void *p[] = {h->rp, h->cp, h->ci, h->ri, h->idx, h->rv, h->cv, h->cdf_r, h->cdf_c, h->coef_r, h->coef_c,
+                 h->zbuf, h->acc, h->small, h->bad, h->status, h->bar, h->iters_done};
+    for (void *q : p)
+        if (q) cudaFree(q);
+    cudaEvent_t e[] = {h->ev0, h->ev1, h->k0, h->k1};
+    for (cudaEvent_t q : e)
+        if (q) cudaEventDestroy(q);
+    delete h;
+}
+
+// squared Frobenius norms of consecutive groups of tau lines, their prefix sums,
+// the last group of nonzero norm
+void group_tables(const std::vector<int64_t> &ptr, const std::vector<double> &val, int64_t lines, int tau,
+                  std::vector<double> &norms, std::vector<double> &cdf, int *fallback) {
+    const int64_t g = (lines + tau - 1) / tau;
+    norms.assign(g, 0.0);
+    cdf.assign(g, 0.0);
+    for (int64_t b = 0; b < g; ++b) {
+        double s = 0.0;
+        const int64_t l1 = std::min(lines, (b + 1) * tau);
+        for (int64_t l = b * tau; l < l1; ++l)
+            for (int64_t e = ptr[l]; e < ptr[l + 1]; ++e) s += val[e] * val[e];
+        norms[b] = s;
+    }
+    double run = 0.0;
+    *fallback = 0;
+    for (int64_t b = 0; b < g; ++b) {
+        run += norms[b];
+        cdf[b] = run;
+        if (norms[b] > 0.0) *fallback = (int)b;
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+rebk_status rebk_sparse_create(rebk_sparse *out, int64_t m, int64_t n, const int64_t *row_ptr,
+                               const int32_t *col_idx, const double *val, int64_t tau_row, int64_t tau_col,
+                               double alpha, const rebk_sparse_options *opt) {
+    set_last_error("");
+    if (!out) return sfail(REBK_EINVAL, "out is NULL");
+    *out = nullptr;
+    if (m < 1 || n < 1 || m > INT32_MAX || n > INT32_MAX) return sfail(REBK_EINVAL, "need 1 <= m, n < 2^31");
+    if (!row_ptr || !col_idx || !val) return sfail(REBK_EINVAL, "NULL CSR array");
+    if (tau_row < 1 || tau_col < 1) return sfail(REBK_EINVAL, "block sizes must be >= 1");
+    if (!std::isfinite(alpha)) return sfail(REBK_EINVAL, "alpha is not finite");
+    rebk_sparse_options o;
+    memset(&o, 0, sizeof(o));
+    if (opt) o = *opt;
+    if (o.num_ctas < 0 || o.check_every < 0 || o.power_iters < 0) return sfail(REBK_EINVAL, "negative option");
+    const int64_t nnz = row_ptr[m];
+    if (row_ptr[0] != 0 || nnz < 0) return sfail(REBK_EINVAL, "row_ptr must start at 0");
+    for (int64_t i = 0; i < m; ++i) {
+        if (row_ptr[i + 1] < row_ptr[i]) return sfail(REBK_EINVAL, "row_ptr must be nondecreasing");
+        for (int64_t e = row_ptr[i]; e < row_ptr[i + 1]; ++e) {
+            if (col_idx[e] < 0 || col_idx[e] >= n) return sfail(REBK_EINVAL, "column index out of range");
+            if (e > row_ptr[i] && col_idx[e] <= col_idx[e - 1])
+                return sfail(REBK_EINVAL, "column indices must increase within a row");
+            if (!std::isfinite(val[e])) return sfail(REBK_EINVAL, "non-finite value");
+        }
+    }
+    rebk_sparse h = new rebk_sparse_s();
+    h->m = m;
+    h->n = n;
+    h->nnz = nnz;
+    h->tau_r = (int)std::min<int64_t>(tau_row, m);
+    h->tau_c = (int)std::min<int64_t>(tau_col, n);
+    h->s = (int)((m + h->tau_r - 1) / h->tau_r);
+    h->t = (int)((n + h->tau_c - 1) / h->tau_c);
+    h->check_every = o.check_every > 0 ? o.check_every : 10;
+    h->stream = static_cast<cudaStream_t>(o.stream);
+    auto fin = [&](rebk_status s) {
+        if (s != REBK_OK) free_sparse(h);
+        return s;
+    };
+    // host CSR and CSC (stable: entries of a column in increasing row order)
+    std::vector<int64_t> rp(row_ptr, row_ptr + m + 1), cp(n + 1, 0);
+    std::vector<int32_t> ci(col_idx, col_idx + nnz), ri(nnz);
+    std::vector<double> rv(val, val + nnz), cv(nnz);
+    for (int64_t e = 0; e < nnz; ++e) ++cp[ci[e] + 1];
+    for (int64_t c = 0; c < n; ++c) cp[c + 1] += cp[c];
+    {
+        std::vector<int64_t> next(cp.begin(), cp.end() - 1);
+        for (int64_t i = 0; i < m; ++i)
+            for (int64_t e = rp[i]; e < rp[i + 1]; ++e) {
+                const int64_t d = next[ci[e]]++;
+                ri[d] = (int32_t)i;
+                cv[d] = rv[e];
+            }
+    }
+    // tables (Algorithm 1 sampling), FP64
+    std::vector<double> nr, nc, cdf_r, cdf_c;
+    group_tables(rp, rv, m, h->tau_r, nr, cdf_r, &h->fb_r);
+    group_tables(cp, cv, n, h->tau_c, nc, cdf_c, &h->fb_c);
+    h->fro2 = h->s > 0 ? cdf_r[h->s - 1] : 0.0;
+    // step: alpha, or 1.75 / beta_max with ||block||_2^2 from power iterations
+    const int piters = o.power_iters > 0 ? o.power_iters : 100;
+    double beta = 0.0;
+    if (alpha <= 0.0) {  // blocks split over host threads; each ratio written once
+        std::vector<double> ratio(h->s + h->t, 0.0);
+        auto work = [&](int first, int stride) {
+            for (int b = first; b < h->s + h->t; b += stride) {
+                if (b < h->s) {
+                    if (nr[b] > 0.0)
+                        ratio[b] = block_spectral_sq(rp, ci, rv, (int64_t)b * h->tau_r,
+                                                     std::min<int64_t>(m, (int64_t)(b + 1) * h->tau_r), n, piters) /
+                                   nr[b];
+                } else {
+                    const int c = b - h->s;
+                    if (nc[c] > 0.0)
+                        ratio[b] = block_spectral_sq(cp, ri, cv, (int64_t)c * h->tau_c,
+                                                     std::min<int64_t>(n, (int64_t)(c + 1) * h->tau_c), m, piters) /
+                                   nc[c];
+                }
+            }
+        };
+        const int nt = (int)std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        std::vector<std::thread> pool;
+        for (int q = 1; q < nt; ++q) pool.emplace_back(work, q, nt);
+        work(0, nt);
+        for (auto &th : pool) th.join();
+        for (double r : ratio) beta = std::max(beta, r);
+    }
+    h->beta = beta;
+    h->alpha = alpha > 0.0 ? alpha : (beta > 0.0 ? 1.75 / beta : 1.0);
+    std::vector<double> kr(h->s), kc(h->t);
+    for (int b = 0; b < h->s; ++b) kr[b] = nr[b] > 0.0 ? h->alpha / nr[b] : 0.0;
+    for (int b = 0; b < h->t; ++b) kc[b] = nc[b] > 0.0 ? h->alpha / nc[b] : 0.0;
+    // device copies
+#define SCKH(call)                                                                                 \
+    do {                                                                                           \
+        cudaError_t e__ = (call);                                                                  \
+        if (e__ != cudaSuccess)                                                                    \
+            return fin(sfail(e__ == cudaErrorMemoryAllocation ? REBK_ENOMEM : REBK_ECUDA,          \
+                             std::string(#call) + ": " + cudaGetErrorString(e__)));                \
+    } while (0)
+    auto up = [&](void **dst, const void *src, size_t bytes) -> cudaError_t {
+        cudaError_t e = cudaMalloc(dst, bytes > 0 ? bytes : 8);
+        if (e == cudaSuccess && bytes > 0) e = cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice);
+        return e;
+    };
+    SCKH(up((void **)&h->rp, rp.data(), sizeof(int64_t) * (m + 1)));
+    SCKH(up((void **)&h->cp, cp.data(), sizeof(int64_t) * (n + 1)));
+    SCKH(up((void **)&h->ci, ci.data(), sizeof(int32_t) * nnz));
+    SCKH(up((void **)&h->ri, ri.data(), sizeof(int32_t) * nnz));
+    SCKH(up((void **)&h->rv, rv.data(), sizeof(double) * nnz));
+    SCKH(up((void **)&h->cv, cv.data(), sizeof(double) * nnz));
+    SCKH(up((void **)&h->cdf_r, cdf_r.data(), sizeof(double) * h->s));
+    SCKH(up((void **)&h->cdf_c, cdf_c.data(), sizeof(double) * h->t));
+    SCKH(up((void **)&h->coef_r, kr.data(), sizeof(double) * h->s));
+    SCKH(up((void **)&h->coef_c, kc.data(), sizeof(double) * h->t));
+    SCKH(cudaMalloc(&h->idx, sizeof(int32_t) * 2 * kSparseChunk));
+    SCKH(cudaMalloc(&h->zbuf, sizeof(double) * m));
+    SCKH(cudaMalloc(&h->acc, sizeof(double) * 4));
+    SCKH(cudaMalloc(&h->small, sizeof(double) * 4));
+    SCKH(cudaMalloc(&h->bad, sizeof(int)));
+    SCKH(cudaMalloc(&h->status, sizeof(int)));
+    SCKH(cudaMalloc(&h->bar, sizeof(unsigned int)));
+    SCKH(cudaMalloc(&h->iters_done, sizeof(int64_t)));
+    SCKH(cudaEventCreate(&h->ev0));
+    SCKH(cudaEventCreate(&h->ev1));
+    SCKH(cudaEventCreate(&h->k0));
+    SCKH(cudaEventCreate(&h->k1));
+    // grid: one CTA per SM (cooperative), enough CTAs for every block's lines
+    int dev = 0, sms = 1, per = 0;
+    SCKH(cudaGetDevice(&dev));
+    SCKH(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    SCKH(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, rebk_sparse_kernel, kST, 0));
+    const int gmax = sms * std::max(1, std::min(per, 1));
+    int G = o.num_ctas > 0 ? std::min(o.num_ctas, gmax) : gmax;
+    const int need = (int)((std::max(h->tau_r, h->tau_c) + kOwnMax - 1) / kOwnMax);
+    if (G < need) G = std::min(gmax, need);
+    if ((int64_t)G * kOwnMax < std::max(h->tau_r, h->tau_c))
+        return fin(sfail(REBK_EUNSUPPORTED, "block size too large for the persistent grid"));
+    h->G = G;
+    *out = h;
+    return REBK_OK;
+}
+
+void rebk_sparse_destroy(rebk_sparse h) { free_sparse(h); }
+
+rebk_status rebk_sparse_info(rebk_sparse h, double *alpha, double *beta_max, int32_t *row_blocks,
+                             int32_t *col_blocks) {
+    if (!h) return sfail(REBK_EINVAL, "NULL handle");
+    if (alpha) *alpha = h->alpha;
+    if (beta_max) *beta_max = h->beta;
+    if (row_blocks) *row_blocks = h->s;
+    if (col_blocks) *col_blocks = h->t;
+    return REBK_OK;
+}
+
+rebk_status rebk_sparse_solve(rebk_sparse h, const double *b, double *x, double tol, int64_t max_iter,
+                              uint64_t seed, const rebk_solve_ext *ext, rebk_stats *stats) {
+    set_last_error("");
+    if (!h) return sfail(REBK_EINVAL, "NULL handle");
+    if (!b || !x) return sfail(REBK_EINVAL, "b and x must be device pointers");
+    if (max_iter < 0 || !std::isfinite(tol)) return sfail(REBK_EINVAL, "bad tol / max_iter");
+    rebk_solve_ext e;
+    memset(&e, 0, sizeof(e));
+    if (ext) e = *ext;
+    if (e.k0 < 0) return sfail(REBK_EINVAL, "k0 < 0");
+    const cudaStream_t st = h->stream;
+    double *z = e.z_out ? e.z_out : h->zbuf;
+    SCK(cudaEventRecord(h->ev0, st));
+    if (e.z0) SCK(cudaMemcpyAsync(z, e.z0, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, st));
+    else SCK(cudaMemcpyAsync(z, b, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, st));
+    if (e.x0) SCK(cudaMemcpyAsync(x, e.x0, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, st));
+    else SCK(cudaMemsetAsync(x, 0, sizeof(double) * h->n, st));
+    double refn = 0.0;
+    if (e.x_ref) {
+        SCK(sum_sq(e.x_ref, h->n, h->small, st));
+        double v[2];
+        SCK(cudaMemcpyAsync(v, h->small, sizeof(v), cudaMemcpyDeviceToHost, st));
+        SCK(cudaStreamSynchronize(st));
+        refn = std::sqrt(v[1]);
+    }
+    const double thr = tol * refn;
+    int64_t extra = e.x_ref ? 2 : 0;  // sum_sq, err_norms
+    int64_t total = 0, launches = 0, grid_launches = 0;
+    double kernel_ms = 0.0;
+    rebk_status result = REBK_MAX_ITER;
+    bool converged = false;
+    while (total < max_iter && h->fro2 > 0.0) {
+        const int64_t K = std::min({max_iter - total, kSparseChunk, kSparseLaunchMax});
+        int32_t *idx = e.idx_out ? e.idx_out + 2 * total : h->idx;
+        SCK(sample_blocks(seed, e.stream_id, e.k0 + total, K, h->cdf_r, h->s, h->cdf_c, h->t, h->fb_r, h->fb_c, idx,
+                          st));
+        SCK(cudaMemsetAsync(h->acc, 0, sizeof(double) * 4, st));
+        SCK(cudaMemsetAsync(h->bad, 0, sizeof(int), st));
+        SCK(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+        SCK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned int), st));
+        SparseArgs a;
+        memset(&a, 0, sizeof(a));
+        a.m = h->m;
+        a.n = h->n;
+        a.tau_r = h->tau_r;
+        a.tau_c = h->tau_c;
+        a.rp = h->rp;
+        a.ci = h->ci;
+        a.rv = h->rv;
+        a.cp = h->cp;
+        a.ri = h->ri;
+        a.cv = h->cv;
+        a.coef_r = h->coef_r;
+        a.coef_c = h->coef_c;
+        a.idx = idx;
+        a.iters = K;
+        a.z = z;
+        a.x = x;
+        a.b = b;
+        a.x_ref = e.x_ref;
+        a.tol2_abs = thr * thr;
+        a.check_every = h->check_every;
+        a.check_offset = total;
+        a.acc = h->acc;
+        a.bad = h->bad;
+        a.bar = h->bar;
+        a.status = h->status;
+        a.iters_done = h->iters_done;
+        a.timeout_ns = kBarrierTimeoutNs;
+        void *params[] = {&a};
+        SCK(cudaEventRecord(h->k0, st));
+        SCK(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(&rebk_sparse_kernel), dim3(h->G), dim3(kST),
+                                        params, 0, st));
+        SCK(cudaEventRecord(h->k1, st));
+        launches += 2;  // sample_kernel, rebk_sparse_kernel
+        ++grid_launches;
+        int ds = 0;
+        int64_t done = 0;
+        SCK(cudaMemcpyAsync(&ds, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+        SCK(cudaMemcpyAsync(&done, h->iters_done, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+        SCK(cudaStreamSynchronize(st));
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, h->k0, h->k1);
+        kernel_ms += ms;
+        if (ds != 6) total += done;
+        if (ds == 6) {
+            result = REBK_BARRIER_TIMEOUT;
+            sfail(result, "device-wide barrier timed out");
+            break;
+        }
+        if (ds == 5) {
+            result = REBK_DIVERGED;
+            sfail(result, "iteration diverged (Inf/NaN)");
+            break;
+        }
+        if (done < K) {
+            converged = true;
+            result = REBK_OK;
+            break;
+        }
+    }
+    double rel = -1.0;
+    if (e.x_ref && result != REBK_BARRIER_TIMEOUT) {
+        SCK(err_norms(nullptr, x, e.x_ref, h->n, h->small, st));
+        double v[2];
+        SCK(cudaMemcpyAsync(v, h->small, sizeof(v), cudaMemcpyDeviceToHost, st));
+        SCK(cudaStreamSynchronize(st));
+        rel = refn > 0 ? std::sqrt(v[0]) / refn : std::sqrt(v[0]);
+        if (!converged && result == REBK_MAX_ITER && rel <= tol) result = REBK_OK;
+    } else if (!e.x_ref && result == REBK_MAX_ITER) {
+        result = REBK_OK;  // fixed iteration count
+    }
+    if (h->fro2 == 0.0) result = REBK_OK;  // A = 0: x = 0 is A^+ b
+    SCK(cudaEventRecord(h->ev1, st));
+    SCK(cudaEventSynchronize(h->ev1));
+    float dms = 0.f;
+    cudaEventElapsedTime(&dms, h->ev0, h->ev1);
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->iterations = total;
+        stats->status = result;
+        stats->rel_err = rel;
+        stats->resid_f = -1;
+        stats->resid_g = -1;
+        stats->device_ms = dms;
+        stats->kernel_ms = kernel_ms;
+        stats->launches = launches + extra;
+        stats->grid_launches = grid_launches;
+    }
+    return result;
+}
+
+}  // extern "C"

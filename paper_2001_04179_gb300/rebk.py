@@ -65,6 +65,11 @@ class RebkBatchStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class RebkSparseOptions(ctypes.Structure):
+    _fields_ = [("num_ctas", ctypes.c_int32), ("check_every", ctypes.c_int32), ("power_iters", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
 _lock = threading.Lock()
 _lib: Optional[ctypes.CDLL] = None
 
@@ -107,6 +112,13 @@ _SIGNATURES = {
     "rebk_mlp_shape": ([_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "rebk_warm_start": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "rebk_warm_start_batch": ([_P, _P, _P, ctypes.c_int64, ctypes.c_int32, _P, _P], ctypes.c_int),
+    "rebk_sparse_create": ([ctypes.POINTER(_P), ctypes.c_int64, ctypes.c_int64, _P, _P, _P, ctypes.c_int64,
+                            ctypes.c_int64, ctypes.c_double, ctypes.POINTER(RebkSparseOptions)], ctypes.c_int),
+    "rebk_sparse_destroy": ([_P], None),
+    "rebk_sparse_solve": ([_P, _P, _P, ctypes.c_double, ctypes.c_int64, ctypes.c_uint64,
+                           ctypes.POINTER(RebkSolveExt), ctypes.POINTER(RebkStats)], ctypes.c_int),
+    "rebk_sparse_info": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
+                          ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "rebk_last_error": ([], ctypes.c_char_p),
     "rebk_version": ([], ctypes.c_char_p),
 }

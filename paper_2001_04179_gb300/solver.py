@@ -167,6 +167,76 @@ class Solver:
         return out
 
 
+class SparseSolver:
+    """REBK on a sparse m x n matrix in CSR form (Algorithm 1 of
+    arXiv:2001.04179 with row blocks over CSR and column blocks over a CSC copy
+    the library builds).  indptr: int64 (m + 1); indices: int32, increasing
+    within each row; data: float64.  alpha <= 0 picks 1.75 / beta_max."""
+
+    def __init__(self, m: int, n: int, indptr, indices, data, tau_row: int, tau_col: int, alpha: float = 0.0,
+                 num_ctas: int = 0, check_every: int = 0, power_iters: int = 0, stream=None):
+        lib = _r.load()
+        self._arrays = (np.ascontiguousarray(indptr, dtype=np.int64), np.ascontiguousarray(indices, dtype=np.int32),
+                        np.ascontiguousarray(data, dtype=np.float64))
+        if self._arrays[0].shape != (m + 1,):
+            raise ValueError("indptr must have m + 1 entries")
+        opt = _r.RebkSparseOptions(num_ctas, check_every, power_iters,
+                                   None if stream is None else ctypes.c_void_p(stream.cuda_stream))
+        h = ctypes.c_void_p()
+        p = [a.ctypes.data_as(ctypes.c_void_p) for a in self._arrays]
+        _r.check(lib.rebk_sparse_create(ctypes.byref(h), int(m), int(n), p[0], p[1], p[2], int(tau_row),
+                                        int(tau_col), float(alpha), ctypes.byref(opt)))
+        self._h = h
+        self.m, self.n = int(m), int(n)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _r.load().rebk_sparse_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        a, bm, s, t = ctypes.c_double(), ctypes.c_double(), ctypes.c_int32(), ctypes.c_int32()
+        _r.check(_r.load().rebk_sparse_info(self._h, ctypes.byref(a), ctypes.byref(bm), ctypes.byref(s),
+                                            ctypes.byref(t)))
+        return {"alpha": a.value, "beta_max": bm.value, "row_blocks": s.value, "col_blocks": t.value}
+
+    @property
+    def alpha(self) -> float:
+        return self.info()["alpha"]
+
+    def solve(self, b, tol: float = 0.0, max_iter: int = 1000, seed: int = 0, x_ref=None, x0=None, z0=None,
+              k0: int = 0, stream_id: int = 0, record: bool = False, return_z: bool = False, x=None,
+              allow=(_r.REBK_OK, _r.REBK_MAX_ITER)):
+        """Plain FP64 Algorithm 1 (as Solver.solve).  Returns dict(x, stats[, z][, idx])."""
+        torch = _torch()
+        _require_cuda_f64(b, self.m, "b")
+        for t, nn, name in [(x_ref, self.n, "x_ref"), (x0, self.n, "x0"), (z0, self.m, "z0")]:
+            if t is not None:
+                _require_cuda_f64(t, nn, name)
+        if x is None:
+            x = torch.empty(self.n, dtype=torch.float64, device=b.device)
+        z = torch.empty(self.m, dtype=torch.float64, device=b.device) if return_z else None
+        idx = torch.zeros(max(2 * max_iter, 2), dtype=torch.int32, device=b.device) if record else None
+        ext = _r.RebkSolveExt(_dptr(x_ref), _dptr(x0), _dptr(z0), _dptr(z), _dptr(idx), int(k0), int(stream_id))
+        stats = _r.RebkStats()
+        st = _r.load().rebk_sparse_solve(self._h, ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                         float(tol), int(max_iter), int(seed), ctypes.byref(ext),
+                                         ctypes.byref(stats))
+        _r.check(st, allow)
+        out = {"x": x, "stats": stats.as_dict(), "status": st}
+        if return_z:
+            out["z"] = z
+        if record:
+            out["idx"] = idx[: 2 * stats.iterations].view(-1, 2)
+        return out
+
+
 class BatchSolver:
     """Many independent systems A_i x = b_i, each with up to eight right-hand
     sides, solved together (mixed precision with FP64 refinement, one

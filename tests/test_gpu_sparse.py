@@ -1,0 +1,88 @@
+"""Sparse REBK (rebk_sparse_*) against the FP64 oracle on the densified matrix.
+
+Algorithm 1 does not depend on how A is stored: on the same matrix, seed and
+step the sparse path draws the same blocks (bit-exact) and its iterates equal
+the oracle's up to summation order (FP64 atomic adds), bar 1e-10 relative."""
+import numpy as np
+import pytest
+
+import oracle as O
+from workloads import contiguous_offsets, sparse_problem
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2001_04179_gb300 import Solver, SparseSolver  # noqa: E402
+from paper_2001_04179_gb300 import rebk as R  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def _t(a):
+    return torch.from_numpy(np.ascontiguousarray(a, dtype=np.float64)).to(DEV)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+CASES = [
+    # m, n, nnz per row, tau_r, tau_c, num_ctas
+    (600, 150, 12, 32, 16, 0),
+    (333, 97, 9, 25, 10, 7),       # ragged last blocks, few CTAs
+    (120, 300, 20, 8, 30, 0),      # underdetermined
+    (64, 40, 5, 1, 1, 3),          # single rows / columns
+    (500, 64, 64, 64, 8, 152),     # dense rows
+]
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: "x".join(map(str, c)))
+def test_indices_and_iterates_match_the_dense_oracle(case):
+    m, n, k, tr, tc, G = case
+    p = sparse_problem(m, n, k, seed=m + n, x_ref=None)
+    A = p.dense()
+    ro, co = contiguous_offsets(m, tr), contiguous_offsets(n, tc)
+    alpha = 1.1 / max(O.beta_max(A, ro, co)) if (tr > 1 or tc > 1) else 1.0
+    sol = SparseSolver(m, n, p.indptr, p.indices, p.data, tr, tc, alpha=alpha, num_ctas=G)
+    iters = 143
+    for seed, k0, sid in [(3, 0, 0), (77, 500, 4)]:
+        out = sol.solve(_t(p.b), tol=0.0, max_iter=iters, seed=seed, k0=k0, stream_id=sid, record=True,
+                        return_z=True)
+        ref = O.rebk(A, p.b, ro, co, alpha, seed=seed, stream=sid, k0=k0, iters=iters, record=True)
+        assert out["stats"]["iterations"] == iters
+        assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"])
+        assert _rel(out["x"].cpu().numpy(), ref["x"]) <= 1e-10
+        assert _rel(out["z"].cpu().numpy(), ref["z"]) <= 1e-10
+
+
+def test_same_blocks_as_the_dense_solver_and_beta_max():
+    p = sparse_problem(400, 100, 10, seed=9, x_ref=None)
+    A = p.dense()
+    sp = SparseSolver(400, 100, p.indptr, p.indices, p.data, 20, 10)
+    de = Solver(A, 20, 10, alpha=sp.alpha, storage=())
+    a = sp.solve(_t(p.b), max_iter=300, seed=5, record=True)["idx"].cpu().numpy()
+    b = de.solve(_t(p.b), max_iter=300, seed=5, record=True)["idx"].cpu().numpy()
+    assert np.array_equal(a, b)
+    beta = max(O.beta_max(A, contiguous_offsets(400, 20), contiguous_offsets(100, 10)))
+    assert sp.info()["beta_max"] == pytest.approx(beta, rel=1e-6)
+    assert sp.alpha == pytest.approx(1.75 / beta, rel=1e-6)
+
+
+@pytest.mark.parametrize("shape", [(800, 200, 12), (150, 400, 30)])
+def test_solves_reach_the_pseudoinverse_solution(shape):
+    m, n, k = shape
+    p = sparse_problem(m, n, k, seed=1, x_ref="lstsq")
+    sol = SparseSolver(m, n, p.indptr, p.indices, p.data, 16, 16)
+    out = sol.solve(_t(p.b), tol=1e-10, max_iter=2_000_000, seed=2, x_ref=_t(p.x_ref))
+    assert out["status"] == R.REBK_OK
+    assert _rel(out["x"].cpu().numpy(), p.x_ref) <= 1e-10
+
+
+def test_zero_matrix_gives_zero():
+    rp = np.zeros(11, dtype=np.int64)
+    sol = SparseSolver(10, 5, rp, np.zeros(0, dtype=np.int32), np.zeros(0), 2, 2, alpha=1.0)
+    out = sol.solve(_t(np.ones(10)), tol=1e-8, max_iter=100, seed=1)
+    assert np.all(out["x"].cpu().numpy() == 0.0)

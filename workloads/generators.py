@@ -32,6 +32,8 @@ __all__ = [
     "spectrum_problem",
     "batched_problems",
     "small_cases",
+    "SparseProblem",
+    "sparse_problem",
 ]
 
 
@@ -238,3 +240,70 @@ def small_cases(seed: int = 0) -> list:
     A = rng.standard_normal((36, 6)) @ rng.standard_normal((6, 20)); finish(A, rng.standard_normal(36), "inconsistent_deficient_over")
     A = rng.standard_normal((16, 5)) @ rng.standard_normal((5, 28)); finish(A, rng.standard_normal(16), "inconsistent_deficient_under")
     return cases
+
+
+@dataclasses.dataclass
+class SparseProblem:
+    """A sparse least-squares problem in CSR form (row pointers int64, column
+    indices int32 sorted within each row, FP64 values) with x_ref = A^+ b."""
+    m: int
+    n: int
+    indptr: np.ndarray
+    indices: np.ndarray
+    data: np.ndarray
+    b: np.ndarray
+    x_ref: Optional[np.ndarray]
+    name: str
+    meta: dict
+
+    @property
+    def nnz(self) -> int:
+        return int(self.indptr[-1])
+
+    def dense(self) -> np.ndarray:
+        A = np.zeros((self.m, self.n))
+        for i in range(self.m):
+            lo, hi = self.indptr[i], self.indptr[i + 1]
+            A[i, self.indices[lo:hi]] = self.data[lo:hi]
+        return A
+
+
+def sparse_problem(m: int, n: int, nnz_row: int, seed: int, noise: float = 0.01, decades: float = 1.0,
+                   x_ref: str = "normal") -> SparseProblem:
+    """Tomography-like sparse A: every row has nnz_row distinct columns drawn
+    uniformly, values U(0, 1) * 10^{u_i} with u_i ~ U(0, decades) per row (row
+    norms spread over `decades` decades); b = A x* + e, x* ~ N(0, I), e Gaussian
+    with ||e|| ~ noise ||A x*||.
+
+    x_ref = A^+ b by a direct method: "normal" solves A^T A x = A^T b by a dense
+    Cholesky factorisation (A of full column rank, m >= n; forward error about
+    kappa(A)^2 eps), "lstsq" uses a dense SVD least-squares solve (small cases,
+    any shape), None skips it.
+    """
+    rng = np.random.default_rng(seed)
+    if nnz_row > n:
+        raise ValueError("nnz_row > n")
+    indptr = np.arange(m + 1, dtype=np.int64) * nnz_row
+    indices = np.empty(m * nnz_row, dtype=np.int32)
+    for i in range(m):
+        indices[i * nnz_row:(i + 1) * nnz_row] = np.sort(rng.choice(n, nnz_row, replace=False))
+    scale = 10.0 ** rng.uniform(0.0, decades, m)
+    data = rng.uniform(0.0, 1.0, m * nnz_row) * np.repeat(scale, nnz_row)
+    xs = rng.standard_normal(n)
+    rows = np.repeat(np.arange(m), nnz_row)
+    ax = np.bincount(rows, weights=data * xs[indices], minlength=m)
+    e = rng.standard_normal(m)
+    b = ax + noise * np.linalg.norm(ax) / np.linalg.norm(e) * e
+    p = SparseProblem(m, n, indptr, indices, data, b, None, f"sparse_{m}x{n}_{nnz_row}",
+                      {"seed": seed, "noise": noise, "decades": decades, "x_star": xs})
+    if x_ref == "lstsq":
+        p.x_ref = np.linalg.lstsq(p.dense(), b, rcond=None)[0]
+    elif x_ref == "normal":
+        import scipy.linalg
+        import scipy.sparse
+        A = scipy.sparse.csr_matrix((data, indices, indptr), shape=(m, n))
+        G = (A.T @ A).toarray()
+        c = A.T @ b
+        L = scipy.linalg.cho_factor(G, lower=True)
+        p.x_ref = scipy.linalg.cho_solve(L, c)
+    return p
