@@ -3,14 +3,15 @@
 //
 // One persistent cooperative launch runs many iterations.  Iteration k (block
 // indices sampled before the launch, as in the dense path):
-//   A. w_c = A_{:,c}^T z for the columns c of J_k: each column belongs to one CTA
-//      (columns strided over the CTAs), whose threads gather over the column's
-//      entries and add up by a block reduction;                      barrier
-//   B. z -= c_J A_{:,J} w: the same CTA scatters its columns' entries into z by
-//      FP64 atomic adds;                                              barrier
-//   C. r_l = A_{l,:} x - b_l + z_l for the rows l of I_k (rows strided over the
-//      CTAs, block reductions), and every check_every iterations each CTA's
-//      share of ||x^{k-1} - x_ref||^2;                                barrier
+//   A. w_c = A_{:,c}^T z for the columns c of J_k: each CTA owns a contiguous
+//      range of the block's columns, whose entries are contiguous in CSC; its
+//      threads gather over them at a stride in one round, adding per-column
+//      running sums into shared memory;                              barrier
+//   B. z -= c_J A_{:,J} w: the same CTA scatters its entries into z by FP64
+//      atomic adds;                                                  barrier
+//   C. r_l = A_{l,:} x - b_l + z_l for the rows l of I_k (contiguous row ranges
+//      per CTA, the same gather over CSR), and every check_every iterations each
+//      CTA's share of ||x^{k-1} - x_ref||^2;                          barrier
 //   D. x -= c_I A_{I,:}^T r: scatter of the rows' entries into x.
 // No barrier follows D: the next gather A reads z only, and every CTA finishes
 // D before it reaches the next barrier, which C waits behind.  Gathers read
@@ -75,9 +76,49 @@ __device__ __forceinline__ double block_sum(double v, double *red) {
     return t;
 }
 
+// Line of entry e among the CTA's nq lines: bnd[q] <= e < bnd[q + 1].
+__device__ __forceinline__ int line_of(const int64_t *bnd, int nq, int64_t e) {
+    int lo = 0, hi = nq;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (bnd[mid] <= e) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// part[q] = sum over the entries e of line q of val[e] * vec[idx[e]], for the CTA's
+// contiguous lines (entries bnd[0] .. bnd[nq]).  Each round, warp w takes 32
+// consecutive entries (sorted by line, so they span one line or a few); the warp
+// adds each line's products with a shuffle sum and one lane adds that to part[].
+__device__ __forceinline__ void gather_lines(const int64_t *bnd, int nq, const int32_t *__restrict__ idx,
+                                             const double *__restrict__ val, const double *vec, double *part) {
+    for (int q = threadIdx.x; q < nq; q += kST) part[q] = 0.0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    for (int64_t base = bnd[0]; base < bnd[nq]; base += kST) {  // uniform over the CTA
+        const int64_t e = base + threadIdx.x;
+        const bool in = e < bnd[nq];
+        int q = 0x7fffffff;
+        double prod = 0.0;
+        if (in) {
+            q = line_of(bnd, nq, e);
+            prod = val[e] * vec[idx[e]];
+        }
+        const int qlo = __reduce_min_sync(0xffffffffu, q);
+        const int qhi = __reduce_max_sync(0xffffffffu, in ? q : -1);
+        for (int qq = qlo; qq <= qhi; ++qq) {  // warp-uniform bounds
+            const double t = warp_sum(in && q == qq ? prod : 0.0);
+            if (lane == 0) atomicAdd(part + qq, t);
+        }
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_constant__ SparseArgs a) {
     __shared__ double red[kSW];
-    __shared__ double own[kOwnMax];  // w_c of the CTA's columns, then r_l of its rows
+    __shared__ double own[kOwnMax];      // w of the CTA's columns, then r of its rows
+    __shared__ int64_t bnd[kOwnMax + 1];  // entry boundaries of the CTA's lines
     __shared__ int s_flag;
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
     const int64_t K = a.iters;
@@ -95,36 +136,28 @@ __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_consta
         const int64_t ja = (int64_t)j * a.tau_c, jb = ja + a.tau_c < a.n ? ja + a.tau_c : a.n;
         const int64_t ia = (int64_t)i * a.tau_r, ib = ia + a.tau_r < a.m ? ia + a.tau_r : a.m;
         const double cJ = a.coef_c[j], cI = a.coef_r[i];
+        // this CTA's contiguous share of the block's columns and rows
+        const int64_t c0 = ja + (jb - ja) * cta / G, c1 = ja + (jb - ja) * (cta + 1) / G;
+        const int64_t l0 = ia + (ib - ia) * cta / G, l1 = ia + (ib - ia) * (cta + 1) / G;
+        const int nqc = (int)(c1 - c0), nqr = (int)(l1 - l0);
         // ---- A: w_c = A_{:,c}^T z^{k-1} for the CTA's columns ----
-        int q = 0;
-        for (int64_t c = ja + cta; c < jb; c += G, ++q) {
-            double v = 0.0;
-            for (int64_t e = a.cp[c] + tid; e < a.cp[c + 1]; e += kST) v = fma(a.cv[e], a.z[a.ri[e]], v);
-            const double w = block_sum(v, red);
-            if (tid == 0) {
-                own[q] = w;
-                if (!isfinite(w)) atomicExch(a.bad, 1);
-            }
-        }
+        for (int q = tid; q <= nqc; q += kST) bnd[q] = a.cp[c0 + q];
+        __syncthreads();
+        if (nqc > 0) gather_lines(bnd, nqc, a.ri, a.cv, a.z, own);
+        if (tid < nqc && !isfinite(own[tid])) atomicExch(a.bad, 1);
         if (!barrier()) return;
         // ---- B: z^k = z^{k-1} - c_J A_{:,J} w ----
-        q = 0;
-        for (int64_t c = ja + cta; c < jb; c += G, ++q) {
-            const double wc = own[q];
-            for (int64_t e = a.cp[c] + tid; e < a.cp[c + 1]; e += kST) atomicAdd(a.z + a.ri[e], -cJ * a.cv[e] * wc);
-        }
+        for (int64_t e = bnd[0] + tid; nqc > 0 && e < bnd[nqc]; e += kST)
+            atomicAdd(a.z + a.ri[e], -cJ * a.cv[e] * own[line_of(bnd, nqc, e)]);
         if (!barrier()) return;
         // ---- C: r_l = A_{l,:} x^{k-1} - b_l + z^k_l; test partial of x^{k-1} ----
-        q = 0;
-        for (int64_t l = ia + cta; l < ib; l += G, ++q) {
-            double v = 0.0;
-            for (int64_t e = a.rp[l] + tid; e < a.rp[l + 1]; e += kST) v = fma(a.rv[e], a.x[a.ci[e]], v);
-            const double r = block_sum(v, red);
-            if (tid == 0) {
-                const double rl = r - a.b[l] + a.z[l];
-                own[q] = rl;
-                if (!isfinite(rl)) atomicExch(a.bad, 1);
-            }
+        for (int q = tid; q <= nqr; q += kST) bnd[q] = a.rp[l0 + q];
+        __syncthreads();
+        if (nqr > 0) gather_lines(bnd, nqr, a.ci, a.rv, a.x, own);
+        for (int q = tid; q < nqr; q += kST) {
+            const double rl = own[q] - a.b[l0 + q] + a.z[l0 + q];
+            own[q] = rl;
+            if (!isfinite(rl)) atomicExch(a.bad, 1);
         }
         const bool due = check && k >= 2 && (a.check_offset + k - 1) % a.check_every == 0;
         if (due) {
@@ -149,12 +182,9 @@ __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_consta
             break;
         }
         // ---- D: x^k = x^{k-1} - c_I A_{I,:}^T r ----
-        q = 0;
-        for (int64_t l = ia + cta; l < ib; l += G, ++q) {
-            const double rl = own[q];
-            for (int64_t e = a.rp[l] + tid; e < a.rp[l + 1]; e += kST) atomicAdd(a.x + a.ci[e], -cI * a.rv[e] * rl);
-        }
-        __syncthreads();  // own[] is rewritten by the next gather
+        for (int64_t e = bnd[0] + tid; nqr > 0 && e < bnd[nqr]; e += kST)
+            atomicAdd(a.x + a.ci[e], -cI * a.rv[e] * own[line_of(bnd, nqr, e)]);
+        __syncthreads();  // bnd[] and own[] are rewritten by the next gather
     }
     if (cta == 0 && tid == 0) {
         *a.iters_done = done;
