@@ -877,13 +877,10 @@ rebk_status rebk_solve_refined(rebk_handle h, const double *b, double *x, double
     int outer = 0;
     rebk_status result = REBK_MAX_ITER;
     double rel = -1, rf = -1, rg = -1, prev_res = -1;
+    bool x_zero = e.x0 == nullptr;  // x^0 = 0: A x vanishes in the first residual
     for (outer = 0; outer < max_outer; ++outer) {
-        // f = b - z - A x, g = A^T z (FP64)
-        s = timed_sweep(h, x, false, z, false, h->ym, h->g);
-        if (s != REBK_OK) return s;
-        LK(h, form_f(b, z, h->ym, h->f, h->m, st));
         double e0 = 0.0;
-        if (use_ref) {
+        if (use_ref) {  // the error test needs x only: before the sweep, which a converged x skips
             LK(h, err_norms(nullptr, x, e.x_ref, h->n, h->ws->small, st));
             double v[2];
             s = fetch_small(h, v, 2);
@@ -894,7 +891,14 @@ rebk_status rebk_solve_refined(rebk_handle h, const double *b, double *x, double
                 result = REBK_OK;
                 break;
             }
-        } else {
+        }
+        // f = b - z - A x, g = A^T z (FP64)
+        if (x_zero) CK(cudaMemsetAsync(h->ym, 0, sizeof(double) * h->m, st));
+        s = timed_sweep(h, x_zero ? nullptr : x, false, z, false, h->ym, h->g);
+        if (s != REBK_OK) return s;
+        x_zero = false;
+        LK(h, form_f(b, z, h->ym, h->f, h->m, st));
+        if (!use_ref) {
             LK(h, sum_sq(h->f, h->m, h->ws->small, st));
             LK(h, sum_sq(h->g, h->n, h->ws->small + 2, st));
             LK(h, sum_sq(b, h->m, h->ws->small + 4, st));
@@ -920,7 +924,7 @@ rebk_status rebk_solve_refined(rebk_handle h, const double *b, double *x, double
         LK(h, fill_zero_f32(h->sd, h->n, st));
         const int64_t iters = std::min(inner_max, max_iter - total);
         int64_t ran = 0;
-        int64_t grow = 2048;  // chunks of 2048, 2048, 4096, 8192, ... iterations
+        int64_t grow = mode == Mode::CorrBF16 ? 2048 : 4096;  // chunks of g, g, 2g, 4g, ... iterations
         int chunks = 0;
         // A pass ends when its error test passes, or (with a reference) when its
         // error stops falling: after a chunk without the test, the error of
