@@ -86,3 +86,34 @@ def test_zero_matrix_gives_zero():
     sol = SparseSolver(10, 5, rp, np.zeros(0, dtype=np.int32), np.zeros(0), 2, 2, alpha=1.0)
     out = sol.solve(_t(np.ones(10)), tol=1e-8, max_iter=100, seed=1)
     assert np.all(out["x"].cpu().numpy() == 0.0)
+
+
+def test_empty_rows_and_columns():
+    """Rows and columns without entries: their blocks have zero norm, are never
+    sampled, and the iterates still match the oracle; the limit is A^+ b."""
+    rng = np.random.default_rng(21)
+    m, n = 90, 40
+    A = np.zeros((m, n))
+    for i in range(m):
+        if i % 7 == 3:
+            continue  # empty row
+        cols = rng.choice([c for c in range(n) if c % 9 != 4], 5, replace=False)  # columns 4, 13, ... stay empty
+        A[i, np.sort(cols)] = rng.uniform(0.5, 2.0, 5)
+    A[:14, :] = 0.0  # a whole empty row block (tau 7: blocks 0 and 1)
+    b = rng.standard_normal(m)
+    indptr = np.concatenate([[0], np.cumsum((A != 0).sum(1))]).astype(np.int64)
+    indices = np.concatenate([np.nonzero(A[i])[0] for i in range(m)]).astype(np.int32)
+    data = A[A != 0]
+    ro, co = contiguous_offsets(m, 7), contiguous_offsets(n, 5)
+    alpha = 1.0 / max(O.beta_max(A, ro, co))
+    sol = SparseSolver(m, n, indptr, indices, data, 7, 5, alpha=alpha)
+    out = sol.solve(_t(b), tol=0.0, max_iter=200, seed=4, record=True, return_z=True)
+    ref = O.rebk(A, b, ro, co, alpha, seed=4, iters=200, record=True)
+    idx = out["idx"].cpu().numpy()
+    assert np.array_equal(idx, ref["idx"])
+    assert not np.any(np.isin(idx[:, 1], [0, 1]))  # zero-norm row blocks never drawn
+    assert _rel(out["x"].cpu().numpy(), ref["x"]) <= 1e-10
+    x_ls = O.pinv_solve(A, b)
+    full = sol.solve(_t(b), tol=1e-10, max_iter=3_000_000, seed=5, x_ref=_t(x_ls))
+    assert full["status"] == R.REBK_OK
+    assert _rel(full["x"].cpu().numpy(), x_ls) <= 1e-10
