@@ -61,6 +61,22 @@ def parse():
     return ap.parse_args()
 
 
+def replica_throughput(elapsed_local: float, units_local: int, world: int, device=None):
+    """Whole-job throughput of `world` independent replicas (one problem per
+    rank, no collective on the data path): every rank processed units_local
+    units in elapsed_local (any time unit); the job took as long as the slowest
+    rank (all-reduce MAX when a process group is up).  Returns (units per time
+    unit over all ranks, the job's elapsed time)."""
+    t = elapsed_local
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        v = torch.tensor([elapsed_local], dtype=torch.float64, device=device)
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        t = float(v.item())
+    return units_local * world / t, t
+
+
 def dist_env():
     return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
             int(os.environ.get("LOCAL_RANK", "0")))
@@ -592,11 +608,8 @@ def main():
     barrier()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = args.steps * world / (ms_max / 1000.0)
+    value, ms_max = replica_throughput(ms / 1000.0, args.steps, world, dev)
+    ms_max *= 1000.0
 
     # ---------------- e2e: host buffers, copies inside the timed region ----------------
     b_host = torch.from_numpy(prob.b).pin_memory()
@@ -615,10 +628,7 @@ def main():
         x_host.copy_(x_d, non_blocking=True)
         torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    te = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(te, op=dist.ReduceOp.MAX)
-    e2e_value = e2e_steps * world / float(te.item())
+    e2e_value, _ = replica_throughput(e2e_s, e2e_steps, world, dev)
 
     # ---------------- plain FP64 path on the same problem ----------------
     plain = None
