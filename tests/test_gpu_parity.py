@@ -9,7 +9,8 @@ Bars (from the method's arithmetic):
 * reduced-precision storage copies: bit-exact to the oracle's rounding;
 * mixed precision: final ||x - A^+ b|| <= 1e-8 ||A^+ b||, and one refinement
   pass against the oracle's pass on the same rounded matrix within 1e-4
-  relative (FP32 arithmetic in the inner sweeps).
+  relative (FP32 arithmetic in the inner sweeps: rounding of ~6e-8 per product,
+  amplified by the non-normal pass over a few thousand iterations).
 """
 import numpy as np
 import pytest
