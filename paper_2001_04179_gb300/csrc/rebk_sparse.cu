@@ -1,22 +1,20 @@
 // rebk_sparse.cu -- Algorithm 1 of Du, Si, Sun (arXiv:2001.04179) on a sparse
 // matrix: CSR for the row blocks, a CSC copy for the column blocks.
 //
-// One persistent cooperative launch runs many iterations.  Iteration k (block
-// indices sampled before the launch, as in the dense path):
-//   A. w_c = A_{:,c}^T z for the columns c of J_k: each CTA owns a contiguous
-//      range of the block's columns, whose entries are contiguous in CSC; its
-//      threads gather over them at a stride in one round, adding per-column
-//      running sums into shared memory;                              barrier
-//   B. z -= c_J A_{:,J} w: the same CTA scatters its entries into z by FP64
-//      atomic adds;                                                  barrier
-//   C. r_l = A_{l,:} x - b_l + z_l for the rows l of I_k (contiguous row ranges
-//      per CTA, the same gather over CSR), and every check_every iterations each
-//      CTA's share of ||x^{k-1} - x_ref||^2;                          barrier
-//   D. x -= c_I A_{I,:}^T r: scatter of the rows' entries into x.
-// No barrier follows D: the next gather A reads z only, and every CTA finishes
-// D before it reaches the next barrier, which C waits behind.  Gathers read
-// state that no CTA writes until the following barrier, so each step sees the
-// previous iterate exactly.
+// One persistent cooperative launch runs many iterations, two device-wide
+// barriers each.  With the block indices sampled before the launch (as in the
+// dense path), iteration k is:
+//   gathers: r^k = A_{I_k,:} x^{k-1} - b_{I_k} + z^k_{I_k} over CSR, the column
+//     gather of the next iteration w = A_{:,J_{k+1}}^T z^k over CSC, and every
+//     check_every iterations each CTA's share of ||x^{k-1} - x_ref||^2;  barrier
+//   scatters: x^k = x^{k-1} - c_I A_{I_k,:}^T r^k and z^{k+1} = z^k -
+//     c_J A_{:,J_{k+1}} w by FP64 atomic adds;                          barrier
+// (z^1 comes from a prologue gather / scatter.)  Gathers only read and
+// scatters only write x and z, so each phase sees the iterates the previous
+// one left.  Each CTA owns a contiguous share of the sampled block's columns
+// (rows), whose entries are one CSC (CSR) range: its threads gather it in one
+// round, warps adding each line's products by shuffles before one shared
+// atomic per line.  On a converged stop at iteration k, x = x^{k-1} and z = z^k.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -117,8 +115,10 @@ __device__ __forceinline__ void gather_lines(const int64_t *bnd, int nq, const i
 
 __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_constant__ SparseArgs a) {
     __shared__ double red[kSW];
-    __shared__ double own[kOwnMax];      // w of the CTA's columns, then r of its rows
-    __shared__ int64_t bnd[kOwnMax + 1];  // entry boundaries of the CTA's lines
+    __shared__ double wq[kOwnMax];          // w of the CTA's columns of J_{k+1}
+    __shared__ double rq[kOwnMax];          // r of the CTA's rows of I_k
+    __shared__ int64_t bc[kOwnMax + 1];     // entry boundaries of those columns (CSC)
+    __shared__ int64_t br[kOwnMax + 1];     // and rows (CSR)
     __shared__ int s_flag;
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
     const int64_t K = a.iters;
@@ -129,36 +129,56 @@ __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_consta
         ++phase;
         return grid_barrier(a.bar, (unsigned)G * phase, a.status, a.timeout_ns, &s_flag);
     };
+    // column gather of iteration kk (A): w for the CTA's contiguous share of J_kk
+    int nqc = 0;
+    double cJ = 0.0;
+    auto gather_cols = [&](int64_t kk) {
+        const int j = __ldg(a.idx + 2 * (kk - 1));
+        const int64_t ja = (int64_t)j * a.tau_c, jb = ja + a.tau_c < a.n ? ja + a.tau_c : a.n;
+        const int64_t c0 = ja + (jb - ja) * cta / G, c1 = ja + (jb - ja) * (cta + 1) / G;
+        cJ = a.coef_c[j];
+        nqc = (int)(c1 - c0);
+        __syncthreads();  // bc[] and wq[] are free
+        for (int q = tid; q <= nqc; q += kST) bc[q] = a.cp[c0 + q];
+        __syncthreads();
+        if (nqc > 0) gather_lines(bc, nqc, a.ri, a.cv, a.z, wq);
+        if (tid < nqc && !isfinite(wq[tid])) atomicExch(a.bad, 1);
+    };
+    // z scatter (B) with the w of the last column gather
+    auto scatter_z = [&]() {
+        for (int64_t e = bc[0] + tid; nqc > 0 && e < bc[nqc]; e += kST)
+            atomicAdd(a.z + a.ri[e], -cJ * a.cv[e] * wq[line_of(bc, nqc, e)]);
+    };
     int64_t done = K;
     int stop = 0;
-    for (int64_t k = 1; k <= K; ++k) {
-        const int j = __ldg(a.idx + 2 * (k - 1)), i = __ldg(a.idx + 2 * (k - 1) + 1);
-        const int64_t ja = (int64_t)j * a.tau_c, jb = ja + a.tau_c < a.n ? ja + a.tau_c : a.n;
+    // prologue: z^1 (column step of iteration 1)
+    if (K >= 1) {
+        gather_cols(1);
+        if (!barrier()) return;
+        if (*reinterpret_cast<volatile int *>(a.bad) != 0) {
+            stop = 5;
+            done = 0;
+        } else {
+            scatter_z();
+            if (!barrier()) return;
+        }
+    }
+    for (int64_t k = 1; stop == 0 && k <= K; ++k) {
+        // ---- gathers: r^k = A_I x^{k-1} - b_I + z^k_I, w^{k+1} = A_J'^T z^k, test of x^{k-1} ----
+        const int i = __ldg(a.idx + 2 * (k - 1) + 1);
         const int64_t ia = (int64_t)i * a.tau_r, ib = ia + a.tau_r < a.m ? ia + a.tau_r : a.m;
-        const double cJ = a.coef_c[j], cI = a.coef_r[i];
-        // this CTA's contiguous share of the block's columns and rows
-        const int64_t c0 = ja + (jb - ja) * cta / G, c1 = ja + (jb - ja) * (cta + 1) / G;
         const int64_t l0 = ia + (ib - ia) * cta / G, l1 = ia + (ib - ia) * (cta + 1) / G;
-        const int nqc = (int)(c1 - c0), nqr = (int)(l1 - l0);
-        // ---- A: w_c = A_{:,c}^T z^{k-1} for the CTA's columns ----
-        for (int q = tid; q <= nqc; q += kST) bnd[q] = a.cp[c0 + q];
+        const int nqr = (int)(l1 - l0);
+        const double cI = a.coef_r[i];
+        for (int q = tid; q <= nqr; q += kST) br[q] = a.rp[l0 + q];
         __syncthreads();
-        if (nqc > 0) gather_lines(bnd, nqc, a.ri, a.cv, a.z, own);
-        if (tid < nqc && !isfinite(own[tid])) atomicExch(a.bad, 1);
-        if (!barrier()) return;
-        // ---- B: z^k = z^{k-1} - c_J A_{:,J} w ----
-        for (int64_t e = bnd[0] + tid; nqc > 0 && e < bnd[nqc]; e += kST)
-            atomicAdd(a.z + a.ri[e], -cJ * a.cv[e] * own[line_of(bnd, nqc, e)]);
-        if (!barrier()) return;
-        // ---- C: r_l = A_{l,:} x^{k-1} - b_l + z^k_l; test partial of x^{k-1} ----
-        for (int q = tid; q <= nqr; q += kST) bnd[q] = a.rp[l0 + q];
-        __syncthreads();
-        if (nqr > 0) gather_lines(bnd, nqr, a.ci, a.rv, a.x, own);
+        if (nqr > 0) gather_lines(br, nqr, a.ci, a.rv, a.x, rq);
         for (int q = tid; q < nqr; q += kST) {
-            const double rl = own[q] - a.b[l0 + q] + a.z[l0 + q];
-            own[q] = rl;
+            const double rl = rq[q] - a.b[l0 + q] + a.z[l0 + q];
+            rq[q] = rl;
             if (!isfinite(rl)) atomicExch(a.bad, 1);
         }
+        if (k < K) gather_cols(k + 1);
         const bool due = check && k >= 2 && (a.check_offset + k - 1) % a.check_every == 0;
         if (due) {
             double e2 = 0.0;
@@ -181,10 +201,11 @@ __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_consta
             done = k - 1;
             break;
         }
-        // ---- D: x^k = x^{k-1} - c_I A_{I,:}^T r ----
-        for (int64_t e = bnd[0] + tid; nqr > 0 && e < bnd[nqr]; e += kST)
-            atomicAdd(a.x + a.ci[e], -cI * a.rv[e] * own[line_of(bnd, nqr, e)]);
-        __syncthreads();  // bnd[] and own[] are rewritten by the next gather
+        // ---- scatters: x^k = x^{k-1} - c_I A_I^T r^k, z^{k+1} = z^k - c_J' A_J' w^{k+1} ----
+        for (int64_t e = br[0] + tid; nqr > 0 && e < br[nqr]; e += kST)
+            atomicAdd(a.x + a.ci[e], -cI * a.rv[e] * rq[line_of(br, nqr, e)]);
+        if (k < K) scatter_z();
+        if (!barrier()) return;
     }
     if (cta == 0 && tid == 0) {
         *a.iters_done = done;
