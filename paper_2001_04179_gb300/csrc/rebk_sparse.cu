@@ -113,12 +113,59 @@ __device__ __forceinline__ void gather_lines(const int64_t *bnd, int nq, const i
     __syncthreads();
 }
 
+// Both gathers of an iteration in one pass: the CTA's rows (CSR entries br[0] ..
+// br[nqr], against x) and columns (CSC entries bc[0] .. bc[nqc], against z) as one
+// list of nqr + nqc lines; part[q] gets line q's sum (rows first).  Each thread
+// takes two entries per round so that both loads and both gathers are in flight.
+__device__ __forceinline__ void gather_rows_cols(const int64_t *br, int nqr, const int32_t *__restrict__ ci,
+                                                 const double *__restrict__ rv, const double *x, const int64_t *bc,
+                                                 int nqc, const int32_t *__restrict__ ri,
+                                                 const double *__restrict__ cv, const double *z, double *part) {
+    const int nl = nqr + nqc;
+    for (int q = threadIdx.x; q < nl; q += kST) part[q] = 0.0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int64_t nr = nqr > 0 ? br[nqr] - br[0] : 0, nc = nqc > 0 ? bc[nqc] - bc[0] : 0, tot = nr + nc;
+    auto entry = [&](int64_t g, int *q, double *prod) {  // entry g of the joint list
+        if (g >= tot) {
+            *q = -1;
+            *prod = 0.0;
+        } else if (g < nr) {
+            const int64_t e = br[0] + g;
+            *q = line_of(br, nqr, e);
+            *prod = rv[e] * x[ci[e]];
+        } else {
+            const int64_t e = bc[0] + (g - nr);
+            *q = nqr + line_of(bc, nqc, e);
+            *prod = cv[e] * z[ri[e]];
+        }
+    };
+    auto add_lines = [&](int q, double prod) {  // per warp: one shuffle sum and one atomic per line
+        const int qlo = __reduce_min_sync(0xffffffffu, q >= 0 ? q : 0x7fffffff);
+        const int qhi = __reduce_max_sync(0xffffffffu, q);
+        for (int qq = qlo; qq <= qhi; ++qq) {
+            const double t = warp_sum(q == qq ? prod : 0.0);
+            if (lane == 0) atomicAdd(part + qq, t);
+        }
+    };
+    for (int64_t base = 0; base < tot; base += 2 * kST) {  // uniform over the CTA
+        int q0, q1;
+        double p0, p1;
+        entry(base + threadIdx.x, &q0, &p0);
+        entry(base + kST + threadIdx.x, &q1, &p1);
+        add_lines(q0, p0);
+        add_lines(q1, p1);
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_constant__ SparseArgs a) {
     __shared__ double red[kSW];
     __shared__ double wq[kOwnMax];          // w of the CTA's columns of J_{k+1}
     __shared__ double rq[kOwnMax];          // r of the CTA's rows of I_k
     __shared__ int64_t bc[kOwnMax + 1];     // entry boundaries of those columns (CSC)
     __shared__ int64_t br[kOwnMax + 1];     // and rows (CSR)
+    __shared__ double part[2 * kOwnMax];    // the joint gather's line sums
     __shared__ int s_flag;
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
     const int64_t K = a.iters;
@@ -170,15 +217,29 @@ __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_consta
         const int64_t l0 = ia + (ib - ia) * cta / G, l1 = ia + (ib - ia) * (cta + 1) / G;
         const int nqr = (int)(l1 - l0);
         const double cI = a.coef_r[i];
+        // the column share of J_{k+1} (none after the last iteration)
+        nqc = 0;
+        int64_t c0 = 0;
+        if (k < K) {
+            const int j = __ldg(a.idx + 2 * k);
+            const int64_t ja = (int64_t)j * a.tau_c, jb = ja + a.tau_c < a.n ? ja + a.tau_c : a.n;
+            c0 = ja + (jb - ja) * cta / G;
+            nqc = (int)(ja + (jb - ja) * (cta + 1) / G - c0);
+            cJ = a.coef_c[j];
+        }
         for (int q = tid; q <= nqr; q += kST) br[q] = a.rp[l0 + q];
+        for (int q = tid; q <= nqc; q += kST) bc[q] = a.cp[c0 + q];
         __syncthreads();
-        if (nqr > 0) gather_lines(br, nqr, a.ci, a.rv, a.x, rq);
+        gather_rows_cols(br, nqr, a.ci, a.rv, a.x, bc, nqc, a.ri, a.cv, a.z, part);
         for (int q = tid; q < nqr; q += kST) {
-            const double rl = rq[q] - a.b[l0 + q] + a.z[l0 + q];
+            const double rl = part[q] - a.b[l0 + q] + a.z[l0 + q];
             rq[q] = rl;
             if (!isfinite(rl)) atomicExch(a.bad, 1);
         }
-        if (k < K) gather_cols(k + 1);
+        for (int q = tid; q < nqc; q += kST) {
+            wq[q] = part[nqr + q];
+            if (!isfinite(wq[q])) atomicExch(a.bad, 1);
+        }
         const bool due = check && k >= 2 && (a.check_offset + k - 1) % a.check_every == 0;
         if (due) {
             double e2 = 0.0;
