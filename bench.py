@@ -51,6 +51,8 @@ def parse():
                     help="precision: the headline solve (default); warm: the learned warm start "
                          "on the 8192 x 2048 spectrum workload (targets, training, warm vs cold)")
     ap.add_argument("--batch-tau", type=int, default=16, help="batch workload block size (0 = autotune)")
+    ap.add_argument("--batch-count", type=int, default=512, help="batch workload: number of systems")
+    ap.add_argument("--batch-scale", type=int, default=1, help="batch workload: divide the size ranges (profiling)")
     ap.add_argument("--warm-train", type=int, default=2048)
     ap.add_argument("--warm-eval", type=int, default=32)
     ap.add_argument("--warm-batch-systems", type=int, default=152)
@@ -430,7 +432,7 @@ def run_batch_workload(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     t0 = time.perf_counter()
-    ps = batched_problems(512, seed=rank, nrhs=8)
+    ps = batched_problems(args.batch_count, seed=rank, nrhs=8, scale_down=args.batch_scale)
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
     bs = BatchSolver([p.A for p in ps], nrhs=8, tau=args.batch_tau)
@@ -454,7 +456,8 @@ def run_batch_workload(args):
         sys_ok += int((errs <= TOL).all(axis=1).sum())
     if rank == 0:
         print(json.dumps({
-            "workload": "batched: 512 systems m~U[200,6000], n~U[50,2000], 30% rank-deficient, 8 RHS each; "
+            "workload": f"batched: {args.batch_count} systems m~U[200,6000]/{args.batch_scale}, "
+                        f"n~U[50,2000]/{args.batch_scale}, 30% rank-deficient, 8 RHS each; "
                         "FP32 inner / FP64 refinement; one CUDA graph per solve; <= 1e5 iterations per system",
             "metric": "right-hand sides solved to 1e-8 per second", "unit": "solves/s",
             "value": rhs_ok / (ms / 1000.0), "steps": steps, "ms_per_step": ms / steps,

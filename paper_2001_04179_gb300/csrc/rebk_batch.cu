@@ -309,10 +309,11 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                 for (int l = warp; l < hr; l += kBW) {
                     float acc[kR] = {0, 0, 0, 0, 0, 0, 0, 0};
                     const float *Ar = A + (i0 + l) * lda;
-                    for (int64_t col0 = lane; col0 < n; col0 += 128) {  // four columns in flight
-                        float av[4], xv[4][kR];
+                    constexpr int CU = 8;  // columns in flight per lane
+                    for (int64_t col0 = lane; col0 < n; col0 += 32 * CU) {
+                        float av[CU], xv[CU][kR];
 #pragma unroll
-                        for (int u = 0; u < 4; ++u) {
+                        for (int u = 0; u < CU; ++u) {
                             const int64_t col = col0 + 32 * u;
                             if (col < n) {
                                 av[u] = __ldg(Ar + col);
@@ -324,7 +325,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                             }
                         }
 #pragma unroll
-                        for (int u = 0; u < 4; ++u)
+                        for (int u = 0; u < CU; ++u)
 #pragma unroll
                             for (int r = 0; r < kR; ++r) acc[r] = fmaf(av[u], xv[u][r], acc[r]);
                     }
