@@ -47,9 +47,10 @@ def parse():
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["precision", "warm", "batch", "sparse"], default="precision",
+    ap.add_argument("--workload", choices=["precision", "warm", "batch", "sparse", "sweep"], default="precision",
                     help="precision: the headline solve (default); warm: the learned warm start "
                          "on the 8192 x 2048 spectrum workload (targets, training, warm vs cold)")
+    ap.add_argument("--sweep-parts", default="", help="sweep workload: comma-separated parts 1-5 (default all)")
     ap.add_argument("--batch-tau", type=int, default=16, help="batch workload block size (0 = autotune)")
     ap.add_argument("--batch-count", type=int, default=512, help="batch workload: number of systems")
     ap.add_argument("--batch-scale", type=int, default=1, help="batch workload: divide the size ranges (profiling)")
@@ -537,10 +538,111 @@ def run_sparse_workload(args):
     return 0
 
 
+def run_sweep(args):
+    """Block size and step size on GB300, measured by the library's autotuner
+    (rebk_tune_tau: time to tolerance of each candidate, mean of several
+    seeded solves).  Parts, each printed as one JSON row per point and one row
+    with the tuner's pick:
+      (1) 8000 x 20000 rank 2000, FP32 mixed precision to 1e-8: tau in
+          {32, 64, 128, 256} at alpha = 1.75 / beta_max, then alpha / beta_max in
+          {0.5, 1, 1.5, 1.75, 1.95, 2.25} at tau = 128;
+      (2) randn(1000, 200) inconsistent, plain FP64 to 1e-10, tau in
+          {5, 10, 20, 40, 100, 200};
+      (3) Fig. 1 shapes: Type I (500 x 250, rank 150, kappa 2) and Type II
+          randn(500, 250), tau = 10, alpha / beta_max from 0.75 to 2.62;
+      (4) Fig. 2 shapes: Type I (20000 x 5000, rank 4500, kappa 2) and Type II
+          randn(20000, 5000), tau in {5, 10, 20, 50, 100, 200}, alpha = 1.75 / beta_max;
+      (5) Fig. 3 shapes: Type I (m x 500, rank 250, kappa 2) and Type II
+          randn(m, 500), m = 2000, 4000, ..., 20000, tau = 10, alpha = 1.75 / beta_max.
+    Parts (3)-(5) stop at ||x - A^+ b|| <= 1e-5 (the absolute rule of Section 3's
+    experiments) in plain FP64."""
+    import torch
+
+    from paper_2001_04179_gb300 import tune_tau
+    from workloads import gaussian_problem, type1_problem
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    only = set(args.sweep_parts.split(",")) if args.sweep_parts else None
+    rows = []
+
+    def emit(name, pts, best, c=None):
+        for p in pts:
+            rows.append({"workload": name, "tau": p["tau"],
+                         "alpha_times_beta_max": c if c is not None else round(p["alpha"] * p["beta_max"], 6),
+                         "beta_max": p["beta_max"], "iterations": p["iterations"],
+                         "ms_per_solve": p["device_ms"], "status": R_STATUS(p["status"])})
+        rows.append({"workload": name, "tuner_best_tau": best})
+
+    def tune(name, A, b, xr, taus, c, storage, tol, trials, max_iter=10**7):
+        best, pts = tune_tau(A, b, taus, x_ref=xr, alpha_factor=c, storage=storage, tol=tol,
+                             max_iter=max_iter, seed=1000 + rank, trials=trials, stream=stream)
+        emit(name, pts, best, c)
+        return best, pts
+
+    if only is None or "1" in only:
+        prob = make_problem(rank, True)
+        A_dev = torch.from_numpy(prob.A).to(dev)
+        b, xr = torch.from_numpy(prob.b).to(dev), torch.from_numpy(prob.x_ref).to(dev)
+        name = "8000x20000 rank 2000, FP32 mixed, tol 1e-8"
+        tune(name, A_dev, b, xr, [32, 64, 128, 256], 1.75, "fp32", TOL, 2)
+        for c in (0.5, 1.0, 1.5, 1.75, 1.95, 2.25):
+            tune(name + ", alpha sweep", A_dev, b, xr, [128], c, "fp32", TOL, 2, max_iter=200000)
+        del A_dev, b, xr, prob
+        torch.cuda.empty_cache()
+    if only is None or "2" in only:
+        g = gaussian_problem(1000, 200, seed=rank)
+        tune("randn(1000,200) inconsistent, plain FP64, tol 1e-10", g.A, torch.from_numpy(g.b).to(dev),
+             torch.from_numpy(g.x_ref).to(dev), [5, 10, 20, 40, 100, 200], 1.75, "fp64", 1e-10, 3)
+
+    def paper_pair(m, n, r, seed):
+        return [("Type I %dx%d r%d k2" % (m, n, r), type1_problem(m, n, r, 2.0, seed)),
+                ("Type II randn(%d,%d)" % (m, n), gaussian_problem(m, n, seed=seed))]
+
+    def abs_tol(p):
+        return 1e-5 / float(np.linalg.norm(p.x_ref))
+
+    if only is None or "3" in only:
+        for label, p in paper_pair(500, 250, 150, 7 + rank):
+            A_dev = torch.from_numpy(p.A).to(dev)
+            b, xr = torch.from_numpy(p.b).to(dev), torch.from_numpy(p.x_ref).to(dev)
+            for c in (0.75, 1.0, 1.25, 1.5, 1.75, 2.0, 2.25, 2.62):
+                tune("Fig. 1 " + label + ", tau 10, abs err 1e-5", A_dev, b, xr, [10], c, "fp64", abs_tol(p),
+                     10, max_iter=400000)
+    if only is None or "4" in only:
+        for label, p in paper_pair(20000, 5000, 4500, 11 + rank):
+            A_dev = torch.from_numpy(p.A).to(dev)
+            b, xr = torch.from_numpy(p.b).to(dev), torch.from_numpy(p.x_ref).to(dev)
+            tune("Fig. 2 " + label + ", alpha 1.75/beta_max, abs err 1e-5", A_dev, b, xr,
+                 [5, 10, 20, 50, 100, 200], 1.75, "fp64", abs_tol(p), 2, max_iter=3000000)
+            del A_dev, b, xr, p
+            torch.cuda.empty_cache()
+    if only is None or "5" in only:
+        for m in range(2000, 20001, 2000):
+            for label, p in paper_pair(m, 500, 250, 13 + m + rank):
+                A_dev = torch.from_numpy(p.A).to(dev)
+                b, xr = torch.from_numpy(p.b).to(dev), torch.from_numpy(p.x_ref).to(dev)
+                tune("Fig. 3 " + label + ", tau 10, alpha 1.75/beta_max, abs err 1e-5", A_dev, b, xr, [10],
+                     1.75, "fp64", abs_tol(p), 3, max_iter=3000000)
+    if rank == 0:
+        for r in rows:
+            print(json.dumps(r), flush=True)
+    return 0
+
+
+def R_STATUS(code: int) -> str:
+    from paper_2001_04179_gb300 import rebk as R
+    return R.STATUS_NAMES.get(code, str(code))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "sweep":
+        return run_sweep(args)
     if args.workload == "sparse":
         return run_sparse_workload(args)
     if args.workload == "warm":

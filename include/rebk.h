@@ -170,6 +170,17 @@ rebk_status rebk_beta_max(rebk_handle h, double *beta_row, double *beta_col);
 /* Step size alpha in use (host double). */
 rebk_status rebk_get_alpha(rebk_handle h, double *alpha);
 
+/*
+ * Replaces the step size alpha of Algorithm 1 (Section 2.2 requires
+ * 0 < alpha < 2 / max(beta^I_max, beta^J_max) for Theorem main) and rebuilds
+ * the per-block coefficients alpha / ||block||_F^2 in FP64 and FP32 on the
+ * handle's stream; the call synchronises that stream.  Any alpha > 0 is
+ * accepted (a value past the bound may diverge: solves then return
+ * REBK_DIVERGED or REBK_MAX_ITER).  Errors: EINVAL (NULL handle, alpha not
+ * finite or <= 0), ECUDA.
+ */
+rebk_status rebk_set_alpha(rebk_handle h, double alpha);
+
 /* Number of row blocks s and column blocks t (host int64). */
 rebk_status rebk_get_blocks(rebk_handle h, int64_t *s, int64_t *t);
 
@@ -186,6 +197,47 @@ rebk_status rebk_get_tables(rebk_handle h, double *nr, double *nc, double *cdf_r
  * even.
  */
 rebk_status rebk_export_storage(rebk_handle h, int32_t storage, void *host_out);
+
+/* ------------------------------------------------------------------------ */
+/* Block-size autotuner                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* One candidate of rebk_tune_tau. */
+typedef struct {
+    int64_t tau;           /* block size of rows and columns (clipped to m and n)      */
+    double beta_max;       /* max(beta^I_max, beta^J_max) at this tau (Section 2.2)    */
+    double alpha;          /* step size used: alpha_factor / beta_max                  */
+    int64_t iterations;    /* mean iterations of the trials                            */
+    double device_ms;      /* mean device time of a solve (rebk_stats.device_ms);
+                              -1 if a trial missed the tolerance                        */
+    int32_t status;        /* REBK_OK, or REBK_MAX_ITER / REBK_DIVERGED of the worst trial */
+} rebk_tune_point;
+
+/*
+ * Measures the time to tolerance of Algorithm 1 for each candidate block size
+ * taus[0..count) -- the same tau for the row and the column partition, as in
+ * the experiments of Section 3 -- and returns the fastest in *best_tau.
+ * For each candidate: a solver is created (A: m x n row-major, leading
+ * dimension lda, on the device if A_on_device, else on the host and uploaded
+ * once), alpha = alpha_factor / max(beta^I_max, beta^J_max) (alpha_factor <= 0
+ * means 1.75, Section 3's empirical choice), one short untimed solve picks the
+ * persistent kernel's launch shape, then `trials` solves with seeds seed,
+ * seed+1, ... run to tol: plain FP64 (storage = REBK_FP64, rebk_solve_ex) or
+ * mixed precision (REBK_FP32 / REBK_BF16, rebk_solve_refined); with x_ref
+ * (device, n) the stop rule is the relative error, else the residual test of
+ * rebk_solve.  b: device, m.  opt supplies stream, num_ctas, check_every and
+ * extra storage (its tau fields are ignored).  points: host array of count
+ * entries, filled in candidate order.
+ * Returns REBK_MAX_ITER (best_tau = 0) when no candidate reached tol.
+ * Errors: EINVAL (NULL pointers, count < 1, a tau < 1, unknown storage,
+ * tol <= 0, max_iter < 1, trials < 1), EUNSUPPORTED (tau > 512), ENOMEM,
+ * ECUDA.
+ */
+rebk_status rebk_tune_tau(const double *A, int64_t m, int64_t n, int64_t lda, int A_on_device,
+                          const double *b, const double *x_ref, const int64_t *taus, int32_t count,
+                          double alpha_factor, int32_t storage, double tol, int64_t max_iter,
+                          uint64_t seed, int32_t trials, const rebk_options *opt,
+                          rebk_tune_point *points, int64_t *best_tau);
 
 /* ------------------------------------------------------------------------ */
 /* Batches of independent systems                                           */

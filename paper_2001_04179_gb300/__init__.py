@@ -5,6 +5,6 @@ arXiv:2001.04179.  The method runs in librebk.so (C ABI in include/rebk.h);
 this package only marshals arguments, with torch for device memory.
 """
 from .rebk import load, library_path, RebkError  # noqa: F401
-from .solver import BatchSolver, Solver, SparseSolver, WarmStartNet  # noqa: F401
+from .solver import BatchSolver, Solver, SparseSolver, WarmStartNet, tune_tau  # noqa: F401
 
-__all__ = ["load", "library_path", "RebkError", "Solver", "SparseSolver", "BatchSolver", "WarmStartNet"]
+__all__ = ["load", "library_path", "RebkError", "Solver", "SparseSolver", "BatchSolver", "WarmStartNet", "tune_tau"]

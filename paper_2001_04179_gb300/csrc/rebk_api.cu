@@ -550,6 +550,20 @@ rebk_status rebk_get_alpha(rebk_handle h, double *alpha) {
     return REBK_OK;
 }
 
+rebk_status rebk_set_alpha(rebk_handle h, double alpha) {
+    g_last_error.clear();
+    if (!h) return fail(REBK_EINVAL, "handle is NULL");
+    if (!(alpha > 0.0) || !std::isfinite(alpha)) return fail(REBK_EINVAL, "alpha must be finite and > 0");
+    const cudaStream_t st = h->stream;
+    cudaError_t e = step_coefficients(h->nr, h->s, alpha, h->coef_r64, h->coef_r32, st);
+    if (e == cudaSuccess) e = step_coefficients(h->nc, h->t, alpha, h->coef_c64, h->coef_c32, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return cuda_fail(e, "step coefficients");
+    h->alpha = alpha;
+    for (int i = 0; i < 3; ++i) h->prepG[i] = 0;  // launch arguments carry alpha
+    return REBK_OK;
+}
+
 rebk_status rebk_get_blocks(rebk_handle h, int64_t *s, int64_t *t) {
     if (!h) return fail(REBK_EINVAL, "handle is NULL");
     if (s) *s = h->s;

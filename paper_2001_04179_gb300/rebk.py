@@ -49,6 +49,14 @@ class RebkRefineOpts(ctypes.Structure):
                 ("inner_iters", ctypes.c_int64), ("inner_reduction", ctypes.c_double)]
 
 
+class RebkTunePoint(ctypes.Structure):
+    _fields_ = [("tau", ctypes.c_int64), ("beta_max", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("iterations", ctypes.c_int64), ("device_ms", ctypes.c_double), ("status", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class RebkBatchOptions(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("inner_reduction", ctypes.c_double),
@@ -87,6 +95,11 @@ _SIGNATURES = {
                             ctypes.POINTER(RebkStats)], ctypes.c_int),
     "rebk_beta_max": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "rebk_get_alpha": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "rebk_set_alpha": ([_P, ctypes.c_double], ctypes.c_int),
+    "rebk_tune_tau": ([_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _P, _P, _P, ctypes.c_int32,
+                       ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_int64, ctypes.c_uint64,
+                       ctypes.c_int32, ctypes.POINTER(RebkOptions), _P, ctypes.POINTER(ctypes.c_int64)],
+                      ctypes.c_int),
     "rebk_get_blocks": ([_P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)], ctypes.c_int),
     "rebk_get_tables": ([_P, _P, _P, _P, _P], ctypes.c_int),
     "rebk_export_storage": ([_P, ctypes.c_int32, _P], ctypes.c_int),

@@ -83,6 +83,11 @@ class Solver:
         _r.check(_r.load().rebk_get_alpha(self._h, ctypes.byref(a)))
         return a.value
 
+    @alpha.setter
+    def alpha(self, value: float):
+        """Replace the step size (block coefficients are rebuilt on the device)."""
+        _r.check(_r.load().rebk_set_alpha(self._h, float(value)))
+
     def blocks(self):
         s, t = ctypes.c_int64(), ctypes.c_int64()
         _r.check(_r.load().rebk_get_blocks(self._h, ctypes.byref(s), ctypes.byref(t)))
@@ -165,6 +170,45 @@ class Solver:
         if record:
             out["idx"] = idx[: 2 * stats.iterations].view(-1, 2)
         return out
+
+
+def tune_tau(A, b, taus: Sequence[int], x_ref=None, alpha_factor: float = 1.75, storage: str = "fp64",
+             tol: float = 1e-8, max_iter: int = 10**7, seed: int = 0, trials: int = 1, num_ctas: int = 0,
+             check_every: int = 0, stream=None):
+    """Block-size autotuner (rebk_tune_tau): time to tolerance for each tau.
+
+    A: CUDA float64 tensor or numpy array (m x n); b, x_ref: CUDA float64.
+    Returns (best_tau, [dict(tau, beta_max, alpha, iterations, device_ms, status)]);
+    best_tau is 0 when no candidate reached tol.
+    """
+    torch = _torch()
+    lib = _r.load()
+    taus = [int(t) for t in taus]
+    arr = (ctypes.c_int64 * len(taus))(*taus)
+    pts = (_r.RebkTunePoint * len(taus))()
+    best = ctypes.c_int64()
+    opt = _r.RebkOptions(0, 0, 0, num_ctas, check_every,
+                         None if stream is None else ctypes.c_void_p(stream.cuda_stream))
+    if isinstance(A, torch.Tensor):
+        if not (A.is_cuda and A.dtype == torch.float64 and A.dim() == 2 and A.stride(1) == 1):
+            raise ValueError("A must be a CUDA float64 matrix with unit column stride")
+        m, n = A.shape
+        ptr, ld, on_dev = A.data_ptr(), A.stride(0), 1
+        keep = A
+    else:
+        keep = np.ascontiguousarray(A, dtype=np.float64)
+        m, n = keep.shape
+        ptr, ld, on_dev = keep.ctypes.data, n, 0
+    _require_cuda_f64(b, m, "b")
+    if x_ref is not None:
+        _require_cuda_f64(x_ref, n, "x_ref")
+    st = lib.rebk_tune_tau(ctypes.c_void_p(ptr), m, n, ld, on_dev, ctypes.c_void_p(b.data_ptr()),
+                           _dptr(x_ref), ctypes.cast(arr, ctypes.c_void_p), len(taus), float(alpha_factor),
+                           _r.STORAGE[storage], float(tol), int(max_iter), int(seed), int(trials),
+                           ctypes.byref(opt), ctypes.cast(pts, ctypes.c_void_p), ctypes.byref(best))
+    del keep
+    _r.check(st, (_r.REBK_OK, _r.REBK_MAX_ITER))
+    return best.value, [p.as_dict() for p in pts]
 
 
 class SparseSolver:

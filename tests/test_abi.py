@@ -72,3 +72,35 @@ def test_network_loss_selection_rejects_bad_arguments_on_the_host():
     lib = R.load()
     assert lib.rebk_mlp_set_loss(None, 0, 1.0) == R.REBK_EINVAL
     assert lib.rebk_batch_solve_ex(None, None, None, None, None, None, 0.0, 0, 0, 0, None, None) == R.REBK_EINVAL
+
+
+def test_step_size_and_tuner_reject_bad_arguments_on_the_host():
+    """rebk_set_alpha and rebk_tune_tau check their arguments before any CUDA call."""
+    import ctypes
+    from paper_2001_04179_gb300 import rebk as R
+    lib = R.load()
+    assert lib.rebk_set_alpha(None, 1.0) == R.REBK_EINVAL
+    A = (ctypes.c_double * 4)(1, 2, 3, 4)
+    b = (ctypes.c_double * 2)(1, 1)
+    taus = (ctypes.c_int64 * 2)(1, 2)
+    pts = (R.RebkTunePoint * 2)()
+    best = ctypes.c_int64(7)
+    P = lambda a: ctypes.cast(a, ctypes.c_void_p)
+
+    def tune(A_=A, m=2, n=2, taus_=taus, count=2, storage=0, tol=1e-6, max_iter=10, trials=1):
+        return lib.rebk_tune_tau(P(A_) if A_ is not None else None, m, n, n, 0, P(b),
+                                 None, P(taus_) if taus_ is not None else None, count, 1.75, storage,
+                                 tol, max_iter, 0, trials, None, P(pts), ctypes.byref(best))
+
+    assert tune(A_=None) == R.REBK_EINVAL
+    assert tune(taus_=None) == R.REBK_EINVAL
+    assert tune(count=0) == R.REBK_EINVAL
+    assert tune(m=0) == R.REBK_EINVAL
+    assert tune(storage=9) == R.REBK_EINVAL
+    assert tune(tol=0.0) == R.REBK_EINVAL
+    assert tune(max_iter=0) == R.REBK_EINVAL
+    assert tune(trials=0) == R.REBK_EINVAL
+    assert best.value == 0
+    zero = (ctypes.c_int64 * 2)(0, 2)
+    assert tune(taus_=zero) == R.REBK_EINVAL
+    assert "tau" in lib.rebk_last_error().decode()
