@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--workload", choices=["precision", "warm", "batch", "sparse", "sweep"], default="precision",
                     help="precision: the headline solve (default); warm: the learned warm start "
                          "on the 8192 x 2048 spectrum workload (targets, training, warm vs cold)")
+    ap.add_argument("--sparse-mixed", action="store_true",
+                    help="with --workload sparse --profile-pass K: run the mixed-precision pass")
     ap.add_argument("--sweep-parts", default="", help="sweep workload: comma-separated parts 1-5 (default all)")
     ap.add_argument("--batch-tau", type=int, default=16, help="batch workload block size (0 = autotune)")
     ap.add_argument("--batch-count", type=int, default=512, help="batch workload: number of systems")
@@ -475,8 +477,9 @@ def run_sparse_workload(args):
     at uniform random columns, values U(0,1) 10^u (u ~ U(0,1) per row: row norms
     spread over a decade), b = A x* + 1% Gaussian noise; tau = 256 (256 row
     blocks over CSR, 64 column blocks over the CSC copy); plain FP64 Algorithm 1
-    to 1e-8 relative error against x_ref from the normal equations (dense
-    Cholesky on the host)."""
+    and the mixed-precision solve (FP32 values and inner sweeps, FP64
+    refinement), each to 1e-8 relative error against x_ref from the normal
+    equations (dense Cholesky on the host)."""
     import torch
 
     from paper_2001_04179_gb300 import SparseSolver
@@ -497,44 +500,59 @@ def run_sparse_workload(args):
     b = torch.from_numpy(p.b).to(dev)
     if args.profile_pass > 0:  # a fixed number of iterations, twice (the second is the one ncu captures)
         for _ in range(2):
-            r = sol.solve(b, tol=0.0, max_iter=args.profile_pass, seed=7)
+            if args.sparse_mixed:
+                r = sol.solve_refined(b, tol=0.0, max_iter=args.profile_pass, seed=7, max_outer=1,
+                                      inner_iters=args.profile_pass)
+            else:
+                r = sol.solve(b, tol=0.0, max_iter=args.profile_pass, seed=7)
         torch.cuda.synchronize()
-        print(json.dumps({"profile_pass": args.profile_pass, "workload": "sparse", "iterations": r["stats"]["iterations"],
+        print(json.dumps({"profile_pass": args.profile_pass, "workload": "sparse",
+                          "mode": "mixed" if args.sparse_mixed else "plain", "iterations": r["stats"]["iterations"],
                           "us_per_iteration": 1000.0 * r["stats"]["kernel_ms"] / args.profile_pass}))
         return 0
     xr = torch.from_numpy(p.x_ref).to(dev)
-    for w in range(max(1, args.warmup)):
-        sol.solve(b, tol=TOL, max_iter=4_000_000, seed=900 + w, x_ref=xr)
     stream = torch.cuda.current_stream()
     steps = max(1, args.steps)
-    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    its, kms = 0, 0.0
-    ev0.record(stream)
-    for s_ in range(steps):
-        out = sol.solve(b, tol=TOL, max_iter=4_000_000, seed=1000 + s_, x_ref=xr)
-        if out["stats"]["rel_err"] > TOL:
-            raise RuntimeError(f"sparse solve did not reach {TOL}: {out['stats']}")
-        its += out["stats"]["iterations"]
-        kms += out["stats"]["kernel_ms"]
-    ev1.record(stream)
-    torch.cuda.synchronize()
-    ms = ev0.elapsed_time(ev1)
     nnz_col_block = p.nnz / info["col_blocks"]
     nnz_row_block = 256 * k
-    # per iteration: both blocks' values (8 B) and indices (4 B) twice (gather, scatter) and the
-    # gathered / scattered vector entries (8 B each)
-    bytes_it = (nnz_col_block + nnz_row_block) * 2 * (8 + 4 + 8)
+
+    def run(mode):
+        call = sol.solve if mode == "plain" else sol.solve_refined
+        for w in range(max(1, args.warmup)):
+            call(b, tol=TOL, max_iter=4_000_000, seed=900 + w, x_ref=xr)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        its, kms, outer = 0, 0.0, 0
+        ev0.record(stream)
+        for s_ in range(steps):
+            out = call(b, tol=TOL, max_iter=4_000_000, seed=1000 + s_, x_ref=xr)
+            if out["stats"]["rel_err"] > TOL:
+                raise RuntimeError(f"sparse {mode} solve did not reach {TOL}: {out['stats']}")
+            its += out["stats"]["iterations"]
+            kms += out["stats"]["kernel_ms"]
+            outer += out["stats"]["outer"]
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        # per iteration: both blocks' values and indices (4 B) twice (gather, scatter) and the
+        # gathered / scattered vector entries (8 B FP64, 4 B FP32 corrections)
+        vb = 8 if mode == "plain" else 4
+        bytes_it = (nnz_col_block + nnz_row_block) * 2 * (vb + 4 + vb)
+        return {"value": steps / (ms / 1000.0), "ms_per_step": ms / steps, "iterations_per_solve": its / steps,
+                "refinement_passes_per_solve": outer / steps, "kernel_ms_per_solve": kms / steps,
+                "block_iterations_per_s": its / (kms / 1000.0), "us_per_iteration": 1000.0 * kms / its,
+                "algorithmic_bytes_per_iteration": bytes_it, "achieved_gbs": bytes_it * its / (kms / 1000.0) / 1e9,
+                "matrix_bytes_csr_plus_csc": 2 * p.nnz * (vb + 4)}
+
+    plain = run("plain")
+    mixed = run("mixed")
     if rank == 0:
         print(json.dumps({
-            "workload": "sparse: 65536x16384 CSR FP64, 96 nnz/row uniform columns, values U(0,1)*10^U(0,1), "
-                        "b = A x* + 1% noise; tau = 256 rows / 256 columns; plain FP64 to 1e-8",
-            "metric": "solves/s to 1e-8 rel err", "unit": "solves/s", "value": steps / (ms / 1000.0),
-            "steps": steps, "ms_per_step": ms / steps, "iterations_per_solve": its / steps,
-            "block_iterations_per_s": its / (kms / 1000.0), "us_per_iteration": 1000.0 * kms / its,
-            "algorithmic_bytes_per_iteration": bytes_it, "achieved_gbs": bytes_it * its / (kms / 1000.0) / 1e9,
-            "nnz": p.nnz, "matrix_bytes_csr_plus_csc": 2 * p.nnz * 12, "alpha": info["alpha"],
-            "beta_max": info["beta_max"], "problem_gen_s": gen_s, "create_s": create_s,
-            "mixed_precision": "not built for sparse storage"}))
+            "workload": "sparse: 65536x16384 CSR, 96 nnz/row uniform columns, values U(0,1)*10^U(0,1), "
+                        "b = A x* + 1% noise; tau = 256 rows / 256 columns; to 1e-8",
+            "metric": "solves/s to 1e-8 rel err", "unit": "solves/s", "steps": steps,
+            "plain_fp64": plain, "mixed_fp32": mixed, "mixed_over_plain": mixed["value"] / plain["value"],
+            "nnz": p.nnz, "alpha": info["alpha"], "beta_max": info["beta_max"], "problem_gen_s": gen_s,
+            "create_s": create_s}))
     return 0
 
 

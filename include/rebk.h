@@ -482,13 +482,28 @@ void rebk_sparse_destroy(rebk_sparse h);
  * x (device, n, output), ext optional (x_ref stop rule checked every
  * check_every iterations, x0, z0, z_out, idx_out, k0, stream_id).  Without
  * x_ref the solve runs max_iter iterations.  One persistent launch runs many
- * iterations: per iteration a column gather, a z scatter and a row gather,
- * separated by device-wide barriers (a row scatter needs none before the next
- * column gather, which reads z only).  Results match the dense solve of the
- * same matrix up to summation order (FP64 atomic adds).
+ * iterations, two device-wide barriers each: the row gather of iteration k and
+ * the column gather of iteration k+1 in one phase, the x and z scatters (FP64
+ * atomic adds) in the next.  Results match the dense solve of the same matrix
+ * up to summation order.
  */
 rebk_status rebk_sparse_solve(rebk_sparse h, const double *b, double *x, double tol, int64_t max_iter,
                               uint64_t seed, const rebk_solve_ext *ext, rebk_stats *stats);
+
+/*
+ * Mixed precision on the sparse matrix, as rebk_solve_refined: the inner
+ * sweeps run the correction form of Algorithm 1 with FP32 copies of the values
+ * (made at creation, round to nearest) and FP32 arithmetic; the residuals
+ * f = b - z - A x, g = A^T z and the updates z <- z - A s, x <- x + A^T v use
+ * the FP64 values (CSR for A p, CSC for A^T q).  ropt->storage must be
+ * REBK_FP32 (REBK_BF16: EUNSUPPORTED).  Stop: relative error <= tol with
+ * ext->x_ref (a pass ends at inner_reduction (default 1e-4) of its starting
+ * error or when the error stops falling), else the residual test of
+ * rebk_solve after each pass.  max_iter bounds the total inner iterations.
+ */
+rebk_status rebk_sparse_solve_refined(rebk_sparse h, const double *b, double *x, double tol, int64_t max_iter,
+                                      uint64_t seed, const rebk_refine_opts *ropt, const rebk_solve_ext *ext,
+                                      rebk_stats *stats);
 
 /* alpha in use, the beta_max estimate and the block counts (host outputs, any NULL). */
 rebk_status rebk_sparse_info(rebk_sparse h, double *alpha, double *beta_max, int32_t *row_blocks,

@@ -43,16 +43,19 @@ struct SparseArgs {
     int tau_r, tau_c;
     const int64_t *rp;   // CSR row pointers (m + 1)
     const int32_t *ci;   // CSR column indices
-    const double *rv;    // CSR values
+    const void *rv;      // CSR values (T)
     const int64_t *cp;   // CSC column pointers (n + 1)
     const int32_t *ri;   // CSC row indices
-    const double *cv;    // CSC values
-    const double *coef_r, *coef_c;  // alpha / ||block||_F^2 (0 for zero blocks)
+    const void *cv;      // CSC values (T)
+    const void *coef_r, *coef_c;  // T: alpha / ||block||_F^2 (0 for zero blocks)
     const int32_t *idx;  // 2 * iters: (j_k, i_k)
     int64_t iters;
-    double *z, *x;
-    const double *b;
+    void *z, *x;         // T: z and x (plain), the corrections dz and dx (CORR)
+    const double *b;     // b (plain), f = b - z - A x (CORR)
+    const double *g;     // CORR: A^T z
+    void *sdual, *vdual; // CORR (T): duals s (n) and v (m), dz = -A s, dx = A^T v
     const double *x_ref;  // NULL = no test
+    const double *x_base; // CORR: the test uses x_base + dx
     double tol2_abs;
     int64_t check_every, check_offset;
     double *acc;          // [3] rotating error accumulators, zeroed before launch
@@ -89,16 +92,17 @@ __device__ __forceinline__ int line_of(const int64_t *bnd, int nq, int64_t e) {
 // contiguous lines (entries bnd[0] .. bnd[nq]).  Each round, warp w takes 32
 // consecutive entries (sorted by line, so they span one line or a few); the warp
 // adds each line's products with a shuffle sum and one lane adds that to part[].
+template <typename T>
 __device__ __forceinline__ void gather_lines(const int64_t *bnd, int nq, const int32_t *__restrict__ idx,
-                                             const double *__restrict__ val, const double *vec, double *part) {
-    for (int q = threadIdx.x; q < nq; q += kST) part[q] = 0.0;
+                                             const T *__restrict__ val, const T *vec, T *part) {
+    for (int q = threadIdx.x; q < nq; q += kST) part[q] = T(0);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     for (int64_t base = bnd[0]; base < bnd[nq]; base += kST) {  // uniform over the CTA
         const int64_t e = base + threadIdx.x;
         const bool in = e < bnd[nq];
         int q = 0x7fffffff;
-        double prod = 0.0;
+        T prod = T(0);
         if (in) {
             q = line_of(bnd, nq, e);
             prod = val[e] * vec[idx[e]];
@@ -106,7 +110,7 @@ __device__ __forceinline__ void gather_lines(const int64_t *bnd, int nq, const i
         const int qlo = __reduce_min_sync(0xffffffffu, q);
         const int qhi = __reduce_max_sync(0xffffffffu, in ? q : -1);
         for (int qq = qlo; qq <= qhi; ++qq) {  // warp-uniform bounds
-            const double t = warp_sum(in && q == qq ? prod : 0.0);
+            const T t = warp_sum(in && q == qq ? prod : T(0));
             if (lane == 0) atomicAdd(part + qq, t);
         }
     }
@@ -117,19 +121,20 @@ __device__ __forceinline__ void gather_lines(const int64_t *bnd, int nq, const i
 // br[nqr], against x) and columns (CSC entries bc[0] .. bc[nqc], against z) as one
 // list of nqr + nqc lines; part[q] gets line q's sum (rows first).  Each thread
 // takes two entries per round so that both loads and both gathers are in flight.
+template <typename T>
 __device__ __forceinline__ void gather_rows_cols(const int64_t *br, int nqr, const int32_t *__restrict__ ci,
-                                                 const double *__restrict__ rv, const double *x, const int64_t *bc,
+                                                 const T *__restrict__ rv, const T *x, const int64_t *bc,
                                                  int nqc, const int32_t *__restrict__ ri,
-                                                 const double *__restrict__ cv, const double *z, double *part) {
+                                                 const T *__restrict__ cv, const T *z, T *part) {
     const int nl = nqr + nqc;
-    for (int q = threadIdx.x; q < nl; q += kST) part[q] = 0.0;
+    for (int q = threadIdx.x; q < nl; q += kST) part[q] = T(0);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t nr = nqr > 0 ? br[nqr] - br[0] : 0, nc = nqc > 0 ? bc[nqc] - bc[0] : 0, tot = nr + nc;
-    auto entry = [&](int64_t g, int *q, double *prod) {  // entry g of the joint list
+    auto entry = [&](int64_t g, int *q, T *prod) {  // entry g of the joint list
         if (g >= tot) {
             *q = -1;
-            *prod = 0.0;
+            *prod = T(0);
         } else if (g < nr) {
             const int64_t e = br[0] + g;
             *q = line_of(br, nqr, e);
@@ -140,17 +145,17 @@ __device__ __forceinline__ void gather_rows_cols(const int64_t *br, int nqr, con
             *prod = cv[e] * z[ri[e]];
         }
     };
-    auto add_lines = [&](int q, double prod) {  // per warp: one shuffle sum and one atomic per line
+    auto add_lines = [&](int q, T prod) {  // per warp: one shuffle sum and one atomic per line
         const int qlo = __reduce_min_sync(0xffffffffu, q >= 0 ? q : 0x7fffffff);
         const int qhi = __reduce_max_sync(0xffffffffu, q);
         for (int qq = qlo; qq <= qhi; ++qq) {
-            const double t = warp_sum(q == qq ? prod : 0.0);
+            const T t = warp_sum(q == qq ? prod : T(0));
             if (lane == 0) atomicAdd(part + qq, t);
         }
     };
     for (int64_t base = 0; base < tot; base += 2 * kST) {  // uniform over the CTA
         int q0, q1;
-        double p0, p1;
+        T p0, p1;
         entry(base + threadIdx.x, &q0, &p0);
         entry(base + kST + threadIdx.x, &q1, &p1);
         add_lines(q0, p0);
@@ -159,15 +164,28 @@ __device__ __forceinline__ void gather_rows_cols(const int64_t *br, int nqr, con
     __syncthreads();
 }
 
+// T = double, CORR = false: Algorithm 1 in FP64 on (z, x).
+// T = float, CORR = true: the same iteration on the corrections (dz, dx) with the
+// FP32 copies of the values and FP32 arithmetic, the residuals f = b - z - A x and
+// g = A^T z held fixed in FP64 (see rebk_solve_refined):
+//   w = A_J^T dz + g_J,  dz <- dz - c_J A_J w,  s_J += c_J w
+//   r = A_I dx - f_I + dz_I,  dx <- dx - c_I A_I^T r,  v_I -= c_I r.
+// The duals are updated in the scatter phase, so a stop after the gathers of
+// iteration k leaves (dx, dz, s, v) consistent: dz = -A s and dx = A^T v.
+template <typename T, bool CORR>
 __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_constant__ SparseArgs a) {
     __shared__ double red[kSW];
-    __shared__ double wq[kOwnMax];          // w of the CTA's columns of J_{k+1}
-    __shared__ double rq[kOwnMax];          // r of the CTA's rows of I_k
+    __shared__ T wq[kOwnMax];               // w of the CTA's columns of J_{k+1}
+    __shared__ T rq[kOwnMax];               // r of the CTA's rows of I_k
     __shared__ int64_t bc[kOwnMax + 1];     // entry boundaries of those columns (CSC)
     __shared__ int64_t br[kOwnMax + 1];     // and rows (CSR)
-    __shared__ double part[2 * kOwnMax];    // the joint gather's line sums
+    __shared__ T part[2 * kOwnMax];         // the joint gather's line sums
     __shared__ int s_flag;
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
+    const T *rv = static_cast<const T *>(a.rv), *cv = static_cast<const T *>(a.cv);
+    const T *coef_r = static_cast<const T *>(a.coef_r), *coef_c = static_cast<const T *>(a.coef_c);
+    T *z = static_cast<T *>(a.z), *x = static_cast<T *>(a.x);
+    T *sdual = static_cast<T *>(a.sdual), *vdual = static_cast<T *>(a.vdual);
     const int64_t K = a.iters;
     const bool check = a.x_ref != nullptr && a.check_every > 0;
     const int64_t xs0 = a.n * cta / G, xs1 = a.n * (cta + 1) / G;  // this CTA's share of the test
@@ -178,23 +196,29 @@ __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_consta
     };
     // column gather of iteration kk (A): w for the CTA's contiguous share of J_kk
     int nqc = 0;
-    double cJ = 0.0;
+    int64_t cc0 = 0;
+    T cJ = T(0);
     auto gather_cols = [&](int64_t kk) {
         const int j = __ldg(a.idx + 2 * (kk - 1));
         const int64_t ja = (int64_t)j * a.tau_c, jb = ja + a.tau_c < a.n ? ja + a.tau_c : a.n;
         const int64_t c0 = ja + (jb - ja) * cta / G, c1 = ja + (jb - ja) * (cta + 1) / G;
-        cJ = a.coef_c[j];
+        cJ = coef_c[j];
+        cc0 = c0;
         nqc = (int)(c1 - c0);
         __syncthreads();  // bc[] and wq[] are free
         for (int q = tid; q <= nqc; q += kST) bc[q] = a.cp[c0 + q];
         __syncthreads();
-        if (nqc > 0) gather_lines(bc, nqc, a.ri, a.cv, a.z, wq);
+        if (nqc > 0) gather_lines(bc, nqc, a.ri, cv, z, wq);
+        if (CORR)
+            for (int q = tid; q < nqc; q += kST) wq[q] += (T)a.g[c0 + q];
         if (tid < nqc && !isfinite(wq[tid])) atomicExch(a.bad, 1);
     };
-    // z scatter (B) with the w of the last column gather
+    // z scatter (B) with the w of the last column gather, and the dual s
     auto scatter_z = [&]() {
         for (int64_t e = bc[0] + tid; nqc > 0 && e < bc[nqc]; e += kST)
-            atomicAdd(a.z + a.ri[e], -cJ * a.cv[e] * wq[line_of(bc, nqc, e)]);
+            atomicAdd(z + a.ri[e], -cJ * cv[e] * wq[line_of(bc, nqc, e)]);
+        if (CORR)
+            for (int q = tid; q < nqc; q += kST) sdual[cc0 + q] += cJ * wq[q];
     };
     int64_t done = K;
     int stop = 0;
@@ -216,7 +240,7 @@ __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_consta
         const int64_t ia = (int64_t)i * a.tau_r, ib = ia + a.tau_r < a.m ? ia + a.tau_r : a.m;
         const int64_t l0 = ia + (ib - ia) * cta / G, l1 = ia + (ib - ia) * (cta + 1) / G;
         const int nqr = (int)(l1 - l0);
-        const double cI = a.coef_r[i];
+        const T cI = coef_r[i];
         // the column share of J_{k+1} (none after the last iteration)
         nqc = 0;
         int64_t c0 = 0;
@@ -225,26 +249,28 @@ __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_consta
             const int64_t ja = (int64_t)j * a.tau_c, jb = ja + a.tau_c < a.n ? ja + a.tau_c : a.n;
             c0 = ja + (jb - ja) * cta / G;
             nqc = (int)(ja + (jb - ja) * (cta + 1) / G - c0);
-            cJ = a.coef_c[j];
+            cJ = coef_c[j];
         }
+        cc0 = c0;
         for (int q = tid; q <= nqr; q += kST) br[q] = a.rp[l0 + q];
         for (int q = tid; q <= nqc; q += kST) bc[q] = a.cp[c0 + q];
         __syncthreads();
-        gather_rows_cols(br, nqr, a.ci, a.rv, a.x, bc, nqc, a.ri, a.cv, a.z, part);
+        gather_rows_cols(br, nqr, a.ci, rv, x, bc, nqc, a.ri, cv, z, part);
         for (int q = tid; q < nqr; q += kST) {
-            const double rl = part[q] - a.b[l0 + q] + a.z[l0 + q];
+            const T rl = part[q] - (T)a.b[l0 + q] + z[l0 + q];
             rq[q] = rl;
             if (!isfinite(rl)) atomicExch(a.bad, 1);
         }
         for (int q = tid; q < nqc; q += kST) {
-            wq[q] = part[nqr + q];
+            wq[q] = CORR ? part[nqr + q] + (T)a.g[c0 + q] : part[nqr + q];
             if (!isfinite(wq[q])) atomicExch(a.bad, 1);
         }
         const bool due = check && k >= 2 && (a.check_offset + k - 1) % a.check_every == 0;
         if (due) {
             double e2 = 0.0;
             for (int64_t c = xs0 + tid; c < xs1; c += kST) {
-                const double d = a.x[c] - a.x_ref[c];
+                const double xc = CORR ? a.x_base[c] + (double)x[c] : (double)x[c];
+                const double d = xc - a.x_ref[c];
                 e2 = fma(d, d, e2);
             }
             e2 = block_sum(e2, red);
@@ -264,7 +290,9 @@ __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_consta
         }
         // ---- scatters: x^k = x^{k-1} - c_I A_I^T r^k, z^{k+1} = z^k - c_J' A_J' w^{k+1} ----
         for (int64_t e = br[0] + tid; nqr > 0 && e < br[nqr]; e += kST)
-            atomicAdd(a.x + a.ci[e], -cI * a.rv[e] * rq[line_of(br, nqr, e)]);
+            atomicAdd(x + a.ci[e], -cI * rv[e] * rq[line_of(br, nqr, e)]);
+        if (CORR)
+            for (int q = tid; q < nqr; q += kST) vdual[l0 + q] -= cI * rq[q];
         if (k < K) scatter_z();
         if (!barrier()) return;
     }
@@ -272,6 +300,31 @@ __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_consta
         *a.iters_done = done;
         if (stop == 5) atomicExch(a.status, 5);
     }
+}
+
+// y[l] = sum over line l's entries of val[e] * p[idx[e]] (one warp per line; FP64
+// products of the FP64 values with an FP64 or FP32 vector): A p over CSR, A^T q over CSC.
+template <typename TP>
+__global__ void sparse_lines_kernel(const int64_t *__restrict__ ptr, const int32_t *__restrict__ idx,
+                                    const double *__restrict__ val, const TP *__restrict__ p, int64_t lines,
+                                    double *__restrict__ y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t wpb = blockDim.x >> 5;
+    for (int64_t l = blockIdx.x * wpb + (threadIdx.x >> 5); l < lines; l += (int64_t)gridDim.x * wpb) {
+        double s = 0.0;
+        for (int64_t e = ptr[l] + lane; e < ptr[l + 1]; e += 32) s = fma(val[e], (double)p[idx[e]], s);
+        s = warp_sum(s);
+        if (lane == 0) y[l] = s;
+    }
+}
+
+template <typename TP>
+cudaError_t sparse_lines(const int64_t *ptr, const int32_t *idx, const double *val, const TP *p, int64_t lines,
+                         double *y, cudaStream_t st) {
+    int64_t blocks = (lines + 7) / 8;
+    if (blocks > 4096) blocks = 4096;
+    sparse_lines_kernel<TP><<<(unsigned)blocks, 256, 0, st>>>(ptr, idx, val, p, lines, y);
+    return cudaGetLastError();
 }
 
 // Host-side power iterations (FP64) for the spectral norms of the blocks.
@@ -331,6 +384,9 @@ struct rebk_sparse_s {
     int32_t *ci = nullptr, *ri = nullptr, *idx = nullptr;
     double *rv = nullptr, *cv = nullptr, *cdf_r = nullptr, *cdf_c = nullptr, *coef_r = nullptr, *coef_c = nullptr;
     double *zbuf = nullptr, *acc = nullptr, *small = nullptr;
+    float *rv32 = nullptr, *cv32 = nullptr, *coef_r32 = nullptr, *coef_c32 = nullptr;  // mixed precision
+    double *f = nullptr, *g = nullptr, *ym = nullptr, *yn = nullptr;                 // FP64 residuals
+    float *dz = nullptr, *dx = nullptr, *sd = nullptr, *vd = nullptr;                // corrections, duals
     int *bad = nullptr, *status = nullptr;
     unsigned int *bar = nullptr;
     int64_t *iters_done = nullptr;
@@ -354,7 +410,8 @@ rebk_status sfail(rebk_status s, const std::string &msg) {
 void free_sparse(rebk_sparse h) {
     if (!h) return;
     void *p[] = {h->rp, h->cp, h->ci, h->ri, h->idx, h->rv, h->cv, h->cdf_r, h->cdf_c, h->coef_r, h->coef_c,
-                 h->zbuf, h->acc, h->small, h->bad, h->status, h->bar, h->iters_done};
+                 h->zbuf, h->acc, h->small, h->bad, h->status, h->bar, h->iters_done, h->rv32, h->cv32,
+                 h->coef_r32, h->coef_c32, h->f, h->g, h->ym, h->yn, h->dz, h->dx, h->sd, h->vd};
     for (void *q : p)
         if (q) cudaFree(q);
     cudaEvent_t e[] = {h->ev0, h->ev1, h->k0, h->k1};
@@ -384,6 +441,87 @@ void group_tables(const std::vector<int64_t> &ptr, const std::vector<double> &va
         cdf[b] = run;
         if (norms[b] > 0.0) *fallback = (int)b;
     }
+}
+
+}  // namespace
+
+namespace {
+
+// Fields of the kernel arguments that every launch of a handle shares.
+SparseArgs sparse_args(rebk_sparse h, bool corr) {
+    SparseArgs a;
+    memset(&a, 0, sizeof(a));
+    a.m = h->m;
+    a.n = h->n;
+    a.tau_r = h->tau_r;
+    a.tau_c = h->tau_c;
+    a.rp = h->rp;
+    a.ci = h->ci;
+    a.cp = h->cp;
+    a.ri = h->ri;
+    a.rv = corr ? (const void *)h->rv32 : (const void *)h->rv;
+    a.cv = corr ? (const void *)h->cv32 : (const void *)h->cv;
+    a.coef_r = corr ? (const void *)h->coef_r32 : (const void *)h->coef_r;
+    a.coef_c = corr ? (const void *)h->coef_c32 : (const void *)h->coef_c;
+    a.check_every = h->check_every;
+    a.acc = h->acc;
+    a.bad = h->bad;
+    a.bar = h->bar;
+    a.status = h->status;
+    a.iters_done = h->iters_done;
+    a.timeout_ns = kBarrierTimeoutNs;
+    return a;
+}
+
+// Samples the blocks of iterations kfirst+1 .. kfirst+K into idx and runs them in one
+// persistent launch; returns the device status (0, 5 diverged, 6 barrier timeout),
+// the iterations done and the launch's CUDA-event time.
+rebk_status sparse_launch(rebk_sparse h, bool corr, SparseArgs &a, uint64_t seed, uint64_t stream_id,
+                          int64_t kfirst, int64_t K, int32_t *idx, int *dev_status, int64_t *done, float *ms) {
+    const cudaStream_t st = h->stream;
+    SCK(sample_blocks(seed, stream_id, kfirst, K, h->cdf_r, h->s, h->cdf_c, h->t, h->fb_r, h->fb_c, idx, st));
+    SCK(cudaMemsetAsync(h->acc, 0, sizeof(double) * 4, st));
+    SCK(cudaMemsetAsync(h->bad, 0, sizeof(int), st));
+    SCK(cudaMemsetAsync(h->status, 0, sizeof(int), st));
+    SCK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned int), st));
+    a.idx = idx;
+    a.iters = K;
+    void *params[] = {&a};
+    void *fn = corr ? reinterpret_cast<void *>(&rebk_sparse_kernel<float, true>)
+                    : reinterpret_cast<void *>(&rebk_sparse_kernel<double, false>);
+    SCK(cudaEventRecord(h->k0, st));
+    SCK(cudaLaunchCooperativeKernel(fn, dim3(h->G), dim3(kST), params, 0, st));
+    SCK(cudaEventRecord(h->k1, st));
+    *dev_status = 0;
+    *done = 0;
+    SCK(cudaMemcpyAsync(dev_status, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
+    SCK(cudaMemcpyAsync(done, h->iters_done, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    SCK(cudaStreamSynchronize(st));
+    *ms = 0.f;
+    cudaEventElapsedTime(ms, h->k0, h->k1);
+    return REBK_OK;
+}
+
+rebk_status fetch(rebk_sparse h, double *v, int count) {
+    SCK(cudaMemcpyAsync(v, h->small, sizeof(double) * count, cudaMemcpyDeviceToHost, h->stream));
+    SCK(cudaStreamSynchronize(h->stream));
+    return REBK_OK;
+}
+
+void sparse_stats(rebk_stats *stats, int64_t iters, int outer, rebk_status result, double rel, double rf,
+                  double rg, double dms, double kms, int64_t launches, int64_t grid_launches) {
+    if (!stats) return;
+    memset(stats, 0, sizeof(*stats));
+    stats->iterations = iters;
+    stats->outer = outer;
+    stats->status = result;
+    stats->rel_err = rel;
+    stats->resid_f = rf;
+    stats->resid_g = rg;
+    stats->device_ms = dms;
+    stats->kernel_ms = kms;
+    stats->launches = launches;
+    stats->grid_launches = grid_launches;
 }
 
 }  // namespace
@@ -505,6 +643,22 @@ rebk_status rebk_sparse_create(rebk_sparse *out, int64_t m, int64_t n, const int
     SCKH(up((void **)&h->cdf_c, cdf_c.data(), sizeof(double) * h->t));
     SCKH(up((void **)&h->coef_r, kr.data(), sizeof(double) * h->s));
     SCKH(up((void **)&h->coef_c, kc.data(), sizeof(double) * h->t));
+    {  // FP32 copies for the mixed-precision solve (round to nearest)
+        std::vector<float> r32(rv.begin(), rv.end()), c32(cv.begin(), cv.end());
+        std::vector<float> kr32(kr.begin(), kr.end()), kc32(kc.begin(), kc.end());
+        SCKH(up((void **)&h->rv32, r32.data(), sizeof(float) * nnz));
+        SCKH(up((void **)&h->cv32, c32.data(), sizeof(float) * nnz));
+        SCKH(up((void **)&h->coef_r32, kr32.data(), sizeof(float) * h->s));
+        SCKH(up((void **)&h->coef_c32, kc32.data(), sizeof(float) * h->t));
+    }
+    SCKH(cudaMalloc(&h->f, sizeof(double) * m));
+    SCKH(cudaMalloc(&h->ym, sizeof(double) * m));
+    SCKH(cudaMalloc(&h->g, sizeof(double) * n));
+    SCKH(cudaMalloc(&h->yn, sizeof(double) * n));
+    SCKH(cudaMalloc(&h->dz, sizeof(float) * m));
+    SCKH(cudaMalloc(&h->vd, sizeof(float) * m));
+    SCKH(cudaMalloc(&h->dx, sizeof(float) * n));
+    SCKH(cudaMalloc(&h->sd, sizeof(float) * n));
     SCKH(cudaMalloc(&h->idx, sizeof(int32_t) * 2 * kSparseChunk));
     SCKH(cudaMalloc(&h->zbuf, sizeof(double) * m));
     SCKH(cudaMalloc(&h->acc, sizeof(double) * 4));
@@ -518,10 +672,12 @@ rebk_status rebk_sparse_create(rebk_sparse *out, int64_t m, int64_t n, const int
     SCKH(cudaEventCreate(&h->k0));
     SCKH(cudaEventCreate(&h->k1));
     // grid: one CTA per SM (cooperative), enough CTAs for every block's lines
-    int dev = 0, sms = 1, per = 0;
+    int dev = 0, sms = 1, per = 0, per32 = 0;
     SCKH(cudaGetDevice(&dev));
     SCKH(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    SCKH(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, rebk_sparse_kernel, kST, 0));
+    SCKH(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, rebk_sparse_kernel<double, false>, kST, 0));
+    SCKH(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per32, rebk_sparse_kernel<float, true>, kST, 0));
+    per = std::min(per, per32);
     const int gmax = sms * std::max(1, std::min(per, 1));
     int G = o.num_ctas > 0 ? std::min(o.num_ctas, gmax) : gmax;
     const int need = (int)((std::max(h->tau_r, h->tau_c) + kOwnMax - 1) / kOwnMax);
@@ -566,8 +722,8 @@ rebk_status rebk_sparse_solve(rebk_sparse h, const double *b, double *x, double 
     if (e.x_ref) {
         SCK(sum_sq(e.x_ref, h->n, h->small, st));
         double v[2];
-        SCK(cudaMemcpyAsync(v, h->small, sizeof(v), cudaMemcpyDeviceToHost, st));
-        SCK(cudaStreamSynchronize(st));
+        rebk_status fs = fetch(h, v, 2);
+        if (fs != REBK_OK) return fs;
         refn = std::sqrt(v[1]);
     }
     const double thr = tol * refn;
@@ -579,55 +735,20 @@ rebk_status rebk_sparse_solve(rebk_sparse h, const double *b, double *x, double 
     while (total < max_iter && h->fro2 > 0.0) {
         const int64_t K = std::min({max_iter - total, kSparseChunk, kSparseLaunchMax});
         int32_t *idx = e.idx_out ? e.idx_out + 2 * total : h->idx;
-        SCK(sample_blocks(seed, e.stream_id, e.k0 + total, K, h->cdf_r, h->s, h->cdf_c, h->t, h->fb_r, h->fb_c, idx,
-                          st));
-        SCK(cudaMemsetAsync(h->acc, 0, sizeof(double) * 4, st));
-        SCK(cudaMemsetAsync(h->bad, 0, sizeof(int), st));
-        SCK(cudaMemsetAsync(h->status, 0, sizeof(int), st));
-        SCK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned int), st));
-        SparseArgs a;
-        memset(&a, 0, sizeof(a));
-        a.m = h->m;
-        a.n = h->n;
-        a.tau_r = h->tau_r;
-        a.tau_c = h->tau_c;
-        a.rp = h->rp;
-        a.ci = h->ci;
-        a.rv = h->rv;
-        a.cp = h->cp;
-        a.ri = h->ri;
-        a.cv = h->cv;
-        a.coef_r = h->coef_r;
-        a.coef_c = h->coef_c;
-        a.idx = idx;
-        a.iters = K;
+        SparseArgs a = sparse_args(h, false);
         a.z = z;
         a.x = x;
         a.b = b;
         a.x_ref = e.x_ref;
         a.tol2_abs = thr * thr;
-        a.check_every = h->check_every;
         a.check_offset = total;
-        a.acc = h->acc;
-        a.bad = h->bad;
-        a.bar = h->bar;
-        a.status = h->status;
-        a.iters_done = h->iters_done;
-        a.timeout_ns = kBarrierTimeoutNs;
-        void *params[] = {&a};
-        SCK(cudaEventRecord(h->k0, st));
-        SCK(cudaLaunchCooperativeKernel(reinterpret_cast<void *>(&rebk_sparse_kernel), dim3(h->G), dim3(kST),
-                                        params, 0, st));
-        SCK(cudaEventRecord(h->k1, st));
-        launches += 2;  // sample_kernel, rebk_sparse_kernel
-        ++grid_launches;
         int ds = 0;
         int64_t done = 0;
-        SCK(cudaMemcpyAsync(&ds, h->status, sizeof(int), cudaMemcpyDeviceToHost, st));
-        SCK(cudaMemcpyAsync(&done, h->iters_done, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
-        SCK(cudaStreamSynchronize(st));
         float ms = 0.f;
-        cudaEventElapsedTime(&ms, h->k0, h->k1);
+        rebk_status ls = sparse_launch(h, false, a, seed, e.stream_id, e.k0 + total, K, idx, &ds, &done, &ms);
+        if (ls != REBK_OK) return ls;
+        launches += 2;  // sample_kernel, rebk_sparse_kernel
+        ++grid_launches;
         kernel_ms += ms;
         if (ds != 6) total += done;
         if (ds == 6) {
@@ -650,8 +771,8 @@ rebk_status rebk_sparse_solve(rebk_sparse h, const double *b, double *x, double 
     if (e.x_ref && result != REBK_BARRIER_TIMEOUT) {
         SCK(err_norms(nullptr, x, e.x_ref, h->n, h->small, st));
         double v[2];
-        SCK(cudaMemcpyAsync(v, h->small, sizeof(v), cudaMemcpyDeviceToHost, st));
-        SCK(cudaStreamSynchronize(st));
+        rebk_status fs = fetch(h, v, 2);
+        if (fs != REBK_OK) return fs;
         rel = refn > 0 ? std::sqrt(v[0]) / refn : std::sqrt(v[0]);
         if (!converged && result == REBK_MAX_ITER && rel <= tol) result = REBK_OK;
     } else if (!e.x_ref && result == REBK_MAX_ITER) {
@@ -662,18 +783,231 @@ rebk_status rebk_sparse_solve(rebk_sparse h, const double *b, double *x, double 
     SCK(cudaEventSynchronize(h->ev1));
     float dms = 0.f;
     cudaEventElapsedTime(&dms, h->ev0, h->ev1);
-    if (stats) {
-        memset(stats, 0, sizeof(*stats));
-        stats->iterations = total;
-        stats->status = result;
-        stats->rel_err = rel;
-        stats->resid_f = -1;
-        stats->resid_g = -1;
-        stats->device_ms = dms;
-        stats->kernel_ms = kernel_ms;
-        stats->launches = launches + extra;
-        stats->grid_launches = grid_launches;
+    sparse_stats(stats, total, 0, result, rel, -1, -1, dms, kernel_ms, launches + extra, grid_launches);
+    return result;
+}
+
+rebk_status rebk_sparse_solve_refined(rebk_sparse h, const double *b, double *x, double tol, int64_t max_iter,
+                                      uint64_t seed, const rebk_refine_opts *ropt, const rebk_solve_ext *ext,
+                                      rebk_stats *stats) {
+    set_last_error("");
+    if (!h) return sfail(REBK_EINVAL, "NULL handle");
+    if (!b || !x) return sfail(REBK_EINVAL, "b and x must be device pointers");
+    if (max_iter < 0 || !std::isfinite(tol)) return sfail(REBK_EINVAL, "bad tol / max_iter");
+    rebk_refine_opts ro;
+    memset(&ro, 0, sizeof(ro));
+    ro.storage = REBK_FP32;
+    if (ropt) ro = *ropt;
+    if (ro.storage == REBK_BF16) return sfail(REBK_EUNSUPPORTED, "sparse mixed precision stores FP32 values only");
+    if (ro.storage != REBK_FP32) return sfail(REBK_EINVAL, "refinement storage must be REBK_FP32");
+    if (ro.max_outer < 0 || ro.inner_iters < 0 || ro.inner_reduction < 0)
+        return sfail(REBK_EINVAL, "negative refinement option");
+    const int max_outer = ro.max_outer > 0 ? ro.max_outer : 30;
+    const double red = ro.inner_reduction > 0 ? ro.inner_reduction : 1e-4;
+    rebk_solve_ext e;
+    memset(&e, 0, sizeof(e));
+    if (ext) e = *ext;
+    if (e.k0 < 0) return sfail(REBK_EINVAL, "k0 < 0");
+    const cudaStream_t st = h->stream;
+    double *z = e.z_out ? e.z_out : h->zbuf;
+    int64_t launches = 0, grid_launches = 0;
+    double kernel_ms = 0.0;
+    SCK(cudaEventRecord(h->ev0, st));
+    if (e.z0) SCK(cudaMemcpyAsync(z, e.z0, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, st));
+    else SCK(cudaMemcpyAsync(z, b, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, st));
+    if (e.x0) SCK(cudaMemcpyAsync(x, e.x0, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, st));
+    else SCK(cudaMemsetAsync(x, 0, sizeof(double) * h->n, st));
+    const bool use_ref = e.x_ref != nullptr;
+    double refn = 0.0;
+    if (use_ref) {
+        SCK(sum_sq(e.x_ref, h->n, h->small, st));
+        ++launches;
+        double v[2];
+        rebk_status fs = fetch(h, v, 2);
+        if (fs != REBK_OK) return fs;
+        refn = std::sqrt(v[1]);
     }
+    int64_t inner_max = ro.inner_iters;
+    if (inner_max <= 0) {
+        if (use_ref) {
+            inner_max = 1000000;
+        } else {
+            const double per_iter = (double)h->tau_r * h->n + (double)h->tau_c * h->m;
+            inner_max = std::max<int64_t>(200, (int64_t)(40.0 * (double)h->m * h->n / per_iter));
+        }
+    }
+    int64_t total = 0;
+    int outer = 0;
+    rebk_status result = REBK_MAX_ITER;
+    double rel = -1, rf = -1, rg = -1, prev_res = -1;
+    bool x_zero = e.x0 == nullptr;  // x^0 = 0: A x vanishes in the first residual
+    for (outer = 0; h->fro2 > 0.0 && max_iter > 0 && outer < max_outer; ++outer) {
+        double e0 = 0.0;
+        if (use_ref) {  // the error test needs x only: before the residuals
+            SCK(err_norms(nullptr, x, e.x_ref, h->n, h->small, st));
+            ++launches;
+            double v[2];
+            rebk_status fs = fetch(h, v, 2);
+            if (fs != REBK_OK) return fs;
+            e0 = std::sqrt(v[0]);
+            rel = refn > 0 ? e0 / refn : e0;
+            if (rel <= tol) {
+                result = REBK_OK;
+                break;
+            }
+        }
+        // f = b - z - A x (CSR), g = A^T z (CSC), FP64 values
+        if (x_zero) SCK(cudaMemsetAsync(h->ym, 0, sizeof(double) * h->m, st));
+        else SCK(sparse_lines<double>(h->rp, h->ci, h->rv, x, h->m, h->ym, st));
+        SCK(sparse_lines<double>(h->cp, h->ri, h->cv, z, h->n, h->g, st));
+        SCK(form_f(b, z, h->ym, h->f, h->m, st));
+        launches += x_zero ? 2 : 3;
+        x_zero = false;
+        if (!use_ref) {
+            SCK(sum_sq(h->f, h->m, h->small, st));
+            SCK(sum_sq(h->g, h->n, h->small + 2, st));
+            launches += 2;
+            double v[4];
+            rebk_status fs = fetch(h, v, 4);
+            if (fs != REBK_OK) return fs;
+            SCK(sum_sq(b, h->m, h->small, st));
+            ++launches;
+            double vb[2];
+            fs = fetch(h, vb, 2);
+            if (fs != REBK_OK) return fs;
+            const double nb = std::sqrt(vb[1]);
+            rf = nb > 0 ? std::sqrt(v[1]) / nb : 0.0;
+            rg = nb > 0 ? std::sqrt(v[3]) / (std::sqrt(h->fro2) * nb) : 0.0;
+            const double res = std::max(rf, rg);
+            if (res <= tol) {
+                result = REBK_OK;
+                break;
+            }
+            if (prev_res > 0 && res > 0.1 * prev_res) inner_max = std::min<int64_t>(inner_max * 2, 1 << 24);
+            prev_res = res;
+        }
+        if (total >= max_iter) break;
+        // inner sweeps on corrections from zero
+        SCK(fill_zero_f32(h->dz, h->m, st));
+        SCK(fill_zero_f32(h->vd, h->m, st));
+        SCK(fill_zero_f32(h->dx, h->n, st));
+        SCK(fill_zero_f32(h->sd, h->n, st));
+        launches += 4;
+        const int64_t iters = std::min(inner_max, max_iter - total);
+        int64_t ran = 0, grow = 4096;  // chunks of 4096, 4096, 8192, ... iterations with a reference
+        int chunks = 0;
+        // The pass ends at its error test, or once the error of x + dx stops falling
+        // (the floor the FP32 values set), as in the dense mixed-precision solve.
+        double e_prev = e0, rate_prev = -1.0;
+        while (ran < iters) {
+            int64_t chunk = std::min({iters - ran, kSparseChunk, kSparseLaunchMax});
+            if (use_ref) {
+                chunk = std::min(chunk, grow);
+                if (++chunks >= 2) grow = std::min<int64_t>(grow * 2, kSparseChunk);
+            }
+            SparseArgs a = sparse_args(h, true);
+            a.z = h->dz;
+            a.x = h->dx;
+            a.b = h->f;
+            a.g = h->g;
+            a.sdual = h->sd;
+            a.vdual = h->vd;
+            a.check_offset = ran;
+            if (use_ref) {
+                const double thr = std::max(tol * refn, red * e0);
+                a.x_ref = e.x_ref;
+                a.x_base = x;
+                a.tol2_abs = thr * thr;
+            }
+            int32_t *idx = e.idx_out ? e.idx_out + 2 * (total + ran) : h->idx;
+            int ds = 0;
+            int64_t done = 0;
+            float ms = 0.f;
+            rebk_status ls = sparse_launch(h, true, a, seed, e.stream_id, e.k0 + total + ran, chunk, idx, &ds, &done,
+                                           &ms);
+            if (ls != REBK_OK) return ls;
+            launches += 2;
+            ++grid_launches;
+            kernel_ms += ms;
+            if (ds == 6) {
+                sparse_stats(stats, total + ran, outer + 1, REBK_BARRIER_TIMEOUT, -1, -1, -1, 0, kernel_ms, launches,
+                             grid_launches);
+                return sfail(REBK_BARRIER_TIMEOUT, "device-wide barrier timed out");
+            }
+            ran += done;
+            if (ds == 5) {
+                sparse_stats(stats, total + ran, outer + 1, REBK_DIVERGED, -1, -1, -1, 0, kernel_ms, launches,
+                             grid_launches);
+                return sfail(REBK_DIVERGED, "inner iteration diverged (Inf/NaN)");
+            }
+            if (done < chunk) break;  // error test met
+            if (use_ref && ran < iters) {
+                SCK(err_norms_f32(x, h->dx, e.x_ref, h->n, h->small, st));
+                ++launches;
+                double v[2];
+                rebk_status fs = fetch(h, v, 2);
+                if (fs != REBK_OK) return fs;
+                const double e_now = std::sqrt(v[0]);
+                if (!(e_now < e_prev)) break;
+                const double rate = std::log(e_prev / e_now) / (double)done;
+                if (rate_prev > 0.0 && rate < 0.1 * rate_prev) break;
+                rate_prev = rate;
+                e_prev = e_now;
+            }
+        }
+        total += ran;
+        // z <- z - A s (CSR), x <- x + A^T v (CSC), FP64 values
+        SCK(sparse_lines<float>(h->rp, h->ci, h->rv, h->sd, h->m, h->ym, st));
+        SCK(sparse_lines<float>(h->cp, h->ri, h->cv, h->vd, h->n, h->yn, st));
+        SCK(apply_update(x, h->yn, h->n, z, h->ym, h->m, st));
+        launches += 3;
+    }
+    if (h->fro2 == 0.0 || max_iter == 0) {
+        result = h->fro2 == 0.0 || !use_ref ? REBK_OK : REBK_MAX_ITER;
+    }
+    if (result != REBK_OK && h->fro2 > 0.0) {  // final test after the last pass
+        if (use_ref) {
+            SCK(err_norms(nullptr, x, e.x_ref, h->n, h->small, st));
+            ++launches;
+            double v[2];
+            rebk_status fs = fetch(h, v, 2);
+            if (fs != REBK_OK) return fs;
+            rel = refn > 0 ? std::sqrt(v[0]) / refn : std::sqrt(v[0]);
+            if (rel <= tol) result = REBK_OK;
+        } else if (max_iter > 0) {
+            SCK(sparse_lines<double>(h->rp, h->ci, h->rv, x, h->m, h->ym, st));
+            SCK(sparse_lines<double>(h->cp, h->ri, h->cv, z, h->n, h->g, st));
+            SCK(form_f(b, z, h->ym, h->f, h->m, st));
+            SCK(sum_sq(h->f, h->m, h->small, st));
+            SCK(sum_sq(h->g, h->n, h->small + 2, st));
+            launches += 5;
+            double v[4];
+            rebk_status fs = fetch(h, v, 4);
+            if (fs != REBK_OK) return fs;
+            SCK(sum_sq(b, h->m, h->small, st));
+            ++launches;
+            double vb[2];
+            fs = fetch(h, vb, 2);
+            if (fs != REBK_OK) return fs;
+            const double nb = std::sqrt(vb[1]);
+            rf = nb > 0 ? std::sqrt(v[1]) / nb : 0.0;
+            rg = nb > 0 ? std::sqrt(v[3]) / (std::sqrt(h->fro2) * nb) : 0.0;
+            if (std::max(rf, rg) <= tol) result = REBK_OK;
+        }
+    }
+    if (use_ref && rel < 0 && result != REBK_BARRIER_TIMEOUT) {
+        SCK(err_norms(nullptr, x, e.x_ref, h->n, h->small, st));
+        ++launches;
+        double v[2];
+        rebk_status fs = fetch(h, v, 2);
+        if (fs != REBK_OK) return fs;
+        rel = refn > 0 ? std::sqrt(v[0]) / refn : std::sqrt(v[0]);
+    }
+    SCK(cudaEventRecord(h->ev1, st));
+    SCK(cudaEventSynchronize(h->ev1));
+    float dms = 0.f;
+    cudaEventElapsedTime(&dms, h->ev0, h->ev1);
+    sparse_stats(stats, total, outer, result, rel, rf, rg, dms, kernel_ms, launches, grid_launches);
     return result;
 }
 

@@ -130,6 +130,9 @@ _SIGNATURES = {
     "rebk_sparse_destroy": ([_P], None),
     "rebk_sparse_solve": ([_P, _P, _P, ctypes.c_double, ctypes.c_int64, ctypes.c_uint64,
                            ctypes.POINTER(RebkSolveExt), ctypes.POINTER(RebkStats)], ctypes.c_int),
+    "rebk_sparse_solve_refined": ([_P, _P, _P, ctypes.c_double, ctypes.c_int64, ctypes.c_uint64,
+                                   ctypes.POINTER(RebkRefineOpts), ctypes.POINTER(RebkSolveExt),
+                                   ctypes.POINTER(RebkStats)], ctypes.c_int),
     "rebk_sparse_info": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "rebk_last_error": ([], ctypes.c_char_p),

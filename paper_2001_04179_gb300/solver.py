@@ -280,6 +280,34 @@ class SparseSolver:
             out["idx"] = idx[: 2 * stats.iterations].view(-1, 2)
         return out
 
+    def solve_refined(self, b, tol: float = 1e-8, max_iter: int = 10**7, seed: int = 0, x_ref=None, x0=None,
+                      z0=None, k0: int = 0, stream_id: int = 0, max_outer: int = 0, inner_iters: int = 0,
+                      inner_reduction: float = 0.0, record: bool = False, return_z: bool = False, x=None,
+                      allow=(_r.REBK_OK, _r.REBK_MAX_ITER)):
+        """Mixed precision (FP32 values and inner sweeps, FP64 refinement).  Returns dict(x, stats, ...)."""
+        torch = _torch()
+        _require_cuda_f64(b, self.m, "b")
+        for t, nn, name in [(x_ref, self.n, "x_ref"), (x0, self.n, "x0"), (z0, self.m, "z0")]:
+            if t is not None:
+                _require_cuda_f64(t, nn, name)
+        if x is None:
+            x = torch.empty(self.n, dtype=torch.float64, device=b.device)
+        z = torch.empty(self.m, dtype=torch.float64, device=b.device) if return_z else None
+        idx = torch.zeros(max(2 * min(max_iter, 10**7), 2), dtype=torch.int32, device=b.device) if record else None
+        ext = _r.RebkSolveExt(_dptr(x_ref), _dptr(x0), _dptr(z0), _dptr(z), _dptr(idx), int(k0), int(stream_id))
+        ro = _r.RebkRefineOpts(_r.REBK_FP32, int(max_outer), int(inner_iters), float(inner_reduction))
+        stats = _r.RebkStats()
+        st = _r.load().rebk_sparse_solve_refined(self._h, ctypes.c_void_p(b.data_ptr()),
+                                                 ctypes.c_void_p(x.data_ptr()), float(tol), int(max_iter),
+                                                 int(seed), ctypes.byref(ro), ctypes.byref(ext), ctypes.byref(stats))
+        _r.check(st, allow)
+        out = {"x": x, "stats": stats.as_dict(), "status": st}
+        if return_z:
+            out["z"] = z
+        if record:
+            out["idx"] = idx[: 2 * stats.iterations].view(-1, 2)
+        return out
+
 
 class BatchSolver:
     """Many independent systems A_i x = b_i, each with up to eight right-hand

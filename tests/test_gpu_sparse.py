@@ -117,3 +117,74 @@ def test_empty_rows_and_columns():
     full = sol.solve(_t(b), tol=1e-10, max_iter=3_000_000, seed=5, x_ref=_t(x_ls))
     assert full["status"] == R.REBK_OK
     assert _rel(full["x"].cpu().numpy(), x_ls) <= 1e-10
+
+
+PASS_CASES = [
+    # m, n, nnz per row, tau_r, tau_c, num_ctas
+    (600, 150, 12, 32, 16, 0),
+    (333, 97, 9, 25, 10, 7),       # ragged last blocks, few CTAs
+    (120, 300, 20, 8, 30, 0),      # underdetermined
+]
+
+
+@pytest.mark.parametrize("case", PASS_CASES, ids=lambda c: "x".join(map(str, c)))
+def test_one_mixed_precision_pass_matches_the_oracle_pass(case):
+    """One refinement pass of the sparse mixed-precision solve (FP64 residuals
+    over CSR / CSC, K inner iterations of the correction form with the FP32
+    values, FP64 update) against the oracle's pass on the same rounded values
+    (dense form): identical blocks; iterates within the FP32 arithmetic of the
+    inner sweeps (the dense path's bar)."""
+    m, n, k, tr, tc, G = case
+    p = sparse_problem(m, n, k, seed=m + 2 * n, x_ref=None)
+    A = p.dense()
+    ro, co = contiguous_offsets(m, tr), contiguous_offsets(n, tc)
+    alpha = 1.5 / max(O.beta_max(A, ro, co))
+    sol = SparseSolver(m, n, p.indptr, p.indices, p.data, tr, tc, alpha=alpha, num_ctas=G)
+    K = 200
+    out = sol.solve_refined(_t(p.b), tol=0.0, max_iter=K, seed=21, max_outer=1, inner_iters=K, record=True,
+                            return_z=True)
+    assert out["stats"]["iterations"] == K and out["stats"]["outer"] == 1
+    ref = O.refine(A, p.b, O.round_fp32(A), ro, co, alpha, seed=21, inner_iters=K, outer_max=1)
+    idx_ref = O.rebk_correction(O.round_fp32(A), *O.dual_residuals(A, p.b, p.b, np.zeros(n)), ro, co,
+                                O.block_norms(A, ro, co), alpha, seed=21, iters=K, record=True)["idx"]
+    assert np.array_equal(out["idx"].cpu().numpy(), idx_ref)
+    assert _rel(out["x"].cpu().numpy(), ref["x"]) <= 1e-4
+    assert np.linalg.norm(out["z"].cpu().numpy() - ref["z"]) <= 1e-4 * np.linalg.norm(p.b)
+
+
+@pytest.mark.parametrize("shape", [(800, 200, 12), (150, 400, 30)])
+def test_mixed_precision_reaches_the_pseudoinverse_solution(shape):
+    m, n, k = shape
+    p = sparse_problem(m, n, k, seed=3, x_ref="lstsq")
+    sol = SparseSolver(m, n, p.indptr, p.indices, p.data, 16, 16)
+    xr = _t(p.x_ref)
+    out = sol.solve_refined(_t(p.b), tol=1e-10, seed=2, x_ref=xr)
+    assert out["status"] == R.REBK_OK
+    assert _rel(out["x"].cpu().numpy(), p.x_ref) <= 1e-10
+    assert out["stats"]["outer"] >= 2  # FP32 alone stops near 1e-6: the refinement did the rest
+    plain = sol.solve(_t(p.b), tol=1e-10, max_iter=2_000_000, seed=2, x_ref=xr)
+    assert out["stats"]["iterations"] <= 2 * plain["stats"]["iterations"] + 8192
+    # without a reference solution: the residual stop rule
+    out2 = sol.solve_refined(_t(p.b), tol=1e-11, seed=4)
+    assert out2["status"] == R.REBK_OK
+    assert _rel(out2["x"].cpu().numpy(), p.x_ref) <= 1e-6
+
+
+def test_mixed_precision_options_and_degenerate_cases():
+    p = sparse_problem(200, 50, 6, seed=5, x_ref=None)
+    sol = SparseSolver(200, 50, p.indptr, p.indices, p.data, 10, 10)
+    b = _t(p.b)
+    lib = R.load()
+    x = torch.empty(50, dtype=torch.float64, device=DEV)
+    for storage, want in [(R.REBK_BF16, R.REBK_EUNSUPPORTED), (R.REBK_FP64, R.REBK_EINVAL)]:
+        ro = R.RebkRefineOpts(storage, 0, 0, 0.0)
+        st = lib.rebk_sparse_solve_refined(sol._h, b.data_ptr(), x.data_ptr(), 1e-8, 100, 0, ro, None, None)
+        assert st == want
+    # max_iter = 0 leaves x = x0 = 0
+    out = sol.solve_refined(b, tol=1e-8, max_iter=0, seed=1)
+    assert out["stats"]["iterations"] == 0 and torch.all(out["x"] == 0)
+    # A = 0: x = 0 = A^+ b
+    rp = np.zeros(11, dtype=np.int64)
+    zero = SparseSolver(10, 5, rp, np.zeros(0, dtype=np.int32), np.zeros(0), 2, 2, alpha=1.0)
+    out = zero.solve_refined(_t(np.ones(10)), tol=1e-8, seed=1)
+    assert out["status"] == R.REBK_OK and torch.all(out["x"] == 0)
