@@ -181,6 +181,38 @@ rebk_status rebk_get_alpha(rebk_handle h, double *alpha);
  */
 rebk_status rebk_set_alpha(rebk_handle h, double alpha);
 
+/* Spectral quantities of Section 2's step-size results (rebk_spectral_estimates). */
+typedef struct {
+    double sigma1_sq;      /* largest Ritz value of A^T A: sigma_1(A)^2, approached from below  */
+    double sigma_r_sq;     /* smallest Ritz value on range(A^T): sigma_r(A)^2 (smallest nonzero
+                              singular value squared), approached from above                  */
+    double fro2;           /* ||A||_F^2                                                         */
+    double alpha_mean_opt; /* 2 ||A||_F^2 / (sigma1_sq + sigma_r_sq): Remark alpha's minimiser of
+                              Theorem ner's rate delta (mean error only: far above 2 / beta_max
+                              for most matrices, where single runs diverge)                     */
+    double delta_opt;      /* (sigma1_sq - sigma_r_sq) / (sigma1_sq + sigma_r_sq), delta there    */
+    double alpha;          /* the handle's alpha, at which the next four are evaluated          */
+    double delta;          /* Theorem ner: max |1 - alpha sigma_i^2 / ||A||_F^2|                  */
+    double eta;            /* Theorem main: 1 - (2 alpha - alpha^2 beta^I_max) sigma_r^2 / ||A||_F^2 */
+    double rho;            /* Lemma estz: 1 - (2 alpha - alpha^2 beta^J_max) sigma_r^2 / ||A||_F^2   */
+    double beta_row;       /* beta^I_max (Section 2.2)                                            */
+    double beta_col;       /* beta^J_max                                                          */
+    int32_t steps;         /* Lanczos steps taken (fewer than asked on an invariant subspace)     */
+} rebk_spectrum;
+
+/*
+ * sigma_1^2 and sigma_r^2 of A (Section 2.1; r = rank A) by Golub-Kahan-Lanczos
+ * bidiagonalisation in FP64 on the device with full reorthogonalisation
+ * (steps in [1, 2048]; the start vector is a fixed function of seed), and the
+ * step-size quantities of Remark alpha, Theorem ner and Theorem main built from
+ * them (host struct *out).  The Ritz values bracket the spectrum from inside:
+ * exact once steps reaches the rank (the iteration stops there), otherwise
+ * sigma1_sq converges fast and sigma_r_sq slowly from above, so eta and rho
+ * are optimistic until then.  Working memory (m + n) (steps + 1) doubles.
+ * Errors: EINVAL (NULL, steps out of range), ENOMEM, ECUDA.  A = 0 gives zeros.
+ */
+rebk_status rebk_spectral_estimates(rebk_handle h, int32_t steps, uint64_t seed, rebk_spectrum *out);
+
 /* Number of row blocks s and column blocks t (host int64). */
 rebk_status rebk_get_blocks(rebk_handle h, int64_t *s, int64_t *t);
 

@@ -564,6 +564,35 @@ rebk_status rebk_set_alpha(rebk_handle h, double alpha) {
     return REBK_OK;
 }
 
+rebk_status rebk_spectral_estimates(rebk_handle h, int32_t steps, uint64_t seed, rebk_spectrum *out) {
+    g_last_error.clear();
+    if (!h || !out) return fail(REBK_EINVAL, "NULL argument");
+    if (steps < 1 || steps > 2048) return fail(REBK_EINVAL, "steps must be in [1, 2048]");
+    memset(out, 0, sizeof(*out));
+    out->fro2 = h->fro2;
+    if (h->fro2 == 0.0) return REBK_OK;  // A = 0: no nonzero singular value
+    double s1 = 0.0, sr = 0.0;
+    int done = 0;
+    cudaError_t e = lanczos_extremes(h->A64, h->lda, h->m, h->n, steps, seed, h->stream, &s1, &sr, &done);
+    if (e != cudaSuccess) return cuda_fail(e, "Lanczos bidiagonalisation");
+    double br = 0.0, bc = 0.0;
+    rebk_status s = rebk_beta_max(h, &br, &bc);
+    if (s != REBK_OK) return s;
+    const double F = h->fro2, a = h->alpha;
+    out->sigma1_sq = s1;
+    out->sigma_r_sq = sr;
+    out->steps = done;
+    out->alpha_mean_opt = 2.0 * F / (s1 + sr);
+    out->delta_opt = (s1 - sr) / (s1 + sr);
+    out->alpha = a;
+    out->delta = std::max(std::fabs(1.0 - a * s1 / F), std::fabs(1.0 - a * sr / F));
+    out->beta_row = br;
+    out->beta_col = bc;
+    out->eta = 1.0 - (2.0 * a - a * a * br) * sr / F;
+    out->rho = 1.0 - (2.0 * a - a * a * bc) * sr / F;
+    return REBK_OK;
+}
+
 rebk_status rebk_get_blocks(rebk_handle h, int64_t *s, int64_t *t) {
     if (!h) return fail(REBK_EINVAL, "handle is NULL");
     if (s) *s = h->s;

@@ -172,6 +172,12 @@ cudaError_t fill_zero_f32(float *p, int64_t n, cudaStream_t st);
 // out = a - b (length n)
 cudaError_t vec_sub(const double *a, const double *b, double *out, int64_t n, cudaStream_t st);
 
+// Extreme Ritz values of A^T A on range(A^T) after up to `steps` Golub-Kahan-Lanczos
+// steps with full reorthogonalisation (rebk_spectral.cu): sigma_1^2 from below and
+// sigma_r^2 from above.  Synchronises st.
+cudaError_t lanczos_extremes(const double *A, int64_t lda, int64_t m, int64_t n, int steps, uint64_t seed,
+                             cudaStream_t st, double *sigma1_sq, double *sigma_r_sq, int *steps_done);
+
 // Sets the message rebk_last_error() returns on this thread (rebk_api.cu).
 void set_last_error(const std::string &msg);
 

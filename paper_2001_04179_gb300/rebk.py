@@ -57,6 +57,16 @@ class RebkTunePoint(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class RebkSpectrum(ctypes.Structure):
+    _fields_ = [("sigma1_sq", ctypes.c_double), ("sigma_r_sq", ctypes.c_double), ("fro2", ctypes.c_double),
+                ("alpha_mean_opt", ctypes.c_double), ("delta_opt", ctypes.c_double), ("alpha", ctypes.c_double),
+                ("delta", ctypes.c_double), ("eta", ctypes.c_double), ("rho", ctypes.c_double),
+                ("beta_row", ctypes.c_double), ("beta_col", ctypes.c_double), ("steps", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class RebkBatchOptions(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("inner_reduction", ctypes.c_double),
@@ -96,6 +106,7 @@ _SIGNATURES = {
     "rebk_beta_max": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "rebk_get_alpha": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "rebk_set_alpha": ([_P, ctypes.c_double], ctypes.c_int),
+    "rebk_spectral_estimates": ([_P, ctypes.c_int32, ctypes.c_uint64, ctypes.POINTER(RebkSpectrum)], ctypes.c_int),
     "rebk_tune_tau": ([_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, _P, _P, _P, ctypes.c_int32,
                        ctypes.c_double, ctypes.c_int32, ctypes.c_double, ctypes.c_int64, ctypes.c_uint64,
                        ctypes.c_int32, ctypes.POINTER(RebkOptions), _P, ctypes.POINTER(ctypes.c_int64)],

@@ -64,6 +64,13 @@ class Solver:
         self.m, self.n = int(m), int(n)
         self.tau_row, self.tau_col = tau_row, tau_col
 
+    @classmethod
+    def rek(cls, A, **kw) -> "Solver":
+        """The randomized extended Kaczmarz special case of Algorithm 1 (single rows
+        and columns, alpha = 1; the remark after Algorithm 1)."""
+        kw.setdefault("storage", ())
+        return cls(A, 1, 1, alpha=1.0, **kw)
+
     # ------------------------------------------------------------------
     def close(self):
         if getattr(self, "_h", None):
@@ -87,6 +94,21 @@ class Solver:
     def alpha(self, value: float):
         """Replace the step size (block coefficients are rebuilt on the device)."""
         _r.check(_r.load().rebk_set_alpha(self._h, float(value)))
+
+    def spectrum(self, steps: int = 200, seed: int = 0) -> dict:
+        """sigma_1^2, sigma_r^2 (device Lanczos) and the step-size quantities of
+        Remark alpha, Theorem ner and Theorem main (rebk_spectral_estimates)."""
+        out = _r.RebkSpectrum()
+        _r.check(_r.load().rebk_spectral_estimates(self._h, int(steps), int(seed), ctypes.byref(out)))
+        return out.as_dict()
+
+    def use_mean_optimal_alpha(self, steps: int = 200, seed: int = 0) -> float:
+        """Set alpha to Remark alpha's 2 ||A||_F^2 / (sigma_1^2 + sigma_r^2), the
+        minimiser of Theorem ner's rate for the mean error.  It usually exceeds
+        2 / beta_max, where Theorem main gives no mean-square convergence."""
+        a = self.spectrum(steps, seed)["alpha_mean_opt"]
+        self.alpha = a
+        return a
 
     def blocks(self):
         s, t = ctypes.c_int64(), ctypes.c_int64()
@@ -143,6 +165,15 @@ class Solver:
         if record:
             out["idx"] = idx[: 2 * stats.iterations].view(-1, 2)
         return out
+
+    def solve_rabk(self, b, **kw):
+        """The RABK special case (the remark after Algorithm 1): z^0 = 0 keeps every
+        z^k = 0, so each step is the weighted block average of eq. (rabk) on A x = b
+        (consistent systems).  Arguments as solve()."""
+        torch = _torch()
+        _require_cuda_f64(b, self.m, "b")
+        kw["z0"] = torch.zeros(self.m, dtype=torch.float64, device=b.device)
+        return self.solve(b, **kw)
 
     def solve_refined(self, b, tol: float = 1e-8, max_iter: int = 10**7, seed: int = 0,
                       storage: str = "fp32", x_ref=None, x0=None, z0=None, k0: int = 0,

@@ -80,6 +80,7 @@ def test_step_size_and_tuner_reject_bad_arguments_on_the_host():
     from paper_2001_04179_gb300 import rebk as R
     lib = R.load()
     assert lib.rebk_set_alpha(None, 1.0) == R.REBK_EINVAL
+    assert lib.rebk_spectral_estimates(None, 10, 0, None) == R.REBK_EINVAL
     assert lib.rebk_sparse_solve_refined(None, None, None, 1e-8, 10, 0, None, None, None) == R.REBK_EINVAL
     A = (ctypes.c_double * 4)(1, 2, 3, 4)
     b = (ctypes.c_double * 2)(1, 1)
