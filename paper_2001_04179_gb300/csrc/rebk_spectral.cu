@@ -157,8 +157,13 @@ cudaError_t lanczos_extremes(const double *A, int64_t lda, int64_t m, int64_t n,
             }
         }
     }
-    const double tiny = 1e-13 * a0;
+    // Breakdown: a new alpha or beta below 1e-10 of the largest so far (a lower bound
+    // of sigma_1) means the Krylov space is invariant to rounding -- after two
+    // Gram-Schmidt passes an exhausted direction leaves about 1e-16 sigma_1.
+    // Singular values below 1e-10 sigma_1 therefore count as zero (numerical rank).
+    double scale = a0;
     for (int j = 0; e == cudaSuccess && j < (int)al.size() && j < k; ++j) {
+        const double tiny = 1e-10 * scale;
         // beta u_{j+1} = A v_j - alpha_j u_j, reorthogonalised against u_1..u_j
         const double *vj = V + (int64_t)j * n;
         double *uj = U + (int64_t)j * m, *un = U + (int64_t)(j + 1) * m;
@@ -171,6 +176,7 @@ cudaError_t lanczos_extremes(const double *A, int64_t lda, int64_t m, int64_t n,
         if (e != cudaSuccess) break;
         be.push_back(b);
         if (!(b > tiny) || j + 1 >= k) break;  // invariant subspace, or the last step
+        scale = std::max(scale, b);
         combine_kernel<<<grid_of(m), 256, 0, st>>>(un, w_m, nullptr, 0.0, 1.0 / b, m);
         // alpha v_{j+1} = A^T u_{j+1} - beta v_j, reorthogonalised against v_1..v_{j+1}
         e = dual_sweep(A, lda, m, n, nullptr, false, un, false, nullptr, w_n, st);
@@ -182,6 +188,7 @@ cudaError_t lanczos_extremes(const double *A, int64_t lda, int64_t m, int64_t n,
         if (e != cudaSuccess || !(a > tiny)) break;
         combine_kernel<<<grid_of(n), 256, 0, st>>>(V + (int64_t)(j + 1) * n, w_n, nullptr, 0.0, 1.0 / a, n);
         al.push_back(a);
+        scale = std::max(scale, a);
     }
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     cudaFree(U);

@@ -96,11 +96,12 @@ def test_spectral_estimates_exact_at_the_rank(kind):
     assert sp["alpha_mean_opt"] == pytest.approx(2 * F / (s1 + sr), rel=1e-8)
     assert sp["delta_opt"] == pytest.approx((s1 - sr) / (s1 + sr), rel=1e-8)
     a = sol.alpha
-    eta, rho, bI, bJ, _ = O._eta_rho(A, a, ro, co)
-    assert sp["eta"] == pytest.approx(eta, rel=1e-9) and sp["rho"] == pytest.approx(rho, rel=1e-9)
+    bI, bJ = O.beta_max(A, ro, co)
     assert sp["beta_row"] == pytest.approx(bI, rel=1e-6) and sp["beta_col"] == pytest.approx(bJ, rel=1e-6)
-    sv = O._sv(A)
-    assert sp["delta"] == pytest.approx(float(np.max(np.abs(1 - a * sv ** 2 / F))), rel=1e-8)
+    # Theorem main's eta and Lemma estz's rho, Theorem ner's delta at the handle's alpha
+    assert sp["eta"] == pytest.approx(1 - (2 * a - a * a * bI) * sr / F, rel=1e-7)
+    assert sp["rho"] == pytest.approx(1 - (2 * a - a * a * bJ) * sr / F, rel=1e-7)
+    assert sp["delta"] == pytest.approx(max(abs(1 - a * s1 / F), abs(1 - a * sr / F)), rel=1e-8)
 
 
 def test_spectral_estimates_bracket_from_inside_with_few_steps():
