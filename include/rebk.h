@@ -208,8 +208,10 @@ typedef struct {
  * them (host struct *out).  The Ritz values bracket the spectrum from inside:
  * exact once steps reaches the rank (the iteration stops there), otherwise
  * sigma1_sq converges fast and sigma_r_sq slowly from above, so eta and rho
- * are optimistic until then.  Singular values below 1e-10 sigma_1 count as
- * zero (the numerical rank).  Working memory (m + n) (steps + 1) doubles.
+ * are optimistic until then.  Ritz values below 1e-12 sigma1_sq count as
+ * zero (the numerical rank; on a rank-deficient A the last steps before the
+ * rank can pick up a null-space direction, whose Ritz value is dropped).
+ * Working memory (m + n) (steps + 1) doubles.
  * Errors: EINVAL (NULL, steps out of range), ENOMEM, ECUDA.  A = 0 gives zeros.
  */
 rebk_status rebk_spectral_estimates(rebk_handle h, int32_t steps, uint64_t seed, rebk_spectrum *out);

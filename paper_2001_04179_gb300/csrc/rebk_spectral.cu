@@ -8,10 +8,11 @@
 //   u_1 random, alpha_1 v_1 = A^T u_1,
 //   beta_{j+1} u_{j+1} = A v_j - alpha_j u_j,
 //   alpha_{j+1} v_{j+1} = A^T u_{j+1} - beta_{j+1} v_j.
-// Every v_j lies in range(A^T), so the Ritz values -- the eigenvalues of the
-// k x k tridiagonal B_k^T B_k (diagonal alpha_j^2 + beta_{j+1}^2, off-diagonal
-// alpha_{j+1} beta_{j+1}) -- lie in [sigma_r^2, sigma_1^2] and approach the ends
-// from inside as k grows; they are exact once the Krylov space is invariant.
+// In exact arithmetic every v_j lies in range(A^T), so the Ritz values -- the
+// eigenvalues of the k x k tridiagonal B_k^T B_k (diagonal alpha_j^2 +
+// beta_{j+1}^2, off-diagonal alpha_{j+1} beta_{j+1}) -- lie in [sigma_r^2,
+// sigma_1^2] and approach the ends from inside as k grows; they are exact once
+// the Krylov space is invariant.
 // The products run in the FP64 sweep kernel of rebk_setup.cu; the two extreme
 // eigenvalues of the tridiagonal come from Sturm-sequence bisection on the host.
 #include <cuda_runtime.h>
@@ -206,8 +207,14 @@ cudaError_t lanczos_extremes(const double *A, int64_t lda, int64_t m, int64_t n,
         d[j] = al[j] * al[j] + bj * bj;
         if (j + 1 < kk) off[j] = al[j + 1] * bj;
     }
-    *sigma1_sq = tridiag_eig(d, off, kk - 1);
-    *sigma_r_sq = tridiag_eig(d, off, 0);
+    // Ritz values below 1e-12 of the largest are numerical zeros: on a matrix of
+    // rounding-level rank deficiency the recurrence amplifies the components along
+    // the tiny singular values, so one Krylov vector can land in the numerical null
+    // space just as the space reaches the rank.  sigma_r^2 is the smallest value above.
+    const double lmax = tridiag_eig(d, off, kk - 1);
+    const int zeros = sturm_below(d, off, 1e-12 * lmax);
+    *sigma1_sq = lmax;
+    *sigma_r_sq = zeros < kk ? tridiag_eig(d, off, zeros) : 0.0;
     *steps_done = kk;
     return cudaSuccess;
 }
