@@ -52,7 +52,7 @@ def parse():
                          "on the 8192 x 2048 spectrum workload (targets, training, warm vs cold)")
     ap.add_argument("--sparse-mixed", action="store_true",
                     help="with --workload sparse --profile-pass K: run the mixed-precision pass")
-    ap.add_argument("--sweep-parts", default="", help="sweep workload: comma-separated parts 1-5 (default all)")
+    ap.add_argument("--sweep-parts", default="", help="sweep workload: comma-separated parts 1-6 (default all)")
     ap.add_argument("--batch-tau", type=int, default=16, help="batch workload block size (0 = autotune)")
     ap.add_argument("--batch-count", type=int, default=512, help="batch workload: number of systems")
     ap.add_argument("--batch-scale", type=int, default=1, help="batch workload: divide the size ranges (profiling)")
@@ -573,7 +573,9 @@ def run_sweep(args):
       (5) Fig. 3 shapes: Type I (m x 500, rank 250, kappa 2) and Type II
           randn(m, 500), m = 2000, 4000, ..., 20000, tau = 10, alpha = 1.75 / beta_max.
     Parts (3)-(5) stop at ||x - A^+ b|| <= 1e-5 (the absolute rule of Section 3's
-    experiments) in plain FP64."""
+    experiments) in plain FP64.  (6) the device Lanczos estimates of sigma_1^2 and
+    sigma_r^2 with Remark alpha's mean-optimal step and the rates of Theorems ner and
+    main, and randn(1000, 200) solved at that step, at 1 / beta_max and at 1.75 / beta_max."""
     import torch
 
     from paper_2001_04179_gb300 import tune_tau
@@ -644,10 +646,47 @@ def run_sweep(args):
                 b, xr = torch.from_numpy(p.b).to(dev), torch.from_numpy(p.x_ref).to(dev)
                 tune("Fig. 3 " + label + ", tau 10, alpha 1.75/beta_max, abs err 1e-5", A_dev, b, xr, [10],
                      1.75, "fp64", abs_tol(p), 3, max_iter=3000000)
+    if only is None or "6" in only:
+        # Section 2's step-size quantities from the device Lanczos estimates, and solves at
+        # Remark alpha's mean-optimal step, at 1 / beta_max (the step Theorem main's bound
+        # favours) and at 1.75 / beta_max
+        from paper_2001_04179_gb300 import Solver
+        g = gaussian_problem(1000, 200, seed=rank)
+        bg, xg = torch.from_numpy(g.b).to(dev), torch.from_numpy(g.x_ref).to(dev)
+        sol = Solver(g.A, 20, 20, alpha=0.0, storage=(), stream=stream)
+        t0 = time.perf_counter()
+        sp = sol.spectrum(steps=200, seed=1)
+        sp_s = time.perf_counter() - t0
+        bmax = max(sp["beta_row"], sp["beta_col"])
+        row = {"workload": "randn(1000,200), tau 20: spectral estimates", "spectrum_s": sp_s,
+               "alpha_mean_opt_times_beta_max": sp["alpha_mean_opt"] * bmax, **sp}
+        for label, a in (("mean_opt", sp["alpha_mean_opt"]), ("1/beta_max", 1.0 / bmax), ("1.75/beta_max", 1.75 / bmax)):
+            sol.alpha = a
+            o = sol.solve(bg, tol=1e-10, max_iter=200000, seed=5, x_ref=xg,
+                          allow=(R_CODE("REBK_OK"), R_CODE("REBK_MAX_ITER"), R_CODE("REBK_DIVERGED")))
+            sp2 = sol.spectrum(steps=200, seed=1)
+            row["solve_" + label] = {"alpha": a, "status": R_STATUS(o["status"]), "iterations": o["stats"]["iterations"],
+                                     "rel_err": o["stats"]["rel_err"], "delta": sp2["delta"], "eta": sp2["eta"],
+                                     "rho": sp2["rho"]}
+        rows.append(row)
+        prob = make_problem(rank, True)
+        A_dev = torch.from_numpy(prob.A).to(dev)
+        sol = Solver(A_dev, 128, 128, alpha=0.0, storage=(), stream=stream)
+        t0 = time.perf_counter()
+        sp = sol.spectrum(steps=300, seed=1)
+        rows.append({"workload": "8000x20000 rank 2000, tau 128: spectral estimates (300 steps)",
+                     "spectrum_s": time.perf_counter() - t0,
+                     "alpha_mean_opt_times_beta_max": sp["alpha_mean_opt"] * max(sp["beta_row"], sp["beta_col"]), **sp})
+        sol.close()
     if rank == 0:
         for r in rows:
             print(json.dumps(r), flush=True)
     return 0
+
+
+def R_CODE(name: str) -> int:
+    from paper_2001_04179_gb300 import rebk as R
+    return getattr(R, name)
 
 
 def R_STATUS(code: int) -> str:
