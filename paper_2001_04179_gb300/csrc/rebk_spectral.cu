@@ -5,14 +5,13 @@
 //
 // Golub-Kahan-Lanczos bidiagonalisation on the device, FP64, with full
 // reorthogonalisation (two classical Gram-Schmidt passes per vector):
-//   u_1 random, alpha_1 v_1 = A^T u_1,
+//   u_1 = A r / ||A r|| (r random), alpha_1 v_1 = A^T u_1,
 //   beta_{j+1} u_{j+1} = A v_j - alpha_j u_j,
 //   alpha_{j+1} v_{j+1} = A^T u_{j+1} - beta_{j+1} v_j.
-// In exact arithmetic every v_j lies in range(A^T), so the Ritz values -- the
-// eigenvalues of the k x k tridiagonal B_k^T B_k (diagonal alpha_j^2 +
-// beta_{j+1}^2, off-diagonal alpha_{j+1} beta_{j+1}) -- lie in [sigma_r^2,
-// sigma_1^2] and approach the ends from inside as k grows; they are exact once
-// the Krylov space is invariant.
+// In exact arithmetic every v_j lies in range(A^T) and every u_j in range(A), so
+// the Ritz values lie in [sigma_r^2, sigma_1^2] and approach the ends from inside
+// as k grows; they are exact once the Krylov space is invariant (rounding: see
+// the end of lanczos_extremes).
 // The products run in the FP64 sweep kernel of rebk_setup.cu; the two extreme
 // eigenvalues of the tridiagonal come from Sturm-sequence bisection on the host.
 #include <cuda_runtime.h>
@@ -143,9 +142,11 @@ cudaError_t lanczos_extremes(const double *A, int64_t lda, int64_t m, int64_t n,
     std::vector<double> al, be;  // alpha_1.., beta_2..
     double a0 = 0.0;
     if (e == cudaSuccess) {
-        start_kernel<<<grid_of(m), 256, 0, st>>>(w_m, m, seed);
+        // u_1 = A r / ||A r|| for a random r: a start inside range(A) (see the end)
+        start_kernel<<<grid_of(n), 256, 0, st>>>(w_n, n, seed);
+        e = dual_sweep(A, lda, m, n, w_n, false, nullptr, false, w_m, nullptr, st);
         double nu = 0.0;
-        e = norm_of(w_m, m, &nu);
+        if (e == cudaSuccess) e = norm_of(w_m, m, &nu);
         if (e == cudaSuccess && nu > 0.0) {
             combine_kernel<<<grid_of(m), 256, 0, st>>>(U, w_m, nullptr, 0.0, 1.0 / nu, m);
             e = dual_sweep(A, lda, m, n, nullptr, false, U, false, nullptr, w_n, st);  // A^T u_1
@@ -199,22 +200,36 @@ cudaError_t lanczos_extremes(const double *A, int64_t lda, int64_t m, int64_t n,
     cudaFree(c);
     cudaFree(nrm);
     if (e != cudaSuccess || al.empty()) return e;
-    // T = B^T B, B the (kk+1) x kk lower bidiagonal with alpha on the diagonal and beta below
+    // Two Rayleigh-Ritz matrices from the same coefficients (kk steps):
+    //   v side: V^T A^T A V = B^T B, B the (kk+1) x kk lower bidiagonal (alpha on the
+    //     diagonal, beta below), tridiagonal with diagonal alpha_j^2 + beta_{j+1}^2;
+    //   u side: U^T A A^T U = Bh Bh^T, Bh its leading kk x kk block (the last beta
+    //     dropped), with the same nonzero eigenvalues as Bh^T Bh.
+    // In rounding, the recurrence scales the components of the v's along null(A) by
+    // about beta / alpha per step and those of the u's along null(A^T) by about
+    // alpha / beta, so one side stays inside range(A^T) (or range(A)) while the
+    // other may pick up null directions whose Ritz values fall toward 0.  Ritz
+    // values of a clean side lie in [sigma_r^2, sigma_1^2]: sigma_r^2 is taken as the
+    // larger of the two sides' smallest values above 1e-12 lambda_max (numerical
+    // zeros dropped), sigma_1^2 as the larger of their largest values.
     const int kk = (int)std::min(al.size(), be.size() > 0 ? be.size() : (size_t)1);
-    std::vector<double> d(kk), off(kk > 1 ? kk - 1 : 0);
-    for (int j = 0; j < kk; ++j) {
-        const double bj = j < (int)be.size() ? be[j] : 0.0;
-        d[j] = al[j] * al[j] + bj * bj;
-        if (j + 1 < kk) off[j] = al[j + 1] * bj;
+    double lmax = 0.0, lmin = 0.0;
+    for (int side = 0; side < 2; ++side) {
+        std::vector<double> d(kk), off(kk > 1 ? kk - 1 : 0);
+        for (int j = 0; j < kk; ++j) {
+            const bool with_beta = j + 1 < kk || side == 0;
+            const double bj = (with_beta && j < (int)be.size()) ? be[j] : 0.0;
+            d[j] = al[j] * al[j] + bj * bj;
+            if (j + 1 < kk) off[j] = al[j + 1] * be[j];
+        }
+        const double top = tridiag_eig(d, off, kk - 1);
+        const int zeros = sturm_below(d, off, 1e-12 * top);
+        const double low = zeros < kk ? tridiag_eig(d, off, zeros) : 0.0;
+        lmax = std::max(lmax, top);
+        lmin = std::max(lmin, low);
     }
-    // Ritz values below 1e-12 of the largest are numerical zeros: on a matrix of
-    // rounding-level rank deficiency the recurrence amplifies the components along
-    // the tiny singular values, so one Krylov vector can land in the numerical null
-    // space just as the space reaches the rank.  sigma_r^2 is the smallest value above.
-    const double lmax = tridiag_eig(d, off, kk - 1);
-    const int zeros = sturm_below(d, off, 1e-12 * lmax);
     *sigma1_sq = lmax;
-    *sigma_r_sq = zeros < kk ? tridiag_eig(d, off, zeros) : 0.0;
+    *sigma_r_sq = lmin;
     *steps_done = kk;
     return cudaSuccess;
 }
