@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=40)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--profile-plain", action="store_true",
+                    help="with --profile-pass K: run K iterations of the plain FP64 kernel instead")
     ap.add_argument("--storage", choices=["fp32", "bf16"], default="fp32")
     ap.add_argument("--plain-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -738,10 +740,13 @@ def main():
         # the first pass also runs the CTA-count autotune; ncu captures the second pass
         K = args.profile_pass
         for _ in range(2):
-            r = sol.solve_refined(b, tol=0.0, max_iter=K, seed=7, storage=S, max_outer=1, inner_iters=K)
+            if args.profile_plain:
+                r = sol.solve(b, tol=0.0, max_iter=K, seed=7)
+            else:
+                r = sol.solve_refined(b, tol=0.0, max_iter=K, seed=7, storage=S, max_outer=1, inner_iters=K)
         torch.cuda.synchronize()
         st = r["stats"]
-        print(json.dumps({"profile_pass": K, "storage": S, "iterations": st["iterations"],
+        print(json.dumps({"profile_pass": K, "storage": "fp64" if args.profile_plain else S, "iterations": st["iterations"],
                           "kernel_ms": st["kernel_ms"], "us_per_iteration": 1000.0 * st["kernel_ms"] / K}))
         return 0
 
