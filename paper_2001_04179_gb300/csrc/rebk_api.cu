@@ -146,7 +146,7 @@ GridArgs base_args(rebk_handle h, Mode mode, int G) {
     a.alpha = h->alpha;
     a.acc = h->acc;
     a.acc_w = h->acc_w;
-    a.acc_r = h->acc_r;
+    a.acc_r = acc_replicas(mode);
     a.nrow_cap = (int)((h->m + G - 1) / G) + 1;
     const int64_t nu = (h->n + 7) / 8;
     a.ncol_cap = (int)(8 * ((nu + G - 1) / G)) + 8;

@@ -121,13 +121,13 @@ __device__ __forceinline__ void red_add4(double *p, double a, double b, double c
     atomicAdd(p + 3, d);
 }
 
-// Sum of the kAccReplicas replicas of one accumulator entry (fixed pairwise order).
-template <typename TS> __device__ __forceinline__ TS sum_replicas(const TS *p, int aw) {
-    TS v[kAccReplicas];
+// Sum of the R replicas of one accumulator entry (fixed pairwise order).
+template <int R, typename TS> __device__ __forceinline__ TS sum_replicas(const TS *p, int aw) {
+    TS v[R];
 #pragma unroll
-    for (int q = 0; q < kAccReplicas; ++q) v[q] = ld_cg_t(p + (int64_t)q * aw);
+    for (int q = 0; q < R; ++q) v[q] = ld_cg_t(p + (int64_t)q * aw);
 #pragma unroll
-    for (int h = kAccReplicas / 2; h > 0; h >>= 1)
+    for (int h = R / 2; h > 0; h >>= 1)
 #pragma unroll
         for (int q = 0; q < h; ++q) v[q] += v[q + h];
     return v[0];
@@ -663,9 +663,12 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
     }
     __syncthreads();
 
-    const int rep = cta % args.acc_r;
+    // replicas per accumulator entry: kAccReplicas (corrections), kAccReplicasF64 (plain FP64),
+    // the same count acc_replicas() gives the host
+    constexpr int RP = CORR ? kAccReplicas : kAccReplicasF64;
+    const int rep = cta % RP;
     const int aw = args.acc_w;
-    const int64_t accset = (int64_t)args.acc_r * aw;
+    const int64_t accset = (int64_t)RP * aw;
     TS *accw_base = static_cast<TS *>(args.acc);   // w partials: 3 sets
     TS *accr_base = accw_base + 3 * accset;        // r partials (+ test partial at tau_r): 3 sets
     const bool check = args.x_ref != nullptr && args.check_every > 0;
@@ -877,7 +880,7 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
                     w[t] = tzero<TS>();
                     continue;
                 }
-                TS sum = sum_replicas(accq + t, aw);
+                TS sum = sum_replicas<RP>(accq + t, aw);
                 if (CORR) sum += (TS)args.gamma[ja + t];
                 w[t] = sum;
                 if (!finite_val(sum)) zf[1] = 1;
@@ -1130,14 +1133,14 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
             const int hr = (int)(ib - ia);
             const TS *accq = accr_base + (p % 3) * accset;
             for (int t = gt; t < hr; t += XT) {
-                const TS sum = sum_replicas(accq + t, aw);
+                const TS sum = sum_replicas<RP>(accq + t, aw);
                 rr[t] = sum;
                 if (!finite_val(sum)) xf[3] = 1;
             }
             if (gt == XT - 1) {
                 int code = 0;
                 if (due) {
-                    const TS e2 = sum_replicas(accq + tau_r, aw);
+                    const TS e2 = sum_replicas<RP>(accq + tau_r, aw);
                     if ((double)e2 <= args.tol2_abs) code = 1;
                 }
                 xf[1] = code;

@@ -21,6 +21,8 @@ constexpr int kZRing = 4;                  // z_I hand-over slots between the tw
 constexpr int kRing = 8;                   // block indices kept ahead / behind
 constexpr size_t kSmemHeader = 512;        // index rings, flags, mbarriers, step coefficients
 constexpr int kAccReplicas = 16;           // replicated accumulators (atomic contention)
+constexpr int kAccReplicasF64 = 2;         // plain FP64: each CTA adds the replicas of every
+                                           // entry in FP64, on the slow FP64 pipe
 constexpr unsigned long long kBarrierTimeoutNs = 2000000000ull;  // 2 s per wait
 constexpr int64_t kMaxItersPerLaunch = 8000000;                 // barrier counter headroom
 
@@ -70,6 +72,8 @@ struct GridArgs {
 };
 
 enum class Mode { PlainF64, CorrF32, CorrBF16 };
+
+inline int acc_replicas(Mode m) { return m == Mode::PlainF64 ? kAccReplicasF64 : kAccReplicas; }
 
 // Shared-memory layout of the persistent kernel (byte offsets, 16-byte aligned).
 struct SmemLayout {

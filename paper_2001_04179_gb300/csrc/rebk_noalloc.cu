@@ -188,7 +188,7 @@ extern "C" rebk_status rebk_solve_noalloc(const double *A, int64_t m, int64_t n,
     a.beta = b;
     a.acc = acc;
     a.acc_w = acc_w;
-    a.acc_r = kAccReplicas;
+    a.acc_r = acc_replicas(Mode::PlainF64);
     a.bar = &ws->bar;
     a.bar_x = &ws->bar_x;
     a.status = &ws->status;
