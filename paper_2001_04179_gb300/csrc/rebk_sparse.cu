@@ -117,32 +117,50 @@ __device__ __forceinline__ void gather_lines(const int64_t *bnd, int nq, const i
     __syncthreads();
 }
 
+// One entry of an iteration's joint list, kept in registers from the gather
+// phase for the scatter phase: its line (rows first, then columns; -1 = none),
+// its index into the other dimension and its value.
+template <typename T> struct Entry {
+    int q;
+    int32_t idx;
+    T val;
+};
+
 // Both gathers of an iteration in one pass: the CTA's rows (CSR entries br[0] ..
 // br[nqr], against x) and columns (CSC entries bc[0] .. bc[nqc], against z) as one
 // list of nqr + nqc lines; part[q] gets line q's sum (rows first).  Each thread
-// takes two entries per round so that both loads and both gathers are in flight.
+// takes two entries per round so that both loads and both gathers are in flight;
+// the entries of the first round are returned in f0, f1 (entries tid and
+// kST + tid of the list) for the scatters.
 template <typename T>
 __device__ __forceinline__ void gather_rows_cols(const int64_t *br, int nqr, const int32_t *__restrict__ ci,
                                                  const T *__restrict__ rv, const T *x, const int64_t *bc,
                                                  int nqc, const int32_t *__restrict__ ri,
-                                                 const T *__restrict__ cv, const T *z, T *part) {
+                                                 const T *__restrict__ cv, const T *z, T *part, Entry<T> &f0,
+                                                 Entry<T> &f1) {
     const int nl = nqr + nqc;
     for (int q = threadIdx.x; q < nl; q += kST) part[q] = T(0);
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int64_t nr = nqr > 0 ? br[nqr] - br[0] : 0, nc = nqc > 0 ? bc[nqc] - bc[0] : 0, tot = nr + nc;
-    auto entry = [&](int64_t g, int *q, T *prod) {  // entry g of the joint list
+    auto entry = [&](int64_t g, Entry<T> &f, T *prod) {  // entry g of the joint list
         if (g >= tot) {
-            *q = -1;
+            f.q = -1;
+            f.idx = 0;
+            f.val = T(0);
             *prod = T(0);
         } else if (g < nr) {
             const int64_t e = br[0] + g;
-            *q = line_of(br, nqr, e);
-            *prod = rv[e] * x[ci[e]];
+            f.q = line_of(br, nqr, e);
+            f.idx = ci[e];
+            f.val = rv[e];
+            *prod = f.val * x[f.idx];
         } else {
             const int64_t e = bc[0] + (g - nr);
-            *q = nqr + line_of(bc, nqc, e);
-            *prod = cv[e] * z[ri[e]];
+            f.q = nqr + line_of(bc, nqc, e);
+            f.idx = ri[e];
+            f.val = cv[e];
+            *prod = f.val * z[f.idx];
         }
     };
     auto add_lines = [&](int q, T prod) {  // per warp: one shuffle sum and one atomic per line
@@ -154,13 +172,18 @@ __device__ __forceinline__ void gather_rows_cols(const int64_t *br, int nqr, con
         }
     };
     for (int64_t base = 0; base < tot; base += 2 * kST) {  // uniform over the CTA
-        int q0, q1;
+        Entry<T> e0, e1;
         T p0, p1;
-        entry(base + threadIdx.x, &q0, &p0);
-        entry(base + kST + threadIdx.x, &q1, &p1);
-        add_lines(q0, p0);
-        add_lines(q1, p1);
+        entry(base + threadIdx.x, e0, &p0);
+        entry(base + kST + threadIdx.x, e1, &p1);
+        add_lines(e0.q, p0);
+        add_lines(e1.q, p1);
+        if (base == 0) {
+            f0 = e0;
+            f1 = e1;
+        }
     }
+    if (tot == 0) f0.q = f1.q = -1;
     __syncthreads();
 }
 
@@ -234,31 +257,50 @@ __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_consta
             if (!barrier()) return;
         }
     }
+    // Block boundaries and b of the rows for the next iteration, loaded during the
+    // previous scatter phase (they do not change) so that a gather phase starts
+    // with its line ranges in place.
+    int64_t nb_r[2] = {0, 0}, nb_c[2] = {0, 0};
+    double nb_b = 0.0;
+    bool have_next = false;
+    auto shares = [&](int64_t kk, int64_t *l0, int *nqr, int64_t *c0, int *nq_c) {
+        const int i = __ldg(a.idx + 2 * (kk - 1) + 1);
+        const int64_t ia = (int64_t)i * a.tau_r, ib = ia + a.tau_r < a.m ? ia + a.tau_r : a.m;
+        *l0 = ia + (ib - ia) * cta / G;
+        *nqr = (int)(ia + (ib - ia) * (cta + 1) / G - *l0);
+        *c0 = 0;
+        *nq_c = 0;
+        if (kk < K) {  // the column share of J_{kk+1} (none after the last iteration)
+            const int j = __ldg(a.idx + 2 * kk);
+            const int64_t ja = (int64_t)j * a.tau_c, jb = ja + a.tau_c < a.n ? ja + a.tau_c : a.n;
+            *c0 = ja + (jb - ja) * cta / G;
+            *nq_c = (int)(ja + (jb - ja) * (cta + 1) / G - *c0);
+        }
+    };
     for (int64_t k = 1; stop == 0 && k <= K; ++k) {
         // ---- gathers: r^k = A_I x^{k-1} - b_I + z^k_I, w^{k+1} = A_J'^T z^k, test of x^{k-1} ----
-        const int i = __ldg(a.idx + 2 * (k - 1) + 1);
-        const int64_t ia = (int64_t)i * a.tau_r, ib = ia + a.tau_r < a.m ? ia + a.tau_r : a.m;
-        const int64_t l0 = ia + (ib - ia) * cta / G, l1 = ia + (ib - ia) * (cta + 1) / G;
-        const int nqr = (int)(l1 - l0);
-        const T cI = coef_r[i];
-        // the column share of J_{k+1} (none after the last iteration)
-        nqc = 0;
-        int64_t c0 = 0;
-        if (k < K) {
-            const int j = __ldg(a.idx + 2 * k);
-            const int64_t ja = (int64_t)j * a.tau_c, jb = ja + a.tau_c < a.n ? ja + a.tau_c : a.n;
-            c0 = ja + (jb - ja) * cta / G;
-            nqc = (int)(ja + (jb - ja) * (cta + 1) / G - c0);
-            cJ = coef_c[j];
-        }
+        int64_t l0, c0;
+        int nqr;
+        shares(k, &l0, &nqr, &c0, &nqc);
+        const T cI = coef_r[__ldg(a.idx + 2 * (k - 1) + 1)];
+        if (nqc > 0) cJ = coef_c[__ldg(a.idx + 2 * k)];
         cc0 = c0;
-        for (int q = tid; q <= nqr; q += kST) br[q] = a.rp[l0 + q];
-        for (int q = tid; q <= nqc; q += kST) bc[q] = a.cp[c0 + q];
+        if (have_next) {  // nqr, nqc <= kOwnMax = kST: entries tid and kST + tid
+            if (tid <= nqr) br[tid] = nb_r[0];
+            if (kST + tid <= nqr) br[kST + tid] = nb_r[1];
+            if (tid <= nqc) bc[tid] = nb_c[0];
+            if (kST + tid <= nqc) bc[kST + tid] = nb_c[1];
+        } else {
+            for (int q = tid; q <= nqr; q += kST) br[q] = a.rp[l0 + q];
+            for (int q = tid; q <= nqc; q += kST) bc[q] = a.cp[c0 + q];
+            nb_b = tid < nqr ? a.b[l0 + tid] : 0.0;
+        }
         __syncthreads();
-        gather_rows_cols(br, nqr, a.ci, rv, x, bc, nqc, a.ri, cv, z, part);
-        for (int q = tid; q < nqr; q += kST) {
-            const T rl = part[q] - (T)a.b[l0 + q] + z[l0 + q];
-            rq[q] = rl;
+        Entry<T> f0, f1;
+        gather_rows_cols(br, nqr, a.ci, rv, x, bc, nqc, a.ri, cv, z, part, f0, f1);
+        if (tid < nqr) {
+            const T rl = part[tid] - (T)nb_b + z[l0 + tid];
+            rq[tid] = rl;
             if (!isfinite(rl)) atomicExch(a.bad, 1);
         }
         for (int q = tid; q < nqc; q += kST) {
@@ -289,11 +331,42 @@ __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_consta
             break;
         }
         // ---- scatters: x^k = x^{k-1} - c_I A_I^T r^k, z^{k+1} = z^k - c_J' A_J' w^{k+1} ----
-        for (int64_t e = br[0] + tid; nqr > 0 && e < br[nqr]; e += kST)
-            atomicAdd(x + a.ci[e], -cI * rv[e] * rq[line_of(br, nqr, e)]);
-        if (CORR)
-            for (int q = tid; q < nqr; q += kST) vdual[l0 + q] -= cI * rq[q];
-        if (k < K) scatter_z();
+        // the first round's entries from registers, the rest of the list reloaded
+        auto scatter = [&](const Entry<T> &f) {
+            if (f.q < 0) return;
+            if (f.q < nqr) atomicAdd(x + f.idx, -cI * f.val * rq[f.q]);
+            else atomicAdd(z + f.idx, -cJ * f.val * wq[f.q - nqr]);
+        };
+        scatter(f0);
+        scatter(f1);
+        {
+            const int64_t nr = nqr > 0 ? br[nqr] - br[0] : 0, nc = nqc > 0 ? bc[nqc] - bc[0] : 0;
+            for (int64_t g = 2 * kST + tid; g < nr + nc; g += kST) {
+                if (g < nr) {
+                    const int64_t e = br[0] + g;
+                    atomicAdd(x + a.ci[e], -cI * rv[e] * rq[line_of(br, nqr, e)]);
+                } else {
+                    const int64_t e = bc[0] + (g - nr);
+                    atomicAdd(z + a.ri[e], -cJ * cv[e] * wq[line_of(bc, nqc, e)]);
+                }
+            }
+        }
+        if (CORR) {
+            if (tid < nqr) vdual[l0 + tid] -= cI * rq[tid];
+            for (int q = tid; q < nqc; q += kST) sdual[cc0 + q] += cJ * wq[q];
+        }
+        // boundaries and b of iteration k + 1 (read-only arrays)
+        have_next = k < K;
+        if (have_next) {
+            int64_t l0n, c0n;
+            int nqrn, nqcn;
+            shares(k + 1, &l0n, &nqrn, &c0n, &nqcn);
+            nb_r[0] = tid <= nqrn ? a.rp[l0n + tid] : 0;
+            nb_r[1] = kST + tid <= nqrn ? a.rp[l0n + kST + tid] : 0;
+            nb_c[0] = tid <= nqcn ? a.cp[c0n + tid] : 0;
+            nb_c[1] = kST + tid <= nqcn ? a.cp[c0n + kST + tid] : 0;
+            nb_b = tid < nqrn ? a.b[l0n + tid] : 0.0;
+        }
         if (!barrier()) return;
     }
     if (cta == 0 && tid == 0) {
