@@ -37,6 +37,20 @@ constexpr int kBT = 512;        // threads per CTA
 constexpr int kBW = kBT / 32;   // warps
 constexpr int kR = 8;           // right-hand-side stride
 constexpr int kDraws = 32;      // block draws prepared at a time (16 iterations)
+constexpr int kColRowsInFlight = 4;  // column step: row loads in flight per lane (fast path)
+
+// L2 prefetch of a block of the system's FP32 copy: rows [r0, r0 + h) x columns
+// [c0, c0 + w), one prefetch per 128-byte line, spread over the CTA.
+__device__ __forceinline__ void prefetch_block(const float *A, int64_t lda, int64_t r0, int64_t h, int64_t c0,
+                                               int64_t w) {
+    if (h <= 0 || w <= 0) return;
+    const int64_t l0 = c0 / 32, l1 = (c0 + w - 1) / 32;  // 32 floats per line
+    const int64_t nl = l1 - l0 + 1;
+    for (int64_t e = threadIdx.x; e < h * nl; e += blockDim.x) {
+        const int64_t r = e / nl, l = e - r * nl;
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(A + (r0 + r) * lda + (l0 + l) * 32));
+    }
+}
 
 struct BatchSys {
     int64_t m, n, lda;
@@ -123,6 +137,10 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
             for (; k < kend; ++k) {
                 const int slot = (int)((k % (kDraws / 2)) * 2);
                 const int j = draws[slot], i = draws[slot + 1];
+                {  // the row block of this iteration streams into L2 during the column step
+                    const int64_t pi0 = (int64_t)i * a.tau;
+                    prefetch_block(A, lda, pi0, pi0 + a.tau <= m ? a.tau : m - pi0, 0, n);
+                }
                 // ================= column step =================
                 const int64_t j0 = (int64_t)j * a.tau;
                 const int wc = (int)((j0 + a.tau <= n ? a.tau : n - j0));
@@ -132,7 +150,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                 const bool fast = wc == a.tau && (j0 & 3) == 0 && wc >= 16 && wc <= 128 && (wc & (wc - 1)) == 0;
                 const int lpr = wc >> 2, rpw = fast ? 32 / lpr : 1, sub = lane % lpr, rrow = lane / lpr;
                 if (fast) {
-                    constexpr int UR = 2;
+                    constexpr int UR = kColRowsInFlight;
                     float acc[4][kR];
 #pragma unroll
                     for (int e = 0; e < 4; ++e)
@@ -229,7 +247,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                 if (fast) {
                     // z update: the lane's 4 columns of W stay in registers; each row's dot is
                     // added over its tau/4 lanes
-                    constexpr int UR = 2;
+                    constexpr int UR = kColRowsInFlight;
                     float wv[4][kR];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) load8(W + (4 * sub + e) * kR, wv[e]);
@@ -303,6 +321,10 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                 }
                 __syncthreads();
                 // ================= row step =================
+                if (k + 1 < kend) {  // the next column block streams into L2 during the row step
+                    const int64_t pj0 = (int64_t)draws[slot + 2] * a.tau;
+                    prefetch_block(A, lda, 0, m, pj0, pj0 + a.tau <= n ? a.tau : n - pj0);
+                }
                 const int64_t i0 = (int64_t)i * a.tau;
                 const int hr = (int)((i0 + a.tau <= m ? a.tau : m - i0));
                 const float cI = a.coef_r[d.tr + i];
