@@ -54,6 +54,8 @@ def parse():
                          "on the 8192 x 2048 spectrum workload (targets, training, warm vs cold)")
     ap.add_argument("--sparse-mixed", action="store_true",
                     help="with --workload sparse --profile-pass K: run the mixed-precision pass")
+    ap.add_argument("--batch-probe", choices=["", "all", "one"], default="",
+                    help="with --workload batch: time one iteration of the batched kernel per system shape")
     ap.add_argument("--sweep-parts", default="", help="sweep workload: comma-separated parts 1-6 (default all)")
     ap.add_argument("--batch-tau", type=int, default=16, help="batch workload block size (0 = autotune)")
     ap.add_argument("--batch-count", type=int, default=512, help="batch workload: number of systems")
@@ -436,6 +438,8 @@ def run_batch_workload(args):
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.batch_probe:
+        return batch_probe(args)
     t0 = time.perf_counter()
     ps = batched_problems(args.batch_count, seed=rank, nrhs=8, scale_down=args.batch_scale)
     gen_s = time.perf_counter() - t0
@@ -471,6 +475,38 @@ def run_batch_workload(args):
             "inner_iterations_per_solve": iters / steps, "max_iterations": st["max_iterations"],
             "problem_gen_s": gen_s, "create_s": create_s,
             "sum_mn": int(sum(p.A.shape[0] * p.A.shape[1] for p in ps))}))
+    return 0
+
+
+def batch_probe(args):
+    """Cost of one iteration of the batched kernel on one SM: one Gaussian system
+    (or `copies` identical ones, one per CTA) with 8 right-hand sides, tau 16, one
+    pass of 2000 iterations (no stopping test), device time of the second solve
+    over the iterations; next to the FP32 FMA work of an iteration at 128 FMA per
+    clock and 2.07 GHz.  --batch-probe one: only the 6000 x 2000 system, once."""
+    import torch
+
+    from paper_2001_04179_gb300 import BatchSolver
+
+    shapes = [(6000, 2000)] if args.batch_probe == "one" else [(6000, 2000), (2000, 2000), (2000, 500), (500, 200)]
+    copies_list = [1] if args.batch_probe == "one" else [1, 152]
+    K = 2000
+    for copies in copies_list:
+        for (m, n) in shapes:
+            rng = np.random.default_rng(m + n)
+            A = rng.standard_normal((m, n))
+            bs = BatchSolver([A] * copies, nrhs=8, tau=16, max_outer=1)
+            B = bs.stack_rhs([rng.standard_normal((m, 8)) for _ in range(copies)], bs.m)
+            for sd in (3, 4):
+                out = bs.solve(B, X_ref=None, tol=0.0, max_iter=K, inner_iters=K, seed=sd)
+            st = out["stats"]
+            its = max(st["max_iterations"], 1)
+            us = 1000.0 * st["device_ms"] / its
+            fma_us = 2 * (m * 16 + 16 * n) * 8 / (128 * 2.07e9) * 1e6
+            print(json.dumps({"probe": "batched iteration cost", "m": m, "n": n, "copies": copies, "iterations": its,
+                              "us_per_iteration": us, "fp32_fma_us": fma_us, "fma_fraction": fma_us / us}),
+                  flush=True)
+            bs.close()
     return 0
 
 
