@@ -480,7 +480,8 @@ def run_batch_workload(args):
 
 def batch_probe(args):
     """Cost of one iteration of the batched kernel on one SM: one Gaussian system
-    (or `copies` identical ones, one per CTA) with 8 right-hand sides, tau 16, one
+    (or `copies` identical ones, one per CTA, stored once) with 8 right-hand sides,
+    tau = --batch-tau (16 when 0), one
     pass of 2000 iterations (no stopping test), device time of the second solve
     over the iterations; next to the FP32 FMA work of an iteration at 128 FMA per
     clock and 2.07 GHz.  --batch-probe one: only the 6000 x 2000 system, once."""
@@ -488,22 +489,25 @@ def batch_probe(args):
 
     from paper_2001_04179_gb300 import BatchSolver
 
-    shapes = [(6000, 2000)] if args.batch_probe == "one" else [(6000, 2000), (2000, 2000), (2000, 500), (500, 200)]
+    shapes = [(6000, 2000)] if args.batch_probe == "one" else [(8192, 2048), (6000, 2000), (2000, 2000),
+                                                                (2000, 500), (500, 200)]
     copies_list = [1] if args.batch_probe == "one" else [1, 152]
+    tau = args.batch_tau if args.batch_tau > 0 else 16
     K = 2000
     for copies in copies_list:
         for (m, n) in shapes:
             rng = np.random.default_rng(m + n)
             A = rng.standard_normal((m, n))
-            bs = BatchSolver([A] * copies, nrhs=8, tau=16, max_outer=1)
+            bs = BatchSolver([A] * copies, nrhs=8, tau=tau, max_outer=1)
             B = bs.stack_rhs([rng.standard_normal((m, 8)) for _ in range(copies)], bs.m)
             for sd in (3, 4):
                 out = bs.solve(B, X_ref=None, tol=0.0, max_iter=K, inner_iters=K, seed=sd)
             st = out["stats"]
             its = max(st["max_iterations"], 1)
             us = 1000.0 * st["device_ms"] / its
-            fma_us = 2 * (m * 16 + 16 * n) * 8 / (128 * 2.07e9) * 1e6
-            print(json.dumps({"probe": "batched iteration cost", "m": m, "n": n, "copies": copies, "iterations": its,
+            fma_us = 2 * (m * tau + tau * n) * 8 / (128 * 2.07e9) * 1e6
+            print(json.dumps({"probe": "batched iteration cost", "m": m, "n": n, "tau": tau, "copies": copies,
+                              "iterations": its,
                               "us_per_iteration": us, "fp32_fma_us": fma_us, "fma_fraction": fma_us / us}),
                   flush=True)
             bs.close()

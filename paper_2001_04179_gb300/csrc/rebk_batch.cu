@@ -38,6 +38,7 @@ constexpr int kBW = kBT / 32;   // warps
 constexpr int kR = 8;           // right-hand-side stride
 constexpr int kDraws = 32;      // block draws prepared at a time (16 iterations)
 constexpr int kColRowsInFlight = 4;  // column step: row loads in flight per lane (fast path)
+constexpr int64_t kPrefetchPoolBytes = 96ll << 20;  // FP32 matrix pool above which blocks are prefetched
 
 // L2 prefetch of a block of the system's FP32 copy: rows [r0, r0 + h) x columns
 // [c0, c0 + w), one prefetch per 128-byte line, spread over the CTA.
@@ -80,6 +81,7 @@ struct InnerArgs {
     const double *thr2;        // per system and RHS: squared error threshold
     int check_every;
     int64_t state_cap;         // floats of shared memory for dZ and dX (systems that fit)
+    int prefetch;              // L2 prefetch of the next blocks (the FP32 pool exceeds L2)
     int64_t iters;             // per-system iteration budget of this pass
     int64_t *iters_done;       // per system, accumulated over passes
     const int64_t *iter_cap;   // per system: total iterations allowed
@@ -148,7 +150,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
             for (; k < kend; ++k) {
                 const int slot = (int)((k % (kDraws / 2)) * 2);
                 const int j = draws[slot], i = draws[slot + 1];
-                {  // the row block of this iteration streams into L2 during the column step
+                if (a.prefetch) {  // the row block of this iteration streams into L2 during the column step
                     const int64_t pi0 = (int64_t)i * a.tau;
                     prefetch_block(A, lda, pi0, pi0 + a.tau <= m ? a.tau : m - pi0, 0, n);
                 }
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                 }
                 __syncthreads();
                 // ================= row step =================
-                if (k + 1 < kend) {  // the next column block streams into L2 during the row step
+                if (a.prefetch && k + 1 < kend) {  // the next column block streams into L2 during the row step
                     const int64_t pj0 = (int64_t)draws[slot + 2] * a.tau;
                     prefetch_block(A, lda, 0, m, pj0, pj0 + a.tau <= n ? a.tau : n - pj0);
                 }
@@ -866,6 +868,9 @@ rebk_status enqueue_solve(rebk_batch h, int tau, double tol, int64_t inner_iters
         a.count = h->count;
         a.queue = h->counters;
         a.A32 = h->A32;
+        // prefetching pays only when the blocks come from HBM: a pool that fits in L2
+        // (one shared matrix, small systems) is read from L2 anyway
+        a.prefetch = (int64_t)sizeof(float) * h->Apool > kPrefetchPoolBytes;
         a.cdf_r = h->cdf_r;
         a.cdf_c = h->cdf_c;
         a.coef_r = h->c32r;
