@@ -80,7 +80,6 @@ struct InnerArgs {
     const double *Xref;        // NULL = no test
     const double *thr2;        // per system and RHS: squared error threshold
     int check_every;
-    int64_t state_cap;         // floats of shared memory for dZ and dX (systems that fit)
     int prefetch;              // L2 prefetch of the next blocks (the FP32 pool exceeds L2)
     int64_t iters;             // per-system iteration budget of this pass
     int64_t *iters_done;       // per system, accumulated over passes
@@ -103,7 +102,6 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
     float *W = Wpart + kBW * 32 * CPL * kR;             // [32*CPL][kR]
     float *Rr = W + 32 * CPL * kR;                      // [tau][kR]
     int *draws = reinterpret_cast<int *>(Rr + 256 * kR);  // [kDraws]
-    float *state = reinterpret_cast<float *>(draws + kDraws);  // [state_cap]: dZ, dX of a system
     __shared__ int s_item, s_stop;
     __shared__ double s_err[kBW][kR];
 
@@ -121,17 +119,8 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
         if (K <= 0) continue;
         const float *A = a.A32 + d.a_off;
         const int64_t m = d.m, n = d.n, lda = d.lda;
-        // The corrections dZ, dX start at zero each pass and only this CTA reads them
-        // within it: they live in shared memory when they fit, which turns their
-        // read-modify-writes into shared-memory traffic (the duals S, Vd go to global
-        // memory, where the FP64 sweeps read them).
-        const bool local_state = (m + n) * kR <= a.state_cap;
-        float *dZ = local_state ? state : a.dZ + d.mrow * kR, *Vd = a.Vd + d.mrow * kR;
-        float *dX = local_state ? state + m * kR : a.dX + d.nrow * kR, *S = a.S + d.nrow * kR;
-        if (local_state) {
-            for (int64_t e = tid; e < (m + n) * kR; e += kBT) state[e] = 0.f;
-            __syncthreads();
-        }
+        float *dZ = a.dZ + d.mrow * kR, *Vd = a.Vd + d.mrow * kR;
+        float *dX = a.dX + d.nrow * kR, *S = a.S + d.nrow * kR;
         const float *F = a.F32 + d.mrow * kR, *G = a.G32 + d.nrow * kR;
         const uint64_t k0 = (uint64_t)a.iters_done[id];
         int64_t k = 0;
@@ -794,15 +783,13 @@ rebk_status build_tables(rebk_batch h, int tau, const std::vector<char> *only = 
 
 int cpl_for(int tau) { return tau <= 32 ? 1 : tau <= 64 ? 2 : tau <= 128 ? 4 : 8; }
 
-size_t inner_smem_base(int cpl) {
+// Dynamic shared memory of the inner kernel.  Kept to what the phases need: the rest
+// of the SM's 256 KB serves as L1, which holds the dZ / dX rows that the lanes of a
+// row and the warps of a row block re-read (reserving it for a system's dZ / dX
+// instead made the systems that do not fit slower).
+size_t inner_smem(int cpl) {
     return sizeof(float) * ((size_t)kBW * 32 * cpl * kR + 32 * cpl * kR + 256 * kR) + sizeof(int) * kDraws;
 }
-
-// Dynamic shared memory of the inner kernel: the working arrays plus the rest of the
-// 227 KB (less the static arrays) for a system's dZ and dX.
-constexpr size_t kInnerSmemMax = 227 * 1024 - 2048;
-size_t inner_smem(int) { return kInnerSmemMax; }
-int64_t inner_state_cap(int cpl) { return (int64_t)((kInnerSmemMax - inner_smem_base(cpl)) / sizeof(float)); }
 
 cudaError_t launch_inner(const InnerArgs &a, int grid, cudaStream_t st) {
     const int cpl = cpl_for(a.tau);
@@ -813,7 +800,6 @@ cudaError_t launch_inner(const InnerArgs &a, int grid, cudaStream_t st) {
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     InnerArgs c = a;
-    c.state_cap = inner_state_cap(cpl);
     void *params[] = {&c};
     return cudaLaunchKernel(k, dim3(grid), dim3(kBT), params, smem, st);
 }
