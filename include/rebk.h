@@ -49,7 +49,7 @@ typedef enum {
     REBK_DIVERGED = 5,          /* a reduced block product became Inf/NaN            */
     REBK_BARRIER_TIMEOUT = 6,   /* a device-wide wait gave up (bounded spin); x and z
                                    are not updated                                   */
-    REBK_EUNSUPPORTED = 7       /* size or option outside what this build handles    */
+    REBK_EUNSUPPORTED = 7       /* size or option outside what the library handles   */
 } rebk_status;
 
 /* Storage precision of the matrix copy used by the inner sweeps. */
