@@ -12,6 +12,7 @@ Functions whose result the paper and mathematics pin (see tests/):
                                  REK and RABK special cases, closed-form mean
                                  recursion, expected-error bounds, Tables 1-2
   rebk_correction / refine    -- equals rebk from the shifted state; limit A^+ b
+  rebk_sparse                 -- equals rebk on the dense form (same picks)
   beta_max                    -- Tables 1-2 step sizes, bounds of Remark rek9
   mlp_*                       -- finite differences, linear special case
 """

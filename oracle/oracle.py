@@ -16,6 +16,8 @@ the plain C file ``rebk_oracle.c`` next to this one, compiled with
   corrections with the reduced-precision matrix, FP64 update of x and z
   through the duals.
 * ``mlp_forward`` / ``mlp_backward``: the warm-start network in FP64.
+* ``rebk_sparse``: Algorithm 1 over the stored entries of a CSR matrix, for
+  matrices whose dense form does not fit (numpy, the same draws as ``rebk``).
 """
 from __future__ import annotations
 
@@ -30,7 +32,7 @@ __all__ = [
     "build_oracle", "lib",
     "philox", "uniform", "pick",
     "block_norms", "cdf", "tables",
-    "rebk", "rebk_correction",
+    "rebk", "rebk_correction", "rebk_sparse",
     "pinv_solve", "mean_closed_form", "beta_max",
     "bound_ner", "bound_estz", "bound_main",
     "round_fp32", "round_bf16",
@@ -218,6 +220,53 @@ def rebk_correction(Alo, f, g, row_off, col_off, norms, alpha, seed, iters, stre
                                      _p(idx, _i32p), _p(work))
     return {"dz": dz, "dx": dx, "s": s, "v": v, "iters": int(done),
             "idx": None if idx is None else idx[:done]}
+
+
+def rebk_sparse(m, n, indptr, indices, data, b, row_off, col_off, alpha, seed, iters, stream=0, k0=0,
+                record=False):
+    """Iterations k0+1 .. k0+iters of Algorithm 1 on a matrix given in CSR form
+    (indptr (m + 1), indices, data), from z^0 = b, x^0 = 0, for matrices whose
+    dense form is too large for ``rebk``.  The same steps with the products
+    written over the stored entries: the squared block norms are sums of the
+    squared entries of each block; w = A_J^T z adds data * z[row] into the
+    entry's column, z -= c_J A_J w subtracts c_J data w[column] from the entry's
+    row; r = A_I x - b_I + z_I and x -= c_I A_I^T r likewise over the row block.
+    Block picks use the same Philox draws and table search as ``rebk``.
+    Returns dict(x, z, idx)."""
+    indptr = np.asarray(indptr, dtype=np.int64)
+    cols = np.asarray(indices, dtype=np.int64)
+    vals = _f64(data)
+    rows = np.repeat(np.arange(m, dtype=np.int64), np.diff(indptr))
+    ro = np.asarray(row_off, dtype=np.int64)
+    co = np.asarray(col_off, dtype=np.int64)
+    s, t = ro.size - 1, co.size - 1
+    rblk = np.searchsorted(ro, rows, side="right") - 1   # row block of each entry
+    cblk = np.searchsorted(co, cols, side="right") - 1   # column block of each entry
+    nr = np.bincount(rblk, weights=vals * vals, minlength=s)
+    nc = np.bincount(cblk, weights=vals * vals, minlength=t)
+    cr, cc = cdf(nr), cdf(nc)
+    b = _f64(b)
+    z = b.copy()
+    x = np.zeros(n)
+    idx = np.zeros((max(iters, 1), 2), dtype=np.int32)
+    for kk in range(iters):
+        k = k0 + kk + 1
+        j = pick(cc, uniform(seed, stream, 2 * (k - 1)))
+        i = pick(cr, uniform(seed, stream, 2 * (k - 1) + 1))
+        idx[kk] = (j, i)
+        # column step on the entries of A_{:,J_j}
+        e = np.nonzero(cblk == j)[0]
+        w = np.bincount(cols[e] - co[j], weights=vals[e] * z[rows[e]], minlength=co[j + 1] - co[j])
+        cJ = alpha / nc[j] if nc[j] > 0 else 0.0
+        z = z - np.bincount(rows[e], weights=cJ * vals[e] * w[cols[e] - co[j]], minlength=m)
+        # row step on the entries of A_{I_i,:}
+        e = np.arange(indptr[ro[i]], indptr[ro[i + 1]])
+        h = ro[i + 1] - ro[i]
+        r = np.bincount(rows[e] - ro[i], weights=vals[e] * x[cols[e]], minlength=h) - b[ro[i]:ro[i + 1]] \
+            + z[ro[i]:ro[i + 1]]
+        cI = alpha / nr[i] if nr[i] > 0 else 0.0
+        x = x - np.bincount(cols[e], weights=cI * vals[e] * r[rows[e] - ro[i]], minlength=n)
+    return {"x": x, "z": z, "idx": idx[:iters] if record else None}
 
 
 # --------------------------------------------------------------------------
