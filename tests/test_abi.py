@@ -106,3 +106,16 @@ def test_step_size_and_tuner_reject_bad_arguments_on_the_host():
     zero = (ctypes.c_int64 * 2)(0, 2)
     assert tune(taus_=zero) == R.REBK_EINVAL
     assert "tau" in lib.rebk_last_error().decode()
+
+
+def test_block_size_above_the_kernel_limit_is_unsupported_before_any_cuda_call():
+    """tau is clamped to m and n first; what remains above 512 is rejected on the host."""
+    import ctypes
+    from paper_2001_04179_gb300 import rebk as R
+    lib = R.load()
+    h = ctypes.c_void_p()
+    A = (ctypes.c_double * 4)(1, 2, 3, 4)   # never read: the call returns before any copy
+    opt = R.RebkOptions(600, 8, 0, 0, 0, None)
+    assert lib.rebk_create(ctypes.byref(h), A, 1000, 1000, 1000, 0, 1.0, ctypes.byref(opt)) == R.REBK_EUNSUPPORTED
+    assert "tau" in lib.rebk_last_error().decode()
+    assert not h.value
