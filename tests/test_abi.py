@@ -119,3 +119,17 @@ def test_block_size_above_the_kernel_limit_is_unsupported_before_any_cuda_call()
     assert lib.rebk_create(ctypes.byref(h), A, 1000, 1000, 1000, 0, 1.0, ctypes.byref(opt)) == R.REBK_EUNSUPPORTED
     assert "tau" in lib.rebk_last_error().decode()
     assert not h.value
+
+
+def test_header_is_plain_c():
+    """The boundary header compiles as C99 (no C++ or torch types) and as C++."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:  # pragma: no cover
+        pytest.skip("gcc not available")
+    hdr = os.path.join(ROOT, "include", "rebk.h")
+    subprocess.run([gcc, "-std=c99", "-fsyntax-only", "-Wall", "-Wextra", "-Werror", "-x", "c", hdr], check=True)
+    gxx = shutil.which("g++")
+    if gxx:
+        subprocess.run([gxx, "-std=c++17", "-fsyntax-only", "-Wall", "-Werror", "-x", "c++", hdr], check=True)
