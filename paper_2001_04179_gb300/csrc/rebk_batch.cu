@@ -39,6 +39,8 @@ constexpr int kR = 8;           // right-hand-side stride
 constexpr int kDraws = 32;      // block draws prepared at a time (16 iterations)
 constexpr int kColRowsInFlight = 4;  // column step: row loads in flight per lane (fast path)
 constexpr int64_t kPrefetchPoolBytes = 96ll << 20;  // FP32 matrix pool above which blocks are prefetched
+constexpr double kIterFloorElems = 900.0;  // per-iteration latency floor of a CTA, in units of the
+                                           // cost of one block element at tau 16 (queue ordering)
 
 // L2 prefetch of a block of the system's FP32 copy: rows [r0, r0 + h) x columns
 // [c0, c0 + w), one prefetch per 128-byte line, spread over the CTA.
@@ -1001,7 +1003,8 @@ rebk_status rebk_batch_create(rebk_batch *out, int32_t count, const int64_t *m, 
     BCKH(cudaMalloc(&h->thr2, sizeof(double) * count * kR));
     BCKH(cudaMalloc(&h->e2, sizeof(double) * count * kR));
     BCKH(cudaMalloc(&h->r2, sizeof(double) * count * kR));
-    // sweep work items and queue order (largest m * n first)
+    // sweep work items and the first solve's queue order (largest m * n first; later
+    // solves order by the previous solve's measured iterations, see run_batch)
     std::vector<int2> items;
     for (int i = 0; i < count; ++i)
         for (int64_t r = 0; r < m[i]; r += kSR) items.push_back(make_int2(i, (int)r));
@@ -1105,6 +1108,20 @@ rebk_status run_batch(rebk_batch h, int tau, double tol, int64_t max_iter, int64
     int conv = 0;
     BCK(cudaMemcpy(it.data(), h->iters_done, sizeof(int64_t) * h->count, cudaMemcpyDeviceToHost));
     BCK(cudaMemcpy(&conv, h->counters + 1, sizeof(int), cudaMemcpyDeviceToHost));
+    if (!only) {
+        // Queue order of the next solve: longest expected time first, from this solve's
+        // iteration counts and a per-iteration cost model of one CTA (a latency floor plus
+        // a term in the block elements, fitted on GB300: about 5.7 us + 6.4 ns x
+        // tau / 16 x (m + n)).  Order changes no result: each system's random stream is
+        // keyed by its index.
+        std::vector<double> cost(h->count);
+        for (int i = 0; i < h->count; ++i)
+            cost[i] = (double)it[i] * (kIterFloorElems + (double)tau / 16.0 * (double)(h->m[i] + h->n[i]));
+        std::vector<int> order(h->count);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        BCK(cudaMemcpy(h->d_order, order.data(), sizeof(int) * h->count, cudaMemcpyHostToDevice));
+    }
     if (stats) {
         memset(stats, 0, sizeof(*stats));
         stats->converged = use_ref ? conv : 0;
