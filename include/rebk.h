@@ -544,6 +544,19 @@ rebk_status rebk_sparse_solve_refined(rebk_sparse h, const double *b, double *x,
 rebk_status rebk_sparse_info(rebk_sparse h, double *alpha, double *beta_max, int32_t *row_blocks,
                              int32_t *col_blocks);
 
+/*
+ * Self-test of the bounded device-wide waits.  One CTA of a launch waits, with
+ * the device-wide barrier and the split-phase wait the sparse kernel uses, for
+ * arrivals that never come; each wait gives up after timeout_ns (in [1e3, 1e9])
+ * and records REBK_BARRIER_TIMEOUT, and the kernel returns -- nothing faults or
+ * traps and the context stays usable.  codes (host, 2): the status of each wait
+ * (REBK_BARRIER_TIMEOUT = they gave up as designed); *elapsed_ms (host, may be
+ * NULL): device time spent in them.  Returns REBK_BARRIER_TIMEOUT when the waits
+ * ran out as designed, REBK_OK if they were somehow satisfied; EINVAL, ENOMEM,
+ * ECUDA otherwise.  Synchronises the device.
+ */
+rebk_status rebk_selftest_waits(int64_t timeout_ns, int32_t *codes, double *elapsed_ms);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *rebk_last_error(void);
 

@@ -133,3 +133,13 @@ def test_header_is_plain_c():
     gxx = shutil.which("g++")
     if gxx:
         subprocess.run([gxx, "-std=c++17", "-fsyntax-only", "-Wall", "-Werror", "-x", "c++", hdr], check=True)
+
+
+def test_wait_selftest_rejects_bad_arguments_on_the_host():
+    import ctypes
+    from paper_2001_04179_gb300 import rebk as R
+    lib = R.load()
+    codes = (ctypes.c_int32 * 2)()
+    assert lib.rebk_selftest_waits(10**6, None, None) == R.REBK_EINVAL
+    assert lib.rebk_selftest_waits(10, ctypes.cast(codes, ctypes.c_void_p), None) == R.REBK_EINVAL
+    assert lib.rebk_selftest_waits(10**10, ctypes.cast(codes, ctypes.c_void_p), None) == R.REBK_EINVAL

@@ -228,3 +228,20 @@ def test_resume_continues_the_random_stream():
     b2 = sol.solve(_t(p.b), max_iter=90, seed=4, k0=60, x0=a["x"].clone(), z0=a["z"].clone(), return_z=True)
     assert _rel(b2["x"].cpu().numpy(), full["x"].cpu().numpy()) <= 1e-13
     assert _rel(b2["z"].cpu().numpy(), full["z"].cpu().numpy()) <= 1e-13
+
+
+def test_bounded_waits_give_up_and_leave_the_context_usable():
+    """Failure detection without a fault: device-wide waits for arrivals that never
+    come end by their own limit with REBK_BARRIER_TIMEOUT, and the next solve runs."""
+    import ctypes
+    lib = R.load()
+    codes = (ctypes.c_int32 * 2)()
+    ms = ctypes.c_double()
+    st = lib.rebk_selftest_waits(5_000_000, ctypes.cast(codes, ctypes.c_void_p), ctypes.byref(ms))
+    assert st == R.REBK_BARRIER_TIMEOUT
+    assert list(codes) == [R.REBK_BARRIER_TIMEOUT, R.REBK_BARRIER_TIMEOUT]
+    assert 10.0 <= ms.value < 2000.0  # two waits of 5 ms each, then the kernel returned
+    p = gaussian_problem(200, 60, seed=2)
+    sol = Solver(p.A, 10, 10, alpha=0.0, storage=())
+    out = sol.solve(_t(p.b), tol=1e-10, max_iter=10**6, seed=1, x_ref=_t(p.x_ref))
+    assert out["status"] == R.REBK_OK and _rel(out["x"].cpu().numpy(), p.x_ref) <= 1e-10
