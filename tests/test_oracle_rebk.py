@@ -335,3 +335,64 @@ def test_round_bf16_is_round_to_nearest_even():
     # bf16 keeps 8 significant bits: 1 + 2^-8 is a tie -> even (1.0); 1 + 3*2^-9 -> 1 + 2^-7
     assert list(got) == [1.0, 1.0, 1.0, 1.0 + 2**-7, -2.5, got[5], 3.0]
     assert abs(got[5] - 1e-30) <= 2**-8 * 1e-30
+
+
+# ---------------------------------------------------------------------------
+# The bound functions against values the mathematics fixes (no Monte Carlo):
+# a 3 x 2 diagonal system whose pseudoinverse solution, b_perp, singular
+# values and block spectral norms are known by hand.
+#   A = [[3, 0], [0, 1], [0, 0]], b = (1, 2, 5):  A^+ b = (1/3, 2),
+#   b_perp = (0, 0, 5), sigma = {3, 1}, ||A||_F^2 = 10, A^T b = (3, 2).
+#   Row blocks {0, 1}, {2}: beta^I = 9 / 10 (the zero block is skipped);
+#   column blocks {0}, {1}: beta^J = 1.
+# ---------------------------------------------------------------------------
+_DA = np.array([[3.0, 0.0], [0.0, 1.0], [0.0, 0.0]])
+_DB = np.array([1.0, 2.0, 5.0])
+_DRO = np.array([0, 2, 3])
+_DCO = np.array([0, 1, 2])
+
+
+def test_bounds_at_k0_equal_the_initial_errors():
+    """At k = 0 every bound is the initial error itself: Theorem ner gives
+    ||x^0 - A^+ b||, Lemma estz ||z^0 - b_perp||^2 and Theorem main
+    ||x^0 - A^+ b||^2 (its tail sum is empty)."""
+    x0 = np.array([0.5, -1.0])
+    z0 = np.array([4.0, -3.0, 7.0])
+    e_x2 = (0.5 - 1.0 / 3.0) ** 2 + (-1.0 - 2.0) ** 2
+    e_z2 = 4.0 ** 2 + 3.0 ** 2 + (7.0 - 5.0) ** 2
+    for alpha in (0.3, 1.0):
+        assert O.bound_ner(_DA, _DB, alpha, 0, z0=z0, x0=x0) == pytest.approx(np.sqrt(e_x2), rel=1e-14)
+        assert O.bound_estz(_DA, _DB, alpha, 0, _DRO, _DCO, z0=z0) == pytest.approx(e_z2, rel=1e-14)
+        for eps in (0.1, 1.0, 3.0):
+            assert O.bound_main(_DA, _DB, alpha, 0, _DRO, _DCO, eps=eps, z0=z0, x0=x0) == \
+                pytest.approx(e_x2, rel=1e-14)
+
+
+def test_bound_rates_on_a_hand_computed_system():
+    """delta, eta and rho at alpha = 1 on the diagonal system:
+    delta = max |1 - sigma_i^2 / 10| = 0.9, rho = 1 - (2 - 1) / 10 = 0.9,
+    eta = 1 - (2 - 0.9) / 10 = 0.89; from x^0 = 0, z^0 = b:
+    ||x^0 - A^+ b||^2 = 1/9 + 4, ||z^0 - b_perp||^2 = 5, ||A^T z^0|| = sqrt(13)."""
+    assert O.beta_max(_DA, _DRO, _DCO) == pytest.approx((0.9, 1.0), rel=1e-14)
+    ex2, ez2 = 1.0 / 9.0 + 4.0, 5.0
+    for k in (1, 2, 7):
+        ner = 0.9 ** k * (np.sqrt(ex2) + k * np.sqrt(13.0) / 10.0)
+        assert O.bound_ner(_DA, _DB, 1.0, k) == pytest.approx(ner, rel=1e-13)
+        assert O.bound_estz(_DA, _DB, 1.0, k, _DRO, _DCO) == pytest.approx(0.9 ** k * ez2, rel=1e-13)
+    # a smaller step: alpha = 0.5 gives delta = max(|1 - 0.45|, |1 - 0.05|) = 0.95
+    assert O.bound_ner(_DA, _DB, 0.5, 3) == pytest.approx(0.95 ** 3 * (np.sqrt(ex2) + 1.5 * np.sqrt(13.0) / 10.0),
+                                                          rel=1e-13)
+
+
+@pytest.mark.parametrize("k,eps", [(1, 0.5), (4, 0.5), (9, 0.05), (6, 2.0)])
+def test_bound_main_tail_is_the_geometric_sum(k, eps):
+    """Theorem main's second term carries sum_{l<k} rho^{k-l} q^l with
+    q = (1 + eps) eta, a geometric sum equal to rho (rho^k - q^k) / (rho - q).
+    With alpha = 1 on the diagonal system (eta = 0.89, rho = 0.9,
+    beta^I = 0.9, ||z^0 - b_perp||^2 = 5, ||A||_F^2 = 10) the bound is
+    q^k (1/9 + 4) + (1 + 1/eps) 0.9 * 5 / 10 * rho (rho^k - q^k) / (rho - q)."""
+    rho, eta = 0.9, 0.89
+    q = (1.0 + eps) * eta
+    tail = rho * (rho ** k - q ** k) / (rho - q)
+    want = q ** k * (1.0 / 9.0 + 4.0) + (1.0 + 1.0 / eps) * 0.9 * 5.0 / 10.0 * tail
+    assert O.bound_main(_DA, _DB, 1.0, k, _DRO, _DCO, eps=eps) == pytest.approx(want, rel=1e-12)
