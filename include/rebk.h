@@ -450,10 +450,11 @@ rebk_status rebk_warm_start_batch(rebk_handle h, rebk_mlp net, const double *B, 
 
 /*
  * Plain FP64 REBK for a fixed number of iterations without allocating any
- * memory.  The paper has no counterpart to this call; it exists for callers
- * that must not call cudaMalloc -- code running while a CUDA graph is being
- * captured, hosts that route every device allocation through their own
- * allocator, serving loops that must not take the driver's allocation locks.
+ * memory.  The paper has no counterpart to this call.  It exists for callers
+ * that must not call cudaMalloc: hosts that route every device allocation
+ * through their own allocator or memory budget and forbid any other, and
+ * real-time serving loops that must not take the driver's allocation locks or
+ * risk an out-of-memory failure mid-request.
  *
  * A (device, m x n row-major, leading dimension lda), b (device, m) are
  * inputs; x (device, n) and z (device, m) are outputs: x^iters and z^iters of
@@ -461,7 +462,8 @@ rebk_status rebk_warm_start_batch(rebk_handle h, rebk_mlp net, const double *B, 
  * iterates rebk_solve_ex gives with stream_id 0 and k0 0, up to the
  * summation order of the device's reductions.  alpha > 0 is required (no
  * beta_max estimate here).  stream is a cudaStream_t (NULL = legacy default).
- * The call synchronises the stream before it returns.
+ * The call reads a few status words back to the host and synchronises the
+ * stream before it returns.
  *
  * Working memory is one 32 MiB device array inside the library (every GPU that
  * loads the library holds it until the process exits).  It must hold a
@@ -472,7 +474,8 @@ rebk_status rebk_warm_start_batch(rebk_handle h, rebk_mlp net, const double *B, 
  * that device is current: make that first call before any stream capture.
  * All calls share the array and each call overwrites and re-zeroes what it
  * needs; calls whose GPU work overlaps (other streams, other host threads on
- * the same device) race on it: serialise them.
+ * the same device) race on it: serialise them.  A launch that runs fewer
+ * iterations than asked returns REBK_ECUDA.
  */
 rebk_status rebk_solve_noalloc(const double *A, int64_t m, int64_t n, int64_t lda, int64_t tau_row,
                                int64_t tau_col, double alpha, const double *b, double *x, double *z,

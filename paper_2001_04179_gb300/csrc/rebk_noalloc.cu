@@ -1,12 +1,13 @@
 // rebk_noalloc.cu -- a solve entry point that allocates no memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured, hosts that install their own allocator and forbid any other
-// device allocation, or real-time services that must not take the driver's
-// allocation locks in their serving loop.  rebk_solve_noalloc serves them: it
-// runs the same persistent FP64 kernel as rebk_solve_ex for a fixed number of
-// iterations, with all of its working memory in one statically sized device
-// array that lives in this file.
+// Some callers cannot call cudaMalloc: hosts that route every device
+// allocation through their own allocator or memory budget and forbid any
+// other allocation, and real-time services that must not take the driver's
+// allocation locks (or risk an out-of-memory failure) inside their serving
+// loop.  rebk_solve_noalloc serves them: it runs the same persistent FP64
+// kernel as rebk_solve_ex for a fixed number of iterations, with all of its
+// working memory in one statically sized device array that lives in this file.
+// The call reads a few words back to the host and synchronises its stream.
 //
 // Scratch array.  g_noalloc_scratch (kNoallocBytes = 32 MiB) exists once on
 // every GPU that loads the library and stays there until the process exits.
@@ -15,7 +16,8 @@
 // cross-CTA accumulators and the barrier / status words.  Host code cannot use
 // the array's name as a device address (in host code it is a host-side
 // stand-in), so the device address is looked up with cudaGetSymbolAddress,
-// once per device, on the first call made while that device is current.
+// once per device, on the first call made while that device is current; that
+// first call on a device should come before any stream capture.
 //
 // Every call shares the array and leaves its contents behind; the call clears
 // what has to start at zero (accumulators, barrier counter, status) itself.
@@ -93,6 +95,11 @@ extern "C" rebk_status rebk_solve_noalloc(const double *A, int64_t m, int64_t n,
     if (tau_row < 1 || tau_col < 1) return na_fail(REBK_EINVAL, "tau must be >= 1");
     if (!(alpha > 0.0)) return na_fail(REBK_EINVAL, "alpha must be > 0 (no beta_max here)");
     if (iters < 0) return na_fail(REBK_EINVAL, "iters < 0");
+    // Each of m and n alone must fit the array as doubles: this keeps every size
+    // product below in range of size_t and the block counts in range of int.
+    if (m > (int64_t)(kNoallocBytes / 8) || n > (int64_t)(kNoallocBytes / 8))
+        return na_fail(REBK_EUNSUPPORTED, "problem needs more scratch than the " + std::to_string(kNoallocBytes) +
+                                              " bytes rebk_solve_noalloc holds (m or n too large)");
     const int64_t tr = std::min(tau_row, m), tc = std::min(tau_col, n);
     if (tr > 512 || tc > 512) return na_fail(REBK_EUNSUPPORTED, "tau > 512");
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -194,13 +201,19 @@ extern "C" rebk_status rebk_solve_noalloc(const double *A, int64_t m, int64_t n,
     a.status = &ws->status;
     a.iters_done = &ws->iters_done;
     a.timeout_ns = kBarrierTimeoutNs;
+    // CTA count: about 2048 block elements per CTA, at most one CTA per SM (the
+    // persistent kernel's cooperative launch), more if the owned slices need them
+    int dev = 0, sms = 0;
+    NA_CK(cudaGetDevice(&dev));
+    NA_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (sms < 1) sms = 1;
     int G = (int)std::max<int64_t>(1, (tr * n + tc * m + 2047) / 2048);
-    G = std::min(G, 152);
+    G = std::min(G, sms);
     for (;;) {
         a.nrow_cap = (int)((m + G - 1) / G) + 1;
         a.ncol_cap = (int)(8 * (((n + 7) / 8 + G - 1) / G)) + 8;
-        if (grid_smem_bytes(Mode::PlainF64, a) <= 200 * 1024 || G >= 152) break;
-        G = std::min(152, G * 2);
+        if (grid_smem_bytes(Mode::PlainF64, a) <= 200 * 1024 || G >= sms) break;
+        G = std::min(sms, G * 2);
     }
     const int maxG = grid_max_ctas(Mode::PlainF64, grid_smem_bytes(Mode::PlainF64, a));
     if (maxG < 1) return na_fail(REBK_EUNSUPPORTED, "persistent kernel does not fit on this GPU");
@@ -225,6 +238,11 @@ extern "C" rebk_status rebk_solve_noalloc(const double *A, int64_t m, int64_t n,
         NA_CK(cudaStreamSynchronize(st));
         if (w.status == 6) return na_fail(REBK_BARRIER_TIMEOUT, "device-wide barrier timed out");
         if (w.status == 5) return na_fail(REBK_DIVERGED, "iteration diverged (Inf/NaN)");
+        // the call promises exactly `iters` iterations: anything else is an error
+        if (w.status != 0 || w.iters_done != chunk)
+            return na_fail(REBK_ECUDA, "persistent kernel ran " + std::to_string(w.iters_done) + " of " +
+                                           std::to_string(chunk) + " iterations (status " +
+                                           std::to_string(w.status) + ")");
         done += chunk;
     }
 #undef NA_CK
