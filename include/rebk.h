@@ -359,6 +359,21 @@ rebk_status rebk_batch_solve_ex(rebk_batch h, const double *B, double *X, const 
                                 int64_t inner_iters, uint64_t seed, int32_t *status_out,
                                 rebk_batch_stats *stats);
 
+/*
+ * Records, during the following solves of the batch, what each system's
+ * Algorithm 1 iterations did (for parity checks against a reference):
+ * idx_out (device, count x idx_cap x 2 int32, or NULL = stop recording): entry
+ * (i, k-1) holds (j_k, i_k), the column and row blocks system i drew at its
+ * iteration k (Philox key (seed, i), the counter layout of rebk_solve), for
+ * the iterations k <= idx_cap that the solve ran (entries past a system's last
+ * iteration are left as they were); Z_out (device, laid out like B, or NULL):
+ * the final z of every right-hand side.  The tuning solves of an autotuned
+ * first solve (tau = 0) record too; set the block size to record one solve.
+ * The buffers must stay valid until recording is switched off.
+ * Errors: EINVAL (NULL handle, idx_out with idx_cap < 1).
+ */
+rebk_status rebk_batch_record(rebk_batch h, int32_t *idx_out, int64_t idx_cap, double *Z_out);
+
 /* Block size in use and the number of systems (host outputs; either may be NULL). */
 rebk_status rebk_batch_info(rebk_batch h, int32_t *tau, int32_t *count);
 

@@ -87,6 +87,8 @@ struct InnerArgs {
     int64_t *iters_done;       // per system, accumulated over passes
     const int64_t *iter_cap;   // per system: total iterations allowed
     const int *active;         // per system: 0 = converged, skip
+    int32_t *idx_out;          // NULL, or per system idx_cap pairs (j_k, i_k) of iterations 1..idx_cap
+    int64_t idx_cap;
     unsigned long long timeout_ns;
 };
 
@@ -133,8 +135,12 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                 const uint64_t it = k0 + (uint64_t)k + (uint64_t)(lane >> 1);  // iteration index - 1
                 const uint64_t dd = 2 * it + (uint64_t)(lane & 1);
                 const double u = draw_uniform(a.seed, (uint64_t)id, dd);
-                draws[lane] = (lane & 1) ? pick_block(a.cdf_r + d.tr, d.s, u, d.fb_r)
-                                         : pick_block(a.cdf_c + d.tc, d.t, u, d.fb_c);
+                const int pick = (lane & 1) ? pick_block(a.cdf_r + d.tr, d.s, u, d.fb_r)
+                                            : pick_block(a.cdf_c + d.tc, d.t, u, d.fb_c);
+                draws[lane] = pick;
+                // record the draws of iterations this pass runs (entry it of the system's row)
+                if (a.idx_out && (int64_t)it < a.idx_cap && k + (int64_t)(lane >> 1) < K)
+                    a.idx_out[((int64_t)id * a.idx_cap + (int64_t)it) * 2 + (lane & 1)] = pick;
             }
             __syncthreads();
             const int64_t kend = (K - k < kDraws / 2) ? K : k + kDraws / 2;
@@ -652,6 +658,10 @@ struct rebk_batch_s {
     int nitems = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     std::vector<cudaEvent_t> evs;
+    // recording (rebk_batch_record): block indices and the final z of the next solves
+    int32_t *rec_idx = nullptr;
+    int64_t rec_cap = 0;
+    double *rec_z = nullptr;
 };
 
 namespace {
@@ -881,6 +891,8 @@ rebk_status enqueue_solve(rebk_batch h, int tau, double tol, int64_t inner_iters
         a.iters_done = h->iters_done;
         a.iter_cap = h->iter_cap;
         a.active = h->active;
+        a.idx_out = h->rec_idx;
+        a.idx_cap = h->rec_cap;
         a.timeout_ns = kBarrierTimeoutNs;
         BCK(launch_inner(a, sms, st));
         ++*launches;
@@ -1026,6 +1038,15 @@ rebk_status rebk_batch_create(rebk_batch *out, int32_t count, const int64_t *m, 
 }
 
 void rebk_batch_destroy(rebk_batch h) { free_batch(h); }
+
+rebk_status rebk_batch_record(rebk_batch h, int32_t *idx_out, int64_t idx_cap, double *Z_out) {
+    if (!h) return bfail(REBK_EINVAL, "NULL handle");
+    if (idx_cap < 0 || (idx_out && idx_cap == 0)) return bfail(REBK_EINVAL, "idx_cap must be >= 1 with idx_out");
+    h->rec_idx = idx_out;
+    h->rec_cap = idx_out ? idx_cap : 0;
+    h->rec_z = Z_out;
+    return REBK_OK;
+}
 
 rebk_status rebk_batch_info(rebk_batch h, int32_t *tau, int32_t *count) {
     if (!h) return bfail(REBK_EINVAL, "NULL handle");
@@ -1201,6 +1222,8 @@ extern "C" rebk_status rebk_batch_solve_ex(rebk_batch h, const double *B, double
     rebk_status rs = run_batch(h, tau, tol, max_iter, inner_iters, seed, use_ref, true, stats);
     if (rs != REBK_OK) return rs;
     batch_unpack_kernel<<<blocks_for(h->Nrows * h->nrhs, 256), 256, 0, st>>>(h->Nrows, h->nrhs, h->Xi, X);
+    if (h->rec_z)
+        batch_unpack_kernel<<<blocks_for(h->Mrows * h->nrhs, 256), 256, 0, st>>>(h->Mrows, h->nrhs, h->Z, h->rec_z);
     BCK(cudaGetLastError());
     if (status_out) BCK(cudaMemcpyAsync(status_out, h->status, sizeof(int) * h->count, cudaMemcpyDeviceToDevice, st));
     BCK(cudaStreamSynchronize(st));

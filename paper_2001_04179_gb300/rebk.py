@@ -122,6 +122,7 @@ _SIGNATURES = {
     "rebk_batch_solve_ex": ([_P, _P, _P, _P, _P, _P, ctypes.c_double, ctypes.c_int64, ctypes.c_int64,
                              ctypes.c_uint64, _P, ctypes.POINTER(RebkBatchStats)], ctypes.c_int),
     "rebk_batch_info": ([_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
+    "rebk_batch_record": ([_P, _P, ctypes.c_int64, _P], ctypes.c_int),
     "rebk_solve_noalloc": ([_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64,
                             ctypes.c_double, _P, _P, _P, ctypes.c_int64, ctypes.c_uint64, _P], ctypes.c_int),
     "rebk_mlp_create": ([ctypes.POINTER(_P), _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int, ctypes.c_int64,

@@ -396,20 +396,40 @@ class BatchSolver:
         return [Xn[self.nrow[i]:self.nrow[i + 1]] for i in range(self.count)]
 
     def solve(self, B, X_ref=None, tol: float = 1e-8, max_iter: int = 200000, inner_iters: int = 0,
-              seed: int = 0, X0=None, Z0=None):
+              seed: int = 0, X0=None, Z0=None, record_iters: int = 0, return_z: bool = False):
         """B: CUDA float64 (sum m_i) x nrhs; X_ref: (sum n_i) x nrhs or None;
         X0 / Z0: starting points laid out like X / B, or None (x = 0, z = b).
-        Returns dict(x, status (per system), stats)."""
+        record_iters > 0: also return "idx", a (count, record_iters, 2) int32
+        tensor of each system's block draws (j_k, i_k) for iterations
+        1..record_iters (entries past a system's last iteration are -1);
+        return_z: also return "z", the final z laid out like B
+        (rebk_batch_record).  Returns dict(x, status (per system), stats)."""
         torch = _torch()
+        lib = _r.load()
         X = torch.empty((int(self.nrow[-1]), self.nrhs), dtype=torch.float64, device=B.device)
         status = torch.zeros(self.count, dtype=torch.int32, device=B.device)
         stats = _r.RebkBatchStats()
         ptr = lambda t: None if t is None else ctypes.c_void_p(t.data_ptr())
-        st = _r.load().rebk_batch_solve_ex(self._h, ptr(B), ptr(X), ptr(X_ref), ptr(X0), ptr(Z0),
-                                           float(tol), int(max_iter), int(inner_iters), int(seed),
-                                           ctypes.c_void_p(status.data_ptr()), ctypes.byref(stats))
+        idx = torch.full((self.count, record_iters, 2), -1, dtype=torch.int32, device=B.device) \
+            if record_iters > 0 else None
+        Z = torch.empty((int(self.mrow[-1]), self.nrhs), dtype=torch.float64, device=B.device) if return_z else None
+        recording = idx is not None or Z is not None
+        if recording:
+            _r.check(lib.rebk_batch_record(self._h, ptr(idx), int(record_iters), ptr(Z)))
+        try:
+            st = lib.rebk_batch_solve_ex(self._h, ptr(B), ptr(X), ptr(X_ref), ptr(X0), ptr(Z0),
+                                         float(tol), int(max_iter), int(inner_iters), int(seed),
+                                         ctypes.c_void_p(status.data_ptr()), ctypes.byref(stats))
+        finally:
+            if recording:
+                lib.rebk_batch_record(self._h, None, 0, None)
         _r.check(st)
-        return {"x": X, "status": status.cpu().numpy(), "stats": stats.as_dict()}
+        out = {"x": X, "status": status.cpu().numpy(), "stats": stats.as_dict()}
+        if idx is not None:
+            out["idx"] = idx
+        if Z is not None:
+            out["z"] = Z
+        return out
 
 
 class WarmStartNet:

@@ -1,9 +1,10 @@
 """Batched systems (rebk_batch_*) against the FP64 oracle.
 
-Bars: one refinement pass per system and right-hand side against the
-oracle's pass on the FP32-rounded matrix within 1e-4 (x) and 1e-4 ||b|| (z is
-not returned; x carries the whole pass), the same bar as the single-system
-mixed path; full solves reach ||x - A^+ b|| <= 1e-8 ||A^+ b|| for every RHS of
+Bars: every system's block draws bit-exact against the oracle's Philox stream
+and table search (key (seed, system index)); one refinement pass per system
+and right-hand side against the oracle's pass on the FP32-rounded matrix
+within 1e-4 (x, as a norm and entry by entry) and 1e-4 ||b|| (z), the same
+bars as the single-system mixed path; full solves reach ||x - A^+ b|| <= 1e-8 ||A^+ b|| for every RHS of
 every converged system, and systems reported converged really are."""
 import numpy as np
 import pytest
@@ -17,6 +18,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():  # pragma: no cover
     pytest.skip("needs a CUDA GPU", allow_module_level=True)
 
+from parity import assert_close  # noqa: E402
 from paper_2001_04179_gb300 import BatchSolver  # noqa: E402
 from paper_2001_04179_gb300 import rebk as R  # noqa: E402
 
@@ -29,6 +31,17 @@ def _alphas(ps, tau):
     return np.array(out)
 
 
+def oracle_draws(A, tau, seed, system, iters):
+    """(j_k, i_k) for k = 1..iters from the oracle's tables and Philox stream."""
+    ro, co = contiguous_offsets(A.shape[0], tau), contiguous_offsets(A.shape[1], tau)
+    _, _, cr, cc = O.tables(A, ro, co)
+    out = np.zeros((iters, 2), dtype=np.int32)
+    for k in range(iters):
+        out[k, 0] = O.pick(cc, O.uniform(seed, system, 2 * k))
+        out[k, 1] = O.pick(cr, O.uniform(seed, system, 2 * k + 1))
+    return out
+
+
 @pytest.mark.parametrize("nrhs,tau", [(8, 16), (3, 7), (1, 32)])
 def test_one_pass_matches_oracle_per_system(nrhs, tau):
     ps = batched_problems(5, seed=11, scale_down=12, nrhs=nrhs)
@@ -36,17 +49,25 @@ def test_one_pass_matches_oracle_per_system(nrhs, tau):
     bs = BatchSolver([p.A for p in ps], nrhs=nrhs, tau=tau, alpha=alphas, max_outer=1)
     B = bs.stack_rhs([p.b for p in ps], bs.m)
     K = 120
-    out = bs.solve(B, X_ref=None, tol=0.0, max_iter=K, inner_iters=K, seed=5)
+    out = bs.solve(B, X_ref=None, tol=0.0, max_iter=K, inner_iters=K, seed=5, record_iters=K, return_z=True)
     assert out["stats"]["iterations"] == K * len(ps)
     xs = bs.split_x(out["x"])
+    Z = out["z"].cpu().numpy()
+    idx = out["idx"].cpu().numpy()
     for sid, p in enumerate(ps):
+        # the batch kernel's own sampler: every draw of every system, bit-exact
+        assert np.array_equal(idx[sid], oracle_draws(p.A, tau, 5, sid, K)), sid
         ro, co = contiguous_offsets(p.m, tau), contiguous_offsets(p.n, tau)
         lo = O.round_fp32(p.A)
+        zs = Z[bs.mrow[sid]:bs.mrow[sid + 1]]
+        b = p.b.reshape(p.m, nrhs)
         for r in range(nrhs):
-            ref = O.refine(p.A, p.b[:, r], lo, ro, co, alphas[sid], seed=5, inner_iters=K, outer_max=1,
+            ref = O.refine(p.A, b[:, r], lo, ro, co, alphas[sid], seed=5, inner_iters=K, outer_max=1,
                            stream=sid)
-            err = np.linalg.norm(xs[sid][:, r] - ref["x"]) / np.linalg.norm(ref["x"])
-            assert err <= 1e-4, (sid, r, err)
+            assert_close(xs[sid][:, r], ref["x"], 1e-4, str((sid, r)))
+            dz = zs[:, r] - ref["z"]
+            assert np.linalg.norm(dz) <= 1e-4 * np.linalg.norm(b[:, r]), (sid, r)
+            assert np.max(np.abs(dz)) <= 1e-4 * np.max(np.abs(b[:, r])), (sid, r)
 
 
 def test_batch_reaches_pseudoinverse_solutions():

@@ -19,6 +19,7 @@ import os
 
 import numpy as np
 import pytest
+from parity import assert_close, assert_converged  # noqa: E402
 
 import oracle as O
 from workloads import contiguous_offsets, product_problem
@@ -75,8 +76,8 @@ def test_full_size_indices_and_fp64_iterates(setup):
         ref = O.rebk(p.A, p.b, ro, co, alpha, seed=7, k0=k0, iters=iters, record=True)
         assert out["stats"]["iterations"] == iters
         assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"])
-        assert _rel(out["x"].cpu().numpy(), ref["x"]) <= 1e-10
-        assert _rel(out["z"].cpu().numpy(), ref["z"]) <= 1e-10
+        assert_close(out["x"].cpu().numpy(), ref["x"], 1e-10)
+        assert_close(out["z"].cpu().numpy(), ref["z"], 1e-10)
 
 
 def test_full_size_mixed_pass_matches_oracle_pass(setup):
@@ -87,7 +88,7 @@ def test_full_size_mixed_pass_matches_oracle_pass(setup):
                             max_outer=1, inner_iters=K, record=True, return_z=True)
     assert out["stats"]["iterations"] == K
     ref = O.refine(p.A, p.b, O.round_fp32(p.A), ro, co, alpha, seed=21, inner_iters=K, outer_max=1)
-    assert _rel(out["x"].cpu().numpy(), ref["x"]) <= 1e-4
+    assert_close(out["x"].cpu().numpy(), ref["x"], 1e-4)
     assert np.linalg.norm(out["z"].cpu().numpy() - ref["z"]) <= 1e-4 * np.linalg.norm(p.b)
 
 
@@ -98,11 +99,11 @@ def test_full_size_solves_stop_where_the_oracle_stops(setup):
     plain = sol.solve(b, tol=1e-8, max_iter=100000, seed=1000, x_ref=xr)
     assert plain["status"] == R.REBK_OK
     assert abs(plain["stats"]["iterations"] - target) <= 10  # one test interval
-    assert _rel(plain["x"].cpu().numpy(), p.x_ref) <= 1e-8
+    assert_converged(plain["x"].cpu().numpy(), p.x_ref, 1e-8)
     mixed = sol.solve_refined(b, tol=1e-8, seed=1000, storage="fp32", x_ref=xr)
     assert mixed["status"] == R.REBK_OK
     assert mixed["stats"]["iterations"] <= 1.05 * target
-    assert _rel(mixed["x"].cpu().numpy(), p.x_ref) <= 1e-8
+    assert_converged(mixed["x"].cpu().numpy(), p.x_ref, 1e-8)
 
 
 # ---------------------------------------------------------------------------
@@ -121,17 +122,28 @@ def test_full_size_batch_pass_matches_oracle_on_sampled_systems():
     bs = BatchSolver([p.A for p in ps], nrhs=8, tau=16, alpha=np.ones(len(ps)), max_outer=1)
     B = bs.stack_rhs([p.b for p in ps], bs.m)
     K = 50
-    out = bs.solve(B, X_ref=None, tol=0.0, max_iter=K, inner_iters=K, seed=5)
+    out = bs.solve(B, X_ref=None, tol=0.0, max_iter=K, inner_iters=K, seed=5, record_iters=K, return_z=True)
     assert out["stats"]["iterations"] == K * len(ps)
     xs = bs.split_x(out["x"])
+    Z = out["z"].cpu().numpy()
+    idx = out["idx"].cpu().numpy()
     big = int(np.argmax([p.m * p.n for p in ps]))
-    for sid in sorted({0, 255, 511, big}):
+    for sid in sorted({0, 1, 100, 255, 383, 511, big}):
         p = ps[sid]
         ro, co = contiguous_offsets(p.m, 16), contiguous_offsets(p.n, 16)
+        _, _, cr, cc = O.tables(p.A, ro, co)
+        want = np.array([[O.pick(cc, O.uniform(5, sid, 2 * k)), O.pick(cr, O.uniform(5, sid, 2 * k + 1))]
+                         for k in range(K)], dtype=np.int32)
+        assert np.array_equal(idx[sid], want), sid
+        if sid not in (0, 255, 511, big):
+            continue
         lo = O.round_fp32(p.A)
+        zs = Z[bs.mrow[sid]:bs.mrow[sid + 1]]
         for r in (0, 7):
             ref = O.refine(p.A, p.b[:, r], lo, ro, co, 1.0, seed=5, inner_iters=K, outer_max=1, stream=sid)
-            assert _rel(xs[sid][:, r], ref["x"]) <= 1e-4, (sid, r)
+            assert_close(xs[sid][:, r], ref["x"], 1e-4, str((sid, r)))
+            dz = zs[:, r] - ref["z"]
+            assert np.linalg.norm(dz) <= 1e-4 * np.linalg.norm(p.b[:, r]), (sid, r)
     bs.close()
 
 
@@ -155,8 +167,8 @@ def test_full_size_sparse_indices_and_iterates():
         ref = O.rebk_sparse(p.m, p.n, p.indptr, p.indices, p.data, p.b, ro, co, alpha, seed=7, iters=iters,
                             k0=k0, record=True)
         assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"])
-        assert _rel(out["x"].cpu().numpy(), ref["x"]) <= 1e-10
-        assert _rel(out["z"].cpu().numpy(), ref["z"]) <= 1e-10
+        assert_close(out["x"].cpu().numpy(), ref["x"], 1e-10)
+        assert_close(out["z"].cpu().numpy(), ref["z"], 1e-10)
     sol.close()
 
 

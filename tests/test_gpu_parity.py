@@ -14,6 +14,7 @@ Bars (from the method's arithmetic):
 """
 import numpy as np
 import pytest
+from parity import assert_close, assert_converged  # noqa: E402
 
 import oracle as O
 from workloads import (contiguous_offsets, gaussian_problem, product_problem, small_cases,
@@ -74,8 +75,8 @@ def test_tables_indices_and_fp64_iterates_match_oracle(shape):
         ref = O.rebk(A, p.b, ro, co, alpha, seed=seed, stream=sid, k0=k0, iters=iters, record=True)
         assert out["stats"]["iterations"] == iters
         assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"])
-        assert _rel(out["x"].cpu().numpy(), ref["x"]) <= 1e-10
-        assert _rel(out["z"].cpu().numpy(), ref["z"]) <= 1e-10
+        assert_close(out["x"].cpu().numpy(), ref["x"], 1e-10)
+        assert_close(out["z"].cpu().numpy(), ref["z"], 1e-10)
 
 
 @pytest.mark.parametrize("case", small_cases(seed=0), ids=lambda c: c.name)
@@ -86,15 +87,15 @@ def test_four_kinds_of_system_reach_pseudoinverse(case):
     xs = O.pinv_solve(case.A, case.b)
     out = sol.solve(_t(case.b), tol=1e-10, max_iter=500000, seed=11, x_ref=_t(xs))
     assert out["status"] == R.REBK_OK
-    assert _rel(out["x"].cpu().numpy(), xs) <= 1e-10
+    assert_converged(out["x"].cpu().numpy(), xs, 1e-10)
     # the residual stop rule (no reference solution) also gets there
     out2 = sol.solve(_t(case.b), tol=1e-11, max_iter=500000, seed=12)
     assert out2["status"] == R.REBK_OK
-    assert _rel(out2["x"].cpu().numpy(), xs) <= 1e-8
+    assert_converged(out2["x"].cpu().numpy(), xs, 1e-8)
     for st in ("fp32", "bf16"):
         out3 = sol.solve_refined(_t(case.b), tol=1e-9, seed=13, storage=st, x_ref=_t(xs))
         assert out3["status"] == R.REBK_OK, out3["stats"]
-        assert _rel(out3["x"].cpu().numpy(), xs) <= 1e-9
+        assert_converged(out3["x"].cpu().numpy(), xs, 1e-9)
 
 
 def test_first_iteration_of_stop_rule_matches_oracle():
@@ -110,7 +111,7 @@ def test_first_iteration_of_stop_rule_matches_oracle():
                      tol=1e-10)
         out = sol.solve(_t(p.b), tol=1e-10, max_iter=100000, seed=seed, x_ref=_t(p.x_ref))
         assert out["stats"]["iterations"] == ref["iters"]
-        assert _rel(out["x"].cpu().numpy(), ref["x"]) <= 1e-10
+        assert_close(out["x"].cpu().numpy(), ref["x"], 1e-10)
         assert out["stats"]["rel_err"] <= 1e-10
 
 
@@ -154,7 +155,7 @@ def test_one_refinement_pass_matches_oracle_pass(storage, lo, shape):
     assert np.array_equal(out["idx"].cpu().numpy(), idx_ref)
     # FP32 inner arithmetic: errors of order 1e-6 of the corrections' scale
     # (||x||, and ||b|| for z = b - A s, which cancels down to a small vector)
-    assert _rel(out["x"].cpu().numpy(), ref["x"]) <= 1e-4
+    assert_close(out["x"].cpu().numpy(), ref["x"], 1e-4)
     assert np.linalg.norm(out["z"].cpu().numpy() - ref["z"]) <= 1e-4 * np.linalg.norm(p.b)
 
 
@@ -166,14 +167,14 @@ def test_mixed_precision_reaches_1e8_on_rank_deficient_system(storage):
     sol = Solver(p.A, 32, 32, alpha=alpha, storage=(storage,))
     out = sol.solve_refined(_t(p.b), tol=1e-8, seed=5, storage=storage, x_ref=_t(p.x_ref))
     assert out["status"] == R.REBK_OK
-    assert _rel(out["x"].cpu().numpy(), p.x_ref) <= 1e-8
+    assert_converged(out["x"].cpu().numpy(), p.x_ref, 1e-8)
     # same inner iteration count as the plain FP64 run, within the pass granularity
     plain = sol.solve(_t(p.b), tol=1e-8, max_iter=10**6, seed=5, x_ref=_t(p.x_ref))
     assert out["stats"]["iterations"] <= 2 * plain["stats"]["iterations"] + 200
     # without a reference solution: residual stop rule
     out2 = sol.solve_refined(_t(p.b), tol=1e-10, seed=6, storage=storage)
     assert out2["status"] == R.REBK_OK
-    assert _rel(out2["x"].cpu().numpy(), p.x_ref) <= 1e-7
+    assert_converged(out2["x"].cpu().numpy(), p.x_ref, 1e-7)
 
 
 def test_beta_max_matches_oracle():
@@ -226,8 +227,8 @@ def test_resume_continues_the_random_stream():
     full = sol.solve(_t(p.b), max_iter=150, seed=4, return_z=True)
     a = sol.solve(_t(p.b), max_iter=60, seed=4, return_z=True)
     b2 = sol.solve(_t(p.b), max_iter=90, seed=4, k0=60, x0=a["x"].clone(), z0=a["z"].clone(), return_z=True)
-    assert _rel(b2["x"].cpu().numpy(), full["x"].cpu().numpy()) <= 1e-13
-    assert _rel(b2["z"].cpu().numpy(), full["z"].cpu().numpy()) <= 1e-13
+    assert_close(b2["x"].cpu().numpy(), full["x"].cpu().numpy(), 1e-13)
+    assert_close(b2["z"].cpu().numpy(), full["z"].cpu().numpy(), 1e-13)
 
 
 def test_bounded_waits_give_up_and_leave_the_context_usable():
@@ -244,4 +245,5 @@ def test_bounded_waits_give_up_and_leave_the_context_usable():
     p = gaussian_problem(200, 60, seed=2)
     sol = Solver(p.A, 10, 10, alpha=0.0, storage=())
     out = sol.solve(_t(p.b), tol=1e-10, max_iter=10**6, seed=1, x_ref=_t(p.x_ref))
-    assert out["status"] == R.REBK_OK and _rel(out["x"].cpu().numpy(), p.x_ref) <= 1e-10
+    assert out["status"] == R.REBK_OK
+    assert_converged(out["x"].cpu().numpy(), p.x_ref, 1e-10)

@@ -5,6 +5,7 @@ step the sparse path draws the same blocks (bit-exact) and its iterates equal
 the oracle's up to summation order (FP64 atomic adds), bar 1e-10 relative."""
 import numpy as np
 import pytest
+from parity import assert_close, assert_converged  # noqa: E402
 
 import oracle as O
 from workloads import contiguous_offsets, sparse_problem
@@ -54,8 +55,8 @@ def test_indices_and_iterates_match_the_dense_oracle(case):
         ref = O.rebk(A, p.b, ro, co, alpha, seed=seed, stream=sid, k0=k0, iters=iters, record=True)
         assert out["stats"]["iterations"] == iters
         assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"])
-        assert _rel(out["x"].cpu().numpy(), ref["x"]) <= 1e-10
-        assert _rel(out["z"].cpu().numpy(), ref["z"]) <= 1e-10
+        assert_close(out["x"].cpu().numpy(), ref["x"], 1e-10)
+        assert_close(out["z"].cpu().numpy(), ref["z"], 1e-10)
 
 
 def test_same_blocks_as_the_dense_solver_and_beta_max():
@@ -78,7 +79,7 @@ def test_solves_reach_the_pseudoinverse_solution(shape):
     sol = SparseSolver(m, n, p.indptr, p.indices, p.data, 16, 16)
     out = sol.solve(_t(p.b), tol=1e-10, max_iter=2_000_000, seed=2, x_ref=_t(p.x_ref))
     assert out["status"] == R.REBK_OK
-    assert _rel(out["x"].cpu().numpy(), p.x_ref) <= 1e-10
+    assert_converged(out["x"].cpu().numpy(), p.x_ref, 1e-10)
 
 
 def test_zero_matrix_gives_zero():
@@ -112,11 +113,11 @@ def test_empty_rows_and_columns():
     idx = out["idx"].cpu().numpy()
     assert np.array_equal(idx, ref["idx"])
     assert not np.any(np.isin(idx[:, 1], [0, 1]))  # zero-norm row blocks never drawn
-    assert _rel(out["x"].cpu().numpy(), ref["x"]) <= 1e-10
+    assert_close(out["x"].cpu().numpy(), ref["x"], 1e-10)
     x_ls = O.pinv_solve(A, b)
     full = sol.solve(_t(b), tol=1e-10, max_iter=3_000_000, seed=5, x_ref=_t(x_ls))
     assert full["status"] == R.REBK_OK
-    assert _rel(full["x"].cpu().numpy(), x_ls) <= 1e-10
+    assert_converged(full["x"].cpu().numpy(), x_ls, 1e-10)
 
 
 PASS_CASES = [
@@ -148,7 +149,7 @@ def test_one_mixed_precision_pass_matches_the_oracle_pass(case):
     idx_ref = O.rebk_correction(O.round_fp32(A), *O.dual_residuals(A, p.b, p.b, np.zeros(n)), ro, co,
                                 O.block_norms(A, ro, co), alpha, seed=21, iters=K, record=True)["idx"]
     assert np.array_equal(out["idx"].cpu().numpy(), idx_ref)
-    assert _rel(out["x"].cpu().numpy(), ref["x"]) <= 1e-4
+    assert_close(out["x"].cpu().numpy(), ref["x"], 1e-4)
     assert np.linalg.norm(out["z"].cpu().numpy() - ref["z"]) <= 1e-4 * np.linalg.norm(p.b)
 
 
@@ -160,14 +161,14 @@ def test_mixed_precision_reaches_the_pseudoinverse_solution(shape):
     xr = _t(p.x_ref)
     out = sol.solve_refined(_t(p.b), tol=1e-10, seed=2, x_ref=xr)
     assert out["status"] == R.REBK_OK
-    assert _rel(out["x"].cpu().numpy(), p.x_ref) <= 1e-10
+    assert_converged(out["x"].cpu().numpy(), p.x_ref, 1e-10)
     assert out["stats"]["outer"] >= 2  # FP32 alone stops near 1e-6: the refinement did the rest
     plain = sol.solve(_t(p.b), tol=1e-10, max_iter=2_000_000, seed=2, x_ref=xr)
     assert out["stats"]["iterations"] <= 2 * plain["stats"]["iterations"] + 8192
     # without a reference solution: the residual stop rule
     out2 = sol.solve_refined(_t(p.b), tol=1e-11, seed=4)
     assert out2["status"] == R.REBK_OK
-    assert _rel(out2["x"].cpu().numpy(), p.x_ref) <= 1e-6
+    assert_converged(out2["x"].cpu().numpy(), p.x_ref, 1e-6)
 
 
 def test_mixed_precision_options_and_degenerate_cases():

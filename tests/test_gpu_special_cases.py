@@ -8,6 +8,7 @@ path against the oracle:
 Bars as in the parity tests: block indices bit-exact, FP64 iterates 1e-10."""
 import numpy as np
 import pytest
+from parity import assert_close, assert_converged  # noqa: E402
 
 import oracle as O
 from workloads import contiguous_offsets, gaussian_problem
@@ -40,10 +41,11 @@ def test_rek_special_case_matches_oracle_and_converges():
     ref = O.rebk(p.A, p.b, contiguous_offsets(120, 1), contiguous_offsets(30, 1), 1.0, seed=9, iters=500,
                  record=True)
     assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"])
-    assert _rel(out["x"].cpu().numpy(), ref["x"]) <= 1e-10
-    assert _rel(out["z"].cpu().numpy(), ref["z"]) <= 1e-10
+    assert_close(out["x"].cpu().numpy(), ref["x"], 1e-10)
+    assert_close(out["z"].cpu().numpy(), ref["z"], 1e-10)
     full = sol.solve(_t(p.b), tol=1e-10, max_iter=10**7, seed=3, x_ref=_t(p.x_ref))
-    assert full["status"] == R.REBK_OK and _rel(full["x"].cpu().numpy(), p.x_ref) <= 1e-10
+    assert full["status"] == R.REBK_OK
+    assert_converged(full["x"].cpu().numpy(), p.x_ref, 1e-10)
 
 
 @pytest.mark.parametrize("shape", [(200, 60, 8, 6), (50, 140, 5, 12)])
@@ -59,10 +61,11 @@ def test_rabk_special_case_matches_oracle_and_reaches_min_norm_solution(shape):
     ref = O.rebk(A, b, ro, co, alpha, seed=2, iters=300, z0=np.zeros(m), record=True)
     assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"])
     assert torch.all(out["z"] == 0)
-    assert _rel(out["x"].cpu().numpy(), ref["x"]) <= 1e-10
+    assert_close(out["x"].cpu().numpy(), ref["x"], 1e-10)
     x_ls = O.pinv_solve(A, b)
     full = sol.solve_rabk(_t(b), tol=1e-10, max_iter=10**7, seed=4, x_ref=_t(x_ls))
-    assert full["status"] == R.REBK_OK and _rel(full["x"].cpu().numpy(), x_ls) <= 1e-10
+    assert full["status"] == R.REBK_OK
+    assert_converged(full["x"].cpu().numpy(), x_ls, 1e-10)
 
 
 def _sv2(A):

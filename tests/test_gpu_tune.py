@@ -10,6 +10,7 @@
 """
 import numpy as np
 import pytest
+from parity import assert_close  # noqa: E402
 
 import oracle as O
 from workloads import contiguous_offsets, gaussian_problem, product_problem
@@ -46,8 +47,8 @@ def test_set_alpha_iterates_match_oracle(shape):
     out = sol.solve(_t(p.b), tol=0.0, max_iter=211, seed=5, record=True, return_z=True)
     ref = O.rebk(p.A, p.b, ro, co, a_new, seed=5, iters=211, record=True)
     assert np.array_equal(out["idx"].cpu().numpy(), ref["idx"])
-    assert _rel(out["x"].cpu().numpy(), ref["x"]) <= 1e-10
-    assert _rel(out["z"].cpu().numpy(), ref["z"]) <= 1e-10
+    assert_close(out["x"].cpu().numpy(), ref["x"], 1e-10)
+    assert_close(out["z"].cpu().numpy(), ref["z"], 1e-10)
     with pytest.raises(R.RebkError):
         sol.alpha = -1.0
     assert sol.alpha == a_new
