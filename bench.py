@@ -47,7 +47,9 @@ def parse():
                     help="with --profile-pass K: run K iterations of the plain FP64 kernel instead")
     ap.add_argument("--storage", choices=["fp32", "bf16"], default="fp32")
     ap.add_argument("--plain-steps", type=int, default=2)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--cpu-seconds", type=float, default=8.0, help="oracle sample per CPU build (seconds)")
+    ap.add_argument("--residual-steps", type=int, default=2,
+                    help="mixed solves timed with the residual stop rule (no known solution)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", choices=["precision", "warm", "batch", "sparse", "sweep"], default="precision",
                     help="precision: the headline solve (default); warm: the learned warm start "
@@ -112,22 +114,41 @@ def load_anchor():
     return out
 
 
-def load_traffic(kernel_tag: str):
-    """DRAM bytes per iteration of the headline kernel from the committed ncu
-    summary, only if it was taken on the current kernel source."""
+# DRAM traffic per iteration of the dominant kernel, from an ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of one profiled pass, divided by
+# its iterations; the capture and its command are summarised in
+# profiles/rebk_grid_precision_8000x20000.md).  Keyed by the kernel's
+# storage form and the source hash of rebk_grid.cu it was taken on: a changed
+# kernel reports null until it is captured again.
+KERNEL_TRAFFIC = {}
+
+
+def kernel_traffic(kernel_tag: str):
+    """(DRAM bytes per iteration, provenance) of the headline kernel, or (None, why)."""
     import hashlib
     src = os.path.join(ROOT, "paper_2001_04179_gb300", "csrc", "rebk_grid.cu")
     sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-    path = os.path.join(ROOT, "profiles", "rebk_grid_precision_8000x20000.md")
-    if not os.path.exists(path):
-        return None
-    for line in open(path):
-        if line.startswith("traffic:"):
-            # traffic: <tag> <source sha> <dram bytes per iteration>
-            parts = line.split()
-            if len(parts) == 4 and parts[1] == kernel_tag and parts[2] == sha:
-                return float(parts[3])
-    return None
+    rec = KERNEL_TRAFFIC.get(kernel_tag)
+    if rec is None or rec["source_sha"] != sha:
+        return None, f"no ncu capture of the current kernel source ({sha})"
+    return rec["dram_bytes_per_iteration"], rec["from"]
+
+
+def cpu_model() -> str:
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith(("model name", "cpu part")):
+                return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def make_problem(seed: int, use_gpu: bool):
@@ -202,27 +223,57 @@ class ClockSampler:
                 "samples": len(sm), "reasons": sorted(reasons)}
 
 
-def cpu_baseline(prob, alpha, iters_per_solve, seconds, source):
-    """The oracle (plain FP64 Algorithm 1, single thread) on a bounded number
-    of iterations of the same workload; solves/s = iterations/s divided by
-    the iterations one solve needs."""
+ORACLE_BUILDS = {
+    "parity": ("C -O2 -ffp-contract=off, the parity build the tests use", 1),
+    "fast": ("C -O3 -ffp-contract=fast (FMA contraction; generic target, no -march flag: the host code "
+             "builds the same on x86-64 and Arm)", 1),
+    "omp": ("C -O3 -ffp-contract=fast -fopenmp, block products split over all host threads", None),
+}
+
+
+def time_oracle(prob, alpha, seconds, variant, seed=1000):
+    """Iterations/s of the oracle's Algorithm 1 (build `variant`) on the workload,
+    over a bounded sample of about `seconds`."""
     import oracle as O
     from workloads import contiguous_offsets
     ro, co = contiguous_offsets(M, TAU), contiguous_offsets(N, TAU)
     norms = O.block_norms(prob.A, ro, co)
+    O.rebk(prob.A, prob.b, ro, co, alpha, seed=seed, iters=2, norms=norms, variant=variant)  # load, threads up
     t0 = time.perf_counter()
-    O.rebk(prob.A, prob.b, ro, co, alpha, seed=1000, iters=3, norms=norms)
-    per = (time.perf_counter() - t0) / 3
+    O.rebk(prob.A, prob.b, ro, co, alpha, seed=seed, iters=8, norms=norms, variant=variant)
+    per = (time.perf_counter() - t0) / 8
     n_it = max(5, int(seconds / max(per, 1e-6)))
     t0 = time.perf_counter()
-    O.rebk(prob.A, prob.b, ro, co, alpha, seed=1000, iters=n_it, norms=norms)
+    O.rebk(prob.A, prob.b, ro, co, alpha, seed=seed, iters=n_it, norms=norms, variant=variant)
     dt = time.perf_counter() - t0
-    its = n_it / dt
-    return {"value": its / iters_per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle",
-            "iterations_per_s": its,
-            "sample": (f"{n_it} iterations of the FP64 oracle (C, -O2, no FMA contraction) of Algorithm 1 "
-                       f"on this workload in {dt:.1f} s; solves/s = iterations/s / {iters_per_solve:.0f} "
-                       f"iterations per solve ({source})")}
+    return n_it / dt, n_it, dt
+
+
+def cpu_baseline(prob, alpha, iters_per_solve, seconds, source):
+    """The oracle (plain FP64 Algorithm 1) on the host cores: the parity build
+    and an -O3 build on one thread, and the OpenMP build on all host threads,
+    each on a bounded sample of iterations of the same workload; solves/s =
+    iterations/s divided by the iterations one solve needs.  The line's value is
+    the fastest build's."""
+    cores = os.cpu_count() or 1
+    builds = {}
+    for variant, (desc, threads) in ORACLE_BUILDS.items():
+        try:
+            its, n_it, dt = time_oracle(prob, alpha, seconds, variant)
+        except Exception as exc:  # an OpenMP runtime missing on the host, say
+            builds[variant] = {"unavailable": f"{type(exc).__name__}: {exc}"[:200]}
+            continue
+        builds[variant] = {"value": its / iters_per_solve, "unit": "solves/s", "iterations_per_s": its,
+                           "threads": threads or int(os.environ.get("OMP_NUM_THREADS", cores)),
+                           "build": desc, "sample": f"{n_it} iterations in {dt:.1f} s"}
+    ok = {k: v for k, v in builds.items() if "value" in v}
+    best = max(ok, key=lambda k: ok[k]["value"])
+    return {"value": ok[best]["value"], "unit": "solves/s", "cores": ok[best]["threads"], "kind": "oracle",
+            "iterations_per_s": ok[best]["iterations_per_s"], "build": best,
+            "host_cores": cores, "cpu_model": cpu_model(), "builds": builds,
+            "sample": (f"the FP64 oracle of Algorithm 1 on this workload, about {seconds:.0f} s of iterations "
+                       f"per build; solves/s = iterations/s / {iters_per_solve:.0f} iterations per solve "
+                       f"({source})")}
 
 
 def run_reference(args):
@@ -247,28 +298,37 @@ def run_reference(args):
     from workloads import contiguous_offsets
     ro, co = contiguous_offsets(M, TAU), contiguous_offsets(N, TAU)
     norms = O.block_norms(prob.A, ro, co)
+    variant = "omp"
+    try:
+        O.lib(variant)
+    except Exception:  # no OpenMP runtime on this host: the single-thread -O3 build
+        variant = "fast"
+    cores = os.cpu_count() or 1
+    threads = int(os.environ.get("OMP_NUM_THREADS", cores)) if variant == "omp" else 1
     # each step: a bounded sample of ~3 s of oracle iterations
+    O.rebk(prob.A, prob.b, ro, co, alpha, seed=1000, iters=2, norms=norms, variant=variant)  # load, threads up
     t0 = time.perf_counter()
-    O.rebk(prob.A, prob.b, ro, co, alpha, seed=1000, iters=2, norms=norms)
-    per = (time.perf_counter() - t0) / 2
+    O.rebk(prob.A, prob.b, ro, co, alpha, seed=1000, iters=8, norms=norms, variant=variant)
+    per = (time.perf_counter() - t0) / 8
     n_it = max(3, int(3.0 / max(per, 1e-6)))
     for _ in range(args.warmup):
-        O.rebk(prob.A, prob.b, ro, co, alpha, seed=1000, iters=max(1, n_it // 10), norms=norms)
+        O.rebk(prob.A, prob.b, ro, co, alpha, seed=1000, iters=max(1, n_it // 10), norms=norms, variant=variant)
     t0 = time.perf_counter()
     for s in range(args.steps):
-        O.rebk(prob.A, prob.b, ro, co, alpha, seed=1000 + s, iters=n_it, norms=norms)
+        O.rebk(prob.A, prob.b, ro, co, alpha, seed=1000 + s, iters=n_it, norms=norms, variant=variant)
     dt = time.perf_counter() - t0
     its = args.steps * n_it / dt
     value = its / ipsolve
-    sample = (f"per step {n_it} iterations of the FP64 oracle of Algorithm 1 on this workload; "
-              f"solves/s = iterations/s / {ipsolve:.0f} iterations per solve "
+    sample = (f"per step {n_it} iterations of the FP64 oracle of Algorithm 1 on this workload "
+              f"({ORACLE_BUILDS[variant][0]}); solves/s = iterations/s / {ipsolve:.0f} iterations per solve "
               f"(oracle's own count to 1e-8, tests/golden/precision_anchor.txt)")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000.0 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "tau": TAU, "alpha": alpha},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
-                             "sample": sample, "iterations_per_s": its},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": threads, "kind": "oracle",
+                             "sample": sample, "iterations_per_s": its, "build": variant,
+                             "host_cores": cores, "cpu_model": cpu_model()},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -765,6 +825,11 @@ def main():
         torch.cuda.synchronize()
 
     hbm_peak, bf16_peak, peak_src = load_peaks()
+    from paper_2001_04179_gb300 import rebk as _R
+    import ctypes as _ct
+    dev_peaks = _R.RebkPeaks()
+    _R.check(_R.load().rebk_device_peaks(_ct.byref(dev_peaks), None))
+    dev_peaks = dev_peaks.as_dict()
     prob = make_problem(rank, True)
     stream = torch.cuda.current_stream()
     A_dev = torch.from_numpy(prob.A).to(dev)
@@ -854,24 +919,51 @@ def main():
         pms = p_ev0.elapsed_time(p_ev1) / args.plain_steps
         it = pagg["iterations"] / args.plain_steps
         flops = 4.0 * TAU * (M + N) * pagg["iterations"]
+        fp64_rate = flops / (pagg["kernel_ms"] / 1000.0) / 1e12
+        fp64_peak = dev_peaks["fp64_tflops"]
         plain = {"value": 1000.0 / pms, "unit": "solves/s", "ms_per_solve": pms, "iterations_per_solve": it,
                  "block_iterations_per_s": pagg["iterations"] / (pagg["kernel_ms"] / 1000.0),
-                 "roofline": {"bound": "alu", "achieved": flops / (pagg["kernel_ms"] / 1000.0) / 1e12,
-                              "peak": 1.25, "unit": "TFLOP/s",
-                              "frac": flops / (pagg["kernel_ms"] / 1000.0) / 1e12 / 1.25,
-                              "peak_source": "nominal GB300 FP64 rate (recipe table); FP64 FMA pipe",
-                              "hbm_gbs": 8.0 * TAU * (M + N) * pagg["iterations"] / (pagg["kernel_ms"] / 1000.0) / 1e9}}
+                 "roofline": {"bound": "alu", "achieved": fp64_rate, "peak": fp64_peak, "unit": "TFLOP/s",
+                              "frac": fp64_rate / fp64_peak,
+                              "peak_source": ("measured: rebk_device_peaks FP64 FMA kernel on this GPU "
+                                              f"(SM clock {dev_peaks['sm_mhz']:.0f} MHz during it)"),
+                              "hbm_gbs": 8.0 * TAU * (M + N) * pagg["iterations"] / (pagg["kernel_ms"] / 1000.0) / 1e9,
+                              "hbm_frac": 8.0 * TAU * (M + N) * pagg["iterations"] / (pagg["kernel_ms"] / 1000.0)
+                              / 1e9 / hbm_peak}}
+
+    # ---------------- residual stop rule: solves without the known solution ----------------
+    resid = None
+    if args.residual_steps > 0:
+        r_ev0, r_ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        errs, its_r = [], 0
+        xs_r = []
+        r_ev0.record(stream)
+        for s in range(args.residual_steps):
+            r = sol.solve_refined(b, tol=TOL, seed=3000 + s, storage=S)
+            its_r += r["stats"]["iterations"]
+            xs_r.append(r["x"])
+        r_ev1.record(stream)
+        torch.cuda.synchronize()
+        for x_ in xs_r:
+            errs.append(float((x_ - xr).norm() / xr.norm()))
+        rms = r_ev0.elapsed_time(r_ev1) / args.residual_steps
+        resid = {"value": 1000.0 / rms, "unit": "solves/s", "ms_per_solve": rms,
+                 "iterations_per_solve": its_r / args.residual_steps, "rel_err_max": max(errs),
+                 "rule": "max(||b - z - A x|| / ||b||, ||A^T z|| / (||A||_F ||b||)) <= 1e-8 after each "
+                         "refinement pass (no x_ref); rel_err_max is the error against A^+ b measured afterwards"}
 
     # ---------------- roofline of the dominant kernel ----------------
     esize = {"fp32": 4, "bf16": 2}[S]
     bytes_per_iter = float(TAU * N + TAU * M) * esize
     kernel_s = agg["kernel_ms"] / 1000.0
     achieved = bytes_per_iter * agg["iterations"] / kernel_s / 1e9
-    traffic_per_iter = load_traffic(f"corr_{S}")
+    traffic_per_iter, traffic_src = kernel_traffic(f"corr_{S}")
     per_launch_iters = agg["iterations"] / max(agg["grid_launches"], 1)
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
             "frac": achieved / hbm_peak, "peak_source": peak_src,
             "traffic": None if traffic_per_iter is None else traffic_per_iter * per_launch_iters,
+            "traffic_source": traffic_src + ("" if traffic_per_iter is None else
+                                             "; per-iteration DRAM bytes scaled to this run's iterations per launch"),
             "algorithmic_bytes_per_launch": bytes_per_iter * per_launch_iters,
             "kernel": f"rebk_grid_kernel<{ 'float' if S == 'fp32' else '__nv_bfloat16' },float,corr>",
             "kernel_share_of_step": kernel_s / (ms_max / 1000.0),
@@ -907,6 +999,8 @@ def main():
             "clocks": clk,
             "plain_fp64": plain,
             "speedup_vs_plain_fp64": None if plain is None else value / plain["value"],
+            "residual_rule": resid,
+            "device_peaks": dev_peaks,
         }
         print(json.dumps(line))
     if world > 1:

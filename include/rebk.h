@@ -575,6 +575,27 @@ rebk_status rebk_sparse_info(rebk_sparse h, double *alpha, double *beta_max, int
  */
 rebk_status rebk_selftest_waits(int64_t timeout_ns, int32_t *codes, double *elapsed_ms);
 
+/* Device rates measured by rebk_device_peaks. */
+typedef struct {
+    double fp64_tflops;  /* FP64 FMA rate (2 FLOPs per FMA), best of 3 launches      */
+    double fp64_ms;      /* duration of that launch                                   */
+    double sm_mhz;       /* SM clock during it (clock64 cycles / global-timer time)   */
+    double l2_gbs;       /* L2 read bandwidth (16-byte loads that bypass L1)          */
+    double l2_ms;        /* duration of the best L2 launch                            */
+    double l2_bytes;     /* size of the buffer read (it fits in L2), read 8 times     */
+} rebk_peaks;
+
+/*
+ * Measures the two rates the REBK paths are bounded by besides HBM bandwidth:
+ * the FP64 FMA rate (the plain FP64 path does one FMA per block element it
+ * loads) and the L2 read bandwidth (the sparse path's working set stays in
+ * L2).  The paper has no counterpart; the numbers serve as roofline peaks.
+ * Kernels run on stream (cudaStream_t, NULL = legacy default) and are timed
+ * with CUDA events; the call allocates 48 MiB and synchronises.
+ * Errors: EINVAL (out NULL), ENOMEM, ECUDA.
+ */
+rebk_status rebk_device_peaks(rebk_peaks *out, void *stream);
+
 /* Message for the last failed call on this thread ("" if none). */
 const char *rebk_last_error(void);
 

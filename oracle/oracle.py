@@ -53,53 +53,77 @@ _i32p = ctypes.POINTER(ctypes.c_int32)
 _u64p = ctypes.POINTER(ctypes.c_uint64)
 
 
-def build_oracle(force: bool = False) -> str:
-    """Compile rebk_oracle.c with gcc (no FMA contraction) into _build/liborc.so."""
+# Builds of the same C file.  "parity" is the reference every test uses (no FMA
+# contraction).  The other two exist only to time the oracle as a CPU baseline:
+# "fast" lets the compiler contract products into FMAs at -O3; "omp" adds
+# -fopenmp, which splits the block products over all host threads (the pragmas
+# in rebk_oracle.c keep each value's summation order).  Host code here is
+# built for the generic target of the machine's compiler (no -march flag), so
+# the same commands work on x86-64 and on Arm.
+_VARIANTS = {
+    "parity": (["-O2", "-ffp-contract=off", "-fno-fast-math"], "liborc.so"),
+    "fast": (["-O3", "-ffp-contract=fast"], "liborc_fast.so"),
+    "omp": (["-O3", "-ffp-contract=fast", "-fopenmp"], "liborc_omp.so"),
+}
+
+
+def build_oracle(force: bool = False, variant: str = "parity") -> str:
+    """Compile rebk_oracle.c with gcc into _build/<lib>.so (see _VARIANTS)."""
+    flags, name = _VARIANTS[variant]
+    so = os.path.join(_BUILD, name)
     os.makedirs(_BUILD, exist_ok=True)
-    if force or not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(_SRC):
-        tmp = _SO + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math",
-               "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
+    if force or not os.path.exists(so) or os.path.getmtime(so) < os.path.getmtime(_SRC):
+        tmp = so + f".tmp{os.getpid()}"
+        cmd = ["gcc"] + flags + ["-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, _SO)
-    return _SO
+        os.replace(tmp, so)
+    return so
 
 
-def lib():
+_variant_libs = {}
+
+
+def _declare(L):
+    L.orc_philox4x64_10.argtypes = [_u64p, _u64p, _u64p]
+    L.orc_philox4x64_10.restype = None
+    L.orc_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
+    L.orc_uniform.restype = ctypes.c_double
+    L.orc_pick.argtypes = [_f64p, ctypes.c_int64, ctypes.c_double]
+    L.orc_pick.restype = ctypes.c_int64
+    L.orc_block_norms.argtypes = [ctypes.c_int64, ctypes.c_int64, _f64p, ctypes.c_int64,
+                                  ctypes.c_int64, _i64p, ctypes.c_int64, _i64p, _f64p, _f64p]
+    L.orc_block_norms.restype = None
+    L.orc_cdf.argtypes = [_f64p, ctypes.c_int64, _f64p]
+    L.orc_cdf.restype = None
+    L.orc_rebk.argtypes = [ctypes.c_int64, ctypes.c_int64, _f64p, ctypes.c_int64,
+                           ctypes.c_int64, _i64p, ctypes.c_int64, _i64p,
+                           _f64p, _f64p, _f64p, _f64p,
+                           ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                           _f64p, _f64p, _f64p,
+                           ctypes.c_int64, ctypes.c_int64, _f64p, ctypes.c_double,
+                           _i32p, _f64p]
+    L.orc_rebk.restype = ctypes.c_int64
+    L.orc_rebk_correction.argtypes = [ctypes.c_int64, ctypes.c_int64, _f64p, ctypes.c_int64,
+                                      ctypes.c_int64, _i64p, ctypes.c_int64, _i64p,
+                                      _f64p, _f64p, _f64p, _f64p,
+                                      ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                      _f64p, _f64p, _f64p, _f64p, _f64p, _f64p,
+                                      ctypes.c_int64, ctypes.c_int64, _f64p, _f64p, ctypes.c_double,
+                                      _i32p, _f64p]
+    L.orc_rebk_correction.restype = ctypes.c_int64
+    return L
+
+
+def lib(variant: str = "parity"):
     global _lib
     with _lock:
-        if _lib is None:
-            so = build_oracle()
-            L = ctypes.CDLL(so)
-            L.orc_philox4x64_10.argtypes = [_u64p, _u64p, _u64p]
-            L.orc_philox4x64_10.restype = None
-            L.orc_uniform.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
-            L.orc_uniform.restype = ctypes.c_double
-            L.orc_pick.argtypes = [_f64p, ctypes.c_int64, ctypes.c_double]
-            L.orc_pick.restype = ctypes.c_int64
-            L.orc_block_norms.argtypes = [ctypes.c_int64, ctypes.c_int64, _f64p, ctypes.c_int64,
-                                          ctypes.c_int64, _i64p, ctypes.c_int64, _i64p, _f64p, _f64p]
-            L.orc_block_norms.restype = None
-            L.orc_cdf.argtypes = [_f64p, ctypes.c_int64, _f64p]
-            L.orc_cdf.restype = None
-            L.orc_rebk.argtypes = [ctypes.c_int64, ctypes.c_int64, _f64p, ctypes.c_int64,
-                                   ctypes.c_int64, _i64p, ctypes.c_int64, _i64p,
-                                   _f64p, _f64p, _f64p, _f64p,
-                                   ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
-                                   _f64p, _f64p, _f64p,
-                                   ctypes.c_int64, ctypes.c_int64, _f64p, ctypes.c_double,
-                                   _i32p, _f64p]
-            L.orc_rebk.restype = ctypes.c_int64
-            L.orc_rebk_correction.argtypes = [ctypes.c_int64, ctypes.c_int64, _f64p, ctypes.c_int64,
-                                              ctypes.c_int64, _i64p, ctypes.c_int64, _i64p,
-                                              _f64p, _f64p, _f64p, _f64p,
-                                              ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
-                                              _f64p, _f64p, _f64p, _f64p, _f64p, _f64p,
-                                              ctypes.c_int64, ctypes.c_int64, _f64p, _f64p, ctypes.c_double,
-                                              _i32p, _f64p]
-            L.orc_rebk_correction.restype = ctypes.c_int64
-            _lib = L
-    return _lib
+        if variant == "parity":
+            if _lib is None:
+                _lib = _declare(ctypes.CDLL(build_oracle()))
+            return _lib
+        if variant not in _variant_libs:
+            _variant_libs[variant] = _declare(ctypes.CDLL(build_oracle(variant=variant)))
+        return _variant_libs[variant]
 
 
 def _p(a, t=_f64p):
@@ -165,13 +189,14 @@ def tables(A, row_off, col_off):
 # --------------------------------------------------------------------------
 
 def rebk(A, b, row_off, col_off, alpha, seed, iters, stream=0, k0=0, z0=None, x0=None,
-         check_every=0, x_ref=None, tol=0.0, record=False, norms=None):
+         check_every=0, x_ref=None, tol=0.0, record=False, norms=None, variant="parity"):
     """Run iterations k0+1 .. k0+iters of Algorithm 1.
 
     z0 defaults to b and x0 to 0 (Section 3).  ``norms`` may pass the block
     norms of another matrix (used for the sampling table and the step sizes);
     by default they are those of A.  Returns dict(x, z, iters, idx) where idx
-    is an (iters, 2) array of (j_k, i_k) when ``record``.
+    is an (iters, 2) array of (j_k, i_k) when ``record``.  ``variant`` picks
+    the build (see _VARIANTS; only "parity" is a reference).
     """
     A = _f64(A)
     m, n = A.shape
@@ -188,7 +213,7 @@ def rebk(A, b, row_off, col_off, alpha, seed, iters, stream=0, k0=0, z0=None, x0
     idx = np.zeros((max(iters, 1), 2), dtype=np.int32) if record else None
     xr = None if x_ref is None else _f64(x_ref)
     work = np.zeros(max(np.max(np.diff(ro)), np.max(np.diff(co))) + 1)
-    done = lib().orc_rebk(m, n, _p(A), n, ro.size - 1, _p(ro, _i64p), co.size - 1, _p(co, _i64p),
+    done = lib(variant).orc_rebk(m, n, _p(A), n, ro.size - 1, _p(ro, _i64p), co.size - 1, _p(co, _i64p),
                           _p(nr), _p(nc), _p(cr), _p(cc), float(alpha), seed, stream, k0,
                           _p(b), _p(z), _p(x), iters, check_every, _p(xr), float(tol),
                           _p(idx, _i32p), _p(work))

@@ -24,7 +24,11 @@
  * block is the smallest index whose cumulative norm exceeds u * ||A||_F^2.
  *
  * Built with -ffp-contract=off: every product and every sum is rounded on its
- * own, in natural index order, so the result is a fixed reference.
+ * own, in natural index order, so the result is a fixed reference.  The
+ * OpenMP pragmas below only split loops whose iterations write separate
+ * outputs (one block column, one row, one column each), so a build with
+ * -fopenmp computes every value in the same order as a serial one; they are
+ * ignored without -fopenmp (the parity build).
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -184,12 +188,14 @@ int64_t orc_rebk(int64_t m, int64_t n, const double *A, int64_t lda,
         int64_t c0 = col_off[j], c1 = col_off[j + 1];
         double cJ = alpha / nc[j];
         double *w = work;
+#pragma omp parallel for schedule(static)
         for (int64_t l = c0; l < c1; ++l) {
             double acc = 0.0;
             for (int64_t r = 0; r < m; ++r)
                 acc += A[r * lda + l] * z[r];
             w[l - c0] = acc;
         }
+#pragma omp parallel for schedule(static)
         for (int64_t r = 0; r < m; ++r) {
             double acc = 0.0;
             for (int64_t l = c0; l < c1; ++l)
@@ -202,12 +208,14 @@ int64_t orc_rebk(int64_t m, int64_t n, const double *A, int64_t lda,
         int64_t r0 = row_off[i], r1 = row_off[i + 1];
         double cI = alpha / nr[i];
         double *res = work;
+#pragma omp parallel for schedule(static)
         for (int64_t l = r0; l < r1; ++l) {
             double acc = 0.0;
             for (int64_t c = 0; c < n; ++c)
                 acc += A[l * lda + c] * x[c];
             res[l - r0] = acc - b[l] + z[l];
         }
+#pragma omp parallel for schedule(static)
         for (int64_t c = 0; c < n; ++c) {
             double acc = 0.0;
             for (int64_t l = r0; l < r1; ++l)

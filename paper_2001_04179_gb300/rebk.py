@@ -83,6 +83,14 @@ class RebkBatchStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class RebkPeaks(ctypes.Structure):
+    _fields_ = [("fp64_tflops", ctypes.c_double), ("fp64_ms", ctypes.c_double), ("sm_mhz", ctypes.c_double),
+                ("l2_gbs", ctypes.c_double), ("l2_ms", ctypes.c_double), ("l2_bytes", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class RebkSparseOptions(ctypes.Structure):
     _fields_ = [("num_ctas", ctypes.c_int32), ("check_every", ctypes.c_int32), ("power_iters", ctypes.c_int32),
                 ("stream", ctypes.c_void_p)]
@@ -148,6 +156,7 @@ _SIGNATURES = {
     "rebk_sparse_info": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "rebk_selftest_waits": ([ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "rebk_device_peaks": ([ctypes.POINTER(RebkPeaks), _P], ctypes.c_int),
     "rebk_last_error": ([], ctypes.c_char_p),
     "rebk_version": ([], ctypes.c_char_p),
 }
