@@ -6,8 +6,9 @@
  * solving least squares", arXiv:2001.04179.  The problem statement (Section 1)
  * is A x = b with A any real m x n matrix -- consistent or not, over- or
  * underdetermined, full rank or rank-deficient -- and the target is A^+ b.
- * The iteration is Algorithm 1 (Section 2); partitions are the contiguous
- * equal-size blocks of Section 3 (the last block may be shorter).
+ * The iteration is Algorithm 1 (Section 2) for any row and column partitions
+ * (rebk_partition); the default is the contiguous equal-size blocks of
+ * Section 3 (the last block may be shorter).
  *
  * Conventions for every call below:
  *  - Matrices are row-major FP64 with leading dimension lda >= n (elements).
@@ -56,8 +57,10 @@ typedef enum {
 typedef enum { REBK_FP64 = 0, REBK_FP32 = 1, REBK_BF16 = 2 } rebk_storage;
 
 typedef struct {
-    int64_t tau_row;       /* row block size tau >= 1 (Section 3 partition of [m])     */
-    int64_t tau_col;       /* column block size >= 1 (partition of [n])                */
+    int64_t tau_row;       /* row block size tau >= 1 (Section 3 partition of [m]);
+                              ignored when rebk_partition gives row offsets             */
+    int64_t tau_col;       /* column block size >= 1 (partition of [n]); ignored when
+                              rebk_partition gives column offsets                       */
     int32_t storage_mask;  /* extra copies to keep: (1<<REBK_FP32) | (1<<REBK_BF16);
                               the FP64 copy is always kept                              */
     int32_t num_ctas;      /* CTAs of the persistent solve kernel; 0 = library choice  */
@@ -105,18 +108,39 @@ typedef struct {
 } rebk_refine_opts;
 
 /*
+ * Partitions of the rows and columns for Algorithm 1 (Section 2: the row
+ * blocks I_1..I_s partition [m], the column blocks J_1..J_t partition [n]).
+ * Offsets are host arrays: block i of the rows is [row_off[i], row_off[i+1]),
+ * with 0 = row_off[0] < row_off[1] < ... < row_off[s] = m (no empty block);
+ * likewise col_off (t + 1 entries) for the columns.  A NULL offset array
+ * selects the contiguous partition of Section 3's experiments: blocks of
+ * rebk_options.tau_row (tau_col) consecutive rows (columns), the last one
+ * shorter (s and t are then ignored).  Every block has at most 512 rows or
+ * columns.  The library copies the offsets.
+ */
+typedef struct {
+    const int64_t *row_off;  /* host, s + 1 entries, or NULL                      */
+    int64_t s;               /* number of row blocks (with row_off)               */
+    const int64_t *col_off;  /* host, t + 1 entries, or NULL                      */
+    int64_t t;               /* number of column blocks (with col_off)            */
+} rebk_partition;
+
+/*
  * Creates a solver for the m x n matrix A (row-major, leading dimension lda,
  * host memory if A_on_device == 0, device memory otherwise; the library copies
- * it).  Builds the block squared Frobenius norm tables and their prefix sums
- * (Algorithm 1 sampling) in FP64 on the device, and the reduced-precision
- * copies named in opt->storage_mask.
+ * it) with the block partitions *part (NULL = contiguous blocks of the sizes in
+ * opt, see rebk_partition).  Builds the block squared Frobenius norm tables
+ * and their prefix sums (Algorithm 1 sampling) in FP64 on the device, and the
+ * reduced-precision copies named in opt->storage_mask.
  * alpha > 0 is the step size of Algorithm 1; alpha <= 0 picks 1.75 / beta_max
  * (Section 3's empirical choice) with beta_max from rebk_beta_max.
- * Errors: EINVAL (m, n, lda, tau out of range, NULL pointers), ENOMEM, ECUDA.
- * A matrix of all zeros is accepted (every solve returns x = 0 = A^+ b).
+ * Errors: EINVAL (m, n, lda, tau out of range, NULL pointers, offsets not
+ * strictly increasing from 0 to m / n), EUNSUPPORTED (a block above 512),
+ * ENOMEM, ECUDA.  A matrix of all zeros is accepted (every solve returns
+ * x = 0 = A^+ b).
  */
 rebk_status rebk_create(rebk_handle *out, const double *A, int64_t m, int64_t n, int64_t lda,
-                        int A_on_device, double alpha, const rebk_options *opt);
+                        int A_on_device, const rebk_partition *part, double alpha, const rebk_options *opt);
 
 /* Releases everything the handle owns.  NULL is ignored. */
 void rebk_destroy(rebk_handle h);
@@ -218,6 +242,14 @@ rebk_status rebk_spectral_estimates(rebk_handle h, int32_t steps, uint64_t seed,
 
 /* Number of row blocks s and column blocks t (host int64). */
 rebk_status rebk_get_blocks(rebk_handle h, int64_t *s, int64_t *t);
+
+/*
+ * Copies the partition in use to host arrays row_off (s + 1 entries) and
+ * col_off (t + 1 entries), either may be NULL; *tau_row / *tau_col (may be
+ * NULL) receive the largest block size of each.
+ */
+rebk_status rebk_get_partition(rebk_handle h, int64_t *row_off, int64_t *col_off, int64_t *tau_row,
+                               int64_t *tau_col);
 
 /*
  * Copies the FP64 block tables to host arrays: nr (s), nc (t) squared

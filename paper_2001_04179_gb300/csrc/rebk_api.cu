@@ -71,6 +71,10 @@ struct rebk_handle_s {
     __nv_bfloat16 *A16 = nullptr;
     double *nr = nullptr, *nc = nullptr, *cdf_r = nullptr, *cdf_c = nullptr;
     int *d_fallback = nullptr;
+    // partition: offsets on the device (NULL = contiguous blocks of tau_r / tau_c)
+    int64_t *d_row_off = nullptr, *d_col_off = nullptr;
+    std::vector<int64_t> row_off, col_off;  // host copies (always filled)
+    int col_align = 0;
     void *acc = nullptr;  // 2 chains x 3 sets x acc_r replicas x acc_w, 8 bytes per entry
     int acc_w = 0, acc_r = kAccReplicas;
     double *coef_r64 = nullptr, *coef_c64 = nullptr;
@@ -101,6 +105,7 @@ namespace {
 void free_handle(rebk_handle h) {
     if (!h) return;
     void *ptrs[] = {h->A64, h->A32, h->A16, h->nr, h->nc, h->cdf_r, h->cdf_c, h->d_fallback, h->acc,
+                    h->d_row_off, h->d_col_off,
                     h->coef_r64, h->coef_c64, h->coef_r32, h->coef_c32,
                     h->ws, h->zbuf, h->f, h->g, h->ym, h->yn, h->dz, h->dx, h->sd, h->vd,
                     h->idxbuf};
@@ -135,6 +140,9 @@ GridArgs base_args(rebk_handle h, Mode mode, int G) {
     a.tau_c = h->tau_c;
     a.s = h->s;
     a.t = h->t;
+    a.row_off = h->d_row_off;
+    a.col_off = h->d_col_off;
+    a.col_align = h->col_align;
     a.cdf_r = h->cdf_r;
     a.cdf_c = h->cdf_c;
     a.nr = h->nr;
@@ -373,6 +381,24 @@ void fill_stats(rebk_handle h, rebk_stats *st, int64_t iters, int outer, rebk_st
     st->device_ms = ms;
 }
 
+// Checks one side of a partition: off[0] = 0 < off[1] < ... < off[nb] = size,
+// every block at most 512 long.  Fills the host copy and the largest block.
+rebk_status check_offsets(const int64_t *off, int64_t nb, int64_t size, const char *what,
+                          std::vector<int64_t> *copy, int64_t *tau) {
+    if (nb < 1 || nb > ((int64_t)1 << 30)) return fail(REBK_EINVAL, std::string(what) + ": block count out of range");
+    if (off[0] != 0 || off[nb] != size)
+        return fail(REBK_EINVAL, std::string(what) + ": offsets must run from 0 to the dimension");
+    int64_t big = 0;
+    for (int64_t b = 0; b < nb; ++b) {
+        if (off[b + 1] <= off[b]) return fail(REBK_EINVAL, std::string(what) + ": offsets must increase strictly");
+        big = std::max(big, off[b + 1] - off[b]);
+    }
+    if (big > 512) return fail(REBK_EUNSUPPORTED, std::string(what) + ": a block larger than 512");
+    copy->assign(off, off + nb + 1);
+    *tau = big;
+    return REBK_OK;
+}
+
 }  // namespace
 
 namespace rebk {
@@ -389,7 +415,8 @@ const char *rebk_version(void) { return "rebk-gb300 0.1 (sm_103a)"; }
 void rebk_destroy(rebk_handle h) { free_handle(h); }
 
 rebk_status rebk_create(rebk_handle *out, const double *A, int64_t m, int64_t n, int64_t lda,
-                        int A_on_device, double alpha, const rebk_options *opt) {
+                                   int A_on_device, const rebk_partition *part, double alpha,
+                                   const rebk_options *opt) {
     g_last_error.clear();
     if (!out) return fail(REBK_EINVAL, "out is NULL");
     *out = nullptr;
@@ -406,6 +433,15 @@ rebk_status rebk_create(rebk_handle *out, const double *A, int64_t m, int64_t n,
     if (o.tau_col == 0) o.tau_col = std::min<int64_t>(n, 64);
     o.tau_row = std::min(o.tau_row, m);
     o.tau_col = std::min(o.tau_col, n);
+    std::vector<int64_t> roff, coff;
+    if (part && part->row_off) {
+        rebk_status ps = check_offsets(part->row_off, part->s, m, "row partition", &roff, &o.tau_row);
+        if (ps != REBK_OK) return ps;
+    }
+    if (part && part->col_off) {
+        rebk_status ps = check_offsets(part->col_off, part->t, n, "column partition", &coff, &o.tau_col);
+        if (ps != REBK_OK) return ps;
+    }
     if (o.tau_row > 512 || o.tau_col > 512) return fail(REBK_EUNSUPPORTED, "tau > 512");
     if (o.check_every < 0) return fail(REBK_EINVAL, "check_every < 0");
     if (o.num_ctas < 0) return fail(REBK_EINVAL, "num_ctas < 0");
@@ -419,8 +455,22 @@ rebk_status rebk_create(rebk_handle *out, const double *A, int64_t m, int64_t n,
     h->lda = round_up(n, 64);
     h->tau_r = (int)o.tau_row;
     h->tau_c = (int)o.tau_col;
-    h->s = (int)((m + h->tau_r - 1) / h->tau_r);
-    h->t = (int)((n + h->tau_c - 1) / h->tau_c);
+    h->s = roff.empty() ? (int)((m + h->tau_r - 1) / h->tau_r) : (int)(roff.size() - 1);
+    h->t = coff.empty() ? (int)((n + h->tau_c - 1) / h->tau_c) : (int)(coff.size() - 1);
+    if (roff.empty())
+        for (int64_t b = 0; b <= h->s; ++b) h->row_off.push_back(std::min<int64_t>(m, b * h->tau_r));
+    else
+        h->row_off = roff;
+    if (coff.empty())
+        for (int64_t b = 0; b <= h->t; ++b) h->col_off.push_back(std::min<int64_t>(n, b * h->tau_c));
+    else
+        h->col_off = coff;
+    if (!coff.empty()) {  // largest power of two (<= 16) dividing every column-block start
+        int al = 16;
+        for (int64_t v : coff)
+            while (al > 1 && v % al != 0) al >>= 1;
+        h->col_align = al;
+    }
     h->check_every = o.check_every;
     h->num_ctas_opt = o.num_ctas;
     h->acc_w = (int)round_up(std::max(h->tau_c, h->tau_r + 1), 32);
@@ -437,6 +487,14 @@ rebk_status rebk_create(rebk_handle *out, const double *A, int64_t m, int64_t n,
     } while (0)
 
     CKH(cudaGetDevice(&h->device));
+    if (!roff.empty()) {
+        CKH(cudaMalloc(&h->d_row_off, sizeof(int64_t) * roff.size()));
+        CKH(cudaMemcpy(h->d_row_off, roff.data(), sizeof(int64_t) * roff.size(), cudaMemcpyHostToDevice));
+    }
+    if (!coff.empty()) {
+        CKH(cudaMalloc(&h->d_col_off, sizeof(int64_t) * coff.size()));
+        CKH(cudaMemcpy(h->d_col_off, coff.data(), sizeof(int64_t) * coff.size(), cudaMemcpyHostToDevice));
+    }
     CKH(cudaEventCreate(&h->ev0));
     CKH(cudaEventCreate(&h->ev1));
     CKH(cudaEventCreate(&h->kev0));
@@ -465,7 +523,7 @@ rebk_status rebk_create(rebk_handle *out, const double *A, int64_t m, int64_t n,
         double *scratch = nullptr;
         CKH(cudaMalloc(&scratch, sizeof(double) * (size_t)(m + n + 64 * n)));
         cudaError_t e = block_tables(h->A64, h->lda, m, n, h->tau_r, h->tau_c, h->s, h->t, h->nr, h->nc,
-                                     h->cdf_r, h->cdf_c, h->d_fallback, scratch, st);
+                                     h->cdf_r, h->cdf_c, h->d_fallback, scratch, st, h->d_row_off, h->d_col_off);
         cudaError_t e2 = cudaStreamSynchronize(st);
         cudaFree(scratch);
         CKH(e);
@@ -526,7 +584,7 @@ rebk_status rebk_beta_max(rebk_handle h, double *beta_row, double *beta_col) {
         CK(cudaMalloc(&br, sizeof(double) * h->s));
         CK(cudaMalloc(&bc, sizeof(double) * h->t));
         cudaError_t e = beta_max_device(h->A64, h->lda, h->m, h->n, h->tau_r, h->tau_c, h->s, h->t, h->nr,
-                                        h->nc, gram, br, bc, st);
+                                        h->nc, gram, br, bc, st, h->d_row_off, h->d_col_off);
         std::vector<double> hr(h->s), hc(h->t);
         if (e == cudaSuccess) e = cudaMemcpyAsync(hr.data(), br, sizeof(double) * h->s, cudaMemcpyDeviceToHost, st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(hc.data(), bc, sizeof(double) * h->t, cudaMemcpyDeviceToHost, st);
@@ -597,6 +655,16 @@ rebk_status rebk_get_blocks(rebk_handle h, int64_t *s, int64_t *t) {
     if (!h) return fail(REBK_EINVAL, "handle is NULL");
     if (s) *s = h->s;
     if (t) *t = h->t;
+    return REBK_OK;
+}
+
+rebk_status rebk_get_partition(rebk_handle h, int64_t *row_off, int64_t *col_off, int64_t *tau_row,
+                               int64_t *tau_col) {
+    if (!h) return fail(REBK_EINVAL, "handle is NULL");
+    if (row_off) std::copy(h->row_off.begin(), h->row_off.end(), row_off);
+    if (col_off) std::copy(h->col_off.begin(), h->col_off.end(), col_off);
+    if (tau_row) *tau_row = h->tau_r;
+    if (tau_col) *tau_col = h->tau_c;
     return REBK_OK;
 }
 

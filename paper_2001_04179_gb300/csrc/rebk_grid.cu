@@ -672,23 +672,42 @@ __global__ void __launch_bounds__(kThreads, 1) rebk_grid_kernel(const __grid_con
     TS *accw_base = static_cast<TS *>(args.acc);   // w partials: 3 sets
     TS *accr_base = accw_base + 3 * accset;        // r partials (+ test partial at tau_r): 3 sets
     const bool check = args.x_ref != nullptr && args.check_every > 0;
-    // column tiles start exactly at their block (tau_c a multiple of the 16-byte vector)
-    const bool fast_c = TMA && args.bw_c == args.tau_c;
+    // Column blocks whose starts are all multiples of calign elements: the
+    // contiguous partition's starts are multiples of tau_c (of its lowest set
+    // bit), a given partition's of args.col_align.
+    const int calign = args.col_off ? args.col_align : (args.tau_c & -args.tau_c);
+    // column tiles start exactly at their block (every start on a 16-byte boundary)
+    const bool fast_c = TMA && calign % args.tma_vx == 0;
     // global-memory column views start on a 16-byte vector (rows are 16-byte aligned)
-    const bool fast_g = !TMA && args.tau_c % V == 0;
+    const bool fast_g = !TMA && calign % V == 0;
     const int wpad = (args.tau_c + 7) / 8 * 8;
     // Any CTA past the arrivals of step q may clear a set that step q + 1 fills:
     // every CTA has read it (step q - 1) before arriving, and nobody adds to it
     // before every CTA has arrived once more.  Each CTA clears a 1/G share.
     const int64_t clr0 = accset * cta / G, clr1 = accset * (cta + 1) / G;
 
+    // block j of the columns / i of the rows: [off[j], off[j+1]) of a given
+    // partition, else the contiguous blocks of tau_c / tau_r (Algorithm 1's
+    // J_j and I_i)
+    const int64_t *__restrict__ col_off = args.col_off;
+    const int64_t *__restrict__ row_off = args.row_off;
     auto col_range = [&](int j, int64_t *a, int64_t *b) {
-        *a = (int64_t)j * args.tau_c;
-        *b = lmin(n, *a + args.tau_c);
+        if (col_off) {
+            *a = __ldg(col_off + j);
+            *b = __ldg(col_off + j + 1);
+        } else {
+            *a = (int64_t)j * args.tau_c;
+            *b = lmin(n, *a + args.tau_c);
+        }
     };
     auto row_range = [&](int i, int64_t *a, int64_t *b) {
-        *a = (int64_t)i * tau_r;
-        *b = lmin(m, *a + tau_r);
+        if (row_off) {
+            *a = __ldg(row_off + i);
+            *b = __ldg(row_off + i + 1);
+        } else {
+            *a = (int64_t)i * tau_r;
+            *b = lmin(m, *a + tau_r);
+        }
     };
     // a wait gave up after its time limit: record it for the host and for the other group
     auto give_up = [&](int code) {
@@ -1217,7 +1236,9 @@ bool tma_geometry(Mode mode, GridArgs &a) {
     const int vx = 16 / es;  // elements per 16 bytes
     a.tma_vx = vx;
     // column tile: own rows x tau_c, widened to cover a start rounded down to 16 bytes
-    a.bw_c = (a.tau_c % vx == 0) ? a.tau_c : ((a.tau_c + vx - 1) / vx) * vx + vx;
+    // when some block starts off a 16-byte boundary
+    const int calign = a.col_off ? a.col_align : (a.tau_c & -a.tau_c);
+    a.bw_c = ((a.tau_c + vx - 1) / vx) * vx + (calign % vx == 0 ? 0 : vx);
     a.bh_c = a.nrow_cap <= 256 ? a.nrow_cap : 256;
     a.nbox_c = (a.nrow_cap + a.bh_c - 1) / a.bh_c;
     // row tile: tau_r rows x own columns (start is a multiple of 8 elements)

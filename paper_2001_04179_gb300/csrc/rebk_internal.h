@@ -38,7 +38,10 @@ struct GridArgs {
     CUtensorMap tmap_r;     // TMA: row tiles (tau_r x own columns box)
     const void *A;          // stored copy, row-major, leading dimension lda (zero padded)
     int64_t lda, m, n;
-    int tau_r, tau_c, s, t; // block sizes and counts (Section 3 partition)
+    int tau_r, tau_c, s, t; // largest block sizes and block counts
+    const int64_t *row_off; // device, s + 1 row-block offsets; NULL = blocks of tau_r rows
+    const int64_t *col_off; // device, t + 1 column-block offsets; NULL = blocks of tau_c columns
+    int col_align;          // with col_off: largest power of two (<= 16) dividing every column-block start
     const double *cdf_r, *cdf_c, *nr, *nc;
     const void *coef_r, *coef_c;  // TS: alpha / ||block||_F^2 (0 for blocks of zero norm)
     int fb_r, fb_c;         // fallback picks (last block of nonzero norm)
@@ -138,18 +141,22 @@ int grid_max_ctas(Mode mode, size_t smem);
 // Setup and sweep kernels (rebk_setup.cu).
 cudaError_t convert_storage(const double *src, int64_t lds, void *dst, int64_t ldd, int64_t m,
                             int64_t n, int storage, cudaStream_t st);
+// Block norms, prefix sums and fallback picks.  row_off / col_off: device offset
+// arrays of the partitions (s + 1, t + 1 entries), or NULL for blocks of tau_r / tau_c.
 cudaError_t block_tables(const double *A, int64_t lda, int64_t m, int64_t n, int tau_r, int tau_c,
                          int s, int t, double *nr, double *nc, double *cdf_r, double *cdf_c,
                          int *fallback /* device int[2] */, double *scratch /* m + n + 64*n */,
-                         cudaStream_t st);
+                         cudaStream_t st, const int64_t *row_off = nullptr, const int64_t *col_off = nullptr);
 // y_m = A p (length m), y_n = A^T q (length n); p or q may be NULL (skipped).
 // TP/TQ: double or float inputs.
 cudaError_t dual_sweep(const double *A, int64_t lda, int64_t m, int64_t n, const void *p,
                        bool p_f32, const void *q, bool q_f32, double *ym, double *yn,
                        cudaStream_t st);
+// tau_r / tau_c: the largest block sizes; row_off / col_off as for block_tables.
 cudaError_t beta_max_device(const double *A, int64_t lda, int64_t m, int64_t n, int tau_r, int tau_c,
                             int s, int t, const double *nr, const double *nc, double *gram_scratch,
-                            double *beta_rows, double *beta_cols, cudaStream_t st);
+                            double *beta_rows, double *beta_cols, cudaStream_t st,
+                            const int64_t *row_off = nullptr, const int64_t *col_off = nullptr);
 // out[0] = sum (a + x - r)^2 over n (a may be NULL), out[1] = sum r^2.
 cudaError_t err_norms(const double *a, const double *x, const double *r, int64_t n, double *out,
                       cudaStream_t st);

@@ -88,37 +88,32 @@ __global__ void col_sq_final_kernel(const double *__restrict__ part, int64_t nch
 }
 
 // nr / nc block sums, inclusive prefix sums, fallback picks (thread 0: rows,
-// thread 1: columns).
+// thread 1: columns).  Block b spans [off[b], off[b+1]) when an offset array is
+// given, else [b tau, min((b+1) tau, size)).
 __global__ void tables_kernel(const double *__restrict__ rowsq, const double *__restrict__ colsq,
                               int64_t m, int64_t n, int tau_r, int tau_c, int s, int t,
+                              const int64_t *__restrict__ row_off, const int64_t *__restrict__ col_off,
                               double *nr, double *nc, double *cdf_r, double *cdf_c, int *fallback) {
-    if (threadIdx.x == 0) {
-        double acc = 0.0;
-        int last = 0;
-        for (int b = 0; b < s; ++b) {
-            double w = 0.0;
-            const int64_t a = (int64_t)b * tau_r, e = lmin(m, a + tau_r);
-            for (int64_t i = a; i < e; ++i) w += rowsq[i];
-            nr[b] = w;
-            acc += w;
-            cdf_r[b] = acc;
-            if (w > 0.0) last = b;
-        }
-        fallback[0] = last;
-    } else if (threadIdx.x == 1) {
-        double acc = 0.0;
-        int last = 0;
-        for (int b = 0; b < t; ++b) {
-            double w = 0.0;
-            const int64_t a = (int64_t)b * tau_c, e = lmin(n, a + tau_c);
-            for (int64_t j = a; j < e; ++j) w += colsq[j];
-            nc[b] = w;
-            acc += w;
-            cdf_c[b] = acc;
-            if (w > 0.0) last = b;
-        }
-        fallback[1] = last;
+    if (threadIdx.x > 1) return;
+    const bool rows = threadIdx.x == 0;
+    const int nb = rows ? s : t, tau = rows ? tau_r : tau_c;
+    const int64_t size = rows ? m : n;
+    const int64_t *off = rows ? row_off : col_off;
+    const double *sq = rows ? rowsq : colsq;
+    double *norm = rows ? nr : nc, *cdf = rows ? cdf_r : cdf_c;
+    double acc = 0.0;
+    int last = 0;
+    for (int b = 0; b < nb; ++b) {
+        double w = 0.0;
+        const int64_t a = off ? off[b] : (int64_t)b * tau;
+        const int64_t e = off ? off[b + 1] : lmin(size, a + tau);
+        for (int64_t i = a; i < e; ++i) w += sq[i];
+        norm[b] = w;
+        acc += w;
+        cdf[b] = acc;
+        if (w > 0.0) last = b;
     }
+    fallback[rows ? 0 : 1] = last;
 }
 
 // ---------------------------------------------------------------------------
@@ -241,15 +236,19 @@ __global__ void __launch_bounds__(256) dual_sweep_kernel(const double *__restric
 // beta_max: Gram matrices of the blocks, then power iteration.
 // ---------------------------------------------------------------------------
 // Row block b: G = A_I A_I^T (h x h, h <= tau_r).  Column block: G = A_J^T A_J.
-// One CTA computes a 16 x 16 tile of one Gram matrix.
+// One CTA computes a 16 x 16 tile of one Gram matrix; block blk0 + blockIdx.z
+// starts at off[.] (offset array) or at (blk0 + blockIdx.z) tau, and its Gram
+// matrix is stored with leading dimension tau at gram + blockIdx.z tau^2.
 __global__ void gram_kernel(const double *__restrict__ A, int64_t lda, int64_t m, int64_t n,
-                            int tau, int rows_mode, double *__restrict__ gram) {
+                            int tau, int rows_mode, const int64_t *__restrict__ offs, int blk0,
+                            double *__restrict__ gram) {
     __shared__ double sa[16][33];
     __shared__ double sb[16][33];
     const int blk = blockIdx.z;
     const int ta = blockIdx.y * 16, tb = blockIdx.x * 16;
-    const int64_t off = (int64_t)blk * tau;
-    const int h = (int)lmin(tau, (rows_mode ? m : n) - off);
+    const int64_t size = rows_mode ? m : n;
+    const int64_t off = offs ? offs[blk0 + blk] : (int64_t)(blk0 + blk) * tau;
+    const int h = (int)(offs ? offs[blk0 + blk + 1] - off : lmin(tau, size - off));
     double *Gb = gram + (int64_t)blk * tau * tau;
     if (ta >= h || tb >= h) return;
     const int ty = threadIdx.y, tx = threadIdx.x;  // 16 x 16 threads
@@ -282,13 +281,16 @@ __global__ void gram_kernel(const double *__restrict__ A, int64_t lda, int64_t m
 }
 
 // lambda_max of each Gram matrix by power iteration (Rayleigh quotient), then
-// beta = lambda_max / trace.  One CTA (256 threads) per block.
+// beta = lambda_max / trace.  One CTA (256 threads) per block; block sizes as
+// in gram_kernel.
 __global__ void power_kernel(const double *__restrict__ gram, int tau, int64_t total, int nblocks,
-                             const double *__restrict__ fro2, double *__restrict__ beta) {
+                             const int64_t *__restrict__ offs, int blk0, const double *__restrict__ fro2,
+                             double *__restrict__ beta) {
     extern __shared__ double sh[];
     double *v = sh, *gv = sh + tau, *red = sh + 2 * tau;
     const int blk = blockIdx.x, tid = threadIdx.x;
-    const int h = (int)lmin(tau, total - (int64_t)blk * tau);
+    const int64_t off = offs ? offs[blk0 + blk] : (int64_t)(blk0 + blk) * tau;
+    const int h = (int)(offs ? offs[blk0 + blk + 1] - off : lmin(tau, total - off));
     const double *G = gram + (int64_t)blk * tau * tau;
     if (fro2[blk] <= 0.0) {
         if (tid == 0) beta[blk] = 0.0;
@@ -426,7 +428,8 @@ cudaError_t convert_storage(const double *src, int64_t lds, void *dst, int64_t l
 
 cudaError_t block_tables(const double *A, int64_t lda, int64_t m, int64_t n, int tau_r, int tau_c,
                          int s, int t, double *nr, double *nc, double *cdf_r, double *cdf_c,
-                         int *fallback, double *scratch, cudaStream_t st) {
+                         int *fallback, double *scratch, cudaStream_t st, const int64_t *row_off,
+                         const int64_t *col_off) {
     double *rowsq = scratch, *colsq = scratch + m, *part = scratch + m + n;
     row_sq_kernel<<<grid_for(m * 32, 256) > 4096 ? 4096 : grid_for(m * 32, 256), 256, 0, st>>>(
         A, lda, m, n, rowsq);
@@ -435,8 +438,8 @@ cudaError_t block_tables(const double *A, int64_t lda, int64_t m, int64_t n, int
     dim3 g((unsigned)((n + 255) / 256), (unsigned)nchunks);
     col_sq_part_kernel<<<g, 256, 0, st>>>(A, lda, m, n, rpc, part);
     col_sq_final_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(part, nchunks, n, colsq);
-    tables_kernel<<<1, 32, 0, st>>>(rowsq, colsq, m, n, tau_r, tau_c, s, t, nr, nc, cdf_r, cdf_c,
-                                    fallback);
+    tables_kernel<<<1, 32, 0, st>>>(rowsq, colsq, m, n, tau_r, tau_c, s, t, row_off, col_off, nr, nc, cdf_r,
+                                    cdf_c, fallback);
     return cudaGetLastError();
 }
 
@@ -471,17 +474,17 @@ cudaError_t dual_sweep(const double *A, int64_t lda, int64_t m, int64_t n, const
 
 cudaError_t beta_max_device(const double *A, int64_t lda, int64_t m, int64_t n, int tau_r, int tau_c,
                             int s, int t, const double *nr, const double *nc, double *gram_scratch,
-                            double *beta_rows, double *beta_cols, cudaStream_t st) {
-    // row blocks
+                            double *beta_rows, double *beta_cols, cudaStream_t st, const int64_t *row_off,
+                            const int64_t *col_off) {
+    // the Gram scratch holds one chunk of blocks: at most 65535 per launch
     {
         const int nt = (tau_r + 15) / 16;
         for (int b0 = 0; b0 < s; b0 += 65535) {
             const int nb = s - b0 < 65535 ? s - b0 : 65535;
             dim3 g(nt, nt, nb);
-            gram_kernel<<<g, dim3(16, 16), 0, st>>>(A + (int64_t)b0 * tau_r * lda, lda,
-                                                   m - (int64_t)b0 * tau_r, n, tau_r, 1, gram_scratch);
-            power_kernel<<<nb, 256, (2 * tau_r + 32) * sizeof(double), st>>>(
-                gram_scratch, tau_r, m - (int64_t)b0 * tau_r, nb, nr + b0, beta_rows + b0);
+            gram_kernel<<<g, dim3(16, 16), 0, st>>>(A, lda, m, n, tau_r, 1, row_off, b0, gram_scratch);
+            power_kernel<<<nb, 256, (2 * tau_r + 32) * sizeof(double), st>>>(gram_scratch, tau_r, m, nb, row_off, b0,
+                                                                           nr + b0, beta_rows + b0);
         }
     }
     {
@@ -489,10 +492,9 @@ cudaError_t beta_max_device(const double *A, int64_t lda, int64_t m, int64_t n, 
         for (int b0 = 0; b0 < t; b0 += 65535) {
             const int nb = t - b0 < 65535 ? t - b0 : 65535;
             dim3 g(nt, nt, nb);
-            gram_kernel<<<g, dim3(16, 16), 0, st>>>(A + (int64_t)b0 * tau_c, lda, m,
-                                                   n - (int64_t)b0 * tau_c, tau_c, 0, gram_scratch);
-            power_kernel<<<nb, 256, (2 * tau_c + 32) * sizeof(double), st>>>(
-                gram_scratch, tau_c, n - (int64_t)b0 * tau_c, nb, nc + b0, beta_cols + b0);
+            gram_kernel<<<g, dim3(16, 16), 0, st>>>(A, lda, m, n, tau_c, 0, col_off, b0, gram_scratch);
+            power_kernel<<<nb, 256, (2 * tau_c + 32) * sizeof(double), st>>>(gram_scratch, tau_c, n, nb, col_off, b0,
+                                                                           nc + b0, beta_cols + b0);
         }
     }
     return cudaGetLastError();

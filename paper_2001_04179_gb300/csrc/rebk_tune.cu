@@ -42,7 +42,7 @@ rebk_status tune_one(const double *A_dev, int64_t m, int64_t n, int64_t lda, con
     o.tau_col = std::min(tau, n);
     if (storage != REBK_FP64) o.storage_mask |= 1 << storage;
     rebk_handle h = nullptr;
-    rebk_status s = rebk_create(&h, A_dev, m, n, lda, 1, 0.0, &o);
+    rebk_status s = rebk_create(&h, A_dev, m, n, lda, 1, nullptr, 0.0, &o);
     if (s != REBK_OK) return s;
     double br = 0.0, bc = 0.0;
     s = rebk_beta_max(h, &br, &bc);

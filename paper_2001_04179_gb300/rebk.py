@@ -83,6 +83,11 @@ class RebkBatchStats(ctypes.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_}
 
 
+class RebkPartition(ctypes.Structure):
+    _fields_ = [("row_off", ctypes.c_void_p), ("s", ctypes.c_int64), ("col_off", ctypes.c_void_p),
+                ("t", ctypes.c_int64)]
+
+
 class RebkPeaks(ctypes.Structure):
     _fields_ = [("fp64_tflops", ctypes.c_double), ("fp64_ms", ctypes.c_double), ("sm_mhz", ctypes.c_double),
                 ("l2_gbs", ctypes.c_double), ("l2_ms", ctypes.c_double), ("l2_bytes", ctypes.c_double)]
@@ -102,7 +107,9 @@ _lib: Optional[ctypes.CDLL] = None
 _P = ctypes.c_void_p
 _SIGNATURES = {
     "rebk_create": ([ctypes.POINTER(_P), _P, ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, ctypes.c_int,
-                     ctypes.c_double, ctypes.POINTER(RebkOptions)], ctypes.c_int),
+                     ctypes.POINTER(RebkPartition), ctypes.c_double, ctypes.POINTER(RebkOptions)], ctypes.c_int),
+    "rebk_get_partition": ([_P, _P, _P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+                           ctypes.c_int),
     "rebk_destroy": ([_P], None),
     "rebk_solve": ([_P, _P, _P, ctypes.c_double, ctypes.c_int64, ctypes.c_uint64,
                     ctypes.POINTER(RebkStats)], ctypes.c_int),

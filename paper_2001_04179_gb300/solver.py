@@ -32,13 +32,16 @@ class Solver:
 
     A: torch CUDA float64 tensor (m x n, row-major) or a numpy float64 array.
     tau_row / tau_col: block sizes of the contiguous partitions (Section 3).
+    row_off / col_off: any partitions instead (Section 2's I_1..I_s and
+    J_1..J_t): int64 offsets 0 = off[0] < ... < off[-1] = m (n), blocks of at
+    most 512; the tau of a side given by offsets is ignored.
     alpha: step size; <= 0 picks 1.75 / beta_max.
     storage: reduced-precision copies to keep for solve_refined ("fp32", "bf16").
     """
 
-    def __init__(self, A, tau_row: int, tau_col: int, alpha: float = 0.0,
+    def __init__(self, A, tau_row: int = 0, tau_col: int = 0, alpha: float = 0.0,
                  storage: Sequence[str] = ("fp32",), num_ctas: int = 0, check_every: int = 0,
-                 stream=None):
+                 stream=None, row_off=None, col_off=None):
         torch = _torch()
         lib = _r.load()
         mask = 0
@@ -47,22 +50,40 @@ class Solver:
         self._stream = stream
         opt = _r.RebkOptions(tau_row, tau_col, mask, num_ctas, check_every,
                              None if stream is None else ctypes.c_void_p(stream.cuda_stream))
+        part = None
+        if row_off is not None or col_off is not None:
+            self._ro = None if row_off is None else np.ascontiguousarray(row_off, dtype=np.int64)
+            self._co = None if col_off is None else np.ascontiguousarray(col_off, dtype=np.int64)
+            part = _r.RebkPartition(None if self._ro is None else self._ro.ctypes.data,
+                                    0 if self._ro is None else self._ro.size - 1,
+                                    None if self._co is None else self._co.ctypes.data,
+                                    0 if self._co is None else self._co.size - 1)
+        pp = None if part is None else ctypes.byref(part)
         h = ctypes.c_void_p()
         if isinstance(A, torch.Tensor):
             if not (A.is_cuda and A.dtype == torch.float64 and A.dim() == 2 and A.stride(1) == 1):
                 raise ValueError("A must be a CUDA float64 matrix with unit column stride")
             m, n = A.shape
-            st = lib.rebk_create(ctypes.byref(h), ctypes.c_void_p(A.data_ptr()), m, n, A.stride(0), 1,
+            st = lib.rebk_create(ctypes.byref(h), ctypes.c_void_p(A.data_ptr()), m, n, A.stride(0), 1, pp,
                                  float(alpha), ctypes.byref(opt))
         else:
             An = np.ascontiguousarray(A, dtype=np.float64)
             m, n = An.shape
-            st = lib.rebk_create(ctypes.byref(h), An.ctypes.data_as(ctypes.c_void_p), m, n, n, 0,
+            st = lib.rebk_create(ctypes.byref(h), An.ctypes.data_as(ctypes.c_void_p), m, n, n, 0, pp,
                                  float(alpha), ctypes.byref(opt))
         _r.check(st)
         self._h = h
         self.m, self.n = int(m), int(n)
-        self.tau_row, self.tau_col = tau_row, tau_col
+        ro, co = self.partition()
+        self.tau_row, self.tau_col = int(np.max(np.diff(ro))), int(np.max(np.diff(co)))
+
+    def partition(self):
+        """(row_off, col_off): the partitions in use, as int64 offset arrays."""
+        s, t = self.blocks()
+        ro, co = np.zeros(s + 1, dtype=np.int64), np.zeros(t + 1, dtype=np.int64)
+        _r.check(_r.load().rebk_get_partition(self._h, ro.ctypes.data_as(ctypes.c_void_p),
+                                              co.ctypes.data_as(ctypes.c_void_p), None, None))
+        return ro, co
 
     @classmethod
     def rek(cls, A, **kw) -> "Solver":

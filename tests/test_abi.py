@@ -45,12 +45,12 @@ def test_invalid_arguments_are_rejected_before_any_launch():
     h = ctypes.c_void_p()
     A = (ctypes.c_double * 4)(1, 2, 3, 4)
     opt = R.RebkOptions(1, 1, 0, 0, 0, None)
-    assert lib.rebk_create(None, A, 2, 2, 2, 0, 1.0, ctypes.byref(opt)) == R.REBK_EINVAL
-    assert lib.rebk_create(ctypes.byref(h), None, 2, 2, 2, 0, 1.0, ctypes.byref(opt)) == R.REBK_EINVAL
-    assert lib.rebk_create(ctypes.byref(h), A, 0, 2, 2, 0, 1.0, ctypes.byref(opt)) == R.REBK_EINVAL
-    assert lib.rebk_create(ctypes.byref(h), A, 2, 2, 1, 0, 1.0, ctypes.byref(opt)) == R.REBK_EINVAL
+    assert lib.rebk_create(None, A, 2, 2, 2, 0, None, 1.0, ctypes.byref(opt)) == R.REBK_EINVAL
+    assert lib.rebk_create(ctypes.byref(h), None, 2, 2, 2, 0, None, 1.0, ctypes.byref(opt)) == R.REBK_EINVAL
+    assert lib.rebk_create(ctypes.byref(h), A, 0, 2, 2, 0, None, 1.0, ctypes.byref(opt)) == R.REBK_EINVAL
+    assert lib.rebk_create(ctypes.byref(h), A, 2, 2, 1, 0, None, 1.0, ctypes.byref(opt)) == R.REBK_EINVAL
     bad = R.RebkOptions(-1, 1, 0, 0, 0, None)
-    assert lib.rebk_create(ctypes.byref(h), A, 2, 2, 2, 0, 1.0, ctypes.byref(bad)) == R.REBK_EINVAL
+    assert lib.rebk_create(ctypes.byref(h), A, 2, 2, 2, 0, None, 1.0, ctypes.byref(bad)) == R.REBK_EINVAL
     big = R.RebkOptions(1000, 1000, 0, 0, 0, None)
     # tau is clamped to m, n first: 2 x 2 with tau 1000 is fine in principle; a
     # tau above the kernel limit on a large matrix is EUNSUPPORTED
@@ -116,7 +116,7 @@ def test_block_size_above_the_kernel_limit_is_unsupported_before_any_cuda_call()
     h = ctypes.c_void_p()
     A = (ctypes.c_double * 4)(1, 2, 3, 4)   # never read: the call returns before any copy
     opt = R.RebkOptions(600, 8, 0, 0, 0, None)
-    assert lib.rebk_create(ctypes.byref(h), A, 1000, 1000, 1000, 0, 1.0, ctypes.byref(opt)) == R.REBK_EUNSUPPORTED
+    assert lib.rebk_create(ctypes.byref(h), A, 1000, 1000, 1000, 0, None, 1.0, ctypes.byref(opt)) == R.REBK_EUNSUPPORTED
     assert "tau" in lib.rebk_last_error().decode()
     assert not h.value
 
@@ -143,3 +143,36 @@ def test_wait_selftest_rejects_bad_arguments_on_the_host():
     assert lib.rebk_selftest_waits(10**6, None, None) == R.REBK_EINVAL
     assert lib.rebk_selftest_waits(10, ctypes.cast(codes, ctypes.c_void_p), None) == R.REBK_EINVAL
     assert lib.rebk_selftest_waits(10**10, ctypes.cast(codes, ctypes.c_void_p), None) == R.REBK_EINVAL
+
+
+def test_partition_offsets_are_checked_before_any_cuda_call():
+    """rebk_create's partition (Section 2's I_1..I_s, J_1..J_t) must run from 0 to
+    m (n) strictly increasing, with blocks of at most 512; anything else is
+    rejected on the host."""
+    import ctypes
+    from paper_2001_04179_gb300 import rebk as R
+    lib = R.load()
+    A = (ctypes.c_double * 4)(1, 2, 3, 4)   # never read: the call returns before any copy
+    opt = R.RebkOptions(4, 4, 0, 0, 0, None)
+
+    def create(row, col, m=100, n=50):
+        h = ctypes.c_void_p()
+        ro = None if row is None else (ctypes.c_int64 * len(row))(*row)
+        co = None if col is None else (ctypes.c_int64 * len(col))(*col)
+        part = R.RebkPartition(None if ro is None else ctypes.cast(ro, ctypes.c_void_p).value,
+                               0 if row is None else len(row) - 1,
+                               None if co is None else ctypes.cast(co, ctypes.c_void_p).value,
+                               0 if col is None else len(col) - 1)
+        st = lib.rebk_create(ctypes.byref(h), A, m, n, n, 0, ctypes.byref(part), 1.0, ctypes.byref(opt))
+        assert not h.value
+        return st
+
+    assert create([1, 50, 100], None) == R.REBK_EINVAL          # does not start at 0
+    assert create([0, 50, 99], None) == R.REBK_EINVAL           # does not end at m
+    assert create([0, 50, 50, 100], None) == R.REBK_EINVAL      # an empty block
+    assert create([0, 60, 40, 100], None) == R.REBK_EINVAL      # decreasing
+    assert create(None, [0, 25]) == R.REBK_EINVAL               # ends short of n
+    assert create(None, [0, 50, 60]) == R.REBK_EINVAL           # past n
+    assert "column partition" in lib.rebk_last_error().decode()
+    assert create([0, 600, 1000], None, m=1000) == R.REBK_EUNSUPPORTED  # a block above 512
+    assert "512" in lib.rebk_last_error().decode()
