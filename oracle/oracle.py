@@ -18,6 +18,8 @@ the plain C file ``rebk_oracle.c`` next to this one, compiled with
 * ``mlp_forward`` / ``mlp_backward``: the warm-start network in FP64.
 * ``rebk_sparse``: Algorithm 1 over the stored entries of a CSR matrix, for
   matrices whose dense form does not fit (numpy, the same draws as ``rebk``).
+* ``rebk_free``: the iteration with index sets drawn without a partition (a
+  reading of Section 4's variants), in C next to Algorithm 1.
 """
 from __future__ import annotations
 
@@ -32,7 +34,7 @@ __all__ = [
     "build_oracle", "lib",
     "philox", "uniform", "pick",
     "block_norms", "cdf", "tables",
-    "rebk", "rebk_correction", "rebk_sparse",
+    "rebk", "rebk_correction", "rebk_sparse", "rebk_free", "uniform_slot",
     "pinv_solve", "mean_closed_form", "beta_max",
     "bound_ner", "bound_estz", "bound_main",
     "round_fp32", "round_bf16",
@@ -111,6 +113,15 @@ def _declare(L):
                                       ctypes.c_int64, ctypes.c_int64, _f64p, _f64p, ctypes.c_double,
                                       _i32p, _f64p]
     L.orc_rebk_correction.restype = ctypes.c_int64
+    L.orc_uniform_slot.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
+    L.orc_uniform_slot.restype = ctypes.c_double
+    L.orc_rebk_free.argtypes = [ctypes.c_int64, ctypes.c_int64, _f64p, ctypes.c_int64,
+                                _f64p, _f64p, _f64p, _f64p, ctypes.c_int64, ctypes.c_int64,
+                                ctypes.c_double, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_int64,
+                                _f64p, _f64p, _f64p,
+                                ctypes.c_int64, ctypes.c_int64, _f64p, ctypes.c_double,
+                                _i32p, _i64p, _i64p, _f64p]
+    L.orc_rebk_free.restype = ctypes.c_int64
     return L
 
 
@@ -217,6 +228,38 @@ def rebk(A, b, row_off, col_off, alpha, seed, iters, stream=0, k0=0, z0=None, x0
                           _p(nr), _p(nc), _p(cr), _p(cc), float(alpha), seed, stream, k0,
                           _p(b), _p(z), _p(x), iters, check_every, _p(xr), float(tol),
                           _p(idx, _i32p), _p(work))
+    return {"x": x, "z": z, "iters": int(done), "idx": None if idx is None else idx[:done]}
+
+
+def uniform_slot(seed: int, stream: int, d: int, q: int) -> float:
+    """u of slot q of draw d (Philox counter (d, q, 0, 0)); slot 0 is ``uniform``."""
+    return lib().orc_uniform_slot(seed, stream, d, q)
+
+
+def rebk_free(A, b, tau_r, tau_c, alpha, seed, iters, stream=0, k0=0, z0=None, x0=None,
+              check_every=0, x_ref=None, tol=0.0, record=False):
+    """Iterations k0+1 .. k0+iters of Algorithm 1 with index sets drawn without a
+    partition (see orc_rebk_free in rebk_oracle.c: tau_c columns and tau_r rows
+    drawn independently with probabilities proportional to their squared norms,
+    the step of Algorithm 1 on the drawn submatrices).  Row and column norms
+    come from ``block_norms`` with blocks of one row / column.  Returns
+    dict(x, z, iters, idx) with idx an (iters, tau_c + tau_r) array (column
+    draws, then row draws) when ``record``."""
+    A = _f64(A)
+    m, n = A.shape
+    rn, cn = block_norms(A, np.arange(m + 1), np.arange(n + 1))
+    cr, cc = cdf(rn), cdf(cn)
+    b = _f64(b)
+    z = _f64(b.copy() if z0 is None else z0).copy()
+    x = np.zeros(n) if x0 is None else _f64(x0).copy()
+    idx = np.zeros((max(iters, 1), tau_c + tau_r), dtype=np.int32) if record else None
+    xr = None if x_ref is None else _f64(x_ref)
+    jset = np.zeros(tau_c, dtype=np.int64)
+    iset = np.zeros(tau_r, dtype=np.int64)
+    work = np.zeros(tau_c + tau_r)
+    done = lib().orc_rebk_free(m, n, _p(A), n, _p(rn), _p(cn), _p(cr), _p(cc), tau_r, tau_c, float(alpha),
+                               seed, stream, k0, _p(b), _p(z), _p(x), iters, check_every, _p(xr), float(tol),
+                               _p(idx, _i32p), _p(jset, _i64p), _p(iset, _i64p), _p(work))
     return {"x": x, "z": z, "iters": int(done), "idx": None if idx is None else idx[:done]}
 
 

@@ -326,3 +326,111 @@ int64_t orc_rebk_correction(int64_t m, int64_t n, const double *Alo, int64_t lda
     }
     return max_iter;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Sampling without partitions (a reading of Section 4's variants)          */
+/* ------------------------------------------------------------------------ */
+
+/* Uniform double in [0, 1) for slot q of draw number d: Philox counter
+ * (d, q, 0, 0), key (seed, stream), word 0.  Slot 0 is orc_uniform's draw. */
+double orc_uniform_slot(uint64_t seed, uint64_t stream, uint64_t d, uint64_t q)
+{
+    uint64_t ctr[4] = {d, q, 0, 0};
+    uint64_t key[2] = {seed, stream};
+    uint64_t out[4];
+    orc_philox4x64_10(ctr, key, out);
+    return (double)(out[0] >> 11) * 0x1.0p-53;
+}
+
+/*
+ * Algorithm 1 with index sets drawn without a partition.  Section 4 names
+ * variants of REBK whose random samplings do not depend on partitions; the
+ * reading taken here: iteration k draws tau_c column indices j_1..j_{tau_c}
+ * independently, each with probability ||A_{:,j}||^2 / ||A||_F^2 (slot q of
+ * column draw 2(k-1)), and tau_r row indices i_1..i_{tau_r} independently with
+ * probability ||A_{i,:}||^2 / ||A||_F^2 (slot q of row draw 2(k-1)+1).  A_J is
+ * the m x tau_c matrix of the drawn columns in draw order (a column drawn
+ * twice appears twice) and A_I the tau_r x n matrix of the drawn rows; the
+ * step is Algorithm 1's with these matrices:
+ *
+ *   z <- z - alpha / ||A_J||_F^2 * A_J A_J^T z
+ *   x <- x - alpha / ||A_I||_F^2 * A_I^T (A_I x - b_I + z_I)
+ *
+ * with ||A_J||_F^2 = sum_q ||A_{:,j_q}||^2 (in draw order), likewise for I.
+ * (This is RABK's step with weights ||a_i||^2 / ||A_I||_F^2 over the drawn
+ * set.)  With tau_r = tau_c = 1 it is the randomized extended Kaczmarz
+ * method.  cn / rn: squared column / row norms; cdf_c / cdf_r: their inclusive
+ * prefix sums.  idx_out (optional): tau_c + tau_r entries per iteration, the
+ * column draws then the row draws.  work: tau_c + tau_r doubles.  Stopping as
+ * orc_rebk.  Returns the number of iterations run.
+ */
+int64_t orc_rebk_free(int64_t m, int64_t n, const double *A, int64_t lda,
+                      const double *rn, const double *cn,
+                      const double *cdf_r, const double *cdf_c,
+                      int64_t tau_r, int64_t tau_c,
+                      double alpha, uint64_t seed, uint64_t stream, int64_t k0,
+                      const double *b, double *z, double *x,
+                      int64_t max_iter, int64_t check_every,
+                      const double *x_ref, double tol,
+                      int32_t *idx_out, int64_t *jset, int64_t *iset, double *work)
+{
+    for (int64_t it = 1; it <= max_iter; ++it) {
+        uint64_t k = (uint64_t)(k0 + it);
+
+        /* column step on z */
+        double fJ = 0.0;
+        for (int64_t q = 0; q < tau_c; ++q) {
+            jset[q] = orc_pick(cdf_c, n, orc_uniform_slot(seed, stream, 2 * (k - 1), (uint64_t)q));
+            fJ += cn[jset[q]];
+        }
+        double cJ = alpha / fJ;
+        double *w = work;
+        for (int64_t q = 0; q < tau_c; ++q) {
+            double acc = 0.0;
+            for (int64_t r = 0; r < m; ++r)
+                acc += A[r * lda + jset[q]] * z[r];
+            w[q] = acc;
+        }
+        for (int64_t r = 0; r < m; ++r) {
+            double acc = 0.0;
+            for (int64_t q = 0; q < tau_c; ++q)
+                acc += A[r * lda + jset[q]] * w[q];
+            z[r] -= cJ * acc;
+        }
+
+        /* row step on x, with the updated z */
+        double fI = 0.0;
+        for (int64_t q = 0; q < tau_r; ++q) {
+            iset[q] = orc_pick(cdf_r, m, orc_uniform_slot(seed, stream, 2 * (k - 1) + 1, (uint64_t)q));
+            fI += rn[iset[q]];
+        }
+        double cI = alpha / fI;
+        double *res = work + tau_c;
+        for (int64_t q = 0; q < tau_r; ++q) {
+            int64_t l = iset[q];
+            double acc = 0.0;
+            for (int64_t c = 0; c < n; ++c)
+                acc += A[l * lda + c] * x[c];
+            res[q] = acc - b[l] + z[l];
+        }
+        for (int64_t c = 0; c < n; ++c) {
+            double acc = 0.0;
+            for (int64_t q = 0; q < tau_r; ++q)
+                acc += A[iset[q] * lda + c] * res[q];
+            x[c] -= cI * acc;
+        }
+
+        if (idx_out) {
+            int32_t *row = idx_out + (it - 1) * (tau_c + tau_r);
+            for (int64_t q = 0; q < tau_c; ++q) row[q] = (int32_t)jset[q];
+            for (int64_t q = 0; q < tau_r; ++q) row[tau_c + q] = (int32_t)iset[q];
+        }
+        if (x_ref && check_every > 0 && it % check_every == 0) {
+            double ref2;
+            double e2 = rel_err2(n, x, x_ref, &ref2);
+            if (e2 <= tol * tol * ref2)
+                return it;
+        }
+    }
+    return max_iter;
+}
