@@ -185,6 +185,33 @@ rebk_status rebk_solve_refined(rebk_handle h, const double *b, double *x, double
                                const rebk_solve_ext *ext, rebk_stats *stats);
 
 /*
+ * Algorithm 1 with index sets drawn without a partition (plain FP64).  Section 4
+ * names variants of REBK whose random samplings do not depend on partitions;
+ * the reading built here: iteration k draws tau_col column indices
+ * independently, each with probability ||A_{:,j}||^2 / ||A||_F^2, and tau_row
+ * row indices likewise with ||A_{i,:}||^2 / ||A||_F^2, and takes Algorithm 1's
+ * step on the drawn columns A_J and rows A_I (a repeated draw repeats its
+ * column or row; ||A_J||_F^2 sums the drawn columns' squared norms):
+ *   z <- z - alpha / ||A_J||_F^2 A_J A_J^T z,
+ *   x <- x - alpha / ||A_I||_F^2 A_I^T (A_I x - b_I + z_I).
+ * Each step is non-expansive for 0 < alpha < 2.  At tau_row = tau_col = 1 it is
+ * the randomized extended Kaczmarz method.  Draw q (0-based) of the column set
+ * of iteration k uses Philox counter (2(k-1), q, 0, 0), of the row set
+ * (2(k-1)+1, q, 0, 0), key (seed, ext->stream_id), word 0 as in rebk_solve.
+ * h: any handle (its FP64 copy of A; the per-row and per-column norm tables
+ * are built on the first call).  alpha > 0: the step; <= 0: the handle's alpha.
+ * tau_row, tau_col in [1, 512].  ext as for rebk_solve_ex (x_ref stop rule
+ * checked every check_every iterations, x0, z0, z_out, k0, stream_id), except
+ * idx_out: device, (tau_col + tau_row) x max_iter int32 -- per iteration the
+ * column draws, then the row draws.  Without x_ref (or tol <= 0) the solve runs
+ * max_iter iterations.  Errors: EINVAL, EUNSUPPORTED (tau above 512), ENOMEM,
+ * ECUDA, DIVERGED, BARRIER_TIMEOUT.
+ */
+rebk_status rebk_solve_free(rebk_handle h, int64_t tau_row, int64_t tau_col, double alpha, const double *b,
+                            double *x, double tol, int64_t max_iter, uint64_t seed, const rebk_solve_ext *ext,
+                            rebk_stats *stats);
+
+/*
  * beta^I_max and beta^J_max of Section 2.2 (largest ||block||_2^2 / ||block||_F^2
  * over the row blocks and over the column blocks), from FP64 block Gram
  * matrices and power iteration on the device.  Outputs are host doubles.

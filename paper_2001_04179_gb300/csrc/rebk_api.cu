@@ -98,6 +98,14 @@ struct rebk_handle_s {
     std::vector<cudaEvent_t> sweep_ev;  // start/stop pairs of the FP64 sweeps
     size_t sweep_used = 0;
     cudaEvent_t kev0 = nullptr, kev1 = nullptr;
+    // partition-free sampling (rebk_solve_free): per-row / per-column tables,
+    // built on first use; draws of one launch; accumulators
+    double *fr_rn = nullptr, *fr_cn = nullptr, *fr_cdf_r = nullptr, *fr_cdf_c = nullptr;
+    int fr_fb[2] = {0, 0};
+    int32_t *fr_idx = nullptr;
+    int64_t fr_idx_cap = 0;  // in int32 entries
+    double *fr_acc = nullptr;
+    int fr_acc_w = 0;
 };
 
 namespace {
@@ -105,7 +113,8 @@ namespace {
 void free_handle(rebk_handle h) {
     if (!h) return;
     void *ptrs[] = {h->A64, h->A32, h->A16, h->nr, h->nc, h->cdf_r, h->cdf_c, h->d_fallback, h->acc,
-                    h->d_row_off, h->d_col_off,
+                    h->d_row_off, h->d_col_off, h->fr_rn, h->fr_cn, h->fr_cdf_r, h->fr_cdf_c,
+                    h->fr_idx, h->fr_acc,
                     h->coef_r64, h->coef_c64, h->coef_r32, h->coef_c32,
                     h->ws, h->zbuf, h->f, h->g, h->ym, h->yn, h->dz, h->dx, h->sd, h->vd,
                     h->idxbuf};
@@ -1111,6 +1120,187 @@ rebk_status rebk_solve_refined(rebk_handle h, const double *b, double *x, double
     float ms = 0.f;
     cudaEventElapsedTime(&ms, h->ev0, h->ev1);
     fill_stats(h, stats, total, outer, result, rel, rf, rg, ms);
+    return result;
+}
+
+rebk_status rebk_solve_free(rebk_handle h, int64_t tau_row, int64_t tau_col, double alpha, const double *b,
+                            double *x, double tol, int64_t max_iter, uint64_t seed, const rebk_solve_ext *ext,
+                            rebk_stats *stats) {
+    g_last_error.clear();
+    if (!h) return fail(REBK_EINVAL, "handle is NULL");
+    if (!b || !x) return fail(REBK_EINVAL, "b and x must be device pointers");
+    if (tau_row < 1 || tau_col < 1) return fail(REBK_EINVAL, "tau_row and tau_col must be >= 1");
+    if (tau_row > 512 || tau_col > 512) return fail(REBK_EUNSUPPORTED, "tau > 512");
+    if (max_iter < 0) return fail(REBK_EINVAL, "max_iter < 0");
+    if (!std::isfinite(tol) || !std::isfinite(alpha)) return fail(REBK_EINVAL, "tol or alpha not finite");
+    rebk_solve_ext e;
+    memset(&e, 0, sizeof(e));
+    if (ext) e = *ext;
+    if (e.k0 < 0) return fail(REBK_EINVAL, "k0 < 0");
+    const cudaStream_t st = h->stream;
+    const int tr = (int)tau_row, tc = (int)tau_col, W = tr + tc;
+    const double a_step = alpha > 0.0 ? alpha : h->alpha;
+    reset_counters(h);
+    // per-row / per-column squared norms and prefix sums (tables with blocks of one)
+    if (!h->fr_rn) {
+        double *scratch = nullptr;
+        int *fb = nullptr;
+        CK(cudaMalloc(&h->fr_rn, sizeof(double) * h->m));
+        CK(cudaMalloc(&h->fr_cdf_r, sizeof(double) * h->m));
+        CK(cudaMalloc(&h->fr_cn, sizeof(double) * h->n));
+        CK(cudaMalloc(&h->fr_cdf_c, sizeof(double) * h->n));
+        CK(cudaMalloc(&scratch, sizeof(double) * (size_t)(h->m + h->n + 64 * h->n)));
+        CK(cudaMalloc(&fb, sizeof(int) * 2));
+        cudaError_t ce = block_tables(h->A64, h->lda, h->m, h->n, 1, 1, (int)h->m, (int)h->n, h->fr_rn, h->fr_cn,
+                                      h->fr_cdf_r, h->fr_cdf_c, fb, scratch, st);
+        if (ce == cudaSuccess) ce = cudaMemcpyAsync(h->fr_fb, fb, sizeof(int) * 2, cudaMemcpyDeviceToHost, st);
+        if (ce == cudaSuccess) ce = cudaStreamSynchronize(st);
+        cudaFree(scratch);
+        cudaFree(fb);
+        CK(ce);
+    }
+    const int acc_w = (int)round_up(W + 1, 32);
+    if (acc_w > h->fr_acc_w) {
+        if (h->fr_acc) cudaFree(h->fr_acc);
+        h->fr_acc = nullptr;
+        h->fr_acc_w = 0;
+        CK(cudaMalloc(&h->fr_acc, sizeof(double) * 3 * (size_t)acc_w));
+        h->fr_acc_w = acc_w;
+    }
+    double *z = e.z_out ? e.z_out : h->zbuf;
+    CK(cudaEventRecord(h->ev0, st));
+    if (e.z0) {
+        if (e.z0 != z) CK(cudaMemcpyAsync(z, e.z0, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, st));
+    } else {
+        CK(cudaMemcpyAsync(z, b, sizeof(double) * h->m, cudaMemcpyDeviceToDevice, st));
+    }
+    if (e.x0) {
+        if (e.x0 != x) CK(cudaMemcpyAsync(x, e.x0, sizeof(double) * h->n, cudaMemcpyDeviceToDevice, st));
+    } else {
+        CK(cudaMemsetAsync(x, 0, sizeof(double) * h->n, st));
+    }
+    double rel = -1.0;
+    if (h->fro2 == 0.0 || max_iter == 0) {
+        CK(cudaStreamSynchronize(st));
+        if (e.x_ref) {
+            rebk_status s = rel_error(h, x, e.x_ref, &rel);
+            if (s != REBK_OK) return s;
+        }
+        fill_stats(h, stats, 0, 0, REBK_OK, rel, -1, -1, 0.0);
+        return REBK_OK;
+    }
+    int G = free_max_ctas(tr, tc);
+    if (G < 1) return fail(REBK_EUNSUPPORTED, "the partition-free kernel does not fit on this GPU");
+    G = (int)std::min<int64_t>(G, std::max<int64_t>(1, std::max(h->m, h->n) / 32));
+    if (h->num_ctas_opt > 0) G = std::min(G, h->num_ctas_opt);
+    const bool use_ref = e.x_ref != nullptr && tol > 0;
+    int64_t check = h->check_every > 0 ? h->check_every : 10;
+    double ref2 = 0.0;
+    if (use_ref) {
+        LK(h, sum_sq(e.x_ref, h->n, h->ws->small, st));
+        double v[2];
+        rebk_status s = fetch_small(h, v, 2);
+        if (s != REBK_OK) return s;
+        ref2 = v[1];
+    }
+    FreeArgs a;
+    memset(&a, 0, sizeof(a));
+    a.A = h->A64;
+    a.lda = h->lda;
+    a.m = h->m;
+    a.n = h->n;
+    a.tau_r = tr;
+    a.tau_c = tc;
+    a.rn = h->fr_rn;
+    a.cn = h->fr_cn;
+    a.alpha = a_step;
+    a.z = z;
+    a.x = x;
+    a.b = b;
+    a.acc = h->fr_acc;
+    a.acc_w = acc_w;
+    a.bar = &h->ws->bar;
+    a.status = &h->ws->status;
+    a.iters_done = &h->ws->iters_done;
+    a.x_ref = use_ref ? e.x_ref : nullptr;
+    a.tol2_abs = tol * tol * ref2;
+    a.check_every = check;
+    a.timeout_ns = kBarrierTimeoutNs;
+    // draws of one launch: at most 2^22 entries in the handle's buffer
+    const int64_t chunk_cap = std::max<int64_t>(1, ((int64_t)1 << 22) / W);
+    int64_t total = 0, grow = 4096;
+    rebk_status result = REBK_MAX_ITER;
+    while (total < max_iter) {
+        int64_t chunk = std::min(max_iter - total, e.idx_out ? kMaxItersPerLaunch : chunk_cap);
+        if (use_ref) {
+            chunk = std::min(chunk, grow);
+            grow = std::min<int64_t>(grow * 2, chunk_cap);
+        }
+        int32_t *dst = e.idx_out ? e.idx_out + (size_t)W * total : nullptr;
+        if (!dst) {
+            if (chunk * W > h->fr_idx_cap) {
+                if (h->fr_idx) cudaFree(h->fr_idx);
+                h->fr_idx = nullptr;
+                h->fr_idx_cap = 0;
+                CK(cudaMalloc(&h->fr_idx, sizeof(int32_t) * (size_t)chunk * W));
+                h->fr_idx_cap = chunk * W;
+            }
+            dst = h->fr_idx;
+        }
+        LK(h, free_sample(seed, e.stream_id, e.k0 + total, chunk, h->fr_cdf_r, h->m, h->fr_cdf_c, h->n, tr, tc,
+                          h->fr_fb[0], h->fr_fb[1], dst, st));
+        a.idx = dst;
+        a.iters = chunk;
+        a.check_offset = total;
+        CK(cudaMemsetAsync(h->fr_acc, 0, sizeof(double) * 3 * (size_t)acc_w, st));
+        CK(cudaMemsetAsync(h->ws, 0, sizeof(Workspace), st));
+        CK(cudaEventRecord(h->kev0, st));
+        CK(launch_free(a, G, st));
+        CK(cudaEventRecord(h->kev1, st));
+        ++h->launches;
+        ++h->grid_launches;
+        Workspace w;
+        CK(cudaMemcpyAsync(&w, h->ws, sizeof(Workspace), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        float kms = 0.f;
+        CK(cudaEventElapsedTime(&kms, h->kev0, h->kev1));
+        h->kernel_ms += kms;
+        total += w.iters_done;
+        if (w.status == 6) {
+            fill_stats(h, stats, total, 0, REBK_BARRIER_TIMEOUT, -1, -1, -1, 0);
+            return fail(REBK_BARRIER_TIMEOUT, "device-wide barrier timed out");
+        }
+        if (w.status == 5) {
+            result = REBK_DIVERGED;
+            break;
+        }
+        if (use_ref) {
+            if (w.iters_done < chunk) {  // stopped by the error test
+                result = REBK_OK;
+                break;
+            }
+            if (total % check == 0) {  // the last iterate of a launch is tested here
+                rebk_status s = rel_error(h, x, e.x_ref, &rel);
+                if (s != REBK_OK) return s;
+                if (rel <= tol) {
+                    result = REBK_OK;
+                    break;
+                }
+            }
+        }
+    }
+    CK(cudaEventRecord(h->ev1, st));
+    CK(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    if (e.x_ref) {
+        rebk_status s = rel_error(h, x, e.x_ref, &rel);
+        if (s != REBK_OK) return s;
+        if (result == REBK_MAX_ITER && use_ref && rel <= tol) result = REBK_OK;
+    }
+    if (!use_ref && result == REBK_MAX_ITER) result = REBK_OK;
+    fill_stats(h, stats, total, 0, result, rel, -1, -1, ms);
+    if (result == REBK_DIVERGED) return fail(REBK_DIVERGED, "iteration diverged (Inf/NaN)");
     return result;
 }
 

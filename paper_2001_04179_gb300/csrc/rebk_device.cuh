@@ -50,6 +50,12 @@ __device__ __forceinline__ double draw_uniform(uint64_t seed, uint64_t stream, u
     return (double)(o.w[0] >> 11) * 0x1.0p-53;
 }
 
+// u in [0, 1) for slot q of draw d: counter (d, q, 0, 0); slot 0 is draw_uniform.
+__device__ __forceinline__ double draw_uniform_slot(uint64_t seed, uint64_t stream, uint64_t d, uint64_t q) {
+    const PhiloxOut o = philox4x64_10(d, q, 0, 0, seed, stream);
+    return (double)(o.w[0] >> 11) * 0x1.0p-53;
+}
+
 // Smallest b in [0, nb) with cdf[b] > u * cdf[nb-1]; if none (the product
 // rounded to the total), the fallback block (last one of nonzero norm).
 __device__ __forceinline__ int pick_block(const double *cdf, int nb, double u, int fallback) {

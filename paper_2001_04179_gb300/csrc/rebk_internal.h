@@ -189,6 +189,37 @@ cudaError_t vec_sub(const double *a, const double *b, double *out, int64_t n, cu
 cudaError_t lanczos_extremes(const double *A, int64_t lda, int64_t m, int64_t n, int steps, uint64_t seed,
                              cudaStream_t st, double *sigma1_sq, double *sigma_r_sq, int *steps_done);
 
+// Arguments of the partition-free kernel (rebk_free.cu): Algorithm 1's step on
+// index sets drawn independently per row / column (plain FP64).
+struct FreeArgs {
+    const double *A;        // FP64 copy, row-major, leading dimension lda
+    int64_t lda, m, n;
+    int tau_r, tau_c;       // rows and columns drawn per iteration
+    const double *rn, *cn;  // squared row / column norms
+    double alpha;
+    const int32_t *idx;     // [iters][tau_c + tau_r]: column draws, then row draws
+    int64_t iters;
+    double *z, *x;
+    const double *b;
+    double *acc;            // 3 sets of acc_w doubles (r, w, test partial), zeroed before launch
+    int acc_w;
+    unsigned int *bar;      // zeroed before launch
+    int *status;            // zeroed before launch
+    int64_t *iters_done;
+    const double *x_ref;    // NULL = no error test
+    double tol2_abs;
+    int64_t check_every, check_offset;
+    unsigned long long timeout_ns;
+};
+// idx[it][q]: draw q of iteration k0 + it + 1 (columns q < tau_c from the
+// column draw's slots, rows after them from the row draw's slots).
+cudaError_t free_sample(uint64_t seed, uint64_t stream, int64_t k0, int64_t K, const double *cdf_r, int64_t m,
+                        const double *cdf_c, int64_t n, int tau_r, int tau_c, int fb_r, int fb_c, int32_t *idx,
+                        cudaStream_t st);
+cudaError_t launch_free(const FreeArgs &a, int G, cudaStream_t st);
+size_t free_smem_bytes(int tau_r, int tau_c);
+int free_max_ctas(int tau_r, int tau_c);
+
 // Sets the message rebk_last_error() returns on this thread (rebk_api.cu).
 void set_last_error(const std::string &msg);
 

@@ -118,6 +118,9 @@ _SIGNATURES = {
     "rebk_solve_refined": ([_P, _P, _P, ctypes.c_double, ctypes.c_int64, ctypes.c_uint64,
                             ctypes.POINTER(RebkRefineOpts), ctypes.POINTER(RebkSolveExt),
                             ctypes.POINTER(RebkStats)], ctypes.c_int),
+    "rebk_solve_free": ([_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, _P, _P, ctypes.c_double,
+                         ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(RebkSolveExt), ctypes.POINTER(RebkStats)],
+                        ctypes.c_int),
     "rebk_beta_max": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "rebk_get_alpha": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "rebk_set_alpha": ([_P, ctypes.c_double], ctypes.c_int),

@@ -187,6 +187,35 @@ class Solver:
             out["idx"] = idx[: 2 * stats.iterations].view(-1, 2)
         return out
 
+    def solve_free(self, b, tau_row: int, tau_col: int, alpha: float = 0.0, tol: float = 0.0,
+                   max_iter: int = 1000, seed: int = 0, x_ref=None, x0=None, z0=None, k0: int = 0,
+                   stream_id: int = 0, record: bool = False, return_z: bool = False, x=None,
+                   allow=(_r.REBK_OK, _r.REBK_MAX_ITER)):
+        """Algorithm 1 with index sets drawn without a partition (rebk_solve_free):
+        tau_col columns and tau_row rows drawn independently with probabilities
+        proportional to their squared norms per iteration.  alpha <= 0 uses the
+        handle's.  Returns dict(x, stats[, z][, idx]); idx is (iterations,
+        tau_col + tau_row): the column draws, then the row draws."""
+        torch = _torch()
+        _require_cuda_f64(b, self.m, "b")
+        if x is None:
+            x = torch.empty(self.n, dtype=torch.float64, device=b.device)
+        z = torch.empty(self.m, dtype=torch.float64, device=b.device) if return_z else None
+        W = int(tau_row) + int(tau_col)
+        idx = torch.zeros(max(W * max_iter, 1), dtype=torch.int32, device=b.device) if record else None
+        ext = self._ext(x_ref, x0, z0, z, idx, k0, stream_id)
+        stats = _r.RebkStats()
+        st = _r.load().rebk_solve_free(self._h, int(tau_row), int(tau_col), float(alpha),
+                                       ctypes.c_void_p(b.data_ptr()), ctypes.c_void_p(x.data_ptr()), float(tol),
+                                       int(max_iter), int(seed), ctypes.byref(ext), ctypes.byref(stats))
+        _r.check(st, allow)
+        out = {"x": x, "stats": stats.as_dict(), "status": st}
+        if return_z:
+            out["z"] = z
+        if record:
+            out["idx"] = idx[: W * stats.iterations].view(-1, W)
+        return out
+
     def solve_rabk(self, b, **kw):
         """The RABK special case (the remark after Algorithm 1): z^0 = 0 keeps every
         z^k = 0, so each step is the weighted block average of eq. (rabk) on A x = b
