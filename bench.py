@@ -66,6 +66,9 @@ def parse():
     ap.add_argument("--warm-eval", type=int, default=32)
     ap.add_argument("--warm-batch-systems", type=int, default=152)
     ap.add_argument("--warm-steps", type=int, default=4000)
+    ap.add_argument("--profile-mlp", type=int, default=0, metavar="K",
+                    help="run K training steps (batch 256) of the 8192 -> 512 -> 512 -> 8192 warm-start network "
+                         "and print the time per step (the case the network's ncu summary captures)")
     ap.add_argument("--profile-pass", type=int, default=0, metavar="K",
                     help="run one K-iteration refinement pass of the workload twice and exit "
                          "(the case the ncu summaries under profiles/ capture)")
@@ -796,10 +799,53 @@ def R_STATUS(code: int) -> str:
     return R.STATUS_NAMES.get(code, str(code))
 
 
+def run_profile_mlp(args):
+    """K training steps of the warm-start network on a random 8192 x 2048 A and
+    random targets (y-space loss): the network's products, Adam and the
+    conversions, timed with CUDA events; warm-up steps first."""
+    import ctypes
+
+    import torch
+
+    from paper_2001_04179_gb300 import WarmStartNet
+    from paper_2001_04179_gb300 import rebk as R
+
+    m, n, B = 8192, 2048, 256
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((m, n)) / np.sqrt(m)
+    net = WarmStartNet(A, hidden=512, batch_capacity=B, seed=1)
+    net.set_loss("y_rel", 0.1)
+    Bm = torch.from_numpy(rng.standard_normal((B, m))).cuda()
+    T = torch.from_numpy(rng.standard_normal((B, m))).cuda()
+    lib = R.load()
+    loss = ctypes.c_double()
+
+    def step():
+        R.check(lib.rebk_mlp_train_step(net._h, ctypes.c_void_p(Bm.data_ptr()), ctypes.c_void_p(T.data_ptr()), B,
+                                        1e-3, ctypes.byref(loss)))
+
+    for _ in range(max(1, args.warmup)):
+        step()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record()
+    for _ in range(args.profile_mlp):
+        step()
+    ev1.record()
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / args.profile_mlp
+    flops = 2.0 * B * (2 * m * 512 + 512 * 512) * 2.5  # forward 1x, weight and input gradients 1.5x
+    print(json.dumps({"profile_mlp": args.profile_mlp, "ms_per_step": ms, "tflops_per_step": flops / (ms * 1e-3) / 1e12,
+                      "loss": loss.value}))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.profile_mlp > 0:
+        return run_profile_mlp(args)
     if args.workload == "sweep":
         return run_sweep(args)
     if args.workload == "sparse":

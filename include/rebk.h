@@ -502,6 +502,22 @@ rebk_status rebk_mlp_get_weights(rebk_mlp h, float *const *weights_host);
 rebk_status rebk_mlp_shape(rebk_mlp h, int64_t *m, int64_t *n);
 
 /*
+ * The BF16 GEMM the warm-start network runs on, for direct use:
+ * C (M x N, FP32, row-major, leading dimension ldc) = alpha * A B^T with A
+ * (M x K) and B (N x K) BF16 (raw bits), row-major with leading dimensions
+ * lda, ldb >= K, all device pointers.  FP32 accumulation.  When K, lda and ldb
+ * are multiples of 8 and A, B are 16-byte aligned it runs on the fifth-
+ * generation tensor cores (tcgen05 with TMA-staged tiles, accumulator in
+ * tensor memory; *path = 1), else on a small mma.sync kernel (*path = 0; path
+ * may be NULL).  stream: cudaStream_t (NULL = legacy default); the call
+ * synchronises it.  The paper has no counterpart.
+ * Errors: EINVAL (NULL pointers, shapes), EUNSUPPORTED (a dimension above
+ * 2^31), ENOMEM, ECUDA (including a bounded wait inside the kernel that gave up).
+ */
+rebk_status rebk_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B, int64_t ldb,
+                           float alpha, float *C, int64_t ldc, void *stream, int32_t *path);
+
+/*
  * Warm start for rebk_solve_ex / rebk_solve_refined: y = net(b),
  * x0 = A^T y and z0 = b - A x0 computed with the solver's FP64 copy of A.
  * b: device, m; x0: device, n; z0: device, m (outputs).  Pass them as

@@ -220,6 +220,21 @@ cudaError_t launch_free(const FreeArgs &a, int G, cudaStream_t st);
 size_t free_smem_bytes(int tau_r, int tau_c);
 int free_max_ctas(int tau_r, int tau_c);
 
+// Tensor-core BF16 GEMM (rebk_umma.cu): C (M x N) = alpha * A B^T with A (M x K)
+// and B (N x K) K-contiguous BF16 rows (leading dimensions lda, ldb); FP32
+// accumulation; epilogue writes FP32 C (ldc), a BF16 copy Cb and a transposed
+// BF16 copy CbT (CbT[j * ldcbt + i]), each optional, after ReLU and a mask
+// (mask[i * ldm + j] > 0).  Splits K when the output has few tiles and the
+// workspace ws (ws_floats floats; umma_workspace_floats() always suffice) holds
+// the partial slices, summed in a fixed order.  *error (device int) is set when
+// a bounded wait gave up.
+bool umma_gemm_supported(int M, int N, int K, const void *A, int64_t lda, const void *B, int64_t ldb);
+size_t umma_workspace_floats();
+cudaError_t umma_gemm(int M, int N, int K, const __nv_bfloat16 *A, int64_t lda, const __nv_bfloat16 *B,
+                      int64_t ldb, float alpha, float *C, int64_t ldc, __nv_bfloat16 *Cb, int64_t ldcb,
+                      __nv_bfloat16 *CbT, int64_t ldcbt, int relu, const float *mask, int64_t ldm, float *ws,
+                      size_t ws_floats, int *error, cudaStream_t st);
+
 // Sets the message rebk_last_error() returns on this thread (rebk_api.cu).
 void set_last_error(const std::string &msg);
 

@@ -14,10 +14,15 @@
 // directions the iteration converges slowest in; the x-space loss shrinks their
 // gradient by sigma^2 instead.
 //
-// Arithmetic: BF16 operands, FP32 accumulation on the tensor cores
-// (mma.sync m16n8k16), FP32 master weights and Adam moments.  The network is a
-// tiny share of a warm-started solve, so one generic tiled GEMM with strided
-// operands serves every product of the forward and backward passes.
+// Arithmetic: BF16 operands, FP32 accumulation on the tensor cores, FP32
+// master weights and Adam moments.  Every product of the forward and backward
+// passes is written C = A B^T with both operands K-contiguous, so that one
+// tcgen05 GEMM (rebk_umma.cu: TMA-staged 128-byte-swizzled tiles, TMEM
+// accumulator) serves them all; the epilogues and the Adam step keep the
+// transposed BF16 copies (activations, output gradients, weights) that the
+// next product reads as its K-major operand.  Shapes the TMA tiles cannot
+// describe (a K or leading dimension off a 16-byte multiple) run on a small
+// mma.sync kernel with strided operands instead.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -49,6 +54,8 @@ struct GemmArgs {
     int64_t ldc;
     __nv_bfloat16 *Cb;
     int64_t ldcb;
+    __nv_bfloat16 *CbT;
+    int64_t ldcbt;
     float alpha, beta;
     int relu;
     const float *mask;
@@ -131,6 +138,7 @@ __global__ void __launch_bounds__(128) mlp_gemm_kernel(const GemmArgs g) {
                 if (g.mask && !(g.mask[(int64_t)i * g.ldm + j] > 0.f)) v = 0.f;
                 if (g.C) g.C[(int64_t)i * g.ldc + j] = v;
                 if (g.Cb) g.Cb[(int64_t)i * g.ldcb + j] = __float2bfloat16_rn(v);
+                if (g.CbT) g.CbT[(int64_t)j * g.ldcbt + i] = __float2bfloat16_rn(v);
             }
 }
 
@@ -142,6 +150,30 @@ __global__ void f64_to_bf16_kernel(const double *src, __nv_bfloat16 *dst, int64_
 __global__ void f32_to_bf16_kernel(const float *src, __nv_bfloat16 *dst, int64_t n) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
         dst[e] = __float2bfloat16_rn(src[e]);
+}
+
+// dst[c * ldd + r] = src[r * lds + c] for a rows x cols BF16 matrix, through
+// 32 x 32 shared-memory tiles (both sides coalesced).  Block 32 x 8 threads.
+__global__ void transpose_bf16_kernel(const __nv_bfloat16 *__restrict__ src, int64_t lds, int64_t rows, int64_t cols,
+                                      __nv_bfloat16 *__restrict__ dst, int64_t ldd) {
+    __shared__ __nv_bfloat16 t[32][33];
+    const int64_t r0 = (int64_t)blockIdx.y * 32, c0 = (int64_t)blockIdx.x * 32;
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int64_t r = r0 + k, c = c0 + threadIdx.x;
+        if (r < rows && c < cols) t[k][threadIdx.x] = src[r * lds + c];
+    }
+    __syncthreads();
+    for (int k = threadIdx.y; k < 32; k += 8) {
+        const int64_t c = c0 + k, r = r0 + threadIdx.x;
+        if (r < rows && c < cols) dst[c * ldd + r] = t[threadIdx.x][k];
+    }
+}
+
+cudaError_t transpose_bf16(const __nv_bfloat16 *src, int64_t lds, int64_t rows, int64_t cols, __nv_bfloat16 *dst,
+                           int64_t ldd, cudaStream_t st) {
+    dim3 grid((unsigned)((cols + 31) / 32), (unsigned)((rows + 31) / 32));
+    transpose_bf16_kernel<<<grid, dim3(32, 8), 0, st>>>(src, lds, rows, cols, dst, ldd);
+    return cudaGetLastError();
 }
 
 __global__ void f32_to_f64_kernel(const float *src, double *dst, int64_t n) {
@@ -197,7 +229,8 @@ __global__ void __launch_bounds__(256) yrel_kernel(const float *Y, const double 
     if (threadIdx.x == 0) atomicAdd(loss, nd * inv);
 }
 
-// Adam on FP32 master weights; refreshes the BF16 copy.
+// Adam on FP32 master weights; refreshes the BF16 copy (the transpose follows
+// by transpose_bf16).
 __global__ void adam_kernel(float *w, const float *grad, float *m1, float *m2, __nv_bfloat16 *wb, int64_t n,
                             float lr, float b1, float b2, float eps, float c1, float c2) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
@@ -247,8 +280,18 @@ struct rebk_mlp_s {
     float *w[3] = {nullptr, nullptr, nullptr}, *g[3] = {nullptr, nullptr, nullptr};
     float *m1[3] = {nullptr, nullptr, nullptr}, *m2[3] = {nullptr, nullptr, nullptr};
     __nv_bfloat16 *wb[3] = {nullptr, nullptr, nullptr};
-    int64_t wsize[3] = {0, 0, 0};
-    __nv_bfloat16 *Ab = nullptr;  // BF16 copy of A (m x n, row-major, ld n)
+    __nv_bfloat16 *wbT[3] = {nullptr, nullptr, nullptr};  // transposed BF16 copies
+    int64_t wsize[3] = {0, 0, 0}, wrows[3] = {0, 0, 0}, wcols[3] = {0, 0, 0};
+    __nv_bfloat16 *Ab = nullptr;   // BF16 copy of A (m x n, row-major, ld n)
+    __nv_bfloat16 *AbT = nullptr;  // its transpose (n x m)
+    // transposed BF16 activations and gradients (feature x capacity): the K-major
+    // operands of the weight-gradient products
+    __nv_bfloat16 *XbT = nullptr, *H1T = nullptr, *H2T = nullptr, *dYT = nullptr, *dH2T = nullptr,
+                  *dH1T = nullptr;
+    int *gemm_err = nullptr;       // device word set by a tensor-core GEMM whose wait gave up
+    float *gemm_ws = nullptr;      // split-K partial sums of the tensor-core GEMM
+    size_t gemm_ws_floats = 0;
+    int64_t umma_calls = 0, legacy_calls = 0;
     // activations (cap rows)
     __nv_bfloat16 *Xb = nullptr, *H1b = nullptr, *H2b = nullptr, *Yb = nullptr, *Rb = nullptr, *dYb = nullptr,
                   *dH2b = nullptr, *dH1b = nullptr;
@@ -281,30 +324,62 @@ rebk_status mfail(rebk_status s, const std::string &msg) {
 void free_mlp(rebk_mlp h) {
     if (!h) return;
     for (int l = 0; l < 3; ++l) {
-        void *p[] = {h->w[l], h->g[l], h->m1[l], h->m2[l], h->wb[l]};
+        void *p[] = {h->w[l], h->g[l], h->m1[l], h->m2[l], h->wb[l], h->wbT[l]};
         for (void *q : p)
             if (q) cudaFree(q);
     }
-    void *p[] = {h->Ab, h->Xb, h->H1b, h->H2b, h->Yb, h->Rb, h->dYb, h->dH2b, h->dH1b, h->H1, h->H2, h->Y,
-                 h->P, h->R, h->dY, h->dH2, h->dH1, h->loss};
+    void *p[] = {h->Ab, h->AbT, h->Xb, h->H1b, h->H2b, h->Yb, h->Rb, h->dYb, h->dH2b, h->dH1b, h->H1, h->H2, h->Y,
+                 h->P, h->R, h->dY, h->dH2, h->dH1, h->loss, h->XbT, h->H1T, h->H2T, h->dYT, h->dH2T, h->dH1T,
+                 h->gemm_err, h->gemm_ws};
     for (void *q : p)
         if (q) cudaFree(q);
     delete h;
 }
 
-// Forward pass for `batch` inputs (rows of Xb): H1, H2 (FP32 + BF16), Y (FP32 + BF16).
-rebk_status forward(rebk_mlp h, int64_t batch) {
+// C (M x N) = alpha * sum_k A[i * lda + k] B[j * ldb + k] (both operands
+// K-contiguous), epilogue as umma_gemm: the tensor-core GEMM when the TMA tiles
+// can describe the operands, else the mma.sync kernel with the same strides.
+rebk_status mm(rebk_mlp h, int64_t M, int64_t N, int64_t K, const __nv_bfloat16 *A, int64_t lda,
+               const __nv_bfloat16 *B, int64_t ldb, float alpha, float *C, int64_t ldc, __nv_bfloat16 *Cb,
+               int64_t ldcb, __nv_bfloat16 *CbT, int64_t ldcbt, int relu = 0, const float *mask = nullptr,
+               int64_t ldm = 0) {
     const cudaStream_t st = h->stream;
-    const int64_t m = h->m, H = h->hidden;
-    GemmArgs g = gemm_args((int)batch, (int)H, (int)m, h->Xb, m, 1, h->wb[0], 1, m, h->H1, H, h->H1b, H);
-    g.relu = 1;
+    if (umma_gemm_supported((int)M, (int)N, (int)K, A, lda, B, ldb) && (C != nullptr || Cb != nullptr)) {
+        ++h->umma_calls;
+        MCK(umma_gemm((int)M, (int)N, (int)K, A, lda, B, ldb, alpha, C, ldc, Cb, ldcb, CbT, ldcbt, relu, mask, ldm,
+                      h->gemm_ws, h->gemm_ws_floats, h->gemm_err, st));
+        return REBK_OK;
+    }
+    ++h->legacy_calls;
+    GemmArgs g = gemm_args((int)M, (int)N, (int)K, A, lda, 1, B, 1, ldb, C, ldc, Cb, ldcb);
+    g.CbT = CbT;
+    g.ldcbt = ldcbt;
+    g.alpha = alpha;
+    g.relu = relu;
+    g.mask = mask;
+    g.ldm = ldm;
     MCK(gemm(g, st));
-    g = gemm_args((int)batch, (int)H, (int)H, h->H1b, H, 1, h->wb[1], 1, H, h->H2, H, h->H2b, H);
-    g.relu = 1;
-    MCK(gemm(g, st));
-    g = gemm_args((int)batch, (int)m, (int)H, h->H2b, H, 1, h->wb[2], 1, H, h->Y, m, h->Yb, m);
-    g.alpha = h->out_scale;
-    MCK(gemm(g, st));
+    return REBK_OK;
+}
+
+// Forward pass for `batch` inputs (rows of Xb, columns of XbT): H1, H2 (FP32,
+// BF16 and transposed BF16), Y (FP32 + BF16).
+rebk_status forward(rebk_mlp h, int64_t batch) {
+    const int64_t m = h->m, H = h->hidden, cap = h->cap;
+    rebk_status s = mm(h, batch, H, m, h->Xb, m, h->wb[0], m, 1.f, h->H1, H, h->H1b, H, h->H1T, cap, 1);
+    if (s == REBK_OK) s = mm(h, batch, H, H, h->H1b, H, h->wb[1], H, 1.f, h->H2, H, h->H2b, H, h->H2T, cap, 1);
+    if (s == REBK_OK) s = mm(h, batch, m, H, h->H2b, H, h->wb[2], H, h->out_scale, h->Y, m, h->Yb, m, nullptr, 0);
+    return s;
+}
+
+// Reads and clears the tensor-core GEMM's error word (after a stream sync).
+rebk_status gemm_status(rebk_mlp h) {
+    int e = 0;
+    MCK(cudaMemcpy(&e, h->gemm_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e != 0) {
+        MCK(cudaMemset(h->gemm_err, 0, sizeof(int)));
+        return mfail(REBK_ECUDA, "tensor-core GEMM: a bounded wait gave up");
+    }
     return REBK_OK;
 }
 
@@ -334,6 +409,9 @@ rebk_status rebk_mlp_create(rebk_mlp *out, const double *A, int64_t m, int64_t n
     h->wsize[0] = hidden * m;
     h->wsize[1] = hidden * hidden;
     h->wsize[2] = m * hidden;
+    h->wrows[0] = hidden; h->wcols[0] = m;
+    h->wrows[1] = hidden; h->wcols[1] = hidden;
+    h->wrows[2] = m;      h->wcols[2] = hidden;
     const cudaStream_t st = h->stream;
     auto fin = [&](rebk_status s) {
         if (s != REBK_OK) free_mlp(h);
@@ -354,6 +432,7 @@ rebk_status rebk_mlp_create(rebk_mlp *out, const double *A, int64_t m, int64_t n
         MCKH(cudaMalloc(&h->m1[l], sizeof(float) * sz));
         MCKH(cudaMalloc(&h->m2[l], sizeof(float) * sz));
         MCKH(cudaMalloc(&h->wb[l], sizeof(__nv_bfloat16) * sz));
+        MCKH(cudaMalloc(&h->wbT[l], sizeof(__nv_bfloat16) * sz));
         MCKH(cudaMemsetAsync(h->m1[l], 0, sizeof(float) * sz, st));
         MCKH(cudaMemsetAsync(h->m2[l], 0, sizeof(float) * sz, st));
         if (init_weights && init_weights[l]) {
@@ -380,6 +459,7 @@ rebk_status rebk_mlp_create(rebk_mlp *out, const double *A, int64_t m, int64_t n
         }
         f32_to_bf16_kernel<<<eblocks(sz), 256, 0, st>>>(h->w[l], h->wb[l], sz);
         MCKH(cudaGetLastError());
+        MCKH(transpose_bf16(h->wb[l], h->wcols[l], h->wrows[l], h->wcols[l], h->wbT[l], h->wrows[l], st));
     }
     // BF16 copy of A (m x n) for the loss-gradient products
     double *Ad = nullptr;
@@ -388,7 +468,10 @@ rebk_status rebk_mlp_create(rebk_mlp *out, const double *A, int64_t m, int64_t n
         MCKH(cudaMemcpyAsync(Ad, A, sizeof(double) * m * n, cudaMemcpyHostToDevice, st));
     }
     MCKH(cudaMalloc(&h->Ab, sizeof(__nv_bfloat16) * m * n));
+    MCKH(cudaMalloc(&h->AbT, sizeof(__nv_bfloat16) * m * n));
     f64_to_bf16_kernel<<<eblocks(m * n), 256, 0, st>>>(A_on_device ? A : Ad, h->Ab, m * n);
+    MCKH(cudaGetLastError());
+    MCKH(transpose_bf16(h->Ab, n, m, n, h->AbT, m, st));
     MCKH(cudaGetLastError());
     MCKH(cudaStreamSynchronize(st));
     if (Ad) cudaFree(Ad);
@@ -410,6 +493,16 @@ rebk_status rebk_mlp_create(rebk_mlp *out, const double *A, int64_t m, int64_t n
     MCKH(cudaMalloc(&h->dH2, sizeof(float) * C * hidden));
     MCKH(cudaMalloc(&h->dH1, sizeof(float) * C * hidden));
     MCKH(cudaMalloc(&h->loss, sizeof(double)));
+    MCKH(cudaMalloc(&h->XbT, sizeof(__nv_bfloat16) * C * m));
+    MCKH(cudaMalloc(&h->H1T, sizeof(__nv_bfloat16) * C * hidden));
+    MCKH(cudaMalloc(&h->H2T, sizeof(__nv_bfloat16) * C * hidden));
+    MCKH(cudaMalloc(&h->dYT, sizeof(__nv_bfloat16) * C * m));
+    MCKH(cudaMalloc(&h->dH2T, sizeof(__nv_bfloat16) * C * hidden));
+    MCKH(cudaMalloc(&h->dH1T, sizeof(__nv_bfloat16) * C * hidden));
+    MCKH(cudaMalloc(&h->gemm_err, sizeof(int)));
+    MCKH(cudaMemset(h->gemm_err, 0, sizeof(int)));
+    h->gemm_ws_floats = umma_workspace_floats();
+    MCKH(cudaMalloc(&h->gemm_ws, sizeof(float) * h->gemm_ws_floats));
 #undef MCKH
     *out = h;
     return REBK_OK;
@@ -429,7 +522,7 @@ rebk_status rebk_mlp_forward(rebk_mlp h, const double *Bm, int64_t batch, double
     f32_to_f64_kernel<<<eblocks(batch * h->m), 256, 0, st>>>(h->Y, Y, batch * h->m);
     MCK(cudaGetLastError());
     MCK(cudaStreamSynchronize(st));
-    return REBK_OK;
+    return gemm_status(h);
 }
 
 rebk_status rebk_mlp_gradients(rebk_mlp h, const double *Bm, const double *Xls, int64_t batch, double *loss,
@@ -438,48 +531,49 @@ rebk_status rebk_mlp_gradients(rebk_mlp h, const double *Bm, const double *Xls, 
     rebk_status s = check_batch(h, batch);
     if (s != REBK_OK) return s;
     const cudaStream_t st = h->stream;
-    const int64_t m = h->m, n = h->n, H = h->hidden;
+    const int64_t m = h->m, n = h->n, H = h->hidden, cap = h->cap;
     f64_to_bf16_kernel<<<eblocks(batch * m), 256, 0, st>>>(Bm, h->Xb, batch * m);
     MCK(cudaGetLastError());
+    MCK(transpose_bf16(h->Xb, m, batch, m, h->XbT, cap, st));
     s = forward(h, batch);
     if (s != REBK_OK) return s;
     MCK(cudaMemsetAsync(h->loss, 0, sizeof(double), st));
     // dY: gradient w.r.t. the last layer's unscaled output (the loss gradient in y times out_scale)
-    GemmArgs g;
     if (h->loss_kind == REBK_MLP_LOSS_X) {
         // P = Y A (batch x n): A^T y for every sample; R = P - X_ls
-        MCK(gemm(gemm_args((int)batch, (int)n, (int)m, h->Yb, m, 1, h->Ab, n, 1, h->P, n, nullptr, 0), st));
+        s = mm(h, batch, n, m, h->Yb, m, h->AbT, m, 1.f, h->P, n, nullptr, 0, nullptr, 0);
+        if (s != REBK_OK) return s;
         residual_kernel<<<eblocks(batch * n), 256, 0, st>>>(h->P, Xls, h->R, h->Rb, batch * n, h->loss);
         MCK(cudaGetLastError());
         // dY = (2 s / batch) R A^T (batch x m)
-        g = gemm_args((int)batch, (int)m, (int)n, h->Rb, n, 1, h->Ab, 1, n, h->dY, m, h->dYb, m);
-        g.alpha = 2.f * h->out_scale / (float)batch;
-        MCK(gemm(g, st));
+        s = mm(h, batch, m, n, h->Rb, n, h->Ab, n, 2.f * h->out_scale / (float)batch, h->dY, m, h->dYb, m, h->dYT,
+               cap);
+        if (s != REBK_OK) return s;
     } else {
         // dY = (2 s / batch) (Y - Y*) / ||Y*||^2 per row
         yrel_kernel<<<(unsigned)batch, 256, 0, st>>>(h->Y, Xls, m, 2.0 * h->out_scale / (double)batch, h->dY,
                                                      h->dYb, h->loss);
         MCK(cudaGetLastError());
+        MCK(transpose_bf16(h->dYb, m, batch, m, h->dYT, cap, st));
     }
     // dW3 = dY^T H2 (m x H)
-    MCK(gemm(gemm_args((int)m, (int)H, (int)batch, h->dYb, 1, m, h->H2b, H, 1, h->g[2], H, nullptr, 0), st));
+    s = mm(h, m, H, batch, h->dYT, cap, h->H2T, cap, 1.f, h->g[2], H, nullptr, 0, nullptr, 0);
     // dH2 = (dY W3) * [H2 > 0]
-    g = gemm_args((int)batch, (int)H, (int)m, h->dYb, m, 1, h->wb[2], H, 1, h->dH2, H, h->dH2b, H);
-    g.mask = h->H2;
-    g.ldm = H;
-    MCK(gemm(g, st));
+    if (s == REBK_OK)
+        s = mm(h, batch, H, m, h->dYb, m, h->wbT[2], m, 1.f, h->dH2, H, h->dH2b, H, h->dH2T, cap, 0, h->H2, H);
     // dW2 = dH2^T H1 (H x H)
-    MCK(gemm(gemm_args((int)H, (int)H, (int)batch, h->dH2b, 1, H, h->H1b, H, 1, h->g[1], H, nullptr, 0), st));
+    if (s == REBK_OK) s = mm(h, H, H, batch, h->dH2T, cap, h->H1T, cap, 1.f, h->g[1], H, nullptr, 0, nullptr, 0);
     // dH1 = (dH2 W2) * [H1 > 0]
-    g = gemm_args((int)batch, (int)H, (int)H, h->dH2b, H, 1, h->wb[1], H, 1, h->dH1, H, h->dH1b, H);
-    g.mask = h->H1;
-    g.ldm = H;
-    MCK(gemm(g, st));
+    if (s == REBK_OK)
+        s = mm(h, batch, H, H, h->dH2b, H, h->wbT[1], H, 1.f, h->dH1, H, h->dH1b, H, h->dH1T, cap, 0, h->H1, H);
     // dW1 = dH1^T X (H x m)
-    MCK(gemm(gemm_args((int)H, (int)m, (int)batch, h->dH1b, 1, H, h->Xb, m, 1, h->g[0], m, nullptr, 0), st));
+    if (s == REBK_OK) s = mm(h, H, m, batch, h->dH1T, cap, h->XbT, cap, 1.f, h->g[0], m, nullptr, 0, nullptr, 0);
+    if (s != REBK_OK) return s;
     double lsum = 0.0;
     MCK(cudaMemcpyAsync(&lsum, h->loss, sizeof(double), cudaMemcpyDeviceToHost, st));
     MCK(cudaStreamSynchronize(st));
+    s = gemm_status(h);
+    if (s != REBK_OK) return s;
     if (loss) *loss = lsum / (double)batch;
     if (grads_host)
         for (int l = 0; l < 3; ++l)
@@ -495,10 +589,12 @@ rebk_status rebk_mlp_train_step(rebk_mlp h, const double *Bm, const double *Xls,
     ++h->step;
     const float b1 = 0.9f, b2 = 0.999f;
     const float c1 = 1.f - std::pow(b1, (float)h->step), c2 = 1.f - std::pow(b2, (float)h->step);
-    for (int l = 0; l < 3; ++l)
-        adam_kernel<<<eblocks(h->wsize[l]), 256, 0, st>>>(h->w[l], h->g[l], h->m1[l], h->m2[l], h->wb[l],
-                                                          h->wsize[l], (float)lr, b1, b2, 1e-8f, c1, c2);
-    MCK(cudaGetLastError());
+    for (int l = 0; l < 3; ++l) {
+        adam_kernel<<<eblocks(h->wsize[l]), 256, 0, st>>>(h->w[l], h->g[l], h->m1[l], h->m2[l], h->wb[l], h->wsize[l],
+                                                          (float)lr, b1, b2, 1e-8f, c1, c2);
+        MCK(cudaGetLastError());
+        MCK(transpose_bf16(h->wb[l], h->wcols[l], h->wrows[l], h->wcols[l], h->wbT[l], h->wrows[l], st));
+    }
     MCK(cudaStreamSynchronize(st));
     return REBK_OK;
 }
@@ -523,6 +619,42 @@ rebk_status rebk_mlp_get_weights(rebk_mlp h, float *const *weights_host) {
     if (!h || !weights_host) return mfail(REBK_EINVAL, "NULL argument");
     for (int l = 0; l < 3; ++l)
         if (weights_host[l]) MCK(cudaMemcpy(weights_host[l], h->w[l], sizeof(float) * h->wsize[l], cudaMemcpyDeviceToHost));
+    return REBK_OK;
+}
+
+rebk_status rebk_gemm_bf16(int64_t M, int64_t N, int64_t K, const void *A, int64_t lda, const void *B, int64_t ldb,
+                           float alpha, float *C, int64_t ldc, void *stream, int32_t *path) {
+    set_last_error("");
+    if (!A || !B || !C) return mfail(REBK_EINVAL, "A, B and C must be device pointers");
+    if (M < 1 || N < 1 || K < 1 || lda < K || ldb < K || ldc < N) return mfail(REBK_EINVAL, "bad shape");
+    if (M > INT32_MAX || N > INT32_MAX || K > INT32_MAX) return mfail(REBK_EUNSUPPORTED, "dimension above 2^31");
+    const cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const __nv_bfloat16 *a = static_cast<const __nv_bfloat16 *>(A), *b = static_cast<const __nv_bfloat16 *>(B);
+    const bool tc = umma_gemm_supported((int)M, (int)N, (int)K, A, lda, B, ldb);
+    if (path) *path = tc ? 1 : 0;
+    if (tc) {
+        int *err = nullptr;
+        float *ws = nullptr;
+        const size_t wsf = umma_workspace_floats();
+        MCK(cudaMalloc(&err, sizeof(int)));
+        cudaError_t e = cudaMalloc(&ws, sizeof(float) * wsf);
+        if (e == cudaSuccess) e = cudaMemsetAsync(err, 0, sizeof(int), st);
+        if (e == cudaSuccess)
+            e = umma_gemm((int)M, (int)N, (int)K, a, lda, b, ldb, alpha, C, ldc, nullptr, 0, nullptr, 0, 0, nullptr, 0,
+                          ws, wsf, err, st);
+        int herr = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        cudaFree(err);
+        if (ws) cudaFree(ws);
+        MCK(e);
+        if (herr) return mfail(REBK_ECUDA, "tensor-core GEMM: a bounded wait gave up");
+        return REBK_OK;
+    }
+    GemmArgs g = gemm_args((int)M, (int)N, (int)K, a, lda, 1, b, 1, ldb, C, ldc, nullptr, 0);
+    g.alpha = alpha;
+    MCK(gemm(g, st));
+    MCK(cudaStreamSynchronize(st));
     return REBK_OK;
 }
 

@@ -166,6 +166,8 @@ _SIGNATURES = {
     "rebk_sparse_info": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double),
                           ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "rebk_selftest_waits": ([ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+    "rebk_gemm_bf16": ([ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, _P, ctypes.c_int64, _P, ctypes.c_int64,
+                        ctypes.c_float, _P, ctypes.c_int64, _P, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "rebk_device_peaks": ([ctypes.POINTER(RebkPeaks), _P], ctypes.c_int),
     "rebk_last_error": ([], ctypes.c_char_p),
     "rebk_version": ([], ctypes.c_char_p),
