@@ -66,6 +66,16 @@ def parse():
     ap.add_argument("--warm-eval", type=int, default=32)
     ap.add_argument("--warm-batch-systems", type=int, default=152)
     ap.add_argument("--warm-steps", type=int, default=4000)
+    ap.add_argument("--no-combined", action="store_true",
+                    help="skip the mixed + warm-start + batched measurement on the 8192 x 2048 stream")
+    ap.add_argument("--combined-train", type=int, default=1024, help="combined form: training right-hand sides")
+    ap.add_argument("--combined-systems", type=int, default=152,
+                    help="combined form: batched systems of 8 held-out right-hand sides (sharing A)")
+    ap.add_argument("--combined-steps", type=int, default=1500, help="combined form: network training steps")
+    ap.add_argument("--combined-target-iters", type=int, default=8000,
+                    help="combined form: inner iterations per refinement pass of the target solves (2 passes)")
+    ap.add_argument("--combined-stream", type=int, default=100000,
+                    help="combined form: stream length over which target generation and training are amortised")
     ap.add_argument("--profile-mlp", type=int, default=0, metavar="K",
                     help="run K training steps (batch 256) of the 8192 -> 512 -> 512 -> 8192 warm-start network "
                          "and print the time per step (the case the network's ncu summary captures)")
@@ -799,6 +809,132 @@ def R_STATUS(code: int) -> str:
     return R.STATUS_NAMES.get(code, str(code))
 
 
+def measure_combined(args, dev, rank):
+    """The metric's combined form on the learned-warm-start workload: A = U
+    diag(i^-1/2) V^T (8192 x 2048), a stream of right-hand sides b = A (M c) +
+    N(0, 1e-3^2), M = randn(2048, 32).  Once per A: training targets from the
+    solver (x_ls = A^+ b by batched solves on A, y* = (A^T)^+ x_ls by batched
+    solves on A^T, a fixed number of passes, no known solution used), then the
+    8192 -> 512 -> 512 -> 8192 network trained on them.  Timed: held-out
+    right-hand sides solved to 1e-8 relative error by the mixed-precision
+    batched solver (systems of 8 right-hand sides sharing A) from the network's
+    x0 = A^T y, z0 = b - A x0 (network and products inside the timed region),
+    every right-hand side checked against A^+ b; next to plain FP64 Algorithm 1
+    one right-hand side at a time on the same right-hand sides."""
+    import torch
+
+    from paper_2001_04179_gb300 import BatchSolver, Solver, WarmStartNet
+    from workloads import spectrum_problem
+
+    m5, n5 = 8192, 2048
+    ntr = max(256, args.combined_train // 256 * 256)
+    nbs = max(1, args.combined_systems)
+    nev = 8 * nbs
+    t0 = time.perf_counter()
+    p = spectrum_problem(m5, n5, seed=100 + rank, latent=32, noise=1e-3, nrhs=ntr + nev)
+    gen_s = time.perf_counter() - t0
+    A = p.A
+    At = np.ascontiguousarray(A.T)
+    stream = torch.cuda.current_stream()
+    sol = Solver(A, TAU, TAU, alpha=0.0, storage=("fp32",), stream=stream)
+    alpha = sol.alpha  # the blocks of A^T are the transposes of A's: the same beta_max
+    ns = ntr // 8
+    iters = args.combined_target_iters
+
+    def targets(mat, rhs_rows):
+        bs = BatchSolver([mat] * ns, nrhs=8, tau=TAU, alpha=[alpha] * ns, max_outer=2)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        out = bs.solve(rhs_rows, X_ref=None, tol=0.0, max_iter=0, inner_iters=iters, seed=3)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t1
+        bs.close()
+        return out["x"], dt
+
+    B_sys = torch.from_numpy(np.ascontiguousarray(
+        np.concatenate([p.b[:, 8 * i:8 * i + 8] for i in range(ns)], axis=0))).to(dev)
+    Xs, tx = targets(A, B_sys)
+    Ys, ty = targets(At, Xs)
+    Xtr = Xs.view(ns, n5, 8).permute(0, 2, 1).reshape(ntr, n5)
+    Ytr = Ys.view(ns, m5, 8).permute(0, 2, 1).reshape(ntr, m5).contiguous()
+    xr_tr = torch.from_numpy(np.ascontiguousarray(p.x_ref[:, :ntr].T)).to(dev)
+    x_err = float(((Xtr - xr_tr).norm(dim=1) / xr_tr.norm(dim=1)).median())
+    Btr = torch.from_numpy(np.ascontiguousarray(p.b[:, :ntr].T)).to(dev)
+    net = WarmStartNet(A, hidden=512, batch_capacity=256, seed=1, stream=stream)
+    out_scale = 0.1 * float(torch.sqrt((Ytr * Ytr).sum(1).mean() / (Btr * Btr).sum(1).mean()))
+    net.set_loss("y_rel", out_scale)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    losses = net.fit(Btr, Ytr, steps=args.combined_steps, lr=1e-3, batch=256)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t1
+    del B_sys, Xs, Ys, Xtr, Ytr, xr_tr, Btr
+    # ---- timed: held-out right-hand sides, warm start + batched mixed precision ----
+    c0 = ntr
+    Bb = torch.from_numpy(np.ascontiguousarray(
+        np.concatenate([p.b[:, c0 + 8 * i:c0 + 8 * i + 8] for i in range(nbs)], axis=0))).to(dev)
+    Xrb = torch.from_numpy(np.ascontiguousarray(
+        np.concatenate([p.x_ref[:, c0 + 8 * i:c0 + 8 * i + 8] for i in range(nbs)], axis=0))).to(dev)
+    bsv = BatchSolver([A] * nbs, nrhs=8, tau=TAU, alpha=[alpha] * nbs, stream=stream)
+    res = {}
+    for mode in ("warm", "cold"):
+        for rep in range(2):  # the first solve also orders the queue; the second is timed
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record(stream)
+            X0 = Z0 = None
+            if mode == "warm":
+                X0, Z0 = net.warm_start_batch(sol, Bb, nev, group=8)
+            out = bsv.solve(Bb, X_ref=Xrb, tol=TOL, max_iter=400000, seed=11 + rep, X0=X0, Z0=Z0)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+        st_ = out["stats"]
+        X = out["x"].view(nbs, n5, 8)
+        Xr = Xrb.view(nbs, n5, 8)
+        errs = ((X - Xr).norm(dim=1) / Xr.norm(dim=1)).flatten()
+        ms = ev0.elapsed_time(ev1)
+        res[mode] = {"solves_per_s": nev / (ms / 1000.0), "ms": ms, "rhs": nev, "systems": nbs,
+                     "rhs_reaching_1e-8": int((errs <= TOL).sum()), "rel_err_max": float(errs.max()),
+                     "iterations_mean_per_system": st_["iterations"] / nbs, "refinement_passes": st_["outer"]}
+    bsv.close()
+    # ---- plain FP64 Algorithm 1, one right-hand side at a time, on held-out right-hand sides ----
+    nplain = 8
+    its = []
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(c0, c0 + nplain):
+        b = torch.from_numpy(np.ascontiguousarray(p.b[:, i])).to(dev)
+        xr = torch.from_numpy(np.ascontiguousarray(p.x_ref[:, i])).to(dev)
+        r = sol.solve(b, tol=TOL, max_iter=10**7, seed=7, x_ref=xr)
+        if r["stats"]["rel_err"] > TOL:
+            raise RuntimeError(f"plain FP64 solve did not reach {TOL}: {r['stats']}")
+        its.append(r["stats"]["iterations"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    plain = {"solves_per_s": nplain / (ev0.elapsed_time(ev1) / 1000.0), "iterations_mean": float(np.mean(its)),
+             "rhs": nplain}
+    once_s = tx + ty + train_s
+    warm = res["warm"]
+    amort = 1.0 / (1.0 / warm["solves_per_s"] + once_s / args.combined_stream)
+    sol.close()
+    return {
+        "workload": ("learned warm start stream: A = U diag(i^-1/2) V^T 8192x2048, b = A(Mc) + N(0,1e-3^2), "
+                     "latent 32; tau 128, alpha 1.75/beta_max, FP32 inner / FP64 refinement; "
+                     "MLP 8192-512-512-8192 on tcgen05 BF16 GEMMs, x0 = A^T y, z0 = b - A x0"),
+        "value": warm["solves_per_s"], "unit": "solves/s",
+        "speedup_vs_plain_fp64": warm["solves_per_s"] / plain["solves_per_s"],
+        "warm_batched": warm, "cold_batched": res["cold"], "plain_fp64": plain,
+        "warm_over_cold_batched": warm["solves_per_s"] / res["cold"]["solves_per_s"],
+        "once_per_A": {"targets_x_ls_s": tx, "targets_y_star_s": ty, "training_s": train_s,
+                       "train_rhs": ntr, "target_passes": 2, "target_iterations_per_pass": iters,
+                       "x_ls_median_rel_err": x_err, "training_steps": args.combined_steps,
+                       "loss_first": losses[0], "loss_last": float(np.mean(losses[-20:]))},
+        "amortised_over_stream": {"stream_rhs": args.combined_stream, "solves_per_s": amort,
+                                  "speedup_vs_plain_fp64": amort / plain["solves_per_s"]},
+        "problem_gen_s": gen_s,
+    }
+
+
 def run_profile_mlp(args):
     """K training steps of the warm-start network on a random 8192 x 2048 A and
     random targets (y-space loss): the network's products, Adam and the
@@ -998,6 +1134,13 @@ def main():
                  "rule": "max(||b - z - A x|| / ||b||, ||A^T z|| / (||A||_F ||b||)) <= 1e-8 after each "
                          "refinement pass (no x_ref); rel_err_max is the error against A^+ b measured afterwards"}
 
+    # ---------------- the combined form (mixed + warm start + batched) ----------------
+    combined = None
+    if not args.no_combined:
+        del b_host, xr_host, x_host, b_d, xr_d, x_d
+        torch.cuda.empty_cache()
+        combined = measure_combined(args, dev, rank)
+
     # ---------------- roofline of the dominant kernel ----------------
     esize = {"fp32": 4, "bf16": 2}[S]
     bytes_per_iter = float(TAU * N + TAU * M) * esize
@@ -1046,6 +1189,7 @@ def main():
             "plain_fp64": plain,
             "speedup_vs_plain_fp64": None if plain is None else value / plain["value"],
             "residual_rule": resid,
+            "combined": combined,
             "device_peaks": dev_peaks,
         }
         print(json.dumps(line))
