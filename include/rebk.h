@@ -533,7 +533,7 @@ rebk_status rebk_warm_start(rebk_handle h, rebk_mlp net, const double *b, double
  * group = 1 is one right-hand side per row.  B: device, count / group blocks of
  * m x group; X0, Z0: device outputs, blocks of n x group and m x group.
  * Errors: EINVAL (NULL pointers, count not a positive multiple of group, shape
- * mismatch), ENOMEM (scratch of 2 x capacity x m doubles), ECUDA.
+ * mismatch), ENOMEM (scratch of capacity x (2 m + n) doubles), ECUDA.
  */
 rebk_status rebk_warm_start_batch(rebk_handle h, rebk_mlp net, const double *B, int64_t count, int32_t group,
                                   double *X0, double *Z0);

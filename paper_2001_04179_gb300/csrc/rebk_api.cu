@@ -866,12 +866,14 @@ rebk_status rebk_warm_start_batch(rebk_handle h, rebk_mlp net, const double *B, 
     const int64_t cap = mlp_batch_capacity(net);
     const cudaStream_t st = h->stream;
     const int64_t chunk = std::min<int64_t>(cap, count);
-    double *Bc = nullptr, *Yc = nullptr;
+    double *Bc = nullptr, *Yc = nullptr, *Xc = nullptr;
     cudaError_t ae = cudaMalloc(&Bc, sizeof(double) * chunk * h->m);
     if (ae == cudaSuccess) ae = cudaMalloc(&Yc, sizeof(double) * chunk * h->m);
+    if (ae == cudaSuccess) ae = cudaMalloc(&Xc, sizeof(double) * chunk * h->n);
     auto release = [&]() {
         if (Bc) cudaFree(Bc);
         if (Yc) cudaFree(Yc);
+        if (Xc) cudaFree(Xc);
     };
     if (ae != cudaSuccess) {
         release();
@@ -886,12 +888,11 @@ rebk_status rebk_warm_start_batch(rebk_handle h, rebk_mlp net, const double *B, 
             out = rebk_mlp_forward(net, Bc, cnt, Yc);  // y for the chunk (rows of m)
             if (out != REBK_OK) break;
         }
-        for (int64_t c = 0; c < cnt && e == cudaSuccess; ++c) {
-            // x0 = A^T y and A x0 with the FP64 copy of A; z0 = b - A x0
-            e = dual_sweep(h->A64, h->lda, h->m, h->n, nullptr, false, Yc + c * h->m, false, nullptr, h->yn, st);
-            if (e == cudaSuccess) e = dual_sweep(h->A64, h->lda, h->m, h->n, h->yn, false, nullptr, false, h->f, nullptr, st);
-            if (e == cudaSuccess) e = group_store_xz(h->yn, h->n, Bc + c * h->m, h->f, h->m, j0 + c, group, X0, Z0, st);
-        }
+        // x0 = A^T y (rows: X0c = Yc A) and A x0 (rows: Yc <- X0c A^T) with the FP64 copy of A,
+        // then z0 = b - A x0, stored in the grouped layouts
+        if (e == cudaSuccess) e = dgemm((int)cnt, (int)h->n, (int)h->m, Yc, h->m, 1, h->A64, h->lda, 1, Xc, h->n, st);
+        if (e == cudaSuccess) e = dgemm((int)cnt, (int)h->m, (int)h->n, Xc, h->n, 1, h->A64, 1, h->lda, Yc, h->m, st);
+        if (e == cudaSuccess) e = group_store_xz_many(Xc, h->n, Bc, Yc, h->m, j0, cnt, group, X0, Z0, st);
         if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) out = fail(REBK_ECUDA, cudaGetErrorString(e));
     }

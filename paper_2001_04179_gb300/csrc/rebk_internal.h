@@ -167,6 +167,12 @@ cudaError_t group_gather(const double *src, int64_t j0, int64_t cnt, int g, int6
                          cudaStream_t st);
 cudaError_t group_store_xz(const double *x, int64_t n, const double *b, const double *ax, int64_t m, int64_t j, int g,
                            double *X0, double *Z0, cudaStream_t st);
+// C (M x N, ldc) = sum_k A[i a_rs + k a_cs] B[k b_rs + j b_cs] in FP64.
+cudaError_t dgemm(int M, int N, int K, const double *A, int64_t a_rs, int64_t a_cs, const double *B, int64_t b_rs,
+                  int64_t b_cs, double *C, int64_t ldc, cudaStream_t st);
+// group_store_xz for right-hand sides j0 .. j0 + cnt - 1 (x: cnt rows of n; b, ax: cnt rows of m).
+cudaError_t group_store_xz_many(const double *x, int64_t n, const double *b, const double *ax, int64_t m, int64_t j0,
+                                int64_t cnt, int g, double *X0, double *Z0, cudaStream_t st);
 // batch capacity of a warm-start network (rebk_mlp.cu)
 int64_t mlp_batch_capacity(::rebk_mlp_s *h);
 // the same with an FP32 x (a correction): out[0] = sum (a + x - r)^2, out[1] = sum r^2.

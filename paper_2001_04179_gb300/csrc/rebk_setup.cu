@@ -506,6 +506,81 @@ cudaError_t err_norms(const double *a, const double *x, const double *r, int64_t
     return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// FP64 GEMM for many vectors at once (the warm start's x0 = A^T y and A x0):
+// C (M x N, ldc) = sum_k Aop(i, k) Bop(k, j), Aop(i, k) = A[i * a_rs + k * a_cs],
+// Bop(k, j) = B[k * b_rs + j * b_cs].  64 x 64 tiles, K slices of 16 through
+// shared memory, 16 x 16 threads computing 4 x 4 outputs each; each operand is
+// loaded with its unit-stride index fastest (coalesced for either layout).
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) dgemm_kernel(int M, int N, int K, const double *__restrict__ A, int64_t a_rs,
+                                                    int64_t a_cs, const double *__restrict__ B, int64_t b_rs,
+                                                    int64_t b_cs, double *__restrict__ C, int64_t ldc) {
+    __shared__ double As[16][64 + 1];  // [k][i]
+    __shared__ double Bs[16][64 + 1];  // [k][j]
+    const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+    const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+    double acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.0;
+    const bool a_kfast = a_cs == 1, b_jfast = b_cs == 1;
+    for (int k0 = 0; k0 < K; k0 += 16) {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int e = tid + 256 * q;
+            const int il = a_kfast ? e / 16 : e % 64, kl = a_kfast ? e % 16 : e / 64;
+            const int i = i0 + il, k = k0 + kl;
+            As[kl][il] = (i < M && k < K) ? A[(int64_t)i * a_rs + (int64_t)k * a_cs] : 0.0;
+            const int jl = b_jfast ? e % 64 : e / 16, kb = b_jfast ? e / 64 : e % 16;
+            const int j = j0 + jl, kk = k0 + kb;
+            Bs[kb][jl] = (j < N && kk < K) ? B[(int64_t)kk * b_rs + (int64_t)j * b_cs] : 0.0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            double a[4], b[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) a[r] = As[k][ty * 4 + r];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) b[c] = Bs[k][tx * 4 + c];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) acc[r][c] = fma(a[r], b[c], acc[r][c]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        const int i = i0 + ty * 4 + r;
+        if (i >= M) continue;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = j0 + tx * 4 + c;
+            if (j < N) C[(int64_t)i * ldc + j] = acc[r][c];
+        }
+    }
+}
+
+// x0 and z0 = b - ax of right-hand sides j0 .. j0 + cnt - 1 (rows of x: n, of b and
+// ax: m) into the grouped layouts.
+__global__ void group_store_xz_many_kernel(const double *__restrict__ x, int64_t n, const double *__restrict__ b,
+                                           const double *__restrict__ ax, int64_t m, int64_t j0, int64_t cnt, int g,
+                                           double *__restrict__ X0, double *__restrict__ Z0) {
+    const int64_t per = n + m;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < cnt * per;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t c = e / per, r = e - c * per, j = j0 + c, gb = j / g, col = j % g;
+        if (r < n) X0[(gb * n + r) * g + col] = x[c * n + r];
+        else {
+            const int64_t k = r - n;
+            Z0[(gb * m + k) * g + col] = b[c * m + k] - ax[c * m + k];
+        }
+    }
+}
+
 // Grouped layout: right-hand side j is column j % g of the row-major (len x g)
 // block j / g.  dst[c * len + k] = entry k of right-hand side j0 + c.
 __global__ void group_gather_kernel(const double *__restrict__ src, int64_t j0, int64_t cnt, int g, int64_t len,
@@ -530,6 +605,21 @@ __global__ void group_store_xz_kernel(const double *__restrict__ x, int64_t n, c
             Z0[(gb * m + k) * g + col] = b[k] - ax[k];
         }
     }
+}
+
+cudaError_t dgemm(int M, int N, int K, const double *A, int64_t a_rs, int64_t a_cs, const double *B, int64_t b_rs,
+                  int64_t b_cs, double *C, int64_t ldc, cudaStream_t st) {
+    dim3 grid((unsigned)((N + 63) / 64), (unsigned)((M + 63) / 64));
+    dgemm_kernel<<<grid, 256, 0, st>>>(M, N, K, A, a_rs, a_cs, B, b_rs, b_cs, C, ldc);
+    return cudaGetLastError();
+}
+
+cudaError_t group_store_xz_many(const double *x, int64_t n, const double *b, const double *ax, int64_t m, int64_t j0,
+                                int64_t cnt, int g, double *X0, double *Z0, cudaStream_t st) {
+    const int64_t tot = cnt * (n + m);
+    group_store_xz_many_kernel<<<grid_for(tot, 256) > 4096 ? 4096 : grid_for(tot, 256), 256, 0, st>>>(
+        x, n, b, ax, m, j0, cnt, g, X0, Z0);
+    return cudaGetLastError();
 }
 
 cudaError_t group_gather(const double *src, int64_t j0, int64_t cnt, int g, int64_t len, double *dst,
