@@ -60,6 +60,8 @@ def parse():
                     help="with --workload batch: time one iteration of the batched kernel per system shape")
     ap.add_argument("--sweep-parts", default="", help="sweep workload: comma-separated parts 1-6 (default all)")
     ap.add_argument("--batch-tau", type=int, default=16, help="batch workload block size (0 = autotune)")
+    ap.add_argument("--batch-probe-shape", default="", help="with --batch-probe one: the system shape m,n")
+    ap.add_argument("--batch-probe-iters", type=int, default=2000, help="batch probe: iterations per pass")
     ap.add_argument("--batch-count", type=int, default=512, help="batch workload: number of systems")
     ap.add_argument("--batch-scale", type=int, default=1, help="batch workload: divide the size ranges (profiling)")
     ap.add_argument("--warm-train", type=int, default=2048)
@@ -564,9 +566,11 @@ def batch_probe(args):
 
     shapes = [(6000, 2000)] if args.batch_probe == "one" else [(8192, 2048), (6000, 2000), (2000, 2000),
                                                                 (2000, 500), (500, 200)]
+    if args.batch_probe == "one" and args.batch_probe_shape:
+        shapes = [tuple(int(v) for v in args.batch_probe_shape.split(","))]
     copies_list = [1] if args.batch_probe == "one" else [1, 152]
     tau = args.batch_tau if args.batch_tau > 0 else 16
-    K = 2000
+    K = args.batch_probe_iters
     for copies in copies_list:
         for (m, n) in shapes:
             rng = np.random.default_rng(m + n)

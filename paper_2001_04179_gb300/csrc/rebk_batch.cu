@@ -42,6 +42,7 @@ constexpr int64_t kPrefetchPoolBytes = 96ll << 20;  // FP32 matrix pool above wh
 constexpr double kIterFloorElems = 900.0;  // per-iteration latency floor of a CTA, in units of the
                                            // cost of one block element at tau 16 (queue ordering)
 
+
 // L2 prefetch of a block of the system's FP32 copy: rows [r0, r0 + h) x columns
 // [c0, c0 + w), one prefetch per 128-byte line, spread over the CTA.
 __device__ __forceinline__ void prefetch_block(const float *A, int64_t lda, int64_t r0, int64_t h, int64_t c0,
@@ -92,12 +93,35 @@ struct InnerArgs {
     unsigned long long timeout_ns;
 };
 
+// Sum over the 32 lanes of 8 per-lane values v[0..7], every shuffle a useful
+// one (exchange halves, keep the other half): afterwards lane L holds the
+// total of value ((L >> 4) & 1) * 4 + ((L >> 3) & 1) * 2 + ((L >> 2) & 1).
+__device__ __forceinline__ float warp_sum8f(const float (&v)[8], int lane) {
+    const bool h4 = (lane & 16) != 0, h3 = (lane & 8) != 0, h2 = (lane & 4) != 0;
+    float a[4], b[2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float keep = h4 ? v[i + 4] : v[i], send = h4 ? v[i] : v[i + 4];
+        a[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+    }
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const float keep = h3 ? a[i + 2] : a[i], send = h3 ? a[i] : a[i + 2];
+        b[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+    }
+    float c = (h2 ? b[1] : b[0]) + __shfl_xor_sync(0xffffffffu, h2 ? b[0] : b[1], 4);
+    c += __shfl_xor_sync(0xffffffffu, c, 2);
+    c += __shfl_xor_sync(0xffffffffu, c, 1);
+    return c;
+}
+
 __device__ __forceinline__ void load8(const float *p, float (&v)[kR]) {
     const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
 
 // One CTA per system; CPL = columns per lane in the column step (tau <= 32 CPL).
+
 template <int CPL>
 __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) {
     extern __shared__ __align__(16) float bsm[];
@@ -208,7 +232,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                         }
                     }
                 } else {
-                    constexpr int UR = CPL >= 8 ? 1 : (CPL >= 4 ? 2 : 4);  // rows in flight per warp
+                    constexpr int UR = CPL >= 8 ? 2 : 4;  // rows in flight per warp
                     float acc[CPL][kR];
 #pragma unroll
                     for (int q = 0; q < CPL; ++q)
@@ -294,8 +318,57 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                         }
                     }
                 }
+                // wide blocks (more than 32 columns): warps over rows, lanes over the columns
+                // lane + 32 q (the column partial's layout, coalesced 128-byte loads), W of the
+                // lane's columns in registers, the 8 sums of a row added over the warp by one
+                // transposed butterfly; rows of UR in flight
+                const bool wide = !fast && CPL >= 2 && wc > 32;
+                if constexpr (CPL >= 2) {
+                    if (wide) {
+                        constexpr int UR = CPL >= 8 ? 2 : 4;
+                        float wv[CPL][kR];
+#pragma unroll
+                        for (int q = 0; q < CPL; ++q) {
+                            const int c = lane + 32 * q;
+                            if (c < wc) {
+                                load8(W + c * kR, wv[q]);
+                            } else {
+#pragma unroll
+                                for (int r = 0; r < kR; ++r) wv[q][r] = 0.f;
+                            }
+                        }
+                        const int ridx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
+                        for (int64_t row0 = (int64_t)warp * UR; row0 < m; row0 += (int64_t)kBW * UR) {
+                            float av[UR][CPL];
+#pragma unroll
+                            for (int u = 0; u < UR; ++u) {
+                                const int64_t row = row0 + u;
+                                const float *Ar = A + row * lda + j0;
+#pragma unroll
+                                for (int q = 0; q < CPL; ++q) {
+                                    const int c = lane + 32 * q;
+                                    av[u][q] = (row < m && c < wc) ? __ldg(Ar + c) : 0.f;
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < UR; ++u) {
+                                float t8[kR];
+#pragma unroll
+                                for (int r = 0; r < kR; ++r) {
+                                    float t = 0.f;
+#pragma unroll
+                                    for (int q = 0; q < CPL; ++q) t = fmaf(av[u][q], wv[q][r], t);
+                                    t8[r] = t;
+                                }
+                                const float v = warp_sum8f(t8, lane);
+                                const int64_t row = row0 + u;
+                                if ((lane & 3) == 0 && row < m) dZ[row * kR + ridx] -= cJ * v;
+                            }
+                        }
+                    }
+                }
                 const bool vec4 = ((j0 & 3) == 0) && ((wc & 3) == 0);
-                for (int64_t row = fast ? m : tid; row < m; row += kBT) {
+                for (int64_t row = (fast || wide) ? m : tid; row < m; row += kBT) {
                     float t8[kR] = {0, 0, 0, 0, 0, 0, 0, 0};
                     const float *Ar = A + row * lda + j0;
                     if (vec4) {
