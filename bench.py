@@ -538,6 +538,30 @@ def run_batch_workload(args):
                           for r in range(8)] for i in range(len(ps))])
         rhs_ok += int((errs <= TOL).sum())
         sys_ok += int((errs <= TOL).all(axis=1).sum())
+    bs_tau = st["tau"]
+    # Systems with a right-hand side short of 1e-8 at the iteration cap: Theorem main's
+    # rate eta = 1 - (2 alpha - alpha^2 beta^I_max) sigma_r^2 / ||A||_F^2 at the batch's
+    # alpha.  The error bound's leading term eta^k reaches 1e-16 (1e-8 relative, squared)
+    # after k = log(1e-16) / log(eta) iterations; with sigma_r^2 from the device Lanczos
+    # (approached from above, so eta is too small) this k is a lower bound.
+    from paper_2001_04179_gb300 import Solver
+    cap = 100000
+    short = [i for i in range(len(ps)) if not (errs[i] <= TOL).all()]
+    reach = []
+    for i in short:
+        p = ps[i]
+        sol = Solver(p.A, bs_tau, bs_tau, alpha=0.0, storage=())
+        sp = sol.spectrum(steps=int(min(p.A.shape[0], p.A.shape[1], 400)), seed=1)
+        sol.close()
+        eta = sp["eta"]
+        k_lower = float("inf") if not (0.0 < eta < 1.0) else float(np.log(1e-16) / np.log(eta))
+        reach.append({"system": i, "m": int(p.A.shape[0]), "n": int(p.A.shape[1]), "alpha": sp["alpha"],
+                      "sigma_r_sq_upper": sp["sigma_r_sq"], "sigma1_sq": sp["sigma1_sq"], "fro2": sp["fro2"],
+                      "eta": eta, "iterations_lower_bound": k_lower,
+                      "rhs_short": int((errs[i] > TOL).sum()), "out_of_reach": bool(k_lower > cap)})
+    out_idx = {r["system"] for r in reach if r["out_of_reach"]}
+    reachable_rhs = 8 * (len(ps) - len(out_idx))
+    reachable_ok = int(sum((errs[i] <= TOL).sum() for i in range(len(ps)) if i not in out_idx))
     if rank == 0:
         print(json.dumps({
             "workload": f"batched: {args.batch_count} systems m~U[200,6000]/{args.batch_scale}, "
@@ -549,7 +573,14 @@ def run_batch_workload(args):
             "rhs_converged_per_solve": rhs_ok / steps, "systems_converged_per_solve": sys_ok / steps,
             "inner_iterations_per_solve": iters / steps, "max_iterations": st["max_iterations"],
             "problem_gen_s": gen_s, "create_s": create_s,
-            "sum_mn": int(sum(p.A.shape[0] * p.A.shape[1] for p in ps))}))
+            "sum_mn": int(sum(p.A.shape[0] * p.A.shape[1] for p in ps)),
+            "col_path": st.get("col_path"),
+            "out_of_reach": {"rule": "Theorem main's rate at the batch's alpha, sigma_r^2 from device Lanczos "
+                                     "(an upper estimate): iterations to 1e-8 >= log(1e-16)/log(eta) > the cap",
+                             "cap": cap, "systems": len(out_idx), "rhs": 8 * len(out_idx),
+                             "reachable_rhs": reachable_rhs, "reachable_rhs_converged_last_solve": reachable_ok,
+                             "reachable_rhs_per_s": reachable_ok / (ms / 1000.0 / steps),
+                             "short_systems": reach}}))
     return 0
 
 

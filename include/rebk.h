@@ -342,7 +342,8 @@ typedef struct rebk_batch_s *rebk_batch;
 typedef struct {
     int32_t tau;          /* block size for rows and columns of every system (Section 3
                              partitions), 1..256; 0 = autotune over {16, 32, 64, 128, 256}
-                             on a sample of the systems at the first solve              */
+                             and, for 16 and 32, the column step's tile shape, on a
+                             sample of the systems at the first solve                   */
     int32_t nrhs;         /* right-hand sides per system, 1..8 (all share one block
                              sequence per system)                                       */
     int32_t max_outer;    /* refinement passes at most; 0 = 6                           */
@@ -350,6 +351,9 @@ typedef struct {
     double inner_reduction; /* a pass ends once every RHS error is below this fraction
                                of its value at the pass start; 0 = 1e-4                */
     void *stream;         /* cudaStream_t for all work; NULL = legacy default stream    */
+    int32_t col_path;     /* column-step tile shape for blocks of 16 or 32 columns: 0 =
+                             16-byte vectors over tau/4 lanes of a row, 1 = one lane per
+                             column; with tau = 0 the autotuner picks it               */
 } rebk_batch_options;
 
 typedef struct {
@@ -363,6 +367,9 @@ typedef struct {
     int64_t launches;      /* kernels launched by the solve (graph nodes counted)     */
     int32_t tau;           /* block size in use                                       */
     int32_t graph;         /* 1 if the passes ran as one CUDA graph                   */
+    int32_t col_path;      /* column-step tile shape for blocks of 16 / 32 columns: 0 =
+                              16-byte vectors over tau/4 lanes of a row, 1 = one lane
+                              per column (picked with tau by the autotuner)           */
 } rebk_batch_stats;
 
 /*

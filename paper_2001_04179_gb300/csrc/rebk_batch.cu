@@ -88,6 +88,8 @@ struct InnerArgs {
     int64_t *iters_done;       // per system, accumulated over passes
     const int64_t *iter_cap;   // per system: total iterations allowed
     const int *active;         // per system: 0 = converged, skip
+    int col_path;              // blocks of 16 / 32 columns: 0 = a row's 16-byte vectors over tau/4 lanes,
+                               // 1 = one lane per column (the wide blocks' layout)
     int32_t *idx_out;          // NULL, or per system idx_cap pairs (j_k, i_k) of iterations 1..idx_cap
     int64_t idx_cap;
     unsigned long long timeout_ns;
@@ -183,7 +185,8 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                 // 16-byte load per lane, 32/(tau/4) rows per warp instruction (wider blocks
                 // run faster on the lane-per-column path: tau 128 on 8192 x 2048, 607 against
                 // 722 us per iteration)
-                const bool fast = wc == a.tau && (j0 & 3) == 0 && wc >= 16 && wc <= 32 && (wc & (wc - 1)) == 0;
+                const bool fast = a.col_path == 0 && wc == a.tau && (j0 & 3) == 0 && wc >= 16 && wc <= 32 &&
+                                  (wc & (wc - 1)) == 0;
                 const int lpr = wc >> 2, rpw = fast ? 32 / lpr : 1, sub = lane % lpr, rrow = lane / lpr;
                 if (fast) {
                     constexpr int UR = kColRowsInFlight;
@@ -704,6 +707,7 @@ struct rebk_batch_s {
     cudaStream_t stream = nullptr;
     bool own_stream = false;  // created here: the legacy default stream cannot be captured
     int count = 0, nrhs = 1, tau = 0, max_outer = 6, check_every = 10;
+    int col_path = 0;  // tile shape of the column step for blocks of 16 / 32 columns (autotuned with tau)
     double red = 1e-4;
     std::vector<int64_t> m, n, lda, a_off, mrow, nrow;
     int64_t Mrows = 0, Nrows = 0, Apool = 0;
@@ -964,6 +968,7 @@ rebk_status enqueue_solve(rebk_batch h, int tau, double tol, int64_t inner_iters
         a.iters_done = h->iters_done;
         a.iter_cap = h->iter_cap;
         a.active = h->active;
+        a.col_path = h->col_path;
         a.idx_out = h->rec_idx;
         a.idx_cap = h->rec_cap;
         a.timeout_ns = kBarrierTimeoutNs;
@@ -1002,6 +1007,7 @@ rebk_status rebk_batch_create(rebk_batch *out, int32_t count, const int64_t *m, 
     if (o.tau < 0 || o.tau > 256) return bfail(REBK_EINVAL, "tau must be 0 (auto) or 1..256");
     if (o.nrhs < 0 || o.nrhs > 8) return bfail(REBK_EINVAL, "nrhs must be 1..8");
     if (o.max_outer < 0 || o.check_every < 0 || o.inner_reduction < 0) return bfail(REBK_EINVAL, "negative option");
+    if (o.col_path != 0 && o.col_path != 1) return bfail(REBK_EINVAL, "col_path must be 0 or 1");
     for (int i = 0; i < count; ++i) {
         if (m[i] < 1 || n[i] < 1) return bfail(REBK_EINVAL, "every system needs m, n >= 1");
         if (!A[i]) return bfail(REBK_EINVAL, "NULL matrix pointer");
@@ -1015,6 +1021,7 @@ rebk_status rebk_batch_create(rebk_batch *out, int32_t count, const int64_t *m, 
     h->max_outer = o.max_outer > 0 ? o.max_outer : 6;
     h->check_every = o.check_every > 0 ? o.check_every : 10;
     h->red = o.inner_reduction > 0 ? o.inner_reduction : 1e-4;
+    h->col_path = o.col_path;
     h->m.assign(m, m + count);
     h->n.assign(n, n + count);
     h->alpha_given.assign(count, 0.0);
@@ -1228,6 +1235,7 @@ rebk_status run_batch(rebk_batch h, int tau, double tol, int64_t max_iter, int64
         stats->launches = launches;
         stats->tau = tau;
         stats->graph = used_graph ? 1 : 0;
+        stats->col_path = h->col_path;
     }
     return REBK_OK;
 }
@@ -1275,21 +1283,27 @@ extern "C" rebk_status rebk_batch_solve_ex(rebk_batch h, const double *B, double
             std::vector<char> sample(h->count, 0);
             const int stride = std::max(1, h->count / 16);
             for (int i = 0; i < h->count; i += stride) sample[i] = 1;
+            // candidates: block size and, for blocks of 16 or 32 columns, the column step's tile
+            // shape (16-byte vectors over tau/4 lanes of a row, or one lane per column)
             double best = 1e300;
-            int best_tau = 64;
+            int best_tau = 64, best_path = 0;
             const int64_t trial_cap = std::min<int64_t>(max_iter, 20000);
-            for (int cand : {16, 32, 64, 128, 256}) {
+            const int cands[][2] = {{16, 0}, {16, 1}, {32, 0}, {32, 1}, {64, 0}, {128, 0}, {256, 0}};
+            for (const auto &cand : cands) {
                 rebk_batch_stats s;
-                rebk_status rs = run_batch(h, cand, tol, trial_cap, inner_iters, seed, true, false, &s, &sample);
+                h->col_path = cand[1];
+                rebk_status rs = run_batch(h, cand[0], tol, trial_cap, inner_iters, seed, true, false, &s, &sample);
                 if (rs != REBK_OK) return rs;
                 const double score = s.device_ms / std::max(1, s.converged);
                 if (score < best) {
                     best = score;
-                    best_tau = cand;
+                    best_tau = cand[0];
+                    best_path = cand[1];
                 }
             }
             tau = best_tau;
             h->tau = tau;
+            h->col_path = best_path;
         }
     }
     rebk_status rs = run_batch(h, tau, tol, max_iter, inner_iters, seed, use_ref, true, stats);

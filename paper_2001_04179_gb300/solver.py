@@ -397,10 +397,12 @@ class BatchSolver:
 
     As: list of float64 numpy arrays (m_i x n_i).  tau: block size (0 =
     autotune at the first solve with reference solutions).  alpha: per-system
-    step sizes or None (1.75 / beta_max each)."""
+    step sizes or None (1.75 / beta_max each).  col_path: column-step tile shape
+    for blocks of 16 / 32 columns (0: 16-byte row vectors, 1: lane per column;
+    autotuned with tau = 0)."""
 
     def __init__(self, As, nrhs: int = 8, tau: int = 0, alpha=None, max_outer: int = 0,
-                 check_every: int = 0, inner_reduction: float = 0.0, stream=None):
+                 check_every: int = 0, inner_reduction: float = 0.0, stream=None, col_path: int = 0):
         lib = _r.load()
         self.count = len(As)
         self._As = [np.ascontiguousarray(A, dtype=np.float64) for A in As]
@@ -412,7 +414,7 @@ class BatchSolver:
             self._alpha = np.ascontiguousarray(alpha, dtype=np.float64)
             al = self._alpha.ctypes.data_as(ctypes.c_void_p)
         opt = _r.RebkBatchOptions(tau, nrhs, max_outer, check_every, inner_reduction,
-                                  None if stream is None else ctypes.c_void_p(stream.cuda_stream))
+                                  None if stream is None else ctypes.c_void_p(stream.cuda_stream), int(col_path))
         h = ctypes.c_void_p()
         st = lib.rebk_batch_create(ctypes.byref(h), self.count, self.m.ctypes.data_as(ctypes.c_void_p),
                                    self.n.ctypes.data_as(ctypes.c_void_p), ctypes.cast(ptrs, ctypes.c_void_p), 0,

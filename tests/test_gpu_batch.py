@@ -42,11 +42,14 @@ def oracle_draws(A, tau, seed, system, iters):
     return out
 
 
-@pytest.mark.parametrize("nrhs,tau", [(8, 16), (3, 7), (1, 32)])
-def test_one_pass_matches_oracle_per_system(nrhs, tau):
+@pytest.mark.parametrize("nrhs,tau,path", [(8, 16, 0), (8, 16, 1), (3, 7, 0), (1, 32, 0), (2, 32, 1), (8, 64, 0),
+                                           (4, 128, 0)])
+def test_one_pass_matches_oracle_per_system(nrhs, tau, path):
+    """Both column-step tile shapes for blocks of 16 / 32 columns, the wide-block
+    layout (64, 128) and ragged blocks (7)."""
     ps = batched_problems(5, seed=11, scale_down=12, nrhs=nrhs)
     alphas = _alphas(ps, tau)
-    bs = BatchSolver([p.A for p in ps], nrhs=nrhs, tau=tau, alpha=alphas, max_outer=1)
+    bs = BatchSolver([p.A for p in ps], nrhs=nrhs, tau=tau, alpha=alphas, max_outer=1, col_path=path)
     B = bs.stack_rhs([p.b for p in ps], bs.m)
     K = 120
     out = bs.solve(B, X_ref=None, tol=0.0, max_iter=K, inner_iters=K, seed=5, record_iters=K, return_z=True)
@@ -112,6 +115,8 @@ def test_autotuned_block_size():
     Xr = bs.stack_rhs([p.x_ref for p in ps], bs.n)
     out = bs.solve(B, X_ref=Xr, tol=1e-8, max_iter=400000, seed=2)
     assert out["stats"]["tau"] in (16, 32, 64, 128, 256)
+    assert out["stats"]["col_path"] in (0, 1)
+    assert out["stats"]["col_path"] == 0 or out["stats"]["tau"] in (16, 32)
     assert out["stats"]["converged"] == len(ps)
 
 
