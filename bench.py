@@ -81,6 +81,8 @@ def parse():
     ap.add_argument("--profile-mlp", type=int, default=0, metavar="K",
                     help="run K training steps (batch 256) of the 8192 -> 512 -> 512 -> 8192 warm-start network "
                          "and print the time per step (the case the network's ncu summary captures)")
+    ap.add_argument("--num-ctas", type=int, default=0,
+                    help="CTAs of the persistent kernel on the precision workload (0 = the library's autotune)")
     ap.add_argument("--profile-pass", type=int, default=0, metavar="K",
                     help="run one K-iteration refinement pass of the workload twice and exit "
                          "(the case the ncu summaries under profiles/ capture)")
@@ -135,7 +137,11 @@ def load_anchor():
 # profiles/rebk_grid_precision_8000x20000.md).  Keyed by the kernel's
 # storage form and the source hash of rebk_grid.cu it was taken on: a changed
 # kernel reports null until it is captured again.
-KERNEL_TRAFFIC = {}
+KERNEL_TRAFFIC = {
+    "corr_fp32": {"source_sha": "13c1267590cf3297", "dram_bytes_per_iteration": 24459010560 / 2000,
+                  "from": "ncu summary, scaled: dram__bytes_read.sum + dram__bytes_write.sum of one "
+                          "2000-iteration pass at 152 CTAs (bench.py --profile-pass 2000 --num-ctas 152)"},
+}
 
 
 def kernel_traffic(kernel_tag: str):
@@ -695,6 +701,19 @@ def run_sparse_workload(args):
 
     plain = run("plain")
     mixed = run("mixed")
+    # The CSR + CSC copies (151 MB FP64, 113 MB FP32) mostly stay in the 129 MB L2
+    # (ncu: 0.27 MB of DRAM traffic per iteration), so the bandwidth roof of this
+    # kernel is L2's: measured here by the library's L2 read microbenchmark.
+    from paper_2001_04179_gb300 import rebk as _R
+    import ctypes as _ct
+    pk = _R.RebkPeaks()
+    _R.check(_R.load().rebk_device_peaks(_ct.byref(pk), None))
+    l2_peak = pk.l2_gbs
+    for res in (plain, mixed):
+        res["roofline"] = {"bound": "l2", "achieved": res["achieved_gbs"], "peak": l2_peak, "unit": "GB/s",
+                           "frac": res["achieved_gbs"] / l2_peak,
+                           "peak_source": "measured: rebk_device_peaks L2 read kernel (16-byte loads that "
+                                          "bypass L1) on this GPU"}
     if rank == 0:
         print(json.dumps({
             "workload": "sparse: 65536x16384 CSR, 96 nnz/row uniform columns, values U(0,1)*10^U(0,1), "
@@ -1050,7 +1069,7 @@ def main():
     prob = make_problem(rank, True)
     stream = torch.cuda.current_stream()
     A_dev = torch.from_numpy(prob.A).to(dev)
-    sol = Solver(A_dev, TAU, TAU, alpha=0.0, storage=("fp32", "bf16"), stream=stream)
+    sol = Solver(A_dev, TAU, TAU, alpha=0.0, storage=("fp32", "bf16"), stream=stream, num_ctas=args.num_ctas)
     del A_dev
     torch.cuda.empty_cache()
     alpha = sol.alpha

@@ -211,6 +211,50 @@ rebk_status rebk_solve_free(rebk_handle h, int64_t tau_row, int64_t tau_col, dou
                             double *x, double tol, int64_t max_iter, uint64_t seed, const rebk_solve_ext *ext,
                             rebk_stats *stats);
 
+/* Options of the multi-right-hand-side solve.  Zero-initialise and set what you need. */
+typedef struct {
+    int32_t storage;          /* REBK_FP32 or REBK_BF16 (must be in storage_mask)        */
+    int32_t group;            /* right-hand sides per launch, 4 or 8; 0 = the largest
+                                 whose tiles fit in shared memory                          */
+    int32_t max_outer;        /* refinement passes per group at most; 0 = 30              */
+    int32_t reserved;         /* 0                                                         */
+    int64_t inner_iters;      /* iterations per pass at most; 0 = library default         */
+    double inner_reduction;   /* as rebk_refine_opts.inner_reduction                      */
+    int32_t *idx_out;         /* device, optional: (j_k, i_k) of the first group's
+                                 iterations, 2 * max_iter int32                            */
+    uint64_t stream_id;       /* Philox key word 1 of the first group; group g uses
+                                 stream_id + g                                             */
+} rebk_multi_opts;
+
+/*
+ * nrhs right-hand sides of one matrix.  Each one is solved as rebk_solve_refined
+ * solves one (Algorithm 1 of Section 2 on corrections with the FP32 or BF16 copy
+ * of A and FP32 arithmetic, inside the FP64 refinement loop on (x, z), x^0 = 0,
+ * z^0 = b), and the right-hand sides run in groups of `group` that share one
+ * block sequence: iteration k of every member draws the (J_k, I_k) that
+ * rebk_solve_refined draws with the same seed and stream id, so one read of a
+ * sampled block serves the whole group.  Group g (right-hand sides g*group ..
+ * g*group + group - 1) uses Philox key (seed, opt->stream_id + g).
+ * B: device, right-hand side j at B + j*ldb (m entries, ldb >= m).  X: device,
+ * solution j written at X + j*ldx (n entries, ldx >= n).  X_ref: device or NULL,
+ * reference j at X_ref + j*ldxr; with it a group stops once every member's
+ * relative error ||x - x_ref|| / ||x_ref|| <= tol, without it once every member
+ * passes the residual test of rebk_solve.  max_iter bounds each group's inner
+ * iterations.  rel_out: host, nrhs doubles or NULL: per right-hand side the final
+ * relative error (with X_ref) or max(resid_f, resid_g).  stats: totals over the
+ * groups (iterations summed, outer the largest pass count, rel_err the largest
+ * error).  Needs the tiles of the persistent kernel to fit a TMA box (tau_row,
+ * tau_col and the owned column slice at most 256).  Errors: EINVAL, EUNSUPPORTED,
+ * ENOMEM, ECUDA, DIVERGED, BARRIER_TIMEOUT; MAX_ITER when a group ends short of tol.
+ */
+rebk_status rebk_solve_multi(rebk_handle h, int64_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
+                             double tol, int64_t max_iter, uint64_t seed, const rebk_multi_opts *opt,
+                             const double *X_ref, int64_t ldxr, double *rel_out, rebk_stats *stats);
+
+/* The group size rebk_solve_multi picks for a storage (REBK_FP32 or REBK_BF16)
+ * when rebk_multi_opts.group is 0: 8, or 4 when the tiles of 8 do not fit. */
+rebk_status rebk_multi_group(rebk_handle h, int32_t storage, int32_t *group);
+
 /*
  * beta^I_max and beta^J_max of Section 2.2 (largest ||block||_2^2 / ||block||_F^2
  * over the row blocks and over the column blocks), from FP64 block Gram

@@ -106,6 +106,9 @@ struct rebk_handle_s {
     int64_t fr_idx_cap = 0;  // in int32 entries
     double *fr_acc = nullptr;
     int fr_acc_w = 0;
+    // several right-hand sides at once (rebk_solve_multi): one device buffer
+    void *mr_buf = nullptr;
+    size_t mr_bytes = 0;
 };
 
 namespace {
@@ -114,7 +117,7 @@ void free_handle(rebk_handle h) {
     if (!h) return;
     void *ptrs[] = {h->A64, h->A32, h->A16, h->nr, h->nc, h->cdf_r, h->cdf_c, h->d_fallback, h->acc,
                     h->d_row_off, h->d_col_off, h->fr_rn, h->fr_cn, h->fr_cdf_r, h->fr_cdf_c,
-                    h->fr_idx, h->fr_acc,
+                    h->fr_idx, h->fr_acc, h->mr_buf,
                     h->coef_r64, h->coef_c64, h->coef_r32, h->coef_c32,
                     h->ws, h->zbuf, h->f, h->g, h->ym, h->yn, h->dz, h->dx, h->sd, h->vd,
                     h->idxbuf};
@@ -408,6 +411,63 @@ rebk_status check_offsets(const int64_t *off, int64_t nb, int64_t size, const ch
     return REBK_OK;
 }
 
+
+// Launch geometry of the multi-right-hand-side kernel: every SM (or the
+// handle's CTA count), the owned slices and TMA tiles of the one-right-hand-side
+// kernel, and the largest group (8, else 4; or `want`) whose tiles fit in shared
+// memory, with the rest of shared memory as the reduction scratch.
+rebk_status multi_setup(rebk_handle h, Mode mode, int want, MultiArgs *Mout, int *Gout, int *nrout) {
+    const bool bf16 = mode == Mode::CorrBF16;
+    int dev = 0, sms = 1;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int G = h->num_ctas_opt > 0 ? std::min(sms, h->num_ctas_opt) : sms;
+    MultiArgs M;
+    memset(&M, 0, sizeof(M));
+    GridArgs &a = M.geo;
+    a.A = bf16 ? (const void *)h->A16 : (const void *)h->A32;
+    a.lda = h->lda;
+    a.m = h->m;
+    a.n = h->n;
+    a.tau_r = h->tau_r;
+    a.tau_c = h->tau_c;
+    a.s = h->s;
+    a.t = h->t;
+    a.row_off = h->d_row_off;
+    a.col_off = h->d_col_off;
+    a.col_align = h->col_align;
+    a.coef_r = h->coef_r32;
+    a.coef_c = h->coef_c32;
+    a.nrow_cap = (int)((h->m + G - 1) / G);
+    a.ncol_cap = (int)std::min<int64_t>(8 * (((h->n + 7) / 8 + G - 1) / G), h->n);
+    a.bar = &h->ws->bar;
+    a.status = &h->ws->status;
+    a.iters_done = &h->ws->iters_done;
+    a.timeout_ns = kBarrierTimeoutNs;
+    if (!tma_geometry(mode, a))
+        return fail(REBK_EUNSUPPORTED, "multi-right-hand-side form: a tile is wider or taller than 256 "
+                                       "(tau or the owned column slice)");
+    a.use_tma = 1;
+    if (tma_encode(mode, a) != cudaSuccess)
+        return fail(REBK_EUNSUPPORTED, "multi-right-hand-side form: no tensor map for the stored copy");
+    int nr = 0;
+    for (int cand : {8, 4}) {
+        if (want != 0 && cand != want) continue;
+        M.scr_floats = 0;
+        const size_t base = multi_smem_bytes(M, cand);
+        if (base + 128 > kSmemLimit) continue;
+        M.scr_floats = (int)std::min<size_t>((kSmemLimit - base - 128) / 4 / 32 * 32, (size_t)512 * cand);
+        const size_t smem = multi_smem_bytes(M, cand);
+        if (smem > kSmemLimit || multi_max_ctas(bf16, cand, smem) < G) continue;
+        nr = cand;
+        break;
+    }
+    if (nr == 0) return fail(REBK_EUNSUPPORTED, "multi-right-hand-side form: the tiles do not fit in shared memory");
+    *Mout = M;
+    *Gout = G;
+    *nrout = nr;
+    return REBK_OK;
+}
 }  // namespace
 
 namespace rebk {
@@ -1302,6 +1362,332 @@ rebk_status rebk_solve_free(rebk_handle h, int64_t tau_row, int64_t tau_col, dou
     if (!use_ref && result == REBK_MAX_ITER) result = REBK_OK;
     fill_stats(h, stats, total, 0, result, rel, -1, -1, ms);
     if (result == REBK_DIVERGED) return fail(REBK_DIVERGED, "iteration diverged (Inf/NaN)");
+    return result;
+}
+
+
+rebk_status rebk_multi_group(rebk_handle h, int32_t storage, int32_t *group) {
+    g_last_error.clear();
+    if (!h || !group) return fail(REBK_EINVAL, "handle or group is NULL");
+    Mode mode;
+    if (storage == REBK_FP32 && h->A32) mode = Mode::CorrF32;
+    else if (storage == REBK_BF16 && h->A16) mode = Mode::CorrBF16;
+    else return fail(REBK_EINVAL, "storage must be REBK_FP32 or REBK_BF16 and kept by the handle");
+    MultiArgs M;
+    int G = 0, nr = 0;
+    rebk_status s = multi_setup(h, mode, 0, &M, &G, &nr);
+    if (s != REBK_OK) return s;
+    *group = nr;
+    return REBK_OK;
+}
+
+rebk_status rebk_solve_multi(rebk_handle h, int64_t nrhs, const double *B, int64_t ldb, double *X, int64_t ldx,
+                             double tol, int64_t max_iter, uint64_t seed, const rebk_multi_opts *opt,
+                             const double *X_ref, int64_t ldxr, double *rel_out, rebk_stats *stats) {
+    g_last_error.clear();
+    if (!h) return fail(REBK_EINVAL, "handle is NULL");
+    if (nrhs < 0) return fail(REBK_EINVAL, "nrhs < 0");
+    if (nrhs > 0 && (!B || !X)) return fail(REBK_EINVAL, "B and X must be device pointers");
+    if (ldb < h->m || ldx < h->n || (X_ref && ldxr < h->n))
+        return fail(REBK_EINVAL, "a leading dimension is below the vector length");
+    if (max_iter < 0) return fail(REBK_EINVAL, "max_iter < 0");
+    if (!std::isfinite(tol)) return fail(REBK_EINVAL, "tol is not finite");
+    rebk_multi_opts o;
+    memset(&o, 0, sizeof(o));
+    o.storage = REBK_FP32;
+    if (opt) o = *opt;
+    Mode mode;
+    if (o.storage == REBK_FP32) {
+        if (!h->A32) return fail(REBK_EINVAL, "FP32 copy not kept (storage_mask)");
+        mode = Mode::CorrF32;
+    } else if (o.storage == REBK_BF16) {
+        if (!h->A16) return fail(REBK_EINVAL, "BF16 copy not kept (storage_mask)");
+        mode = Mode::CorrBF16;
+    } else {
+        return fail(REBK_EINVAL, "storage must be REBK_FP32 or REBK_BF16");
+    }
+    const bool bf16 = mode == Mode::CorrBF16;
+    if (o.group != 0 && o.group != 4 && o.group != 8) return fail(REBK_EINVAL, "group must be 0, 4 or 8");
+    if (o.max_outer < 0 || o.inner_iters < 0 || o.inner_reduction < 0 || o.reserved != 0)
+        return fail(REBK_EINVAL, "negative or reserved option set");
+    const int max_outer = o.max_outer > 0 ? o.max_outer : 30;
+    const double red = o.inner_reduction > 0 ? o.inner_reduction : (bf16 ? 1e-2 : 1e-4);
+    const cudaStream_t st = h->stream;
+    const int64_t m = h->m, n = h->n;
+    const bool use_ref = X_ref != nullptr;
+    reset_counters(h);
+    if (nrhs == 0) {
+        fill_stats(h, stats, 0, 0, REBK_OK, -1, -1, -1, 0.0);
+        return REBK_OK;
+    }
+
+    MultiArgs M;
+    int G = 0, nr = 0;
+    rebk_status ms_ = multi_setup(h, mode, o.group, &M, &G, &nr);
+    if (ms_ != REBK_OK) return ms_;
+    GridArgs &a = M.geo;
+    const int aw = (int)round_up((int64_t)(a.tau_r + a.tau_c) * nr, 4);
+
+    // device buffers (one allocation kept by the handle)
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o0 = off;
+        off = (off + bytes + 255) & ~(size_t)255;
+        return o0;
+    };
+    const size_t mv = (size_t)m * nr, nv = (size_t)n * nr;
+    const size_t oB = take(8 * mv), oZ = take(8 * mv), oX = take(8 * nv), oXr = take(8 * nv), oYm = take(8 * mv),
+                 oYn = take(8 * nv), oSm = take(8 * 64), oF = take(4 * mv), oG = take(4 * nv), odZ = take(4 * mv),
+                 oV = take(4 * mv), odX = take(4 * nv), oS = take(4 * nv),
+                 oAcc = take(sizeof(float) * 3 * kMultiReplicas * (size_t)aw);
+    if (off > h->mr_bytes) {
+        if (h->mr_buf) cudaFree(h->mr_buf);
+        h->mr_buf = nullptr;
+        h->mr_bytes = 0;
+        CK(cudaMalloc(&h->mr_buf, off));
+        h->mr_bytes = off;
+    }
+    char *base = static_cast<char *>(h->mr_buf);
+    double *Bq = (double *)(base + oB), *Zq = (double *)(base + oZ), *Xq = (double *)(base + oX);
+    double *Xr = (double *)(base + oXr), *Ym = (double *)(base + oYm), *Yn = (double *)(base + oYn);
+    double *small = (double *)(base + oSm);
+    float *F = (float *)(base + oF), *Gf = (float *)(base + oG), *dZ = (float *)(base + odZ);
+    float *V = (float *)(base + oV), *dX = (float *)(base + odX), *S = (float *)(base + oS);
+    float *acc = (float *)(base + oAcc);
+    M.dZ = dZ;
+    M.dX = dX;
+    M.S = S;
+    M.V = V;
+    M.F = F;
+    M.G = Gf;
+    a.acc = acc;
+    a.acc_w = aw;
+    auto fetch = [&](double *host, int count) -> rebk_status {
+        CK(cudaMemcpyAsync(host, small, sizeof(double) * count, cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        return REBK_OK;
+    };
+    int64_t inner_default = o.inner_iters;
+    if (inner_default <= 0) {
+        if (use_ref) {
+            inner_default = 1000000;
+        } else {
+            const double per_iter = (double)h->tau_r * n + (double)h->tau_c * m;
+            inner_default = std::max<int64_t>(200, (int64_t)(40.0 * (double)m * n / per_iter));
+        }
+    }
+
+    CK(cudaEventRecord(h->ev0, st));
+    const int64_t ngroups = (nrhs + nr - 1) / nr;
+    int64_t all_iters = 0;
+    int outer_max_seen = 0;
+    double worst = -1.0;
+    rebk_status result = REBK_OK;
+    for (int64_t gi = 0; gi < ngroups; ++gi) {
+        const int64_t j0 = gi * nr;
+        const int cnt = (int)std::min<int64_t>(nr, nrhs - j0);
+        LK(h, multi_gather(B + j0 * ldb, ldb, cnt, m, nr, Bq, st));
+        CK(cudaMemcpyAsync(Zq, Bq, 8 * mv, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemsetAsync(Xq, 0, 8 * nv, st));
+        double v[4 * 8];
+        double refn[8] = {0}, bn[8] = {0}, rel[8], res[8];
+        for (int q = 0; q < 8; ++q) rel[q] = res[q] = -1.0;
+        if (use_ref) {
+            LK(h, multi_gather(X_ref + j0 * ldxr, ldxr, cnt, n, nr, Xr, st));
+            LK(h, multi_norms(nullptr, nullptr, Xr, n, nr, small, st));
+        } else {
+            LK(h, multi_norms(nullptr, nullptr, Bq, m, nr, small, st));
+        }
+        rebk_status s = fetch(v, 2 * nr);
+        if (s != REBK_OK) return s;
+        for (int q = 0; q < nr; ++q) (use_ref ? refn : bn)[q] = std::sqrt(v[nr + q]);
+        // residual test of every member (after a sweep that left F and G current)
+        auto residual_test = [&](double *worst_res) -> rebk_status {
+            LK(h, multi_norms(nullptr, F, nullptr, m, nr, small, st));
+            LK(h, multi_norms(nullptr, Gf, nullptr, n, nr, small + 2 * nr, st));
+            rebk_status s2 = fetch(v, 4 * nr);
+            if (s2 != REBK_OK) return s2;
+            *worst_res = 0.0;
+            for (int q = 0; q < cnt; ++q) {
+                const double rf = bn[q] > 0 ? std::sqrt(v[q]) / bn[q] : 0.0;
+                const double rg = bn[q] > 0 ? std::sqrt(v[2 * nr + q]) / (std::sqrt(h->fro2) * bn[q]) : 0.0;
+                res[q] = std::max(rf, rg);
+                *worst_res = std::max(*worst_res, res[q]);
+            }
+            return REBK_OK;
+        };
+        auto error_test = [&](const float *corr, double *e) -> rebk_status {
+            LK(h, multi_norms(Xq, corr, Xr, n, nr, small, st));
+            rebk_status s2 = fetch(v, nr);
+            if (s2 != REBK_OK) return s2;
+            for (int q = 0; q < nr; ++q) e[q] = std::sqrt(v[q]);
+            return REBK_OK;
+        };
+        bool converged = false, x_zero = true;
+        int64_t total = 0, inner_max = inner_default;
+        double prev_res = -1.0;
+        int outer = 0;
+        if (h->fro2 == 0.0) converged = true;  // x = 0 is A^+ b
+        for (; !converged && outer < max_outer; ++outer) {
+            double e0[8] = {0};
+            if (use_ref) {
+                s = error_test(nullptr, e0);
+                if (s != REBK_OK) return s;
+                bool all = true;
+                for (int q = 0; q < cnt; ++q) {
+                    rel[q] = refn[q] > 0 ? e0[q] / refn[q] : e0[q];
+                    all = all && rel[q] <= tol;
+                }
+                if (all) {
+                    converged = true;
+                    break;
+                }
+            }
+            // F = b - z - A x, G = A^T z (FP64)
+            if (x_zero) CK(cudaMemsetAsync(Ym, 0, 8 * mv, st));
+            else LK(h, multi_ap(h->A64, h->lda, m, n, nr, Xq, false, Ym, st));
+            LK(h, multi_atq(h->A64, h->lda, m, n, nr, Zq, false, Yn, st));
+            x_zero = false;
+            LK(h, multi_form(Bq, Zq, Ym, F, m, Yn, Gf, n, nr, st));
+            if (!use_ref) {
+                double wr = 0.0;
+                s = residual_test(&wr);
+                if (s != REBK_OK) return s;
+                if (wr <= tol) {
+                    converged = true;
+                    break;
+                }
+                if (prev_res > 0 && wr > 0.1 * prev_res) inner_max = std::min<int64_t>(inner_max * 2, 1 << 24);
+                prev_res = wr;
+            }
+            if (total >= max_iter) break;
+            CK(cudaMemsetAsync(dZ, 0, 4 * mv, st));
+            CK(cudaMemsetAsync(V, 0, 4 * mv, st));
+            CK(cudaMemsetAsync(dX, 0, 4 * nv, st));
+            CK(cudaMemsetAsync(S, 0, 4 * nv, st));
+            const int64_t iters = std::min(inner_max, max_iter - total);
+            int64_t ran = 0, chunk_next = use_ref ? 512 : iters;
+            // A pass ends (with a reference) once every member's error x + dx is below
+            // its threshold or has stopped falling, as in rebk_solve_refined; the next
+            // chunk is sized from the slowest member's observed rate.
+            double e_prev[8], rate_prev[8];
+            bool fin[8];
+            for (int q = 0; q < 8; ++q) {
+                e_prev[q] = e0[q];
+                rate_prev[q] = -1.0;
+                fin[q] = q >= cnt;
+            }
+            while (ran < iters) {
+                const int64_t chunk = std::min(std::min(iters - ran, chunk_next), kMaxItersPerLaunch);
+                int32_t *dst = (gi == 0 && o.idx_out) ? o.idx_out + 2 * (total + ran) : nullptr;
+                if (!dst) {
+                    if (chunk > h->idx_cap) {
+                        if (h->idxbuf) cudaFree(h->idxbuf);
+                        h->idxbuf = nullptr;
+                        h->idx_cap = 0;
+                        const int64_t cap = std::max<int64_t>(chunk, 65536);
+                        CK(cudaMalloc(&h->idxbuf, sizeof(int32_t) * 2 * cap));
+                        h->idx_cap = cap;
+                    }
+                    dst = h->idxbuf;
+                }
+                LK(h, sample_blocks(seed, o.stream_id + (uint64_t)gi, total + ran, chunk, h->cdf_r, h->s, h->cdf_c,
+                                    h->t, h->fb[0], h->fb[1], dst, st));
+                a.idx = dst;
+                a.k0 = total + ran;
+                a.iters = chunk;
+                CK(cudaMemsetAsync(acc, 0, sizeof(float) * 3 * kMultiReplicas * (size_t)aw, st));
+                CK(cudaMemsetAsync(h->ws, 0, sizeof(Workspace), st));
+                CK(cudaEventRecord(h->kev0, st));
+                CK(launch_multi(M, bf16, nr, G, st));
+                CK(cudaEventRecord(h->kev1, st));
+                ++h->launches;
+                ++h->grid_launches;
+                Workspace w;
+                CK(cudaMemcpyAsync(&w, h->ws, sizeof(Workspace), cudaMemcpyDeviceToHost, st));
+                CK(cudaStreamSynchronize(st));
+                float kms = 0.f;
+                CK(cudaEventElapsedTime(&kms, h->kev0, h->kev1));
+                h->kernel_ms += kms;
+                ran += w.iters_done;
+                if (w.status == 6) {
+                    fill_stats(h, stats, all_iters + total + ran, outer + 1, REBK_BARRIER_TIMEOUT, -1, -1, -1, 0);
+                    return fail(REBK_BARRIER_TIMEOUT, "device-wide barrier or tile copy timed out");
+                }
+                if (w.status == 5) {
+                    fill_stats(h, stats, all_iters + total + ran, outer + 1, REBK_DIVERGED, -1, -1, -1, 0);
+                    return fail(REBK_DIVERGED, "inner iteration diverged (Inf/NaN)");
+                }
+                if (w.status != 0 || w.iters_done != chunk)
+                    return fail(REBK_ECUDA, "multi-right-hand-side kernel ran fewer iterations than launched");
+                if (!use_ref || ran >= iters) continue;
+                double e_now[8];
+                s = error_test(dX, e_now);
+                if (s != REBK_OK) return s;
+                bool all = true;
+                double need = 0.0;
+                for (int q = 0; q < cnt; ++q) {
+                    if (fin[q]) continue;
+                    const double thr = std::max(tol * refn[q], red * e0[q]);
+                    const double rate = e_now[q] > 0 ? std::log(e_prev[q] / e_now[q]) / (double)chunk : 1.0;
+                    if (e_now[q] <= thr || !(e_now[q] < e_prev[q]) || (rate_prev[q] > 0.0 && rate < 0.1 * rate_prev[q])) {
+                        fin[q] = true;
+                        continue;
+                    }
+                    all = false;
+                    rate_prev[q] = rate;
+                    e_prev[q] = e_now[q];
+                    need = std::max(need, std::log(e_now[q] / thr) / rate);
+                }
+                if (all) break;
+                chunk_next = std::min<int64_t>(std::max<int64_t>((int64_t)(need * 1.06) + 32, 128), (int64_t)1 << 20);
+            }
+            total += ran;
+            // z <- z - A s, x <- x + A^T v (FP64 A)
+            LK(h, multi_ap(h->A64, h->lda, m, n, nr, S, true, Ym, st));
+            LK(h, multi_atq(h->A64, h->lda, m, n, nr, V, true, Yn, st));
+            LK(h, multi_apply(Xq, Yn, n, Zq, Ym, m, nr, st));
+        }
+        if (!converged) {  // the test after the last pass
+            if (use_ref) {
+                double e[8];
+                s = error_test(nullptr, e);
+                if (s != REBK_OK) return s;
+                converged = true;
+                for (int q = 0; q < cnt; ++q) {
+                    rel[q] = refn[q] > 0 ? e[q] / refn[q] : e[q];
+                    converged = converged && rel[q] <= tol;
+                }
+            } else {
+                LK(h, multi_ap(h->A64, h->lda, m, n, nr, Xq, false, Ym, st));
+                LK(h, multi_atq(h->A64, h->lda, m, n, nr, Zq, false, Yn, st));
+                LK(h, multi_form(Bq, Zq, Ym, F, m, Yn, Gf, n, nr, st));
+                double wr = 0.0;
+                s = residual_test(&wr);
+                if (s != REBK_OK) return s;
+                converged = wr <= tol;
+            }
+        } else if (use_ref && h->fro2 == 0.0) {
+            double e[8];
+            s = error_test(nullptr, e);
+            if (s != REBK_OK) return s;
+            for (int q = 0; q < cnt; ++q) rel[q] = refn[q] > 0 ? e[q] / refn[q] : e[q];
+        }
+        LK(h, multi_scatter(Xq, cnt, n, nr, X + j0 * ldx, ldx, st));
+        for (int q = 0; q < cnt; ++q) {
+            const double r = use_ref ? rel[q] : res[q];
+            if (rel_out) rel_out[j0 + q] = r;
+            worst = std::max(worst, r);
+        }
+        all_iters += total;
+        outer_max_seen = std::max(outer_max_seen, outer);
+        if (!converged) result = REBK_MAX_ITER;
+    }
+    CK(cudaEventRecord(h->ev1, st));
+    CK(cudaEventSynchronize(h->ev1));
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+    fill_stats(h, stats, all_iters, outer_max_seen, result, use_ref ? worst : -1.0, use_ref ? -1.0 : worst, -1.0, ms);
     return result;
 }
 

@@ -241,6 +241,77 @@ cudaError_t umma_gemm(int M, int N, int K, const __nv_bfloat16 *A, int64_t lda, 
                       __nv_bfloat16 *CbT, int64_t ldcbt, int relu, const float *mask, int64_t ldm, float *ws,
                       size_t ws_floats, int *error, cudaStream_t st);
 
+// Several right-hand sides of one matrix at once (rebk_multi.cu): Algorithm 1 in
+// the correction form for NR right-hand sides sharing one block sequence.
+// Vectors of NR right-hand sides are interleaved: entry (row i, right-hand side
+// q) at [i * NR + q].
+struct MultiArgs {
+    // matrix copy (A, lda, m, n), blocks (tau_r, tau_c, s, t, row_off, col_off),
+    // FP32 step coefficients (coef_r, coef_c), draws (idx, iters), tensor maps and
+    // tile geometry (bw_c, bh_c, nbox_c, bw_r, tile bytes, tma_vx), owned-slice
+    // capacities, FP32 accumulators (acc: 3 sets x kMultiReplicas x acc_w), barrier,
+    // status, iters_done and timeout
+    GridArgs geo;
+    float *dZ, *dX, *S, *V;  // corrections and duals: [m][NR], [n][NR], [n][NR], [m][NR]
+    const float *F, *G;      // f = b - z - A x ([m][NR]) and g = A^T z ([n][NR]), rounded to FP32
+    int scr_floats;          // reduction scratch in shared memory (floats)
+};
+
+constexpr int kMultiReplicas = 4;
+
+struct MultiSmem {
+    size_t tc0, tc1, tr0, tr1, zeta, xi, w, r, scr, total;
+};
+
+// Shared-memory layout of the multi kernel (byte offsets): 512-byte header
+// (mbarriers, flags, step coefficients), two column tiles, two row tiles, dZ of
+// the owned rows ([nrow_cap][NR]), dX of the owned columns (q-major: [NR][xs]),
+// w (q-major: [NR][ws]), r ([tau_r][NR]) and the scratch.
+__host__ __device__ inline int multi_xs(int ncol_cap) { return (ncol_cap + 31) / 32 * 32 + 4; }
+__host__ __device__ inline int multi_ws(int tau_c) { return (tau_c + 31) / 32 * 32 + 4; }
+__host__ __device__ inline MultiSmem multi_smem_layout(int nrow_cap, int ncol_cap, int tau_r, int tau_c, int nr,
+                                                       int64_t tile_c_bytes, int64_t tile_r_bytes, int scr_floats) {
+    auto al128 = [](size_t x) { return (x + 127) & ~(size_t)127; };
+    MultiSmem L;
+    size_t o = 512;
+    L.tc0 = o; o = al128(o + (size_t)tile_c_bytes);
+    L.tc1 = o; o = al128(o + (size_t)tile_c_bytes);
+    L.tr0 = o; o = al128(o + (size_t)tile_r_bytes);
+    L.tr1 = o; o = al128(o + (size_t)tile_r_bytes);
+    L.zeta = o; o = al128(o + (size_t)nrow_cap * nr * 4);
+    L.xi = o;   o = al128(o + (size_t)nr * multi_xs(ncol_cap) * 4);
+    L.w = o;    o = al128(o + (size_t)nr * multi_ws(tau_c) * 4);
+    L.r = o;    o = al128(o + (size_t)tau_r * nr * 4);
+    L.scr = o;  o = al128(o + (size_t)scr_floats * 4);
+    L.total = o;
+    return L;
+}
+size_t multi_smem_bytes(const MultiArgs &M, int nr);
+cudaError_t launch_multi(const MultiArgs &M, bool bf16, int nr, int G, cudaStream_t st);
+int multi_max_ctas(bool bf16, int nr, size_t smem);
+// FP64 products with nr interleaved vectors: Y = A P (P: [n][nr], Y: [m][nr]) and
+// Y = A^T Q (Q: [m][nr], Y: [n][nr]); P / Q FP64 or FP32 (p_f32); Y is overwritten.
+cudaError_t multi_ap(const double *A, int64_t lda, int64_t m, int64_t n, int nr, const void *P, bool p_f32,
+                     double *Y, cudaStream_t st);
+cudaError_t multi_atq(const double *A, int64_t lda, int64_t m, int64_t n, int nr, const void *Q, bool q_f32,
+                      double *Y, cudaStream_t st);
+// out[q] = sum_i (a + b - r)^2 and out[nr + q] = sum_i r^2 over i < len for the
+// interleaved vectors a (FP64), b (FP32), r (FP64); a, b may be NULL (zero).
+cudaError_t multi_norms(const double *a, const float *b, const double *r, int64_t len, int nr, double *out,
+                        cudaStream_t st);
+// Interleave cnt vectors of length len (vector j at src + j * ld) into dst [len][nr]
+// (vectors cnt .. nr - 1 zero), and back (the first cnt).
+cudaError_t multi_gather(const double *src, int64_t ld, int64_t cnt, int64_t len, int nr, double *dst,
+                         cudaStream_t st);
+cudaError_t multi_scatter(const double *src, int64_t cnt, int64_t len, int nr, double *dst, int64_t ld,
+                          cudaStream_t st);
+// F = fp32(B - Z - Ym) (len m x nr), G = fp32(Yn) (len n x nr).
+cudaError_t multi_form(const double *B, const double *Z, const double *Ym, float *F, int64_t m, const double *Yn,
+                       float *G, int64_t n, int nr, cudaStream_t st);
+// X += Yn (n x nr), Z -= Ym (m x nr).
+cudaError_t multi_apply(double *X, const double *Yn, int64_t n, double *Z, const double *Ym, int64_t m, int nr,
+                        cudaStream_t st);
+
 // Sets the message rebk_last_error() returns on this thread (rebk_api.cu).
 void set_last_error(const std::string &msg);
 

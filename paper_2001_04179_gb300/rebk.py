@@ -49,6 +49,12 @@ class RebkRefineOpts(ctypes.Structure):
                 ("inner_iters", ctypes.c_int64), ("inner_reduction", ctypes.c_double)]
 
 
+class RebkMultiOpts(ctypes.Structure):
+    _fields_ = [("storage", ctypes.c_int32), ("group", ctypes.c_int32), ("max_outer", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("inner_iters", ctypes.c_int64), ("inner_reduction", ctypes.c_double),
+                ("idx_out", ctypes.c_void_p), ("stream_id", ctypes.c_uint64)]
+
+
 class RebkTunePoint(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_int64), ("beta_max", ctypes.c_double), ("alpha", ctypes.c_double),
                 ("iterations", ctypes.c_int64), ("device_ms", ctypes.c_double), ("status", ctypes.c_int32)]
@@ -121,6 +127,10 @@ _SIGNATURES = {
     "rebk_solve_free": ([_P, ctypes.c_int64, ctypes.c_int64, ctypes.c_double, _P, _P, ctypes.c_double,
                          ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(RebkSolveExt), ctypes.POINTER(RebkStats)],
                         ctypes.c_int),
+    "rebk_solve_multi": ([_P, ctypes.c_int64, _P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_double,
+                          ctypes.c_int64, ctypes.c_uint64, ctypes.POINTER(RebkMultiOpts), _P, ctypes.c_int64, _P,
+                          ctypes.POINTER(RebkStats)], ctypes.c_int),
+    "rebk_multi_group": ([_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)], ctypes.c_int),
     "rebk_beta_max": ([_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "rebk_get_alpha": ([_P, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
     "rebk_set_alpha": ([_P, ctypes.c_double], ctypes.c_int),

@@ -216,6 +216,48 @@ class Solver:
             out["idx"] = idx[: W * stats.iterations].view(-1, W)
         return out
 
+    def solve_multi(self, B, tol: float = 1e-8, max_iter: int = 10**7, seed: int = 0, storage: str = "fp32",
+                    group: int = 0, X_ref=None, max_outer: int = 0, inner_iters: int = 0,
+                    inner_reduction: float = 0.0, stream_id: int = 0, record: bool = False, X=None,
+                    allow=(_r.REBK_OK, _r.REBK_MAX_ITER)):
+        """Several right-hand sides at once (rebk_solve_multi): B is a CUDA
+        float64 (nrhs, m) tensor with unit column stride; each row is solved as
+        solve_refined solves one, in groups of `group` (4 or 8, 0 = library
+        choice) that share one block sequence.  Returns dict(X (nrhs, n), rel
+        (per right-hand side: error with X_ref, else residual), stats[, idx of
+        the first group])."""
+        torch = _torch()
+        if not (B.is_cuda and B.dtype == torch.float64 and B.dim() == 2 and B.shape[1] == self.m
+                and B.stride(1) == 1):
+            raise ValueError(f"B must be a CUDA float64 (nrhs, {self.m}) tensor with unit column stride")
+        nrhs = B.shape[0]
+        if X is None:
+            X = torch.empty(nrhs, self.n, dtype=torch.float64, device=B.device)
+        if X_ref is not None and not (X_ref.is_cuda and X_ref.dtype == torch.float64 and X_ref.dim() == 2
+                                      and tuple(X_ref.shape) == (nrhs, self.n) and X_ref.stride(1) == 1):
+            raise ValueError(f"X_ref must be a CUDA float64 ({nrhs}, {self.n}) tensor with unit column stride")
+        idx = torch.zeros(max(2 * min(max_iter, 10**7), 2), dtype=torch.int32, device=B.device) if record else None
+        opt = _r.RebkMultiOpts(_r.STORAGE[storage], int(group), int(max_outer), 0, int(inner_iters),
+                               float(inner_reduction), _dptr(idx), int(stream_id))
+        rel = (ctypes.c_double * max(nrhs, 1))()
+        stats = _r.RebkStats()
+        st = _r.load().rebk_solve_multi(self._h, nrhs, _dptr(B), B.stride(0) if nrhs else self.m, _dptr(X),
+                                        X.stride(0) if nrhs else self.n, float(tol), int(max_iter), int(seed),
+                                        ctypes.byref(opt), _dptr(X_ref),
+                                        X_ref.stride(0) if X_ref is not None else 0,
+                                        ctypes.cast(rel, ctypes.c_void_p), ctypes.byref(stats))
+        _r.check(st, allow)
+        out = {"X": X, "rel": np.array(rel[:nrhs]), "stats": stats.as_dict(), "status": st}
+        if record:
+            out["idx"] = idx
+        return out
+
+    def multi_group(self, storage: str = "fp32") -> int:
+        """Group size solve_multi picks for `storage` (rebk_multi_group)."""
+        g = ctypes.c_int32()
+        _r.check(_r.load().rebk_multi_group(self._h, _r.STORAGE[storage], ctypes.byref(g)))
+        return g.value
+
     def solve_rabk(self, b, **kw):
         """The RABK special case (the remark after Algorithm 1): z^0 = 0 keeps every
         z^k = 0, so each step is the weighted block average of eq. (rabk) on A x = b
