@@ -83,6 +83,11 @@ def parse():
                          "and print the time per step (the case the network's ncu summary captures)")
     ap.add_argument("--num-ctas", type=int, default=0,
                     help="CTAs of the persistent kernel on the precision workload (0 = the library's autotune)")
+    ap.add_argument("--multi-rhs", type=int, default=16,
+                    help="precision workload: right-hand sides of the multi-right-hand-side leg (0 = skip)")
+    ap.add_argument("--multi-steps", type=int, default=2, help="timed steps of the multi-right-hand-side leg")
+    ap.add_argument("--profile-multi", type=int, default=0, metavar="K",
+                    help="run one K-iteration pass of the multi-right-hand-side kernel (one group) twice and exit")
     ap.add_argument("--profile-pass", type=int, default=0, metavar="K",
                     help="run one K-iteration refinement pass of the workload twice and exit "
                          "(the case the ncu summaries under profiles/ capture)")
@@ -172,7 +177,52 @@ def cpu_model() -> str:
     return "unknown"
 
 
-def make_problem(seed: int, use_gpu: bool):
+def measure_multi(args, sol, prob, dev, rank, storage, stream, hbm_peak):
+    """The precision workload's A with args.multi_rhs right-hand sides solved by
+    rebk_solve_multi: groups that share one block sequence, each member to 1e-8
+    against its own A^+ b (verified).  solves/s = right-hand sides per second."""
+    import torch
+    nrhs = args.multi_rhs
+    pm = make_problem(rank, True, nrhs=nrhs)  # the same factors, hence the same A
+    if not (np.array_equal(pm.A[0], prob.A[0]) and np.array_equal(pm.A[-1], prob.A[-1])):
+        raise RuntimeError("multi-right-hand-side leg: regenerated A differs from the solver's")
+    B = torch.from_numpy(np.ascontiguousarray(pm.b.T)).to(dev)
+    Xr = torch.from_numpy(np.ascontiguousarray(pm.x_ref.T)).to(dev)
+    del pm
+    group = sol.multi_group(storage)
+    sol.solve_multi(B[:group], tol=TOL, seed=600, storage=storage, X_ref=Xr[:group])
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    agg = {"iterations": 0, "kernel_ms": 0.0, "launches": 0, "grid_launches": 0}
+    worst = 0.0
+    ev0.record(stream)
+    for s_ in range(args.multi_steps):
+        r = sol.solve_multi(B, tol=TOL, seed=610 + s_, storage=storage, X_ref=Xr)
+        if r["status"] != 0 or float(r["rel"].max()) > TOL:
+            raise RuntimeError(f"multi-right-hand-side solve did not reach {TOL}: {r['stats']}")
+        worst = max(worst, float(r["rel"].max()))
+        for k in agg:
+            agg[k] += r["stats"][k]
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    groups = args.multi_steps * ((nrhs + group - 1) // group)
+    esize = {"fp32": 4, "bf16": 2}[storage]
+    bytes_it = float(TAU * N + TAU * M) * esize
+    kernel_s = agg["kernel_ms"] / 1000.0
+    return {"value": nrhs * args.multi_steps / (ms / 1000.0), "unit": "solves/s", "storage": storage,
+            "rhs_per_step": nrhs, "group": group, "steps": args.multi_steps, "ms_per_step": ms / args.multi_steps,
+            "iterations_per_group": agg["iterations"] / groups, "kernel_ms_per_step": agg["kernel_ms"] / args.multi_steps,
+            "us_per_iteration": 1000.0 * agg["kernel_ms"] / max(agg["iterations"], 1),
+            "rhs_iterations_per_s": group * agg["iterations"] / kernel_s,
+            "rel_err_max": worst, "gpu_launches": agg["launches"],
+            "kernel_hbm_gbs": bytes_it * agg["iterations"] / kernel_s / 1e9,
+            "kernel_hbm_frac": bytes_it * agg["iterations"] / kernel_s / 1e9 / hbm_peak,
+            "note": "every member of a group draws the same blocks (one TMA read of a block serves the group); "
+                    "each right-hand side verified <= 1e-8 against its own A^+ b; FP64 refinement sweeps included"}
+
+
+def make_problem(seed: int, use_gpu: bool, nrhs: int = 0):
     from workloads import product_problem
     mm = None
     if use_gpu:
@@ -184,7 +234,7 @@ def make_problem(seed: int, use_gpu: bool):
             r = (ta @ tb).cpu().numpy()
             del ta, tb
             return r
-    return product_problem(M, N, RANK, seed=seed, noise=0.01, matmul=mm)
+    return product_problem(M, N, RANK, seed=seed, noise=0.01, matmul=mm, nrhs=nrhs)
 
 
 class ClockSampler:
@@ -1077,6 +1127,21 @@ def main():
     xr = torch.from_numpy(prob.x_ref).to(dev)
     S = args.storage
 
+    if args.profile_multi > 0:
+        # one group of right-hand sides of the same A; ncu captures the second pass
+        K = args.profile_multi
+        g = sol.multi_group(S)
+        pm = make_problem(rank, True, nrhs=g)
+        B = torch.from_numpy(np.ascontiguousarray(pm.b.T)).to(dev)
+        del pm
+        for _ in range(2):
+            r = sol.solve_multi(B, tol=0.0, max_iter=K, seed=7, storage=S, max_outer=1, inner_iters=K)
+        torch.cuda.synchronize()
+        st = r["stats"]
+        print(json.dumps({"profile_multi": K, "storage": S, "group": g, "iterations": st["iterations"],
+                          "kernel_ms": st["kernel_ms"], "us_per_iteration": 1000.0 * st["kernel_ms"] / K}))
+        return 0
+
     if args.profile_pass > 0:
         # the first pass also runs the CTA-count autotune; ncu captures the second pass
         K = args.profile_pass
@@ -1188,6 +1253,11 @@ def main():
                  "rule": "max(||b - z - A x|| / ||b||, ||A^T z|| / (||A||_F ||b||)) <= 1e-8 after each "
                          "refinement pass (no x_ref); rel_err_max is the error against A^+ b measured afterwards"}
 
+    # ---------------- several right-hand sides at once (shared block sequence) ----------------
+    multi = None
+    if args.multi_rhs > 0:
+        multi = measure_multi(args, sol, prob, dev, rank, S, stream, hbm_peak)
+
     # ---------------- the combined form (mixed + warm start + batched) ----------------
     combined = None
     if not args.no_combined:
@@ -1244,6 +1314,7 @@ def main():
             "speedup_vs_plain_fp64": None if plain is None else value / plain["value"],
             "residual_rule": resid,
             "combined": combined,
+            "multi_rhs": multi,
             "device_peaks": dev_peaks,
         }
         print(json.dumps(line))

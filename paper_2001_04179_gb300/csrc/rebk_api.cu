@@ -448,21 +448,54 @@ rebk_status multi_setup(rebk_handle h, Mode mode, int want, MultiArgs *Mout, int
         return fail(REBK_EUNSUPPORTED, "multi-right-hand-side form: a tile is wider or taller than 256 "
                                        "(tau or the owned column slice)");
     a.use_tma = 1;
-    if (tma_encode(mode, a) != cudaSuccess)
-        return fail(REBK_EUNSUPPORTED, "multi-right-hand-side form: no tensor map for the stored copy");
+    const GridArgs plain = a;
+    // Tensor-core geometry (FP32 storage, groups of 8): column-tile rows 4 floats off a
+    // multiple of 32 bytes and row-tile rows 8 floats off a multiple of 64 bytes, so
+    // the fragment loads of the products hit distinct banks; each tile buffer keeps
+    // slack for the reads past the box that the 16 x 8 fragments make.
+    auto mma_geometry = [&](GridArgs &g) {
+        if (g.bw_c % 8 == 0) g.bw_c += 4;
+        if (g.bw_r % 8 != 0) g.bw_r += 8 - g.bw_r % 8;
+        if (g.bw_r % 16 == 0) g.bw_r += 8;
+        if (g.bw_c > 256 || g.bw_r > 256) return false;
+        const int64_t es = 4;
+        g.tile_c_bytes_tx = (int64_t)g.nbox_c * g.bh_c * g.bw_c * es;
+        g.tile_r_bytes_tx = (int64_t)g.tau_r * g.bw_r * es;
+        const int64_t rows_c = std::max<int64_t>((int64_t)g.nbox_c * g.bh_c, (g.nrow_cap + 15) / 16 * 16);
+        const int64_t rows_r = (g.tau_r + 15) / 16 * 16;
+        g.tile_c_bytes = (rows_c * g.bw_c * es + 256 + 127) / 128 * 128;
+        g.tile_r_bytes = (rows_r * g.bw_r * es + 256 + 127) / 128 * 128;
+        return true;
+    };
+    struct Cand { int nr; bool mma; };
+    const Cand cands[] = {{8, true}, {8, false}, {4, false}};
     int nr = 0;
-    for (int cand : {8, 4}) {
-        if (want != 0 && cand != want) continue;
+    for (const Cand &c : cands) {
+        if (want != 0 && c.nr != want) continue;
+        if (c.mma && bf16) continue;
+        a = plain;
+        M.mma = 0;
+        if (c.mma) {
+            if (!mma_geometry(a)) continue;
+            M.mma = 1;
+        }
+        if (tma_encode(mode, a) != cudaSuccess) continue;
         M.scr_floats = 0;
-        const size_t base = multi_smem_bytes(M, cand);
+        const size_t base = multi_smem_bytes(M, c.nr);
         if (base + 128 > kSmemLimit) continue;
-        M.scr_floats = (int)std::min<size_t>((kSmemLimit - base - 128) / 4 / 32 * 32, (size_t)512 * cand);
-        const size_t smem = multi_smem_bytes(M, cand);
-        if (smem > kSmemLimit || multi_max_ctas(bf16, cand, smem) < G) continue;
-        nr = cand;
+        M.scr_floats = (int)std::min<size_t>((kSmemLimit - base - 128) / 4 / 32 * 32, (size_t)512 * c.nr);
+        // the two products of a stage accumulate side by side in the scratch
+        auto r16 = [](int v) { return (v + 15) / 16 * 16; };
+        if (c.mma && M.scr_floats < 8 * std::max(r16(a.ncol_cap) + r16(a.nrow_cap), r16(a.tau_r) + r16(a.tau_c)))
+            continue;
+        const size_t smem = multi_smem_bytes(M, c.nr);
+        if (smem > kSmemLimit || multi_max_ctas(bf16, c.nr, c.mma, smem) < G) continue;
+        nr = c.nr;
         break;
     }
-    if (nr == 0) return fail(REBK_EUNSUPPORTED, "multi-right-hand-side form: the tiles do not fit in shared memory");
+    if (nr == 0)
+        return fail(REBK_EUNSUPPORTED, "multi-right-hand-side form: no tensor map, or the tiles do not fit in "
+                                       "shared memory");
     *Mout = M;
     *Gout = G;
     *nrout = nr;

@@ -255,9 +255,11 @@ struct MultiArgs {
     float *dZ, *dX, *S, *V;  // corrections and duals: [m][NR], [n][NR], [n][NR], [m][NR]
     const float *F, *G;      // f = b - z - A x ([m][NR]) and g = A^T z ([n][NR]), rounded to FP32
     int scr_floats;          // reduction scratch in shared memory (floats)
+    int mma;                 // products on tensor cores (FP32 storage, NR = 8): tile strides and
+                             // slack set for them (multi_setup)
 };
 
-constexpr int kMultiReplicas = 4;
+constexpr int kMultiReplicas = 2;
 
 struct MultiSmem {
     size_t tc0, tc1, tr0, tr1, zeta, xi, w, r, scr, total;
@@ -265,8 +267,10 @@ struct MultiSmem {
 
 // Shared-memory layout of the multi kernel (byte offsets): 512-byte header
 // (mbarriers, flags, step coefficients), two column tiles, two row tiles, dZ of
-// the owned rows ([nrow_cap][NR]), dX of the owned columns (q-major: [NR][xs]),
-// w (q-major: [NR][ws]), r ([tau_r][NR]) and the scratch.
+// the owned rows ([nrow_cap rounded up to 8][NR]), dX of the owned columns
+// (q-major: [NR][xs]), w (q-major: [NR][ws]), r ([tau_r rounded up to 8][NR]) and
+// the scratch.  Tile sizes include the slack the tensor-core products read past
+// the copied box (zero-filled at launch).
 __host__ __device__ inline int multi_xs(int ncol_cap) { return (ncol_cap + 31) / 32 * 32 + 4; }
 __host__ __device__ inline int multi_ws(int tau_c) { return (tau_c + 31) / 32 * 32 + 4; }
 __host__ __device__ inline MultiSmem multi_smem_layout(int nrow_cap, int ncol_cap, int tau_r, int tau_c, int nr,
@@ -278,17 +282,17 @@ __host__ __device__ inline MultiSmem multi_smem_layout(int nrow_cap, int ncol_ca
     L.tc1 = o; o = al128(o + (size_t)tile_c_bytes);
     L.tr0 = o; o = al128(o + (size_t)tile_r_bytes);
     L.tr1 = o; o = al128(o + (size_t)tile_r_bytes);
-    L.zeta = o; o = al128(o + (size_t)nrow_cap * nr * 4);
+    L.zeta = o; o = al128(o + (size_t)((nrow_cap + 7) / 8 * 8) * nr * 4);
     L.xi = o;   o = al128(o + (size_t)nr * multi_xs(ncol_cap) * 4);
     L.w = o;    o = al128(o + (size_t)nr * multi_ws(tau_c) * 4);
-    L.r = o;    o = al128(o + (size_t)tau_r * nr * 4);
+    L.r = o;    o = al128(o + (size_t)((tau_r + 7) / 8 * 8) * nr * 4);
     L.scr = o;  o = al128(o + (size_t)scr_floats * 4);
     L.total = o;
     return L;
 }
 size_t multi_smem_bytes(const MultiArgs &M, int nr);
 cudaError_t launch_multi(const MultiArgs &M, bool bf16, int nr, int G, cudaStream_t st);
-int multi_max_ctas(bool bf16, int nr, size_t smem);
+int multi_max_ctas(bool bf16, int nr, bool mma, size_t smem);
 // FP64 products with nr interleaved vectors: Y = A P (P: [n][nr], Y: [m][nr]) and
 // Y = A^T Q (Q: [m][nr], Y: [n][nr]); P / Q FP64 or FP32 (p_f32); Y is overwritten.
 cudaError_t multi_ap(const double *A, int64_t lda, int64_t m, int64_t n, int nr, const void *P, bool p_f32,

@@ -13,19 +13,32 @@
 //
 // GB300 mapping.  One cooperative launch, one CTA of 512 threads per SM.  CTA c
 // owns the rows R_c (its dZ and V rows) and the 8-aligned columns C_c (its dX and
-// S columns).  One device-wide barrier per iteration; round t
-//   1. finishes iteration t-1's row step on the owned columns (it needs Rr^{t-1}),
-//   2. does iteration t's column step on the owned rows (it needs W^t),
-//   3. adds its partials of Rr^t (A_{I_t, C_c} dX, plus dZ_I - F_I on owned rows)
+// S columns).  One device-wide barrier per iteration; round t, in three stages
+// that each end in a CTA barrier,
+//   A. reads Rr^{t-1} and W^t (one pass over the accumulators),
+//   B. finishes iteration t-1's row step on the owned columns and does iteration
+//      t's column step on the owned rows (independent of each other),
+//   C. adds its partials of Rr^t (A_{I_t, C_c} dX, plus dZ_I - F_I on owned rows)
 //      and of W^{t+1} (A_{R_c, J_{t+1}}^T dZ) into the next of three rotating
-//      accumulator sets (4 replicas, red.global.add.v4.f32 over 4 right-hand
+//      accumulator sets (2 replicas, red.global.add.v4.f32 over 4 right-hand
 //      sides at a time), clears its share of the set after that, and arrives.
 // Tiles of the sampled blocks (FP32 or BF16 storage) reach shared memory by 2-D
 // TMA copies, two buffers per kind: a column tile serves the partial of W in one
 // round and the column step of the next, a row tile the partial of Rr in one
 // round and the row step of the next, so each tile is read from HBM once.
 //
-// Products along tile rows (Rr partials, the column step) run a warp per row with
+// With FP32 storage and groups of 8 the four products run on tensor cores:
+// mma.sync m16n8k8 with three TF32 products per step (a_hi b_hi + a_hi b_lo +
+// a_lo b_hi, hi = the top 19 bits, lo = the FP32 remainder), which keeps FP32
+// accuracy to about 2^-20 relative; the (16-row tile, K step) pairs of a stage's
+// two products are split evenly over the 16 warps, whose tile sums meet in two
+// shared buffers.  Each product
+// is 128 x 136 x 8 or smaller, too small for the asynchronous tcgen05 issue /
+// commit / TMEM read-back to pay inside a step that a device-wide reduction
+// bounds; the warp-level form cuts the instructions of a step about sixfold
+// against the FP32 FMA form below.
+//
+// Otherwise products along tile rows (Rr partials, the column step) run a warp per row with
 // the vector of each half-warp's NR/2 right-hand sides held in registers and a
 // half-warp butterfly that ends with each sum on one lane; products along tile
 // columns (the row step, W partials) run a thread per (column, 4 right-hand
@@ -196,7 +209,89 @@ __device__ __forceinline__ void col_products(const TA *T, int ld, int rows, int 
     }
 }
 
-template <typename TA, int NR>
+__device__ __forceinline__ uint32_t tf32_hi(float a) { return __float_as_uint(a) & 0xffffe000u; }
+
+__device__ __forceinline__ void mma_tf32(float (&d)[4], const uint32_t (&a)[4], uint32_t b0, uint32_t b1) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0, %1, %2, %3}, {%4, %5, %6, %7}, {%8, %9}, "
+        "{%0, %1, %2, %3};"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One product of mma_pair: Y (rows up to M rounded up to 16, 8 columns,
+// row-major; zero on entry) += A B for the M x K matrix A(m, k) = A[m am + k ak]
+// and the K x 8 matrix B(k, q) = B[k bk + q bq] in shared memory.  Reads A for
+// rows up to M rounded up to 16 and columns up to K rounded up to 8, B for rows
+// up to K rounded up to 8: B must be zero there, A finite and in bounds.
+struct MmaProd {
+    const float *A;
+    int am, ak, M;
+    const float *B;
+    int bk, bq, K;
+    float *Y;
+};
+
+// (16-row tile, K step) pairs lo .. hi - 1 (tile-major) of one product on one warp;
+// each tile's sum goes to Y by shared-memory atomics when the warp leaves it.
+__device__ __forceinline__ void mma_range(const MmaProd &p, int lo, int hi, int lane) {
+    const int KS = (p.K + 7) >> 3;
+    const int g = lane >> 2, t = lane & 3;
+    const int am = p.am, ak = p.ak, bk = p.bk;
+    int mt = lo / KS, ks = lo - mt * KS;
+    const float *pb = p.B + t * bk + g * p.bq;
+    // three accumulators (lo*hi, hi*lo, hi*hi): independent chains of tensor-core operations
+    float d[4] = {0.f, 0.f, 0.f, 0.f}, e1[4] = {0.f, 0.f, 0.f, 0.f}, e2[4] = {0.f, 0.f, 0.f, 0.f};
+    auto flush = [&]() {
+        float *y = p.Y + (mt * 16 + g) * 8 + 2 * t;
+        atomicAdd(y, d[0] + (e1[0] + e2[0]));
+        atomicAdd(y + 1, d[1] + (e1[1] + e2[1]));
+        atomicAdd(y + 64, d[2] + (e1[2] + e2[2]));
+        atomicAdd(y + 65, d[3] + (e1[3] + e2[3]));
+#pragma unroll
+        for (int i = 0; i < 4; ++i) d[i] = e1[i] = e2[i] = 0.f;
+    };
+    const float *pa = p.A + (mt * 16 + g) * am + t * ak;
+#pragma unroll 2
+    for (int idx = lo; idx < hi; ++idx) {
+        if (ks == KS) {
+            flush();
+            ++mt;
+            ks = 0;
+            pa += 16 * am;
+        }
+        const int ko = ks * 8;
+        const float af[4] = {pa[ko * ak], pa[ko * ak + 8 * am], pa[(ko + 4) * ak], pa[(ko + 4) * ak + 8 * am]};
+        const float bf0 = pb[ko * bk], bf1 = pb[(ko + 4) * bk];
+        uint32_t ah[4], al[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            ah[i] = tf32_hi(af[i]);
+            al[i] = __float_as_uint(af[i] - __uint_as_float(ah[i]));
+        }
+        const uint32_t bh0 = tf32_hi(bf0), bh1 = tf32_hi(bf1);
+        const uint32_t bl0 = __float_as_uint(bf0 - __uint_as_float(bh0));
+        const uint32_t bl1 = __float_as_uint(bf1 - __uint_as_float(bh1));
+        mma_tf32(e1, al, bh0, bh1);
+        mma_tf32(e2, ah, bl0, bl1);
+        mma_tf32(d, ah, bh0, bh1);
+        ++ks;
+    }
+    flush();
+}
+
+// Two independent products on tensor cores in one pass: the (tile, K step) pairs
+// of both (the first product's first) are split into 16 equal shares, one per warp.
+__device__ __forceinline__ void mma_pair(const MmaProd &p1, const MmaProd &p2, int warp, int lane) {
+    const int T1 = (p1.M > 0 && p1.K > 0) ? ((p1.M + 15) >> 4) * ((p1.K + 7) >> 3) : 0;
+    const int T2 = (p2.M > 0 && p2.K > 0) ? ((p2.M + 15) >> 4) * ((p2.K + 7) >> 3) : 0;
+    const int T = T1 + T2;
+    const int lo = warp * T / kMW, hi = (warp + 1) * T / kMW;
+    if (lo < T1 && lo < hi) mma_range(p1, lo, hi < T1 ? hi : T1, lane);
+    if (hi > T1 && lo < hi) mma_range(p2, (lo > T1 ? lo : T1) - T1, hi - T1, lane);
+}
+
+template <typename TA, int NR, bool MMA>
 __global__ void __launch_bounds__(kMT, 1) rebk_multi_kernel(const __grid_constant__ MultiArgs M) {
     extern __shared__ __align__(128) unsigned char msm[];
     const GridArgs &a = M.geo;
@@ -214,9 +309,15 @@ __global__ void __launch_bounds__(kMT, 1) rebk_multi_kernel(const __grid_constan
                                           a.tile_r_bytes, M.scr_floats);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(msm);    // [0, 1] column tiles, [2, 3] row tiles
     int *flags = reinterpret_cast<int *>(msm + 64);        // [0] non-finite, [1] a copy wait gave up, [2] barrier
-    float *coefs = reinterpret_cast<float *>(msm + 96);    // [0] cI, [1] cJ
-    TA *tcb[2] = {reinterpret_cast<TA *>(msm + L.tc0), reinterpret_cast<TA *>(msm + L.tc1)};
-    TA *trb[2] = {reinterpret_cast<TA *>(msm + L.tr0), reinterpret_cast<TA *>(msm + L.tr1)};
+    // ring of upcoming draws and step coefficients, slot u & 7 for iteration u:
+    // J_u, I_u, alpha / ||A_{:,J_u}||_F^2, alpha / ||A_{I_u,:}||_F^2 (thread 0 fills it
+    // three iterations ahead, so no dependent global load sits on a round's path)
+    int *ring_j = reinterpret_cast<int *>(msm + 128), *ring_i = ring_j + 8;
+    float *ring_cj = reinterpret_cast<float *>(msm + 192), *ring_ci = ring_cj + 8;
+    TA *const tc0 = reinterpret_cast<TA *>(msm + L.tc0), *const tc1 = reinterpret_cast<TA *>(msm + L.tc1);
+    TA *const tr0 = reinterpret_cast<TA *>(msm + L.tr0), *const tr1 = reinterpret_cast<TA *>(msm + L.tr1);
+    auto tcb = [&](int64_t b) { return (b & 1) ? tc1 : tc0; };
+    auto trb = [&](int64_t b) { return (b & 1) ? tr1 : tr0; };
     float *zeta = reinterpret_cast<float *>(msm + L.zeta);  // [nrow][NR]: dZ of the owned rows
     float *xi = reinterpret_cast<float *>(msm + L.xi);      // [NR][xs]: dX of the owned columns
     float *sw = reinterpret_cast<float *>(msm + L.w);       // [NR][ws]: W of the current column block
@@ -248,82 +349,165 @@ __global__ void __launch_bounds__(kMT, 1) rebk_multi_kernel(const __grid_constan
             *ib = *ia + tau_r < m ? *ia + tau_r : m;
         }
     };
-    auto jdraw = [&](int64_t t) { return __ldg(a.idx + 2 * (t - 1)); };
-    auto idraw = [&](int64_t t) { return __ldg(a.idx + 2 * (t - 1) + 1); };
+    auto jdraw = [&](int64_t t) { return ring_j[t & 7]; };
+    auto idraw = [&](int64_t t) { return ring_i[t & 7]; };
 
+    {  // zero everything after the header: tile slack, the padding of the vectors
+        uint4 *p = reinterpret_cast<uint4 *>(msm + 512);
+        const int words = (int)((L.total - 512) / 16);
+        for (int e = tid; e < words; e += kMT) p[e] = make_uint4(0u, 0u, 0u, 0u);
+    }
+    __syncthreads();
     for (int e = tid; e < nrow * NR; e += kMT) zeta[e] = M.dZ[r0 * NR + e];
     for (int e = tid; e < ncol * NR; e += kMT) xi[(e % NR) * xs + e / NR] = M.dX[c0 * NR + e];
+    // thread 0's draw pipeline: indices of iteration t + 4 load at the start of round
+    // t, coefficients of iteration t + 3 at the start of round t, and the ring slot of
+    // iteration t + 3 is written at the end of round t
+    int nj = 0, ni = 0, wj = 0, wi = 0;
+    float wcj = 0.f, wci = 0.f;
     if (tid == 0) {
         for (int i = 0; i < 4; ++i) m_mbar_init(&mbar[i], 1);
         flags[0] = 0;
         flags[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        for (int64_t u = 1; u <= 3 && u <= K; ++u) {
+            const int j = __ldg(a.idx + 2 * (u - 1)), i = __ldg(a.idx + 2 * (u - 1) + 1);
+            ring_j[u & 7] = j;
+            ring_i[u & 7] = i;
+            ring_cj[u & 7] = __ldg(coef_c + j);
+            ring_ci[u & 7] = __ldg(coef_r + i);
+        }
+        if (K >= 4) {
+            nj = __ldg(a.idx + 6);
+            ni = __ldg(a.idx + 7);
+        }
     }
     __syncthreads();
+    // G_J of the next column block, read a round ahead (entry tid + k * kMT)
+    float gpre[4] = {0.f, 0.f, 0.f, 0.f};
+    auto prefetch_g = [&](int64_t u) {
+        if (u > K) return;
+        int64_t ja, jb;
+        col_range(jdraw(u), &ja, &jb);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int e = tid + k * kMT;
+            if (e < (int)(jb - ja) * NR) gpre[k] = __ldg(M.G + ja * NR + e);
+        }
+    };
+    // duals of the owned rows of I_u (entry tid + k * kMT of the intersection), read
+    // a round ahead of their update; the owner is the only writer
+    float vpre[2] = {0.f, 0.f}, spre[4] = {0.f, 0.f, 0.f, 0.f};
+    auto prefetch_v = [&](int64_t u) {
+        if (u > K) return;
+        int64_t ia, ib;
+        row_range(idraw(u), &ia, &ib);
+        const int64_t la = ia > r0 ? ia : r0, lb = ib < r1 ? ib : r1;
+#pragma unroll
+        for (int k = 0; k < 2; ++k) {
+            const int64_t e = tid + k * kMT;
+            if (e < (lb - la) * NR) vpre[k] = M.V[la * NR + e];
+        }
+    };
+    auto prefetch_s = [&](int64_t u) {
+        if (u > K) return;
+        int64_t ja, jb;
+        col_range(jdraw(u), &ja, &jb);
+        const int64_t la = ja > c0 ? ja : c0, lb = jb < c1 ? jb : c1;
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t e = tid + k * kMT;
+            if (e < (lb - la) * NR) spre[k] = M.S[la * NR + e];
+        }
+    };
 
     // Tiles: the column tile of J_t in column buffer t & 1, the row tile of I_t in
     // row buffer t & 1.  Every thread tracks the phases; thread 0 issues.
-    uint32_t cpar[2] = {0u, 0u}, rpar[2] = {0u, 0u};
-    bool cpend[2] = {false, false}, rpend[2] = {false, false};
-    int64_t cx0[2] = {0, 0};
+    // per buffer b: phase parity (bit b) and copy in flight (bit 2 + b), in registers
+    uint32_t cst = 0u, rst = 0u;
+    int64_t cxa = 0, cxb = 0;  // first column of the copied box, column buffers 0 and 1
+    auto cx0 = [&](int64_t b) { return (b & 1) ? cxb : cxa; };
     auto issue_c = [&](int64_t t) {
         if (t < 1 || t > K || nrow == 0) return;
         const int b = (int)(t & 1);
         int64_t ja, jb;
         col_range(jdraw(t), &ja, &jb);
         const int x0 = (int)(ja & ~(int64_t)(a.tma_vx - 1));
-        cx0[b] = x0;
-        cpend[b] = true;
+        if (b) cxb = x0;
+        else cxa = x0;
+        cst |= 4u << b;
         if (tid == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             m_expect_tx(&mbar[b], (uint32_t)a.tile_c_bytes_tx);
             for (int bx = 0; bx < a.nbox_c; ++bx)
-                m_tma_2d(tcb[b] + (size_t)bx * a.bh_c * a.bw_c, &a.tmap_c, x0, (int)(r0 + (int64_t)bx * a.bh_c),
+                m_tma_2d(tcb(b) + (size_t)bx * a.bh_c * a.bw_c, &a.tmap_c, x0, (int)(r0 + (int64_t)bx * a.bh_c),
                          &mbar[b]);
         }
     };
     auto issue_r = [&](int64_t t) {
         if (t < 1 || t > K || ncol == 0) return;
         const int b = (int)(t & 1);
-        rpend[b] = true;
+        rst |= 4u << b;
         if (tid == 0) {
             int64_t ia, ib;
             row_range(idraw(t), &ia, &ib);
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             m_expect_tx(&mbar[2 + b], (uint32_t)a.tile_r_bytes_tx);
-            m_tma_2d(trb[b], &a.tmap_r, (int)c0, (int)ia, &mbar[2 + b]);
+            m_tma_2d(trb(b), &a.tmap_r, (int)c0, (int)ia, &mbar[2 + b]);
         }
     };
     auto wait_c = [&](int64_t t) {
         const int b = (int)(t & 1);
-        if (!cpend[b]) return;
-        if (m_wait(&mbar[b], cpar[b], a.timeout_ns)) {
-            cpar[b] ^= 1u;
-            cpend[b] = false;
+        if (!(cst & (4u << b))) return;
+        if (m_wait(&mbar[b], (cst >> b) & 1u, a.timeout_ns)) {
+            cst ^= 1u << b;
+            cst &= ~(4u << b);
         } else {
             flags[1] = 1;
         }
     };
     auto wait_r = [&](int64_t t) {
         const int b = (int)(t & 1);
-        if (!rpend[b]) return;
-        if (m_wait(&mbar[2 + b], rpar[b], a.timeout_ns)) {
-            rpar[b] ^= 1u;
-            rpend[b] = false;
+        if (!(rst & (4u << b))) return;
+        if (m_wait(&mbar[2 + b], (rst >> b) & 1u, a.timeout_ns)) {
+            rst ^= 1u << b;
+            rst &= ~(4u << b);
         } else {
             flags[1] = 1;
+        }
+    };
+    // partial of W^t over the owned rows (column tile of J_t) into accumulator set dst
+    // MMA scratch: the two products of a stage accumulate in two zeroed buffers
+    float *Y1 = scr, *Y2x = scr + ((a.ncol_cap + 15) & ~15) * 8, *Y2w = scr + ((a.tau_r + 15) & ~15) * 8;
+    // W partials (rows j < wc of Y) into accumulator set dst; Y zeroed for reuse
+    auto deliver_w = [&](const float *Yc, int wc, float *dst) {
+        float *base = dst + (int64_t)rep * aw + tau_r * NR;
+        for (int e = tid; e < ((wc + 15) & ~15) * 2; e += kMT) {
+            float4 *y = reinterpret_cast<float4 *>(const_cast<float *>(Yc)) + e;
+            const float4 v = *y;
+            *y = make_float4(0.f, 0.f, 0.f, 0.f);
+            if ((e >> 1) < wc) m_red4(base + (e >> 1) * NR + 4 * (e & 1), v.x, v.y, v.z, v.w);
         }
     };
     // partial of W^t over the owned rows (column tile of J_t) into accumulator set dst
     auto partial_w = [&](int64_t t, float *dst) {
         int64_t ja, jb;
         col_range(jdraw(t), &ja, &jb);
-        const TA *T = tcb[t & 1] + (ja - cx0[t & 1]);
-        float *base = dst + (int64_t)rep * aw + tau_r * NR;
-        col_products<TA, NR>(T, a.bw_c, nrow, (int)(jb - ja), zeta, scr, M.scr_floats, tid,
-                             [&](int j, int g, const float(&s)[4]) {
-                                 m_red4(base + j * NR + 4 * g, s[0], s[1], s[2], s[3]);
-                             });
+        const TA *T = tcb(t) + (ja - cx0(t));
+        const int wc = (int)(jb - ja);
+        if constexpr (MMA) {
+            const MmaProd none{nullptr, 0, 0, 0, nullptr, 0, 0, 0, nullptr};
+            const MmaProd pw{reinterpret_cast<const float *>(T), 1, a.bw_c, wc, zeta, NR, 1, nrow, Y2w};
+            mma_pair(none, pw, warp, lane);
+            __syncthreads();
+            deliver_w(Y2w, wc, dst);
+        } else {
+            float *base = dst + (int64_t)rep * aw + tau_r * NR;
+            col_products<TA, NR>(T, a.bw_c, nrow, wc, zeta, scr, M.scr_floats, tid,
+                                 [&](int j, int g, const float(&s)[4]) {
+                                     m_red4(base + j * NR + 4 * g, s[0], s[1], s[2], s[3]);
+                                 });
+        }
     };
 
     int64_t done = K;
@@ -341,6 +525,9 @@ __global__ void __launch_bounds__(kMT, 1) rebk_multi_kernel(const __grid_constan
         } else {
             partial_w(1, acc);
         }
+        prefetch_g(1);
+        prefetch_s(1);
+        prefetch_v(1);
     }
     grid_arrive(a.bar);
     for (int64_t t = 1; alive && t <= K + 1; ++t) {
@@ -349,127 +536,190 @@ __global__ void __launch_bounds__(kMT, 1) rebk_multi_kernel(const __grid_constan
             break;
         }
         const float *accS = acc + ((t - 1) % 3) * accset;
-        // ---- 1. Rr^{t-1} and the row step of iteration t-1 on the owned columns ----
-        if (t >= 2) {
-            int64_t ia, ib;
-            row_range(idraw(t - 1), &ia, &ib);
-            const int hr = (int)(ib - ia);
-            for (int e = tid; e < hr * NR; e += kMT) {
-                float v = 0.f;
+        if (tid == 0 && t + 3 <= K) {
+            wj = nj;
+            wi = ni;
+            wcj = __ldg(coef_c + wj);
+            wci = __ldg(coef_r + wi);
+            if (t + 4 <= K) {
+                nj = __ldg(a.idx + 2 * (t + 3));
+                ni = __ldg(a.idx + 2 * (t + 3) + 1);
+            }
+        }
+        // ---- A. Rr^{t-1} and W^t from the accumulators ----
+        const bool rowstep = t >= 2, colstep = t <= K;
+        int64_t ia = 0, ib = 0, ja = 0, jb = 0;
+        if (rowstep) row_range(idraw(t - 1), &ia, &ib);
+        if (colstep) col_range(jdraw(t), &ja, &jb);
+        const int hr = (int)(ib - ia), wc = (int)(jb - ja);
+        for (int e = tid; e < ((hr + 7) & ~7) * NR; e += kMT) {
+            float v = 0.f;
+            if (e < hr * NR) {
 #pragma unroll
                 for (int q = 0; q < kMultiReplicas; ++q) v += __ldcg(accS + (int64_t)q * aw + e);
-                sr[e] = v;
-                if (!isfinite(v)) flags[0] = 1;
             }
-            if (tid == 0) coefs[0] = coef_r[idraw(t - 1)];
-            __syncthreads();
-            if (flags[0]) {
-                if (tid == 0) atomicExch(a.status, 5);
-                done = t - 2;
-                break;
-            }
-            const float cI = coefs[0];
-            col_products<TA, NR>(trb[(t - 1) & 1], a.bw_r, hr, ncol, sr, scr, M.scr_floats, tid,
-                                 [&](int c, int g, const float(&s)[4]) {
-#pragma unroll
-                                     for (int i = 0; i < 4; ++i) xi[(4 * g + i) * xs + c] -= cI * s[i];
-                                 });
-            {  // dual V on the owned rows of I_{t-1}
-                const int64_t la = ia > r0 ? ia : r0, lb = ib < r1 ? ib : r1;
-                for (int64_t e = tid; e < (lb - la) * NR; e += kMT) M.V[la * NR + e] -= cI * sr[(la - ia) * NR + e];
-            }
-            __syncthreads();
-            issue_r(t + 1);  // the buffer of I_{t-1} takes I_{t+1}
-        } else {
-            issue_r(2);
-        }
-        if (t == K + 1) break;
-        // ---- 2. W^t and the column step of iteration t on the owned rows ----
-        int64_t ja, jb;
-        col_range(jdraw(t), &ja, &jb);
-        const int wc = (int)(jb - ja);
-        for (int e = tid; e < wc * NR; e += kMT) {
-            float v = M.G[ja * NR + e];
-#pragma unroll
-            for (int q = 0; q < kMultiReplicas; ++q) v += __ldcg(accS + (int64_t)q * aw + tau_r * NR + e);
-            sw[(e % NR) * ws + e / NR] = v;
+            sr[e] = v;
             if (!isfinite(v)) flags[0] = 1;
         }
-        if (tid == 0) coefs[1] = coef_c[jdraw(t)];
+        auto fill_w = [&](int e, float g) {
+            float v = 0.f;
+            if (e < wc * NR) {
+                v = g;
+#pragma unroll
+                for (int q = 0; q < kMultiReplicas; ++q) v += __ldcg(accS + (int64_t)q * aw + tau_r * NR + e);
+            }
+            sw[(e % NR) * ws + e / NR] = v;
+            if (!isfinite(v)) flags[0] = 1;
+        };
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (tid + k * kMT < ((wc + 7) & ~7) * NR) fill_w(tid + k * kMT, gpre[k]);
+        for (int e = tid + 4 * kMT; e < ((wc + 7) & ~7) * NR; e += kMT)
+            fill_w(e, e < wc * NR ? __ldg(M.G + ja * NR + e) : 0.f);
         __syncthreads();
         if (flags[0]) {
             if (tid == 0) atomicExch(a.status, 5);
-            done = t - 1;
+            done = t >= 2 ? t - 2 : 0;
             break;
         }
-        {
-            const float cJ = coefs[1];
-            constexpr int SP = 16 / (NR / 2);
-            row_products<TA, NR, kCMw>(tcb[t & 1] + (ja - cx0[t & 1]), a.bw_c, nrow, wc, sw, ws, warp, lane,
-                                       [&](int rl, float v, bool) {
-                                           if ((lane & (SP - 1)) == 0)
-                                               zeta[rl * NR + (NR / 2) * (lane >> 4) + (lane & 15) / SP] -= cJ * v;
-                                       });
-            // dual S on the owned columns of J_t
+        const float cI = rowstep ? ring_ci[(t - 1) & 7] : 0.f, cJ = colstep ? ring_cj[t & 7] : 0.f;
+        // ---- B. row step of iteration t-1 (owned columns), column step of iteration t (owned rows) ----
+        if constexpr (MMA) {
+            const MmaProd px{reinterpret_cast<const float *>(trb(t - 1)), 1, a.bw_r, rowstep ? ncol : 0, sr, NR, 1,
+                             hr, Y1};
+            const MmaProd pz{reinterpret_cast<const float *>(tcb(t) + (ja - cx0(t))), a.bw_c, 1, colstep ? nrow : 0,
+                             sw, 1, ws, wc, Y2x};
+            mma_pair(px, pz, warp, lane);
+            __syncthreads();
+            if (rowstep) {
+                for (int e = tid; e < ((ncol + 15) & ~15) * NR; e += kMT) {
+                    const float v = Y1[e];
+                    Y1[e] = 0.f;
+                    if ((e >> 3) < ncol) xi[(e & 7) * xs + (e >> 3)] -= cI * v;
+                }
+            }
+            if (colstep) {
+                for (int e = tid; e < ((nrow + 15) & ~15) * NR; e += kMT) {
+                    const float v = Y2x[e];
+                    Y2x[e] = 0.f;
+                    if (e < nrow * NR) zeta[e] -= cJ * v;
+                }
+            }
+        } else {
+            if (rowstep)
+                col_products<TA, NR>(trb(t - 1), a.bw_r, hr, ncol, sr, scr, M.scr_floats, tid,
+                                     [&](int c, int g, const float(&s)[4]) {
+#pragma unroll
+                                         for (int i = 0; i < 4; ++i) xi[(4 * g + i) * xs + c] -= cI * s[i];
+                                     });
+            if (colstep) {
+                constexpr int SP = 16 / (NR / 2);
+                row_products<TA, NR, kCMw>(tcb(t) + (ja - cx0(t)), a.bw_c, nrow, wc, sw, ws, warp, lane,
+                                           [&](int rl, float v, bool) {
+                                               if ((lane & (SP - 1)) == 0)
+                                                   zeta[rl * NR + (NR / 2) * (lane >> 4) + (lane & 15) / SP] -=
+                                                       cJ * v;
+                                           });
+            }
+        }
+        if (rowstep) {  // dual V on the owned rows of I_{t-1} (entries read a round ahead), then read I_t's
+            const int64_t la = ia > r0 ? ia : r0, lb = ib < r1 ? ib : r1;
+#pragma unroll
+            for (int k = 0; k < 2; ++k) {
+                const int64_t e = tid + k * kMT;
+                if (e < (lb - la) * NR) M.V[la * NR + e] = vpre[k] - cI * sr[(la - ia) * NR + e];
+            }
+            for (int64_t e = tid + 2 * kMT; e < (lb - la) * NR; e += kMT) M.V[la * NR + e] -= cI * sr[(la - ia) * NR + e];
+            prefetch_v(t);
+        }
+        if (colstep) {  // dual S on the owned columns of J_t (entries read a round ahead), then read J_{t+1}'s
             const int64_t la = ja > c0 ? ja : c0, lb = jb < c1 ? jb : c1;
-            for (int64_t e = tid; e < (lb - la) * NR; e += kMT)
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t e = tid + k * kMT;
+                if (e < (lb - la) * NR) M.S[la * NR + e] = spre[k] + cJ * sw[(e % NR) * ws + (la - ja) + e / NR];
+            }
+            for (int64_t e = tid + 4 * kMT; e < (lb - la) * NR; e += kMT)
                 M.S[la * NR + e] += cJ * sw[(e % NR) * ws + (la - ja) + e / NR];
+            prefetch_s(t + 1);
         }
         __syncthreads();
-        issue_c(t + 2);  // the buffer of J_t takes J_{t+2}
-        // ---- 3. partials of round t into set t % 3 ----
+        issue_r(t + 1);  // the buffer of I_{t-1} takes I_{t+1}
+        if (!colstep) break;  // t = K + 1: the last row step is done
+        issue_c(t + 2);       // the buffer of J_t takes J_{t+2}
+        // ---- C. partials of Rr^t and W^{t+1} into set t % 3 ----
         float *accT = acc + (t % 3) * accset;
+        const bool wnext = t + 1 <= K;
         wait_r(t);
+        if (wnext) wait_c(t + 1);
         __syncthreads();
         if (flags[1]) {
             if (tid == 0) atomicExch(a.status, 6);
             done = t - 1;
             break;
         }
-        {  // Rr^t = A_{I_t, C_c} dX^{t-1} (+ dZ^t_I - F_I on the owned rows)
-            int64_t ia, ib;
-            row_range(idraw(t), &ia, &ib);
-            float *base = accT + (int64_t)rep * aw;
+        int64_t ia2, ib2, ja2 = 0, jb2 = 0;
+        row_range(idraw(t), &ia2, &ib2);
+        if (wnext) col_range(jdraw(t + 1), &ja2, &jb2);
+        const int hr2 = (int)(ib2 - ia2), wc2 = (int)(jb2 - ja2);
+        float *rbase = accT + (int64_t)rep * aw;
+        // Rr^t = A_{I_t, C_c} dX^{t-1} (+ dZ^t_I - F_I on the owned rows), 4 right-hand sides per red
+        auto deliver_r = [&](int l, int q0, float (&o)[4], bool first) {
+            const int64_t row = ia2 + l;
+            const bool own = first && row >= r0 && row < r1;
+            if (ncol == 0 && !own) return;
+            if (own) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) o[i] += zeta[(row - r0) * NR + q0 + i] - M.F[row * NR + q0 + i];
+            }
+            m_red4(rbase + l * NR + q0, o[0], o[1], o[2], o[3]);
+        };
+        if constexpr (MMA) {
+            const MmaProd pr{reinterpret_cast<const float *>(trb(t)), a.bw_r, 1, hr2, xi, 1, xs, ncol, Y1};
+            const MmaProd pw{reinterpret_cast<const float *>(tcb(t + 1) + (ja2 - cx0(t + 1))), 1, a.bw_c, wc2, zeta, NR,
+                             1, nrow, Y2w};
+            mma_pair(pr, pw, warp, lane);
+            __syncthreads();
+            for (int e = tid; e < ((hr2 + 15) & ~15) * 2; e += kMT) {
+                float4 *y = reinterpret_cast<float4 *>(Y1) + e;
+                const float4 v = *y;
+                *y = make_float4(0.f, 0.f, 0.f, 0.f);
+                float o[4] = {v.x, v.y, v.z, v.w};
+                if ((e >> 1) < hr2) deliver_r(e >> 1, 4 * (e & 1), o, true);
+            }
+            if (wnext) deliver_w(Y2w, wc2, accT);
+        } else {
             const int src0 = NR == 8 ? (lane & 16) : 0, step = NR == 8 ? 4 : 8;
             const bool writer = NR == 8 ? (lane & 15) == 0 : lane == 0;
             const int q0 = NR == 8 ? 4 * (lane >> 4) : 0;
-            row_products<TA, NR, kCMx>(
-                trb[t & 1], a.bw_r, (int)(ib - ia), ncol, xi, xs, warp, lane, [&](int l, float v, bool first) {
-                    float o[4];
+            row_products<TA, NR, kCMx>(trb(t), a.bw_r, hr2, ncol, xi, xs, warp, lane,
+                                       [&](int l, float v, bool first) {
+                                           float o[4];
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) o[i] = __shfl_sync(0xffffffffu, v, src0 + step * i);
-                    const int64_t row = ia + l;
-                    const bool own = first && row >= r0 && row < r1;
-                    if (writer && (ncol > 0 || own)) {
-                        if (own) {
-#pragma unroll
-                            for (int i = 0; i < 4; ++i) o[i] += zeta[(row - r0) * NR + q0 + i] - M.F[row * NR + q0 + i];
-                        }
-                        m_red4(base + l * NR + q0, o[0], o[1], o[2], o[3]);
-                    }
-                });
-        }
-        if (t + 1 <= K) {  // W^{t+1} over the owned rows
-            wait_c(t + 1);
-            __syncthreads();
-            if (flags[1]) {
-                if (tid == 0) atomicExch(a.status, 6);
-                done = t - 1;
-                break;
-            }
-            partial_w(t + 1, accT);
+                                           for (int i = 0; i < 4; ++i) o[i] = __shfl_sync(0xffffffffu, v, src0 + step * i);
+                                           if (writer) deliver_r(l, q0, o, first);
+                                       });
+            if (wnext) partial_w(t + 1, accT);
         }
         {  // this CTA's share of the set that round t + 1 fills
             float *accN = acc + ((t + 1) % 3) * accset;
             for (int64_t e = clr0 + tid; e < clr1; e += kMT) accN[e] = 0.f;
+        }
+        prefetch_g(t + 1);
+        if (tid == 0 && t + 3 <= K) {
+            const int u = (int)((t + 3) & 7);
+            ring_j[u] = wj;
+            ring_i[u] = wi;
+            ring_cj[u] = wcj;
+            ring_ci[u] = wci;
         }
         grid_arrive(a.bar);
     }
     // no tensor copy may still be writing shared memory when the CTA leaves
     if (tid == 0) {
         for (int b = 0; b < 2; ++b) {
-            if (cpend[b]) m_wait(&mbar[b], cpar[b], a.timeout_ns);
-            if (rpend[b]) m_wait(&mbar[2 + b], rpar[b], a.timeout_ns);
+            if (cst & (4u << b)) m_wait(&mbar[b], (cst >> b) & 1u, a.timeout_ns);
+            if (rst & (4u << b)) m_wait(&mbar[2 + b], (rst >> b) & 1u, a.timeout_ns);
         }
     }
     __syncthreads();
@@ -478,11 +728,14 @@ __global__ void __launch_bounds__(kMT, 1) rebk_multi_kernel(const __grid_constan
     if (cta == 0 && tid == 0) *a.iters_done = done;
 }
 
-template <typename TA, int NR> void *multi_ptr() { return reinterpret_cast<void *>(&rebk_multi_kernel<TA, NR>); }
+template <typename TA, int NR, bool MMA> void *multi_ptr() {
+    return reinterpret_cast<void *>(&rebk_multi_kernel<TA, NR, MMA>);
+}
 
-void *multi_kernel(bool bf16, int nr) {
-    if (bf16) return nr == 8 ? multi_ptr<__nv_bfloat16, 8>() : multi_ptr<__nv_bfloat16, 4>();
-    return nr == 8 ? multi_ptr<float, 8>() : multi_ptr<float, 4>();
+void *multi_kernel(bool bf16, int nr, bool mma) {
+    if (bf16) return nr == 8 ? multi_ptr<__nv_bfloat16, 8, false>() : multi_ptr<__nv_bfloat16, 4, false>();
+    if (nr == 8) return mma ? multi_ptr<float, 8, true>() : multi_ptr<float, 8, false>();
+    return multi_ptr<float, 4, false>();
 }
 
 // ---------------------------------------------------------------------------
@@ -623,8 +876,8 @@ size_t multi_smem_bytes(const MultiArgs &M, int nr) {
         .total;
 }
 
-int multi_max_ctas(bool bf16, int nr, size_t smem) {
-    void *k = multi_kernel(bf16, nr);
+int multi_max_ctas(bool bf16, int nr, bool mma, size_t smem) {
+    void *k = multi_kernel(bf16, nr, mma);
     if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
         cudaGetLastError();
         return 0;
@@ -641,7 +894,7 @@ int multi_max_ctas(bool bf16, int nr, size_t smem) {
 
 cudaError_t launch_multi(const MultiArgs &M, bool bf16, int nr, int G, cudaStream_t st) {
     const size_t smem = multi_smem_bytes(M, nr);
-    void *k = multi_kernel(bf16, nr);
+    void *k = multi_kernel(bf16, nr, M.mma != 0);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     MultiArgs copy = M;
