@@ -193,7 +193,7 @@ def measure_multi(args, sol, prob, dev, rank, storage, stream, hbm_peak):
     sol.solve_multi(B[:group], tol=TOL, seed=600, storage=storage, X_ref=Xr[:group])
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    agg = {"iterations": 0, "kernel_ms": 0.0, "launches": 0, "grid_launches": 0}
+    agg = {"iterations": 0, "kernel_ms": 0.0, "sweep_ms": 0.0, "launches": 0, "grid_launches": 0}
     worst = 0.0
     ev0.record(stream)
     for s_ in range(args.multi_steps):
@@ -213,6 +213,7 @@ def measure_multi(args, sol, prob, dev, rank, storage, stream, hbm_peak):
     return {"value": nrhs * args.multi_steps / (ms / 1000.0), "unit": "solves/s", "storage": storage,
             "rhs_per_step": nrhs, "group": group, "steps": args.multi_steps, "ms_per_step": ms / args.multi_steps,
             "iterations_per_group": agg["iterations"] / groups, "kernel_ms_per_step": agg["kernel_ms"] / args.multi_steps,
+            "fp64_products_ms_per_step": agg["sweep_ms"] / args.multi_steps,
             "us_per_iteration": 1000.0 * agg["kernel_ms"] / max(agg["iterations"], 1),
             "rhs_iterations_per_s": group * agg["iterations"] / kernel_s,
             "rel_err_max": worst, "gpu_launches": agg["launches"],

@@ -1500,6 +1500,24 @@ rebk_status rebk_solve_multi(rebk_handle h, int64_t nrhs, const double *B, int64
         CK(cudaStreamSynchronize(st));
         return REBK_OK;
     };
+    // FP64 products of the refinement loop, timed like the one-right-hand-side sweeps
+    auto products = [&](const void *P, bool p_f32, const void *Q, bool q_f32) -> rebk_status {
+        if (h->sweep_used + 2 > h->sweep_ev.size()) {
+            for (int i = 0; i < 2; ++i) {
+                cudaEvent_t ev;
+                CK(cudaEventCreate(&ev));
+                h->sweep_ev.push_back(ev);
+            }
+        }
+        cudaEvent_t e0 = h->sweep_ev[h->sweep_used], e1 = h->sweep_ev[h->sweep_used + 1];
+        h->sweep_used += 2;
+        CK(cudaEventRecord(e0, st));
+        if (P) LK(h, multi_ap(h->A64, h->lda, m, n, nr, P, p_f32, Ym, st));
+        else CK(cudaMemsetAsync(Ym, 0, 8 * mv, st));
+        LK(h, multi_atq(h->A64, h->lda, m, n, nr, Q, q_f32, Yn, st));
+        CK(cudaEventRecord(e1, st));
+        return REBK_OK;
+    };
     int64_t inner_default = o.inner_iters;
     if (inner_default <= 0) {
         if (use_ref) {
@@ -1577,9 +1595,8 @@ rebk_status rebk_solve_multi(rebk_handle h, int64_t nrhs, const double *B, int64
                 }
             }
             // F = b - z - A x, G = A^T z (FP64)
-            if (x_zero) CK(cudaMemsetAsync(Ym, 0, 8 * mv, st));
-            else LK(h, multi_ap(h->A64, h->lda, m, n, nr, Xq, false, Ym, st));
-            LK(h, multi_atq(h->A64, h->lda, m, n, nr, Zq, false, Yn, st));
+            s = products(x_zero ? nullptr : Xq, false, Zq, false);
+            if (s != REBK_OK) return s;
             x_zero = false;
             LK(h, multi_form(Bq, Zq, Ym, F, m, Yn, Gf, n, nr, st));
             if (!use_ref) {
@@ -1677,8 +1694,8 @@ rebk_status rebk_solve_multi(rebk_handle h, int64_t nrhs, const double *B, int64
             }
             total += ran;
             // z <- z - A s, x <- x + A^T v (FP64 A)
-            LK(h, multi_ap(h->A64, h->lda, m, n, nr, S, true, Ym, st));
-            LK(h, multi_atq(h->A64, h->lda, m, n, nr, V, true, Yn, st));
+            s = products(S, true, V, true);
+            if (s != REBK_OK) return s;
             LK(h, multi_apply(Xq, Yn, n, Zq, Ym, m, nr, st));
         }
         if (!converged) {  // the test after the last pass
@@ -1692,8 +1709,8 @@ rebk_status rebk_solve_multi(rebk_handle h, int64_t nrhs, const double *B, int64
                     converged = converged && rel[q] <= tol;
                 }
             } else {
-                LK(h, multi_ap(h->A64, h->lda, m, n, nr, Xq, false, Ym, st));
-                LK(h, multi_atq(h->A64, h->lda, m, n, nr, Zq, false, Yn, st));
+                s = products(Xq, false, Zq, false);
+                if (s != REBK_OK) return s;
                 LK(h, multi_form(Bq, Zq, Ym, F, m, Yn, Gf, n, nr, st));
                 double wr = 0.0;
                 s = residual_test(&wr);
