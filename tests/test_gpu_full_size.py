@@ -106,6 +106,30 @@ def test_full_size_solves_stop_where_the_oracle_stops(setup):
     assert_converged(mixed["x"].cpu().numpy(), p.x_ref, 1e-8)
 
 
+def test_full_size_multi_rhs_pass_matches_oracle_per_member(setup):
+    """Several right-hand sides at once at full size, in the benchmark's launch
+    (groups of 8, one CTA per SM, products on tensor cores): the workload's b and 7
+    more of the same law after one pass of 100 iterations, each against the
+    oracle's pass on its own right-hand side, block indices bit-exact."""
+    p, _, alpha, sol = setup
+    ro, co = contiguous_offsets(M, TAU), contiguous_offsets(N, TAU)
+    assert sol.multi_group("fp32") == 8
+    rng = np.random.default_rng(11)
+    B = np.array([p.b] + [p.A @ rng.standard_normal(N) + 0.01 * rng.standard_normal(M) for _ in range(7)])
+    K = 100
+    out = sol.solve_multi(torch.from_numpy(B).to(DEV), tol=0.0, max_iter=K, seed=21, storage="fp32", max_outer=1,
+                          inner_iters=K, record=True)
+    assert out["stats"]["iterations"] == K
+    lo = O.round_fp32(p.A)
+    idx_ref = O.rebk_correction(lo, *O.dual_residuals(p.A, B[0], B[0], np.zeros(N)), ro, co,
+                                O.block_norms(p.A, ro, co), alpha, seed=21, iters=K, record=True)["idx"]
+    assert np.array_equal(out["idx"][: 2 * K].view(-1, 2).cpu().numpy(), idx_ref)
+    X = out["X"].cpu().numpy()
+    for j in range(len(B)):
+        ref = O.refine(p.A, B[j], lo, ro, co, alpha, seed=21, inner_iters=K, outer_max=1)
+        assert_close(X[j], ref["x"], 1e-4)
+
+
 # ---------------------------------------------------------------------------
 # Batched systems at full size: 512 systems, m ~ U[200, 6000], n ~ U[50, 2000],
 # 8 right-hand sides each, tau 16 (the benchmark's batch).
