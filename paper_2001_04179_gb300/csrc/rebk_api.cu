@@ -1192,8 +1192,11 @@ rebk_status rebk_solve_refined(rebk_handle h, const double *b, double *x, double
             }
         }
         total += ran;
-        // z <- z - A s, x <- x + A^T v (FP64 A)
-        s = timed_sweep(h, h->sd, true, h->vd, true, h->ym, h->yn);
+        // z <- z - A s, x <- x + A^T v (FP64 A); the FP32 duals are widened first into
+        // g and f, which the next pass recomputes
+        LK(h, widen_f32(h->sd, h->g, h->n, st));
+        LK(h, widen_f32(h->vd, h->f, h->m, st));
+        s = timed_sweep(h, h->g, false, h->f, false, h->ym, h->yn);
         if (s != REBK_OK) return s;
         LK(h, apply_update(x, h->yn, h->n, z, h->ym, h->m, st));
     }
@@ -1471,7 +1474,7 @@ rebk_status rebk_solve_multi(rebk_handle h, int64_t nrhs, const double *B, int64
     const size_t mv = (size_t)m * nr, nv = (size_t)n * nr;
     const size_t oB = take(8 * mv), oZ = take(8 * mv), oX = take(8 * nv), oXr = take(8 * nv), oYm = take(8 * mv),
                  oYn = take(8 * nv), oSm = take(8 * 64), oF = take(4 * mv), oG = take(4 * nv), odZ = take(4 * mv),
-                 oV = take(4 * mv), odX = take(4 * nv), oS = take(4 * nv),
+                 oV = take(4 * mv), odX = take(4 * nv), oS = take(4 * nv), oSd = take(8 * nv), oVd = take(8 * mv),
                  oAcc = take(sizeof(float) * 3 * kMultiReplicas * (size_t)aw);
     if (off > h->mr_bytes) {
         if (h->mr_buf) cudaFree(h->mr_buf);
@@ -1487,6 +1490,7 @@ rebk_status rebk_solve_multi(rebk_handle h, int64_t nrhs, const double *B, int64
     float *F = (float *)(base + oF), *Gf = (float *)(base + oG), *dZ = (float *)(base + odZ);
     float *V = (float *)(base + oV), *dX = (float *)(base + odX), *S = (float *)(base + oS);
     float *acc = (float *)(base + oAcc);
+    double *Sd = (double *)(base + oSd), *Vd = (double *)(base + oVd);
     M.dZ = dZ;
     M.dX = dX;
     M.S = S;
@@ -1694,7 +1698,9 @@ rebk_status rebk_solve_multi(rebk_handle h, int64_t nrhs, const double *B, int64
             }
             total += ran;
             // z <- z - A s, x <- x + A^T v (FP64 A)
-            s = products(S, true, V, true);
+            LK(h, widen_f32(S, Sd, (int64_t)nv, st));
+            LK(h, widen_f32(V, Vd, (int64_t)mv, st));
+            s = products(Sd, false, Vd, false);
             if (s != REBK_OK) return s;
             LK(h, multi_apply(Xq, Yn, n, Zq, Ym, m, nr, st));
         }

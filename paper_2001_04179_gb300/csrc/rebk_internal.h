@@ -186,6 +186,8 @@ cudaError_t form_f(const double *b, const double *z, const double *ym, double *f
 cudaError_t apply_update(double *x, const double *yn, int64_t n, double *z, const double *ym,
                          int64_t m, cudaStream_t st);
 cudaError_t fill_zero_f32(float *p, int64_t n, cudaStream_t st);
+// dst = (double) src, n entries
+cudaError_t widen_f32(const float *src, double *dst, int64_t n, cudaStream_t st);
 // out = a - b (length n)
 cudaError_t vec_sub(const double *a, const double *b, double *out, int64_t n, cudaStream_t st);
 

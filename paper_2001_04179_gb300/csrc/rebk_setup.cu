@@ -398,6 +398,13 @@ __global__ void vec_sub_kernel(const double *a, const double *b, double *out, in
         out[e] = a[e] - b[e];
 }
 
+// FP32 -> FP64 once per vector: on GB300 a conversion costs FP64-pipe time, so the
+// FP64 products take FP64 inputs instead of converting inside their inner loops.
+__global__ void widen_f32_kernel(const float *src, double *dst, int64_t n) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        dst[e] = (double)src[e];
+}
+
 __global__ void fill_zero_f32_kernel(float *p, int64_t n) {
     for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
          e += (int64_t)gridDim.x * blockDim.x)
@@ -673,6 +680,11 @@ cudaError_t step_coefficients(const double *norms, int nb, double alpha, double 
 
 cudaError_t vec_sub(const double *a, const double *b, double *out, int64_t n, cudaStream_t st) {
     vec_sub_kernel<<<grid_for(n, 256) > 2048 ? 2048 : grid_for(n, 256), 256, 0, st>>>(a, b, out, n);
+    return cudaGetLastError();
+}
+
+cudaError_t widen_f32(const float *src, double *dst, int64_t n, cudaStream_t st) {
+    widen_f32_kernel<<<grid_for(n, 256) > 2048 ? 2048 : grid_for(n, 256), 256, 0, st>>>(src, dst, n);
     return cudaGetLastError();
 }
 
