@@ -974,8 +974,12 @@ rebk_status enqueue_solve(rebk_batch h, int tau, double tol, int64_t inner_iters
         a.timeout_ns = kBarrierTimeoutNs;
         BCK(launch_inner(a, sms, st));
         ++*launches;
-        // z <- z - A s, x <- x + A^T v
-        BCK(sweep(nullptr, h->S, nullptr, h->Vd, h->YM, h->YN));
+        // z <- z - A s, x <- x + A^T v; the FP32 duals are widened once into G and F
+        // (free until the next pass) so the FP64 sweep converts nothing in its loops
+        BCK(widen_f32(h->S, h->G, totn * kR, st));
+        BCK(widen_f32(h->Vd, h->F, totm * kR, st));
+        *launches += 2;
+        BCK(sweep(h->G, nullptr, h->F, nullptr, h->YM, h->YN));
         batch_update_kernel<<<blocks_for((totm + totn) * kR, 256), 256, 0, st>>>(totm, totn, h->Xi, h->YN, h->Z,
                                                                                 h->YM);
         ++*launches;
