@@ -395,31 +395,16 @@ __global__ void __launch_bounds__(kMT, 1) rebk_multi_kernel(const __grid_constan
             if (e < (int)(jb - ja) * NR) gpre[k] = __ldg(M.G + ja * NR + e);
         }
     };
-    // duals of the owned rows of I_u (entry tid + k * kMT of the intersection), read
-    // a round ahead of their update; the owner is the only writer
-    float vpre[2] = {0.f, 0.f}, spre[4] = {0.f, 0.f, 0.f, 0.f};
-    auto prefetch_v = [&](int64_t u) {
-        if (u > K) return;
-        int64_t ia, ib;
-        row_range(idraw(u), &ia, &ib);
-        const int64_t la = ia > r0 ? ia : r0, lb = ib < r1 ? ib : r1;
+    // duals of the owned rows (V) and columns (S): entry e = tid + k * kMT of the CTA's
+    // slice stays in a register for the whole launch (the CTA is its only writer);
+    // slices longer than 4 * kMT entries keep the rest in global memory
+    float vreg[4], sreg[4];
 #pragma unroll
-        for (int k = 0; k < 2; ++k) {
-            const int64_t e = tid + k * kMT;
-            if (e < (lb - la) * NR) vpre[k] = M.V[la * NR + e];
-        }
-    };
-    auto prefetch_s = [&](int64_t u) {
-        if (u > K) return;
-        int64_t ja, jb;
-        col_range(jdraw(u), &ja, &jb);
-        const int64_t la = ja > c0 ? ja : c0, lb = jb < c1 ? jb : c1;
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-            const int64_t e = tid + k * kMT;
-            if (e < (lb - la) * NR) spre[k] = M.S[la * NR + e];
-        }
-    };
+    for (int k = 0; k < 4; ++k) {
+        const int e = tid + k * kMT;
+        vreg[k] = e < nrow * NR ? M.V[r0 * NR + e] : 0.f;
+        sreg[k] = e < ncol * NR ? M.S[c0 * NR + e] : 0.f;
+    }
 
     // Tiles: the column tile of J_t in column buffer t & 1, the row tile of I_t in
     // row buffer t & 1.  Every thread tracks the phases; thread 0 issues.
@@ -526,8 +511,6 @@ __global__ void __launch_bounds__(kMT, 1) rebk_multi_kernel(const __grid_constan
             partial_w(1, acc);
         }
         prefetch_g(1);
-        prefetch_s(1);
-        prefetch_v(1);
     }
     grid_arrive(a.bar);
     for (int64_t t = 1; alive && t <= K + 1; ++t) {
@@ -622,26 +605,29 @@ __global__ void __launch_bounds__(kMT, 1) rebk_multi_kernel(const __grid_constan
                                            });
             }
         }
-        if (rowstep) {  // dual V on the owned rows of I_{t-1} (entries read a round ahead), then read I_t's
-            const int64_t la = ia > r0 ? ia : r0, lb = ib < r1 ? ib : r1;
-#pragma unroll
-            for (int k = 0; k < 2; ++k) {
-                const int64_t e = tid + k * kMT;
-                if (e < (lb - la) * NR) M.V[la * NR + e] = vpre[k] - cI * sr[(la - ia) * NR + e];
-            }
-            for (int64_t e = tid + 2 * kMT; e < (lb - la) * NR; e += kMT) M.V[la * NR + e] -= cI * sr[(la - ia) * NR + e];
-            prefetch_v(t);
-        }
-        if (colstep) {  // dual S on the owned columns of J_t (entries read a round ahead), then read J_{t+1}'s
-            const int64_t la = ja > c0 ? ja : c0, lb = jb < c1 ? jb : c1;
+        if (rowstep) {  // dual V on the owned rows of I_{t-1}
 #pragma unroll
             for (int k = 0; k < 4; ++k) {
-                const int64_t e = tid + k * kMT;
-                if (e < (lb - la) * NR) M.S[la * NR + e] = spre[k] + cJ * sw[(e % NR) * ws + (la - ja) + e / NR];
+                const int e = tid + k * kMT;
+                const int64_t row = r0 + e / NR;
+                if (e < nrow * NR && row >= ia && row < ib) vreg[k] -= cI * sr[(row - ia) * NR + e % NR];
             }
-            for (int64_t e = tid + 4 * kMT; e < (lb - la) * NR; e += kMT)
-                M.S[la * NR + e] += cJ * sw[(e % NR) * ws + (la - ja) + e / NR];
-            prefetch_s(t + 1);
+            for (int e = tid + 4 * kMT; e < nrow * NR; e += kMT) {
+                const int64_t row = r0 + e / NR;
+                if (row >= ia && row < ib) M.V[r0 * NR + e] -= cI * sr[(row - ia) * NR + e % NR];
+            }
+        }
+        if (colstep) {  // dual S on the owned columns of J_t
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int e = tid + k * kMT;
+                const int64_t c = c0 + e / NR;
+                if (e < ncol * NR && c >= ja && c < jb) sreg[k] += cJ * sw[(e % NR) * ws + (c - ja)];
+            }
+            for (int e = tid + 4 * kMT; e < ncol * NR; e += kMT) {
+                const int64_t c = c0 + e / NR;
+                if (c >= ja && c < jb) M.S[c0 * NR + e] += cJ * sw[(e % NR) * ws + (c - ja)];
+            }
         }
         __syncthreads();
         issue_r(t + 1);  // the buffer of I_{t-1} takes I_{t+1}
@@ -724,6 +710,12 @@ __global__ void __launch_bounds__(kMT, 1) rebk_multi_kernel(const __grid_constan
     }
     __syncthreads();
     for (int e = tid; e < nrow * NR; e += kMT) M.dZ[r0 * NR + e] = zeta[e];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const int e = tid + k * kMT;
+        if (e < nrow * NR) M.V[r0 * NR + e] = vreg[k];
+        if (e < ncol * NR) M.S[c0 * NR + e] = sreg[k];
+    }
     for (int e = tid; e < ncol * NR; e += kMT) M.dX[c0 * NR + e] = xi[(e % NR) * xs + e / NR];
     if (cta == 0 && tid == 0) *a.iters_done = done;
 }
