@@ -1,20 +1,28 @@
 // rebk_sparse.cu -- Algorithm 1 of Du, Si, Sun (arXiv:2001.04179) on a sparse
 // matrix: CSR for the row blocks, a CSC copy for the column blocks.
 //
-// One persistent cooperative launch runs many iterations, two device-wide
-// barriers each.  With the block indices sampled before the launch (as in the
-// dense path), iteration k is:
-//   gathers: r^k = A_{I_k,:} x^{k-1} - b_{I_k} + z^k_{I_k} over CSR, the column
-//     gather of the next iteration w = A_{:,J_{k+1}}^T z^k over CSC, and every
-//     check_every iterations each CTA's share of ||x^{k-1} - x_ref||^2;  barrier
-//   scatters: x^k = x^{k-1} - c_I A_{I_k,:}^T r^k and z^{k+1} = z^k -
-//     c_J A_{:,J_{k+1}} w by FP64 atomic adds;                          barrier
-// (z^1 comes from a prologue gather / scatter.)  Gathers only read and
-// scatters only write x and z, so each phase sees the iterates the previous
-// one left.  Each CTA owns a contiguous share of the sampled block's columns
-// (rows), whose entries are one CSC (CSR) range: its threads gather it in one
-// round, warps adding each line's products by shuffles before one shared
-// atomic per line.  On a converged stop at iteration k, x = x^{k-1} and z = z^k.
+// One persistent cooperative launch runs many iterations, one device-wide
+// barrier each.  x and z have two copies each: at iteration k one copy of x holds
+// x^{k-1} and the other x^{k-2}, one copy of z holds z^k and the other z^{k-1}.
+// With the block indices sampled before the launch (as in the dense path),
+// iteration k is one phase:
+//   gathers from the current copies: r^k = A_{I_k,:} x^{k-1} - b_{I_k} + z^k_{I_k}
+//     over CSR, the column gather of the next iteration w = A_{:,J_{k+1}}^T z^k
+//     over CSC, and every check_every iterations each CTA's share of
+//     ||x^{k-1} - x_ref||^2;
+//   scatters into the other copies, by FP64 atomic adds: -c_I A_{I_k,:}^T r^k and
+//     again the previous iteration's -c_I' A_{I_{k-1},:}^T r^{k-1} into x (which
+//     turns x^{k-2} into x^k), -c_J A_{:,J_{k+1}} w^{k+1} and again -c_J'
+//     A_{:,J_k} w^k into z (z^{k-1} into z^{k+1});                      barrier
+// so no copy is read and written in the same phase.  Each update is added twice,
+// once into each copy, in exchange for the second barrier per iteration.  (z^1
+// comes from a prologue gather / scatter.)  Each CTA owns a contiguous share of
+// the sampled block's columns (rows), whose entries are one CSC (CSR) range: its
+// threads gather it in one round, warps adding each line's products by shuffles
+// before one shared atomic per line; it keeps its lines' r and w, and their entry
+// ranges, for the replay of the next iteration.  On a converged stop at iteration
+// k, x = x^{k-1} and z = z^k; the final iterates are copied into x and z (the
+// first copies) before the kernel ends.
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -36,7 +44,7 @@ constexpr int kST = 512;                     // threads per CTA
 constexpr int kSW = kST / 32;
 constexpr int kOwnMax = 512;                 // columns / rows of a block one CTA may own
 constexpr int64_t kSparseChunk = 1 << 20;    // iterations sampled per launch
-constexpr int64_t kSparseLaunchMax = 4000000;  // 3 barriers per iteration: counter headroom
+constexpr int64_t kSparseLaunchMax = 4000000;  // barrier counter headroom (one barrier per iteration)
 
 struct SparseArgs {
     int64_t m, n;
@@ -51,6 +59,7 @@ struct SparseArgs {
     const int32_t *idx;  // 2 * iters: (j_k, i_k)
     int64_t iters;
     void *z, *x;         // T: z and x (plain), the corrections dz and dx (CORR)
+    void *z2, *x2;       // T: second copies, equal to z and x at launch
     const double *b;     // b (plain), f = b - z - A x (CORR)
     const double *g;     // CORR: A^T z
     void *sdual, *vdual; // CORR (T): duals s (n) and v (m), dz = -A s, dx = A^T v
@@ -198,68 +207,73 @@ __device__ __forceinline__ void gather_rows_cols(const int64_t *br, int nqr, con
 template <typename T, bool CORR>
 __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_constant__ SparseArgs a) {
     __shared__ double red[kSW];
-    __shared__ T wq[kOwnMax];               // w of the CTA's columns of J_{k+1}
-    __shared__ T rq[kOwnMax];               // r of the CTA's rows of I_k
-    __shared__ int64_t bc[kOwnMax + 1];     // entry boundaries of those columns (CSC)
-    __shared__ int64_t br[kOwnMax + 1];     // and rows (CSR)
+    // two slots each, by iteration parity: w of the CTA's columns of J_u (slot u & 1),
+    // r of its rows of I_u (slot u & 1), and those lines' entry boundaries
+    __shared__ T wq[2][kOwnMax];
+    __shared__ T rq[2][kOwnMax];
+    __shared__ int64_t bc[2][kOwnMax + 1];
+    __shared__ int64_t br[2][kOwnMax + 1];
     __shared__ T part[2 * kOwnMax];         // the joint gather's line sums
     __shared__ int s_flag;
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x;
     const T *rv = static_cast<const T *>(a.rv), *cv = static_cast<const T *>(a.cv);
     const T *coef_r = static_cast<const T *>(a.coef_r), *coef_c = static_cast<const T *>(a.coef_c);
-    T *z = static_cast<T *>(a.z), *x = static_cast<T *>(a.x);
+    T *const x0 = static_cast<T *>(a.x), *const x1 = static_cast<T *>(a.x2);
+    T *const z0 = static_cast<T *>(a.z), *const z1 = static_cast<T *>(a.z2);
+    auto xb = [&](int64_t u) { return (u & 1) ? x1 : x0; };
+    auto zb = [&](int64_t u) { return (u & 1) ? z1 : z0; };
     T *sdual = static_cast<T *>(a.sdual), *vdual = static_cast<T *>(a.vdual);
     const int64_t K = a.iters;
     const bool check = a.x_ref != nullptr && a.check_every > 0;
-    const int64_t xs0 = a.n * cta / G, xs1 = a.n * (cta + 1) / G;  // this CTA's share of the test
+    const int64_t xs0 = a.n * cta / G, xs1 = a.n * (cta + 1) / G;  // this CTA's share of x
+    const int64_t zs0 = a.m * cta / G, zs1 = a.m * (cta + 1) / G;  // and of z
     unsigned int phase = 0;
     auto barrier = [&]() -> bool {
         ++phase;
         return grid_barrier(a.bar, (unsigned)G * phase, a.status, a.timeout_ns, &s_flag);
     };
-    // column gather of iteration kk (A): w for the CTA's contiguous share of J_kk
-    int nqc = 0;
-    int64_t cc0 = 0;
-    T cJ = T(0);
-    auto gather_cols = [&](int64_t kk) {
-        const int j = __ldg(a.idx + 2 * (kk - 1));
-        const int64_t ja = (int64_t)j * a.tau_c, jb = ja + a.tau_c < a.n ? ja + a.tau_c : a.n;
-        const int64_t c0 = ja + (jb - ja) * cta / G, c1 = ja + (jb - ja) * (cta + 1) / G;
-        cJ = coef_c[j];
-        cc0 = c0;
-        nqc = (int)(c1 - c0);
-        __syncthreads();  // bc[] and wq[] are free
-        for (int q = tid; q <= nqc; q += kST) bc[q] = a.cp[c0 + q];
-        __syncthreads();
-        if (nqc > 0) gather_lines(bc, nqc, a.ri, cv, z, wq);
-        if (CORR)
-            for (int q = tid; q < nqc; q += kST) wq[q] += (T)a.g[c0 + q];
-        if (tid < nqc && !isfinite(wq[tid])) atomicExch(a.bad, 1);
+    // -c A^T r (rows, into x) or -c A w (columns, into z) for a CTA's lines, all entries
+    // reloaded from the matrix
+    auto scatter_rows = [&](T *dst, const int64_t *b, int nq, const T *rr, T c) {
+        for (int64_t e = (nq > 0 ? b[0] : 0) + tid; nq > 0 && e < b[nq]; e += kST)
+            atomicAdd(dst + a.ci[e], -c * rv[e] * rr[line_of(b, nq, e)]);
     };
-    // z scatter (B) with the w of the last column gather, and the dual s
-    auto scatter_z = [&]() {
-        for (int64_t e = bc[0] + tid; nqc > 0 && e < bc[nqc]; e += kST)
-            atomicAdd(z + a.ri[e], -cJ * cv[e] * wq[line_of(bc, nqc, e)]);
-        if (CORR)
-            for (int q = tid; q < nqc; q += kST) sdual[cc0 + q] += cJ * wq[q];
+    auto scatter_cols = [&](T *dst, const int64_t *b, int nq, const T *ww, T c) {
+        for (int64_t e = (nq > 0 ? b[0] : 0) + tid; nq > 0 && e < b[nq]; e += kST)
+            atomicAdd(dst + a.ri[e], -c * cv[e] * ww[line_of(b, nq, e)]);
     };
     int64_t done = K;
     int stop = 0;
-    // prologue: z^1 (column step of iteration 1)
+    bool z_from_first = false;  // the prologue stopped: z^0 is in the first copy
+    // the previous iteration's lines, for the replays: rows of I_{k-1}, columns of J_k
+    int64_t lp0 = 0, cp0 = 0;
+    int nqrp = 0, nqcp = 0;
+    T cIp = T(0), cJp = T(0);
+    // prologue: w^1 from z^0 (first copy), -c A w^1 into the second copy (z^1)
     if (K >= 1) {
-        gather_cols(1);
+        const int j = __ldg(a.idx);
+        const int64_t ja = (int64_t)j * a.tau_c, jb = ja + a.tau_c < a.n ? ja + a.tau_c : a.n;
+        cp0 = ja + (jb - ja) * cta / G;
+        nqcp = (int)(ja + (jb - ja) * (cta + 1) / G - cp0);
+        cJp = coef_c[j];
+        for (int q = tid; q <= nqcp; q += kST) bc[1][q] = a.cp[cp0 + q];
+        __syncthreads();
+        if (nqcp > 0) gather_lines(bc[1], nqcp, a.ri, cv, z0, wq[1]);
+        if (CORR)
+            for (int q = tid; q < nqcp; q += kST) wq[1][q] += (T)a.g[cp0 + q];
+        if (tid < nqcp && !isfinite(wq[1][tid])) atomicExch(a.bad, 1);
+        __syncthreads();
+        scatter_cols(z1, bc[1], nqcp, wq[1], cJp);
         if (!barrier()) return;
         if (*reinterpret_cast<volatile int *>(a.bad) != 0) {
             stop = 5;
             done = 0;
-        } else {
-            scatter_z();
-            if (!barrier()) return;
+            z_from_first = true;
         }
     }
     // Block boundaries and b of the rows for the next iteration, loaded during the
-    // previous scatter phase (they do not change) so that a gather phase starts
-    // with its line ranges in place.
+    // previous phase (they do not change) so that a phase starts with its line
+    // ranges in place.
     int64_t nb_r[2] = {0, 0}, nb_c[2] = {0, 0};
     double nb_b = 0.0;
     bool have_next = false;
@@ -277,83 +291,81 @@ __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_consta
             *nq_c = (int)(ja + (jb - ja) * (cta + 1) / G - *c0);
         }
     };
+    int64_t l0 = 0;
+    int nqr = 0;
+    T cI = T(0);
     for (int64_t k = 1; stop == 0 && k <= K; ++k) {
-        // ---- gathers: r^k = A_I x^{k-1} - b_I + z^k_I, w^{k+1} = A_J'^T z^k, test of x^{k-1} ----
-        int64_t l0, c0;
-        int nqr;
+        const int sk = (int)(k & 1), sn = (int)((k + 1) & 1);  // slots of I_k / J_k and of J_{k+1}
+        int64_t c0;
+        int nqc;
         shares(k, &l0, &nqr, &c0, &nqc);
-        const T cI = coef_r[__ldg(a.idx + 2 * (k - 1) + 1)];
-        if (nqc > 0) cJ = coef_c[__ldg(a.idx + 2 * k)];
-        cc0 = c0;
+        cI = coef_r[__ldg(a.idx + 2 * (k - 1) + 1)];
+        const T cJ = nqc > 0 ? coef_c[__ldg(a.idx + 2 * k)] : T(0);
         if (have_next) {  // nqr, nqc <= kOwnMax = kST: entries tid and kST + tid
-            if (tid <= nqr) br[tid] = nb_r[0];
-            if (kST + tid <= nqr) br[kST + tid] = nb_r[1];
-            if (tid <= nqc) bc[tid] = nb_c[0];
-            if (kST + tid <= nqc) bc[kST + tid] = nb_c[1];
+            if (tid <= nqr) br[sk][tid] = nb_r[0];
+            if (kST + tid <= nqr) br[sk][kST + tid] = nb_r[1];
+            if (tid <= nqc) bc[sn][tid] = nb_c[0];
+            if (kST + tid <= nqc) bc[sn][kST + tid] = nb_c[1];
         } else {
-            for (int q = tid; q <= nqr; q += kST) br[q] = a.rp[l0 + q];
-            for (int q = tid; q <= nqc; q += kST) bc[q] = a.cp[c0 + q];
+            for (int q = tid; q <= nqr; q += kST) br[sk][q] = a.rp[l0 + q];
+            for (int q = tid; q <= nqc; q += kST) bc[sn][q] = a.cp[c0 + q];
             nb_b = tid < nqr ? a.b[l0 + tid] : 0.0;
         }
         __syncthreads();
+        // ---- gathers from x^{k-1} and z^k: r^k, w^{k+1}, test of x^{k-1} ----
+        const T *xc = xb(k - 1), *zc = zb(k);
         Entry<T> f0, f1;
-        gather_rows_cols(br, nqr, a.ci, rv, x, bc, nqc, a.ri, cv, z, part, f0, f1);
+        gather_rows_cols(br[sk], nqr, a.ci, rv, xc, bc[sn], nqc, a.ri, cv, zc, part, f0, f1);
         if (tid < nqr) {
-            const T rl = part[tid] - (T)nb_b + z[l0 + tid];
-            rq[tid] = rl;
+            const T rl = part[tid] - (T)nb_b + zc[l0 + tid];
+            rq[sk][tid] = rl;
             if (!isfinite(rl)) atomicExch(a.bad, 1);
         }
         for (int q = tid; q < nqc; q += kST) {
-            wq[q] = CORR ? part[nqr + q] + (T)a.g[c0 + q] : part[nqr + q];
-            if (!isfinite(wq[q])) atomicExch(a.bad, 1);
+            wq[sn][q] = CORR ? part[nqr + q] + (T)a.g[c0 + q] : part[nqr + q];
+            if (!isfinite(wq[sn][q])) atomicExch(a.bad, 1);
         }
         const bool due = check && k >= 2 && (a.check_offset + k - 1) % a.check_every == 0;
         if (due) {
             double e2 = 0.0;
             for (int64_t c = xs0 + tid; c < xs1; c += kST) {
-                const double xc = CORR ? a.x_base[c] + (double)x[c] : (double)x[c];
-                const double d = xc - a.x_ref[c];
+                const double xv = CORR ? a.x_base[c] + (double)xc[c] : (double)xc[c];
+                const double d = xv - a.x_ref[c];
                 e2 = fma(d, d, e2);
             }
             e2 = block_sum(e2, red);
             if (tid == 0) atomicAdd(a.acc + k % 3, e2);
         }
         if (cta == 0 && tid == 0) a.acc[(k + 1) % 3] = 0.0;  // the slot two tests ahead
-        if (!barrier()) return;
-        if (*reinterpret_cast<volatile int *>(a.bad) != 0) {
-            stop = 5;
-            done = k - 1;
-            break;
-        }
-        if (due && __ldcg(a.acc + k % 3) <= a.tol2_abs) {  // every CTA reads the same sum
-            stop = 1;
-            done = k - 1;
-            break;
-        }
-        // ---- scatters: x^k = x^{k-1} - c_I A_I^T r^k, z^{k+1} = z^k - c_J' A_J' w^{k+1} ----
-        // the first round's entries from registers, the rest of the list reloaded
+        __syncthreads();  // rq, wq complete
+        // ---- scatters into the other copies: x^{k-2} -> x^k, z^{k-1} -> z^{k+1} ----
+        T *xo = xb(k), *zo = zb(k + 1);
+        // the first round's entries of this iteration from registers, the rest reloaded
         auto scatter = [&](const Entry<T> &f) {
             if (f.q < 0) return;
-            if (f.q < nqr) atomicAdd(x + f.idx, -cI * f.val * rq[f.q]);
-            else atomicAdd(z + f.idx, -cJ * f.val * wq[f.q - nqr]);
+            if (f.q < nqr) atomicAdd(xo + f.idx, -cI * f.val * rq[sk][f.q]);
+            else atomicAdd(zo + f.idx, -cJ * f.val * wq[sn][f.q - nqr]);
         };
         scatter(f0);
         scatter(f1);
         {
-            const int64_t nr = nqr > 0 ? br[nqr] - br[0] : 0, nc = nqc > 0 ? bc[nqc] - bc[0] : 0;
+            const int64_t nr = nqr > 0 ? br[sk][nqr] - br[sk][0] : 0, nc = nqc > 0 ? bc[sn][nqc] - bc[sn][0] : 0;
             for (int64_t g = 2 * kST + tid; g < nr + nc; g += kST) {
                 if (g < nr) {
-                    const int64_t e = br[0] + g;
-                    atomicAdd(x + a.ci[e], -cI * rv[e] * rq[line_of(br, nqr, e)]);
+                    const int64_t e = br[sk][0] + g;
+                    atomicAdd(xo + a.ci[e], -cI * rv[e] * rq[sk][line_of(br[sk], nqr, e)]);
                 } else {
-                    const int64_t e = bc[0] + (g - nr);
-                    atomicAdd(z + a.ri[e], -cJ * cv[e] * wq[line_of(bc, nqc, e)]);
+                    const int64_t e = bc[sn][0] + (g - nr);
+                    atomicAdd(zo + a.ri[e], -cJ * cv[e] * wq[sn][line_of(bc[sn], nqc, e)]);
                 }
             }
         }
-        if (CORR) {
-            if (tid < nqr) vdual[l0 + tid] -= cI * rq[tid];
-            for (int q = tid; q < nqc; q += kST) sdual[cc0 + q] += cJ * wq[q];
+        // the previous iteration's updates again: r^{k-1} into x, w^k into z
+        if (k >= 2) scatter_rows(xo, br[sn], nqrp, rq[sn], cIp);
+        scatter_cols(zo, bc[sk], nqcp, wq[sk], cJp);
+        if (CORR) {  // duals one iteration behind, so that a stop leaves them consistent
+            if (k >= 2 && tid < nqrp) vdual[lp0 + tid] -= cIp * rq[sn][tid];
+            for (int q = tid; q < nqcp; q += kST) sdual[cp0 + q] += cJp * wq[sk][q];
         }
         // boundaries and b of iteration k + 1 (read-only arrays)
         have_next = k < K;
@@ -367,7 +379,37 @@ __global__ void __launch_bounds__(kST, 1) rebk_sparse_kernel(const __grid_consta
             nb_c[1] = kST + tid <= nqcn ? a.cp[c0n + kST + tid] : 0;
             nb_b = tid < nqrn ? a.b[l0n + tid] : 0.0;
         }
+        lp0 = l0;
+        nqrp = nqr;
+        cIp = cI;
+        cp0 = c0;
+        nqcp = nqc;
+        cJp = cJ;
         if (!barrier()) return;
+        if (*reinterpret_cast<volatile int *>(a.bad) != 0) {
+            stop = 5;
+            done = k - 1;
+            break;
+        }
+        if (due && __ldcg(a.acc + k % 3) <= a.tol2_abs) {  // every CTA reads the same sum
+            stop = 1;
+            done = k - 1;
+            break;
+        }
+    }
+    if (CORR && stop == 0 && K >= 1) {  // the last iteration's r into v
+        const int sl = (int)(K & 1);
+        if (tid < nqr) vdual[l0 + tid] -= cI * rq[sl][tid];
+    }
+    // x^done and z^(done+1) (z^K after K iterations, z^0 after a prologue stop) into the
+    // first copies; every CTA has passed the last barrier, so no phase is running
+    if (K >= 1) {
+        const T *xf = xb(done);
+        const T *zf = z_from_first ? z0 : (stop == 0 ? zb(K) : zb(done + 1));
+        if (xf != x0)
+            for (int64_t c = xs0 + tid; c < xs1; c += kST) x0[c] = xf[c];
+        if (zf != z0)
+            for (int64_t r = zs0 + tid; r < zs1; r += kST) z0[r] = zf[r];
     }
     if (cta == 0 && tid == 0) {
         *a.iters_done = done;
@@ -460,6 +502,7 @@ struct rebk_sparse_s {
     float *rv32 = nullptr, *cv32 = nullptr, *coef_r32 = nullptr, *coef_c32 = nullptr;  // mixed precision
     double *f = nullptr, *g = nullptr, *ym = nullptr, *yn = nullptr;                 // FP64 residuals
     float *dz = nullptr, *dx = nullptr, *sd = nullptr, *vd = nullptr;                // corrections, duals
+    void *copy2 = nullptr;  // the kernel's second copies of x and z (8 (m + n) + 256 bytes)
     int *bad = nullptr, *status = nullptr;
     unsigned int *bar = nullptr;
     int64_t *iters_done = nullptr;
@@ -484,7 +527,7 @@ void free_sparse(rebk_sparse h) {
     if (!h) return;
     void *p[] = {h->rp, h->cp, h->ci, h->ri, h->idx, h->rv, h->cv, h->cdf_r, h->cdf_c, h->coef_r, h->coef_c,
                  h->zbuf, h->acc, h->small, h->bad, h->status, h->bar, h->iters_done, h->rv32, h->cv32,
-                 h->coef_r32, h->coef_c32, h->f, h->g, h->ym, h->yn, h->dz, h->dx, h->sd, h->vd};
+                 h->coef_r32, h->coef_c32, h->f, h->g, h->ym, h->yn, h->dz, h->dx, h->sd, h->vd, h->copy2};
     for (void *q : p)
         if (q) cudaFree(q);
     cudaEvent_t e[] = {h->ev0, h->ev1, h->k0, h->k1};
@@ -559,6 +602,13 @@ rebk_status sparse_launch(rebk_sparse h, bool corr, SparseArgs &a, uint64_t seed
     SCK(cudaMemsetAsync(h->bar, 0, sizeof(unsigned int), st));
     a.idx = idx;
     a.iters = K;
+    // second copies of x and z, equal to them at launch (the kernel writes the final
+    // iterates back into x and z)
+    const size_t es = corr ? sizeof(float) : sizeof(double);
+    a.x2 = h->copy2;
+    a.z2 = static_cast<char *>(h->copy2) + (((size_t)h->n * es + 255) & ~(size_t)255);
+    SCK(cudaMemcpyAsync(a.x2, a.x, (size_t)h->n * es, cudaMemcpyDeviceToDevice, st));
+    SCK(cudaMemcpyAsync(a.z2, a.z, (size_t)h->m * es, cudaMemcpyDeviceToDevice, st));
     void *params[] = {&a};
     void *fn = corr ? reinterpret_cast<void *>(&rebk_sparse_kernel<float, true>)
                     : reinterpret_cast<void *>(&rebk_sparse_kernel<double, false>);
@@ -734,6 +784,7 @@ rebk_status rebk_sparse_create(rebk_sparse *out, int64_t m, int64_t n, const int
     SCKH(cudaMalloc(&h->sd, sizeof(float) * n));
     SCKH(cudaMalloc(&h->idx, sizeof(int32_t) * 2 * kSparseChunk));
     SCKH(cudaMalloc(&h->zbuf, sizeof(double) * m));
+    SCKH(cudaMalloc(&h->copy2, sizeof(double) * (m + n) + 256));  // z's copy starts 256-aligned
     SCKH(cudaMalloc(&h->acc, sizeof(double) * 4));
     SCKH(cudaMalloc(&h->small, sizeof(double) * 4));
     SCKH(cudaMalloc(&h->bad, sizeof(int)));
