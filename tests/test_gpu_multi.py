@@ -52,6 +52,9 @@ CASES = [
     ("gauss_fp32_g4_ragged_count", lambda: gaussian_problem(700, 333, seed=1), 24, 16, "fp32", 4, 6),
     ("product_bf16_g8", lambda: product_problem(640, 500, 160, seed=2), 32, 40, "bf16", 8, 5),
     ("product_fp32_g4", lambda: product_problem(480, 900, 200, seed=3), 40, 24, "fp32", 4, 4),
+    # wide blocks: K runs of up to 256 on the tensor-core path, two register segments on the FMA path
+    ("wide_blocks_fp32_g8", lambda: product_problem(900, 700, 300, seed=5), 256, 200, "fp32", 8, 8),
+    ("wide_blocks_bf16_g4", lambda: gaussian_problem(900, 700, seed=6), 200, 256, "bf16", 4, 4),
 ]
 
 
@@ -107,22 +110,25 @@ def test_residual_rule_without_reference():
         assert np.linalg.norm(X[j] - xs) <= 1e-7 * np.linalg.norm(xs)
 
 
-def test_ragged_partition_one_pass():
+@pytest.mark.parametrize("group", [4, 8])
+def test_ragged_partition_one_pass(group):
+    """Blocks of 1 to 150 rows / columns, column starts off every 16-byte boundary;
+    group 8 runs the tensor-core products, group 4 the FMA ones."""
     from test_gpu_partitions import ragged
     p = gaussian_problem(640, 500, seed=8)
     ro, co = ragged(640, 3, 150), ragged(500, 4, 120, small=(1, 7))
     alpha = 1.5 / max(O.beta_max(p.A, ro, co))
     sol = Solver(p.A, alpha=alpha, storage=("fp32",), row_off=ro, col_off=co)
-    B = _rhs(p, 4, 2)
+    B = _rhs(p, group, 2)
     K = 150
-    out = sol.solve_multi(_dev(B), tol=0.0, max_iter=K, seed=21, storage="fp32", group=4, max_outer=1,
+    out = sol.solve_multi(_dev(B), tol=0.0, max_iter=K, seed=21, storage="fp32", group=group, max_outer=1,
                           inner_iters=K, record=True)
     lo = O.round_fp32(p.A)
     idx_ref = O.rebk_correction(lo, *O.dual_residuals(p.A, B[0], B[0], np.zeros(500)), ro, co,
                                 O.block_norms(p.A, ro, co), alpha, seed=21, iters=K, record=True)["idx"]
     assert np.array_equal(out["idx"][: 2 * K].view(-1, 2).cpu().numpy(), idx_ref)
     X = out["X"].cpu().numpy()
-    for j in range(4):
+    for j in range(group):
         ref = O.refine(p.A, B[j], lo, ro, co, alpha, seed=21, inner_iters=K, outer_max=1)
         assert_close(X[j], ref["x"], 1e-4)
 
