@@ -176,3 +176,17 @@ def test_partition_offsets_are_checked_before_any_cuda_call():
     assert "column partition" in lib.rebk_last_error().decode()
     assert create([0, 600, 1000], None, m=1000) == R.REBK_EUNSUPPORTED  # a block above 512
     assert "512" in lib.rebk_last_error().decode()
+
+
+def test_multi_right_hand_side_entry_points_reject_bad_arguments_on_the_host():
+    """rebk_solve_multi and rebk_multi_group check the handle before any CUDA call."""
+    import ctypes
+    from paper_2001_04179_gb300 import rebk as R
+    lib = R.load()
+    opt = R.RebkMultiOpts(R.REBK_FP32, 0, 0, 0, 0, 0.0, None, 0)
+    stats = R.RebkStats()
+    assert lib.rebk_solve_multi(None, 1, None, 1, None, 1, 1e-8, 10, 0, ctypes.byref(opt), None, 0, None,
+                                ctypes.byref(stats)) == R.REBK_EINVAL
+    assert "NULL" in lib.rebk_last_error().decode()
+    g = ctypes.c_int32(0)
+    assert lib.rebk_multi_group(None, R.REBK_FP32, ctypes.byref(g)) == R.REBK_EINVAL
