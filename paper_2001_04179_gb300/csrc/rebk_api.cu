@@ -1424,7 +1424,7 @@ rebk_status rebk_solve_multi(rebk_handle h, int64_t nrhs, const double *B, int64
     if (!h) return fail(REBK_EINVAL, "handle is NULL");
     if (nrhs < 0) return fail(REBK_EINVAL, "nrhs < 0");
     if (nrhs > 0 && (!B || !X)) return fail(REBK_EINVAL, "B and X must be device pointers");
-    if (ldb < h->m || ldx < h->n || (X_ref && ldxr < h->n))
+    if (nrhs > 0 && (ldb < h->m || ldx < h->n || (X_ref && ldxr < h->n)))
         return fail(REBK_EINVAL, "a leading dimension is below the vector length");
     if (max_iter < 0) return fail(REBK_EINVAL, "max_iter < 0");
     if (!std::isfinite(tol)) return fail(REBK_EINVAL, "tol is not finite");
