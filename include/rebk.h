@@ -612,7 +612,7 @@ rebk_status rebk_warm_start_batch(rebk_handle h, rebk_mlp net, const double *B, 
  * about 520 n + 48 (m/tau_row + n/tau_col) bytes; larger problems are
  * rejected with REBK_EUNSUPPORTED before any GPU work.  The first call on a
  * device looks up the array's device address (cudaGetSymbolAddress) while
- * that device is current: make that first call before any stream capture.
+ * that device is current.
  * All calls share the array and each call overwrites and re-zeroes what it
  * needs; calls whose GPU work overlaps (other streams, other host threads on
  * the same device) race on it: serialise them.  A launch that runs fewer

@@ -16,8 +16,7 @@
 // cross-CTA accumulators and the barrier / status words.  Host code cannot use
 // the array's name as a device address (in host code it is a host-side
 // stand-in), so the device address is looked up with cudaGetSymbolAddress,
-// once per device, on the first call made while that device is current; that
-// first call on a device should come before any stream capture.
+// once per device, on the first call made while that device is current.
 //
 // Every call shares the array and leaves its contents behind; the call clears
 // what has to start at zero (accumulators, barrier counter, status) itself.
