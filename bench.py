@@ -60,6 +60,10 @@ def parse():
                     help="with --workload batch: time one iteration of the batched kernel per system shape")
     ap.add_argument("--sweep-parts", default="", help="sweep workload: comma-separated parts 1-6 (default all)")
     ap.add_argument("--batch-tau", type=int, default=16, help="batch workload block size (0 = autotune)")
+    ap.add_argument("--batch-cluster", type=int, default=0,
+                    help="batch workload: CTAs per cluster for the longest systems (1 = none, 0 = library choice)")
+    ap.add_argument("--batch-joint-frac", type=float, default=0.0,
+                    help="batch workload: cluster threshold as a fraction of the mean load per CTA (0 = 0.25)")
     ap.add_argument("--batch-probe-shape", default="", help="with --batch-probe one: the system shape m,n")
     ap.add_argument("--batch-probe-iters", type=int, default=2000, help="batch probe: iterations per pass")
     ap.add_argument("--batch-count", type=int, default=512, help="batch workload: number of systems")
@@ -576,7 +580,8 @@ def run_batch_workload(args):
     ps = batched_problems(args.batch_count, seed=rank, nrhs=8, scale_down=args.batch_scale)
     gen_s = time.perf_counter() - t0
     t0 = time.perf_counter()
-    bs = BatchSolver([p.A for p in ps], nrhs=8, tau=args.batch_tau)
+    bs = BatchSolver([p.A for p in ps], nrhs=8, tau=args.batch_tau, cluster=args.batch_cluster,
+                     joint_frac=args.batch_joint_frac)
     B = bs.stack_rhs([p.b for p in ps], bs.m)
     Xr = bs.stack_rhs([p.x_ref for p in ps], bs.n)
     torch.cuda.synchronize()
@@ -631,7 +636,7 @@ def run_batch_workload(args):
             "inner_iterations_per_solve": iters / steps, "max_iterations": st["max_iterations"],
             "problem_gen_s": gen_s, "create_s": create_s,
             "sum_mn": int(sum(p.A.shape[0] * p.A.shape[1] for p in ps)),
-            "col_path": st.get("col_path"),
+            "col_path": st.get("col_path"), "cluster": st.get("cluster"), "systems_on_clusters": st.get("joint"),
             "out_of_reach": {"rule": "Theorem main's rate at the batch's alpha, sigma_r^2 from device Lanczos "
                                      "(an upper estimate): iterations to 1e-8 >= log(1e-16)/log(eta) > the cap",
                              "cap": cap, "systems": len(out_idx), "rhs": 8 * len(out_idx),

@@ -398,6 +398,16 @@ typedef struct {
     int32_t col_path;     /* column-step tile shape for blocks of 16 or 32 columns: 0 =
                              16-byte vectors over tau/4 lanes of a row, 1 = one lane per
                              column; with tau = 0 the autotuner picks it               */
+    int32_t cluster;      /* CTAs per thread-block cluster for the systems predicted to
+                             run longest: each such system runs on a whole cluster (its
+                             rows and columns split over the CTAs, the two block
+                             products added up through distributed shared memory), the
+                             others on one CTA each; 1 = every system on one CTA,
+                             2 / 4 / 8, 0 = library choice (2)                        */
+    double joint_frac;    /* a system runs on a cluster when its predicted time (the
+                             previous solve's iterations times a per-iteration cost
+                             model) is at least joint_frac x the mean load per CTA;
+                             0 = 0.25                                                   */
 } rebk_batch_options;
 
 typedef struct {
@@ -414,6 +424,8 @@ typedef struct {
     int32_t col_path;      /* column-step tile shape for blocks of 16 / 32 columns: 0 =
                               16-byte vectors over tau/4 lanes of a row, 1 = one lane
                               per column (picked with tau by the autotuner)           */
+    int32_t cluster;       /* CTAs per cluster of the launches (1 = no clusters)      */
+    int32_t joint;         /* systems run on a whole cluster                          */
 } rebk_batch_stats;
 
 /*

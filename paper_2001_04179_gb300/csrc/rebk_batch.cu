@@ -7,9 +7,13 @@
 // x += A^T v), applied to every system of the batch.
 //
 // GB300 mapping.  The systems are small (A_i of at most a few tens of MB), so a
-// system belongs to one CTA: the iteration needs only __syncthreads, no device
-// barrier.  A persistent grid of one CTA per SM takes systems from a queue
-// (largest estimated work first).  The right-hand sides of a system share its
+// system belongs to one CTA, or to one thread-block cluster: the iteration needs
+// only __syncthreads (and cluster barriers), no device barrier.  A persistent
+// grid takes systems from a queue, longest predicted time first; the systems
+// predicted to take the longest run on a cluster of CTAs (2 by default), which
+// splits their rows and columns and adds the block products up through
+// distributed shared memory, so that they do not set the pass's makespan alone
+// on one SM.  The right-hand sides of a system share its
 // block sequence, so every element of a sampled block that a CTA reads feeds
 // eight FMAs per product: the column step is W = A_J^T dZ + G_J (tau x 8) and
 // dZ -= cJ A_J W; the row step is R = A_I dX - F_I + dZ_I and dX -= cI A_I^T R.
@@ -39,6 +43,8 @@ constexpr int kR = 8;           // right-hand-side stride
 constexpr int kDraws = 32;      // block draws prepared at a time (16 iterations)
 constexpr int kColRowsInFlight = 4;  // column step: row loads in flight per lane (fast path)
 constexpr int64_t kPrefetchPoolBytes = 96ll << 20;  // FP32 matrix pool above which blocks are prefetched
+constexpr int kDefaultCluster = 2;       // CTAs per cluster for the longest systems, library choice
+constexpr double kDefaultJointFrac = 0.25;  // their threshold: this fraction of the mean load per CTA
 constexpr double kIterFloorElems = 900.0;  // per-iteration latency floor of a CTA, in units of the
                                            // cost of one block element at tau 16 (queue ordering)
 
@@ -93,6 +99,8 @@ struct InnerArgs {
     int32_t *idx_out;          // NULL, or per system idx_cap pairs (j_k, i_k) of iterations 1..idx_cap
     int64_t idx_cap;
     unsigned long long timeout_ns;
+    int njoint;                // order[0 .. njoint) run on a whole cluster each (cluster launches only)
+    int *queue_joint;          // next joint queue position (zeroed before launch)
 };
 
 // Sum over the 32 lanes of 8 per-lane values v[0..7], every shuffle a useful
@@ -117,14 +125,65 @@ __device__ __forceinline__ float warp_sum8f(const float (&v)[8], int lane) {
     return c;
 }
 
+// Thread-block cluster helpers: rank and size of the cluster, a cluster-wide
+// barrier (release / acquire at cluster scope, every thread of every CTA), and
+// loads from another CTA's shared memory (distributed shared memory).
+__device__ __forceinline__ uint32_t cluster_rank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ uint32_t cluster_size() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;" : "=r"(r));
+    return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// shared::cluster address of the object at p in the CTA of the given rank
+__device__ __forceinline__ uint32_t cluster_map(const void *p, uint32_t rank) {
+    uint32_t a;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+                 : "=r"(a)
+                 : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+    return a;
+}
+__device__ __forceinline__ float ld_cluster_f32(uint32_t a) {
+    float v;
+    asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ double ld_cluster_f64(uint32_t a) {
+    double v;
+    asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+    return v;
+}
+__device__ __forceinline__ int ld_cluster_s32(uint32_t a) {
+    int v;
+    asm volatile("ld.shared::cluster.s32 %0, [%1];" : "=r"(v) : "r"(a) : "memory");
+    return v;
+}
+
 __device__ __forceinline__ void load8(const float *p, float (&v)[kR]) {
     const float4 a = *reinterpret_cast<const float4 *>(p), b = *reinterpret_cast<const float4 *>(p + 4);
     v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w; v[4] = b.x; v[5] = b.y; v[6] = b.z; v[7] = b.w;
 }
 
 // One CTA per system; CPL = columns per lane in the column step (tau <= 32 CPL).
+//
+// Cluster launches (cluster of CS CTAs): the systems order[0 .. njoint), the
+// ones predicted to run longest, are each run by a whole cluster.  CTA rank q
+// of the cluster owns rows [m q / CS, m (q+1) / CS) in the column step and
+// columns [n q / CS, n (q+1) / CS) in the row step; the two block products of
+// an iteration (W = A_J^T dZ and R = A_I dX) are per-CTA partial sums, which
+// every CTA adds up in rank order from the others' shared memory after a
+// cluster barrier (double-buffered by iteration parity, so one barrier per
+// product), and each CTA then updates its own rows of dZ / columns of dX.
+// Rank 0 alone writes the duals S, V and the recorded indices.  Once the joint
+// queue is empty, the CTAs of a cluster take the other systems one each.
 
-template <int CPL>
+template <int CPL, bool CL>
 __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) {
     extern __shared__ __align__(16) float bsm[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -132,15 +191,35 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
     float *W = Wpart + kBW * 32 * CPL * kR;             // [32*CPL][kR]
     float *Rr = W + 32 * CPL * kR;                      // [tau][kR]
     int *draws = reinterpret_cast<int *>(Rr + 256 * kR);  // [kDraws]
+    // cluster launches (CL): this CTA's partial products, two buffers each
+    // ([2][tau][kR] for W, then for R), then the test sums ([2][kR] doubles)
+    auto wc_buf = [&](int par) { return reinterpret_cast<float *>(draws + kDraws) + (size_t)par * a.tau * kR; };
+    auto rc_buf = [&](int par) { return wc_buf(2) + (size_t)par * a.tau * kR; };
+    auto ec_buf = [&](int par) { return reinterpret_cast<double *>(wc_buf(4)) + par * kR; };
     __shared__ int s_item, s_stop;
     __shared__ double s_err[kBW][kR];
+    bool joint = CL && a.njoint > 0;
 
     for (;;) {
-        if (tid == 0) s_item = atomicAdd(a.queue, 1);
-        __syncthreads();
-        const int item = s_item;
-        __syncthreads();
-        if (item >= a.count) break;
+        int item;
+        if (CL && joint) {  // rank 0 takes the next joint system for the whole cluster
+            if (cluster_rank() == 0 && tid == 0) s_item = atomicAdd(a.queue_joint, 1);
+            cluster_sync();
+            item = ld_cluster_s32(cluster_map(&s_item, 0));
+            cluster_sync();  // read by every CTA before rank 0 takes another
+            if (item >= a.njoint) {
+                joint = false;
+                continue;
+            }
+        } else {
+            if (tid == 0) s_item = a.njoint + atomicAdd(a.queue, 1);
+            __syncthreads();
+            item = s_item;
+            __syncthreads();
+            if (item >= a.count) break;
+        }
+        // ranks sharing this system: the cluster (joint systems) or this CTA alone
+        const int NRK = (CL && joint) ? (int)cluster_size() : 1, rk = (CL && joint) ? (int)cluster_rank() : 0;
         const int id = a.order[item];
         if (!a.active[id]) continue;
         const BatchSys d = a.sys[id];
@@ -152,6 +231,9 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
         float *dZ = a.dZ + d.mrow * kR, *Vd = a.Vd + d.mrow * kR;
         float *dX = a.dX + d.nrow * kR, *S = a.S + d.nrow * kR;
         const float *F = a.F32 + d.mrow * kR, *G = a.G32 + d.nrow * kR;
+        // this rank's rows (column step) and columns (row step)
+        const int rbeg = (int)(m * rk / NRK), rend = (int)(m * (rk + 1) / NRK);
+        const int cbeg = (int)(n * rk / NRK), cend = (int)(n * (rk + 1) / NRK);
         const uint64_t k0 = (uint64_t)a.iters_done[id];
         int64_t k = 0;
         bool stopped = false;
@@ -165,7 +247,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                                             : pick_block(a.cdf_c + d.tc, d.t, u, d.fb_c);
                 draws[lane] = pick;
                 // record the draws of iterations this pass runs (entry it of the system's row)
-                if (a.idx_out && (int64_t)it < a.idx_cap && k + (int64_t)(lane >> 1) < K)
+                if (a.idx_out && rk == 0 && (int64_t)it < a.idx_cap && k + (int64_t)(lane >> 1) < K)
                     a.idx_out[((int64_t)id * a.idx_cap + (int64_t)it) * 2 + (lane & 1)] = pick;
             }
             __syncthreads();
@@ -173,9 +255,10 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
             for (; k < kend; ++k) {
                 const int slot = (int)((k % (kDraws / 2)) * 2);
                 const int j = draws[slot], i = draws[slot + 1];
+                const int par = (int)(k & 1);  // reduction buffers of this iteration (cluster launches)
                 if (a.prefetch) {  // the row block of this iteration streams into L2 during the column step
                     const int64_t pi0 = (int64_t)i * a.tau;
-                    prefetch_block(A, lda, pi0, pi0 + a.tau <= m ? a.tau : m - pi0, 0, n);
+                    prefetch_block(A, lda, pi0, pi0 + a.tau <= m ? a.tau : m - pi0, cbeg, cend - cbeg);
                 }
                 // ================= column step =================
                 const int64_t j0 = (int64_t)j * a.tau;
@@ -195,13 +278,14 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                     for (int e = 0; e < 4; ++e)
 #pragma unroll
                         for (int r = 0; r < kR; ++r) acc[e][r] = 0.f;
-                    for (int64_t row0 = (int64_t)warp * rpw * UR; row0 < m; row0 += (int64_t)kBW * rpw * UR) {
+                    for (int64_t row0 = rbeg + (int64_t)warp * rpw * UR; row0 < rend;
+                         row0 += (int64_t)kBW * rpw * UR) {
                         float4 av[UR];
                         float z[UR][kR];
 #pragma unroll
                         for (int u = 0; u < UR; ++u) {
                             const int64_t row = row0 + (int64_t)u * rpw + rrow;
-                            if (row < m) {
+                            if (row < rend) {
                                 av[u] = __ldg(reinterpret_cast<const float4 *>(A + row * lda + j0) + sub);
                                 load8(dZ + row * kR, z[u]);
                             } else {
@@ -241,12 +325,12 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                     for (int q = 0; q < CPL; ++q)
 #pragma unroll
                         for (int r = 0; r < kR; ++r) acc[q][r] = 0.f;
-                    for (int64_t row0 = warp; row0 < m; row0 += (int64_t)kBW * UR) {
+                    for (int64_t row0 = rbeg + warp; row0 < rend; row0 += (int64_t)kBW * UR) {
                         float z[UR][kR], av[UR][CPL];
 #pragma unroll
                         for (int u = 0; u < UR; ++u) {
                             const int64_t row = row0 + (int64_t)u * kBW;
-                            if (row < m) {
+                            if (row < rend) {
                                 load8(dZ + row * kR, z[u]);
                                 const float *Ar = A + row * lda + j0;
 #pragma unroll
@@ -276,11 +360,27 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                     }
                 }
                 __syncthreads();
-                for (int e = tid; e < wc * kR; e += kBT) {
-                    float sum = G[(j0 + e / kR) * kR + e % kR];
-                    for (int w2 = 0; w2 < kBW; ++w2) sum += Wpart[(size_t)w2 * 32 * CPL * kR + e];
-                    W[e] = sum;
-                    S[(j0 + e / kR) * kR + e % kR] += cJ * sum;
+                if (!CL || NRK == 1) {
+                    for (int e = tid; e < wc * kR; e += kBT) {
+                        float sum = G[(j0 + e / kR) * kR + e % kR];
+                        for (int w2 = 0; w2 < kBW; ++w2) sum += Wpart[(size_t)w2 * 32 * CPL * kR + e];
+                        W[e] = sum;
+                        S[(j0 + e / kR) * kR + e % kR] += cJ * sum;
+                    }
+                } else {  // this CTA's rows, then every rank's partial in rank order
+                    float *wmine = wc_buf(par);
+                    for (int e = tid; e < wc * kR; e += kBT) {
+                        float sum = 0.f;
+                        for (int w2 = 0; w2 < kBW; ++w2) sum += Wpart[(size_t)w2 * 32 * CPL * kR + e];
+                        wmine[e] = sum;
+                    }
+                    cluster_sync();
+                    for (int e = tid; e < wc * kR; e += kBT) {
+                        float sum = G[(j0 + e / kR) * kR + e % kR];
+                        for (int q = 0; q < NRK; ++q) sum += ld_cluster_f32(cluster_map(wmine + e, (uint32_t)q));
+                        W[e] = sum;
+                        if (rk == 0) S[(j0 + e / kR) * kR + e % kR] += cJ * sum;
+                    }
                 }
                 __syncthreads();
                 if (fast) {
@@ -290,13 +390,14 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                     float wv[4][kR];
 #pragma unroll
                     for (int e = 0; e < 4; ++e) load8(W + (4 * sub + e) * kR, wv[e]);
-                    for (int64_t row0 = (int64_t)warp * rpw * UR; row0 < m; row0 += (int64_t)kBW * rpw * UR) {
+                    for (int64_t row0 = rbeg + (int64_t)warp * rpw * UR; row0 < rend;
+                         row0 += (int64_t)kBW * rpw * UR) {
                         float4 av[UR];
 #pragma unroll
                         for (int u = 0; u < UR; ++u) {
                             const int64_t row = row0 + (int64_t)u * rpw + rrow;
-                            av[u] = row < m ? __ldg(reinterpret_cast<const float4 *>(A + row * lda + j0) + sub)
-                                            : make_float4(0.f, 0.f, 0.f, 0.f);
+                            av[u] = row < rend ? __ldg(reinterpret_cast<const float4 *>(A + row * lda + j0) + sub)
+                                               : make_float4(0.f, 0.f, 0.f, 0.f);
                         }
 #pragma unroll
                         for (int u = 0; u < UR; ++u) {
@@ -313,7 +414,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
 #pragma unroll
                                 for (int r = 0; r < kR; ++r) t8[r] += __shfl_xor_sync(0xffffffffu, t8[r], o);
                             const int64_t row = row0 + (int64_t)u * rpw + rrow;
-                            if (sub == 0 && row < m) {
+                            if (sub == 0 && row < rend) {
                                 float *zr = dZ + row * kR;
 #pragma unroll
                                 for (int r = 0; r < kR; ++r) zr[r] -= cJ * t8[r];
@@ -341,7 +442,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                             }
                         }
                         const int ridx = ((lane >> 4) & 1) * 4 + ((lane >> 3) & 1) * 2 + ((lane >> 2) & 1);
-                        for (int64_t row0 = (int64_t)warp * UR; row0 < m; row0 += (int64_t)kBW * UR) {
+                        for (int64_t row0 = rbeg + (int64_t)warp * UR; row0 < rend; row0 += (int64_t)kBW * UR) {
                             float av[UR][CPL];
 #pragma unroll
                             for (int u = 0; u < UR; ++u) {
@@ -350,7 +451,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
 #pragma unroll
                                 for (int q = 0; q < CPL; ++q) {
                                     const int c = lane + 32 * q;
-                                    av[u][q] = (row < m && c < wc) ? __ldg(Ar + c) : 0.f;
+                                    av[u][q] = (row < rend && c < wc) ? __ldg(Ar + c) : 0.f;
                                 }
                             }
 #pragma unroll
@@ -365,13 +466,13 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                                 }
                                 const float v = warp_sum8f(t8, lane);
                                 const int64_t row = row0 + u;
-                                if ((lane & 3) == 0 && row < m) dZ[row * kR + ridx] -= cJ * v;
+                                if ((lane & 3) == 0 && row < rend) dZ[row * kR + ridx] -= cJ * v;
                             }
                         }
                     }
                 }
                 const bool vec4 = ((j0 & 3) == 0) && ((wc & 3) == 0);
-                for (int64_t row = (fast || wide) ? m : tid; row < m; row += kBT) {
+                for (int64_t row = (fast || wide) ? rend : rbeg + tid; row < rend; row += kBT) {
                     float t8[kR] = {0, 0, 0, 0, 0, 0, 0, 0};
                     const float *Ar = A + row * lda + j0;
                     if (vec4) {
@@ -411,7 +512,7 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                 // ================= row step =================
                 if (a.prefetch && k + 1 < kend) {  // the next column block streams into L2 during the row step
                     const int64_t pj0 = (int64_t)draws[slot + 2] * a.tau;
-                    prefetch_block(A, lda, 0, m, pj0, pj0 + a.tau <= n ? a.tau : n - pj0);
+                    prefetch_block(A, lda, rbeg, rend - rbeg, pj0, pj0 + a.tau <= n ? a.tau : n - pj0);
                 }
                 const int64_t i0 = (int64_t)i * a.tau;
                 const int hr = (int)((i0 + a.tau <= m ? a.tau : m - i0));
@@ -420,12 +521,12 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                     float acc[kR] = {0, 0, 0, 0, 0, 0, 0, 0};
                     const float *Ar = A + (i0 + l) * lda;
                     constexpr int CU = 8;  // columns in flight per lane
-                    for (int64_t col0 = lane; col0 < n; col0 += 32 * CU) {
+                    for (int64_t col0 = cbeg + lane; col0 < cend; col0 += 32 * CU) {
                         float av[CU], xv[CU][kR];
 #pragma unroll
                         for (int u = 0; u < CU; ++u) {
                             const int64_t col = col0 + 32 * u;
-                            if (col < n) {
+                            if (col < cend) {
                                 av[u] = __ldg(Ar + col);
                                 load8(dX + col * kR, xv[u]);
                             } else {
@@ -446,11 +547,23 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
 #pragma unroll
                         for (int r = 1; r < kR; ++r)
                             if (lane == r) v = acc[r];
-                        Rr[l * kR + lane] = v - F[(i0 + l) * kR + lane] + dZ[(i0 + l) * kR + lane];
+                        if (!CL || NRK == 1) Rr[l * kR + lane] = v - F[(i0 + l) * kR + lane] + dZ[(i0 + l) * kR + lane];
+                        else rc_buf(par)[l * kR + lane] = v;
                     }
                 }
-                __syncthreads();
-                for (int64_t col = tid; col < n; col += kBT) {
+                if (!CL || NRK == 1) {
+                    __syncthreads();
+                } else {  // every rank's partial in rank order; dZ_I rows of other ranks through L2
+                    cluster_sync();
+                    const float *rmine = rc_buf(par);
+                    for (int e = tid; e < hr * kR; e += kBT) {
+                        float sum = 0.f;
+                        for (int q = 0; q < NRK; ++q) sum += ld_cluster_f32(cluster_map(rmine + e, (uint32_t)q));
+                        Rr[e] = sum - F[i0 * kR + e] + __ldcg(dZ + i0 * kR + e);
+                    }
+                    __syncthreads();
+                }
+                for (int64_t col = cbeg + tid; col < cend; col += kBT) {
                     float t8[kR] = {0, 0, 0, 0, 0, 0, 0, 0};
                     for (int l0 = 0; l0 < hr; l0 += 8) {  // eight rows in flight
                         float av[8];
@@ -470,13 +583,14 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
 #pragma unroll
                     for (int r = 0; r < kR; ++r) xr[r] -= cI * t8[r];
                 }
-                for (int e = tid; e < hr * kR; e += kBT) Vd[i0 * kR + e] -= cI * Rr[e];
+                if (rk == 0)
+                    for (int e = tid; e < hr * kR; e += kBT) Vd[i0 * kR + e] -= cI * Rr[e];
                 __syncthreads();
                 // ================= stopping test =================
                 if (a.Xref && a.check_every > 0 && ((int64_t)k0 + k + 1) % a.check_every == 0) {
                     double e2[kR] = {0, 0, 0, 0, 0, 0, 0, 0};
                     const double *xb = a.Xb + d.nrow * kR, *xr = a.Xref + d.nrow * kR;
-                    for (int64_t col = tid; col < n; col += kBT) {
+                    for (int64_t col = cbeg + tid; col < cend; col += kBT) {
 #pragma unroll
                         for (int r = 0; r < kR; ++r) {
                             const double df = xb[col * kR + r] + (double)dX[col * kR + r] - xr[col * kR + r];
@@ -489,14 +603,33 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
 #pragma unroll
                         for (int r = 0; r < kR; ++r) s_err[warp][r] = e2[r];
                     __syncthreads();
-                    if (tid == 0) {
-                        int ok = 1;
-                        for (int r = 0; r < kR; ++r) {
-                            double t = 0.0;
-                            for (int w2 = 0; w2 < kBW; ++w2) t += s_err[w2][r];
-                            if (!(t <= a.thr2[(int64_t)id * kR + r])) ok = 0;
+                    if (!CL || NRK == 1) {
+                        if (tid == 0) {
+                            int ok = 1;
+                            for (int r = 0; r < kR; ++r) {
+                                double t = 0.0;
+                                for (int w2 = 0; w2 < kBW; ++w2) t += s_err[w2][r];
+                                if (!(t <= a.thr2[(int64_t)id * kR + r])) ok = 0;
+                            }
+                            s_stop = ok;
                         }
-                        s_stop = ok;
+                    } else {  // this CTA's columns, then every rank's sum in rank order
+                        double *emine = ec_buf((int)(((int64_t)k0 + k + 1) / a.check_every & 1));
+                        if (tid < kR) {
+                            double t = 0.0;
+                            for (int w2 = 0; w2 < kBW; ++w2) t += s_err[w2][tid];
+                            emine[tid] = t;
+                        }
+                        cluster_sync();
+                        if (tid == 0) {
+                            int ok = 1;
+                            for (int r = 0; r < kR; ++r) {
+                                double t = 0.0;
+                                for (int q = 0; q < NRK; ++q) t += ld_cluster_f64(cluster_map(emine + r, (uint32_t)q));
+                                if (!(t <= a.thr2[(int64_t)id * kR + r])) ok = 0;
+                            }
+                            s_stop = ok;
+                        }
                     }
                     __syncthreads();
                     if (s_stop) {
@@ -507,9 +640,11 @@ __global__ void __launch_bounds__(kBT, 1) batch_inner_kernel(const InnerArgs a) 
                 }
             }
         }
-        if (tid == 0) a.iters_done[id] += k;
+        if (tid == 0 && rk == 0) a.iters_done[id] += k;
         __syncthreads();
     }
+    // no CTA leaves while another may still read its shared memory
+    if (CL) cluster_sync();
 }
 
 // ---------------------------------------------------------------------------
@@ -708,6 +843,11 @@ struct rebk_batch_s {
     bool own_stream = false;  // created here: the legacy default stream cannot be captured
     int count = 0, nrhs = 1, tau = 0, max_outer = 6, check_every = 10;
     int col_path = 0;  // tile shape of the column step for blocks of 16 / 32 columns (autotuned with tau)
+    int cluster = 1;   // CTAs per cluster for the longest systems (1 = every system on one CTA)
+    double joint_frac = kDefaultJointFrac;  // joint when predicted time >= joint_frac x the mean load per CTA
+    int njoint = 0;           // systems at the front of the queue order run jointly in this solve
+    int grid = 0, grid_cs = 0, grid_tau = 0;  // persistent grid size for (cluster, tau)
+    std::vector<int64_t> hist_it;  // the previous solve's iterations per system (empty: none)
     double red = 1e-4;
     std::vector<int64_t> m, n, lda, a_off, mrow, nrow;
     int64_t Mrows = 0, Nrows = 0, Apool = 0;
@@ -878,21 +1018,74 @@ int cpl_for(int tau) { return tau <= 32 ? 1 : tau <= 64 ? 2 : tau <= 128 ? 4 : 8
 // of the SM's 256 KB serves as L1, which holds the dZ / dX rows that the lanes of a
 // row and the warps of a row block re-read (reserving it for a system's dZ / dX
 // instead made the systems that do not fit slower).
-size_t inner_smem(int cpl) {
-    return sizeof(float) * ((size_t)kBW * 32 * cpl * kR + 32 * cpl * kR + 256 * kR) + sizeof(int) * kDraws;
+size_t inner_smem(int cpl, int tau, int cluster) {
+    size_t b = sizeof(float) * ((size_t)kBW * 32 * cpl * kR + 32 * cpl * kR + 256 * kR) + sizeof(int) * kDraws;
+    if (cluster > 1)  // the partial products and test sums read by the other CTAs of the cluster
+        b += sizeof(float) * 4 * (size_t)tau * kR + sizeof(double) * 2 * kR;
+    return b;
 }
 
-cudaError_t launch_inner(const InnerArgs &a, int grid, cudaStream_t st) {
+void *inner_kernel(int cpl, bool cl) {
+    if (cl)
+        return cpl == 1 ? (void *)&batch_inner_kernel<1, true>
+               : cpl == 2 ? (void *)&batch_inner_kernel<2, true>
+               : cpl == 4 ? (void *)&batch_inner_kernel<4, true> : (void *)&batch_inner_kernel<8, true>;
+    return cpl == 1 ? (void *)&batch_inner_kernel<1, false>
+           : cpl == 2 ? (void *)&batch_inner_kernel<2, false>
+           : cpl == 4 ? (void *)&batch_inner_kernel<4, false> : (void *)&batch_inner_kernel<8, false>;
+}
+
+// CTAs of a persistent launch: one per SM, or for clusters of cs CTAs as many
+// whole clusters as can be resident at once (cs CTAs each).
+int inner_grid(int tau, int cs, int sms) {
+    if (cs <= 1) return sms;
+    const int cpl = cpl_for(tau);
+    const size_t smem = inner_smem(cpl, tau, cs);
+    void *k = inner_kernel(cpl, true);
+    if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) return 0;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(sms / cs * cs);
+    cfg.blockDim = dim3(kBT);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = cs;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    if (cudaOccupancyMaxActiveClusters(&nc, k, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return nc * cs;
+}
+
+cudaError_t launch_inner(const InnerArgs &a, int grid, int cs, cudaStream_t st) {
     const int cpl = cpl_for(a.tau);
-    const size_t smem = inner_smem(cpl);
-    void *k = cpl == 1 ? (void *)&batch_inner_kernel<1>
-              : cpl == 2 ? (void *)&batch_inner_kernel<2>
-              : cpl == 4 ? (void *)&batch_inner_kernel<4> : (void *)&batch_inner_kernel<8>;
+    const size_t smem = inner_smem(cpl, a.tau, cs);
+    void *k = inner_kernel(cpl, cs > 1);
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     InnerArgs c = a;
     void *params[] = {&c};
-    return cudaLaunchKernel(k, dim3(grid), dim3(kBT), params, smem, st);
+    if (cs <= 1) return cudaLaunchKernel(k, dim3(grid), dim3(kBT), params, smem, st);
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kBT);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = cs;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, k, params);
 }
 
 // Queues the kernels of one batched solve (graph-capturable: no host syncs).
@@ -938,6 +1131,7 @@ rebk_status enqueue_solve(rebk_batch h, int tau, double tol, int64_t inner_iters
             *launches += 2;
         }
         BCK(cudaMemsetAsync(h->counters, 0, sizeof(int), st));
+        BCK(cudaMemsetAsync(h->counters + 2, 0, sizeof(int), st));
         InnerArgs a;
         memset(&a, 0, sizeof(a));
         a.sys = h->d_sys;
@@ -972,7 +1166,10 @@ rebk_status enqueue_solve(rebk_batch h, int tau, double tol, int64_t inner_iters
         a.idx_out = h->rec_idx;
         a.idx_cap = h->rec_cap;
         a.timeout_ns = kBarrierTimeoutNs;
-        BCK(launch_inner(a, sms, st));
+        a.queue_joint = h->counters + 2;
+        const bool clus = h->cluster > 1 && h->grid >= h->cluster;
+        a.njoint = clus ? h->njoint : 0;
+        BCK(launch_inner(a, clus ? h->grid : sms, clus ? h->cluster : 1, st));
         ++*launches;
         // z <- z - A s, x <- x + A^T v; the FP32 duals are widened once into G and F
         // (free until the next pass) so the FP64 sweep converts nothing in its loops
@@ -1012,6 +1209,9 @@ rebk_status rebk_batch_create(rebk_batch *out, int32_t count, const int64_t *m, 
     if (o.nrhs < 0 || o.nrhs > 8) return bfail(REBK_EINVAL, "nrhs must be 1..8");
     if (o.max_outer < 0 || o.check_every < 0 || o.inner_reduction < 0) return bfail(REBK_EINVAL, "negative option");
     if (o.col_path != 0 && o.col_path != 1) return bfail(REBK_EINVAL, "col_path must be 0 or 1");
+    if (o.cluster != 0 && o.cluster != 1 && o.cluster != 2 && o.cluster != 4 && o.cluster != 8)
+        return bfail(REBK_EINVAL, "cluster must be 0 (library choice), 1, 2, 4 or 8");
+    if (!(o.joint_frac >= 0.0) || !std::isfinite(o.joint_frac)) return bfail(REBK_EINVAL, "joint_frac must be >= 0");
     for (int i = 0; i < count; ++i) {
         if (m[i] < 1 || n[i] < 1) return bfail(REBK_EINVAL, "every system needs m, n >= 1");
         if (!A[i]) return bfail(REBK_EINVAL, "NULL matrix pointer");
@@ -1026,6 +1226,8 @@ rebk_status rebk_batch_create(rebk_batch *out, int32_t count, const int64_t *m, 
     h->check_every = o.check_every > 0 ? o.check_every : 10;
     h->red = o.inner_reduction > 0 ? o.inner_reduction : 1e-4;
     h->col_path = o.col_path;
+    h->cluster = o.cluster > 0 ? o.cluster : kDefaultCluster;
+    h->joint_frac = o.joint_frac > 0 ? o.joint_frac : kDefaultJointFrac;
     h->m.assign(m, m + count);
     h->n.assign(n, n + count);
     h->alpha_given.assign(count, 0.0);
@@ -1173,6 +1375,49 @@ rebk_status run_batch(rebk_batch h, int tau, double tol, int64_t max_iter, int64
     std::vector<double> big(h->count * kR, 1e300);
     BCK(cudaMemcpyAsync(h->thr2, big.data(), sizeof(double) * big.size(), cudaMemcpyHostToDevice, st));
     BCK(cudaMemsetAsync(h->counters, 0, sizeof(int) * 4, st));
+    {
+        // Queue plan: predicted time of each system on one CTA -- the previous solve's
+        // iteration count (1 without one) times a per-iteration cost model fitted on
+        // GB300 (a latency floor plus a term in the block elements: about 5.7 us +
+        // 6.4 ns x tau / 16 x (m + n)) -- longest first.  With clusters, the systems
+        // predicted to take at least joint_frac x the mean load per CTA go first and
+        // run on a whole cluster each.  The order changes no result: each system's
+        // random stream is keyed by its index.
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (h->cluster > 1 && (h->grid_cs != h->cluster || h->grid_tau != tau)) {
+            h->grid = inner_grid(tau, h->cluster, sms);
+            h->grid_cs = h->cluster;
+            h->grid_tau = tau;
+        }
+        const bool hist = (int)h->hist_it.size() == h->count;
+        std::vector<double> cost(h->count, 0.0);
+        double total = 0.0;
+        for (int i = 0; i < h->count; ++i) {
+            if (only && !(*only)[i]) continue;
+            const double its = hist ? (double)std::max<int64_t>(h->hist_it[i], 1) : 1.0;
+            cost[i] = its * (kIterFloorElems + (double)tau / 16.0 * (double)(h->m[i] + h->n[i]));
+            total += cost[i];
+        }
+        std::vector<char> jt(h->count, 0);
+        h->njoint = 0;
+        if (h->cluster > 1 && h->grid >= h->cluster) {
+            const double load = total / h->grid;
+            for (int i = 0; i < h->count; ++i)
+                if (cost[i] > 0.0 && cost[i] >= h->joint_frac * load) {
+                    jt[i] = 1;
+                    ++h->njoint;
+                }
+        }
+        std::vector<int> order(h->count);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            if (jt[a] != jt[b]) return jt[a] > jt[b];
+            return cost[a] > cost[b];
+        });
+        BCK(cudaMemcpyAsync(h->d_order, order.data(), sizeof(int) * h->count, cudaMemcpyHostToDevice, st));
+    }
     BCK(cudaStreamSynchronize(st));
     const int passes = h->max_outer;
     int launches = 0;
@@ -1213,20 +1458,7 @@ rebk_status run_batch(rebk_batch h, int tau, double tol, int64_t max_iter, int64
     int conv = 0;
     BCK(cudaMemcpy(it.data(), h->iters_done, sizeof(int64_t) * h->count, cudaMemcpyDeviceToHost));
     BCK(cudaMemcpy(&conv, h->counters + 1, sizeof(int), cudaMemcpyDeviceToHost));
-    if (!only) {
-        // Queue order of the next solve: longest expected time first, from this solve's
-        // iteration counts and a per-iteration cost model of one CTA (a latency floor plus
-        // a term in the block elements, fitted on GB300: about 5.7 us + 6.4 ns x
-        // tau / 16 x (m + n)).  Order changes no result: each system's random stream is
-        // keyed by its index.
-        std::vector<double> cost(h->count);
-        for (int i = 0; i < h->count; ++i)
-            cost[i] = (double)it[i] * (kIterFloorElems + (double)tau / 16.0 * (double)(h->m[i] + h->n[i]));
-        std::vector<int> order(h->count);
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
-        BCK(cudaMemcpy(h->d_order, order.data(), sizeof(int) * h->count, cudaMemcpyHostToDevice));
-    }
+    if (!only) h->hist_it = it;  // the next solve's queue plan
     if (stats) {
         memset(stats, 0, sizeof(*stats));
         stats->converged = use_ref ? conv : 0;
@@ -1240,6 +1472,8 @@ rebk_status run_batch(rebk_batch h, int tau, double tol, int64_t max_iter, int64
         stats->tau = tau;
         stats->graph = used_graph ? 1 : 0;
         stats->col_path = h->col_path;
+        stats->cluster = h->cluster > 1 && h->grid >= h->cluster ? h->cluster : 1;
+        stats->joint = h->njoint;
     }
     return REBK_OK;
 }

@@ -76,14 +76,16 @@ class RebkSpectrum(ctypes.Structure):
 class RebkBatchOptions(ctypes.Structure):
     _fields_ = [("tau", ctypes.c_int32), ("nrhs", ctypes.c_int32), ("max_outer", ctypes.c_int32),
                 ("check_every", ctypes.c_int32), ("inner_reduction", ctypes.c_double),
-                ("stream", ctypes.c_void_p), ("col_path", ctypes.c_int32)]
+                ("stream", ctypes.c_void_p), ("col_path", ctypes.c_int32), ("cluster", ctypes.c_int32),
+                ("joint_frac", ctypes.c_double)]
 
 
 class RebkBatchStats(ctypes.Structure):
     _fields_ = [("converged", ctypes.c_int32), ("outer", ctypes.c_int32), ("iterations", ctypes.c_int64),
                 ("max_iterations", ctypes.c_int64), ("device_ms", ctypes.c_double),
                 ("inner_ms", ctypes.c_double), ("sweep_ms", ctypes.c_double), ("launches", ctypes.c_int64),
-                ("tau", ctypes.c_int32), ("graph", ctypes.c_int32), ("col_path", ctypes.c_int32)]
+                ("tau", ctypes.c_int32), ("graph", ctypes.c_int32), ("col_path", ctypes.c_int32),
+                ("cluster", ctypes.c_int32), ("joint", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -441,10 +441,14 @@ class BatchSolver:
     autotune at the first solve with reference solutions).  alpha: per-system
     step sizes or None (1.75 / beta_max each).  col_path: column-step tile shape
     for blocks of 16 / 32 columns (0: 16-byte row vectors, 1: lane per column;
-    autotuned with tau = 0)."""
+    autotuned with tau = 0).  cluster: CTAs per thread-block cluster for the
+    systems predicted to run longest (1: one CTA per system; 0: library
+    choice, 2); joint_frac: their threshold as a fraction of the mean load per
+    CTA (0: 0.25)."""
 
     def __init__(self, As, nrhs: int = 8, tau: int = 0, alpha=None, max_outer: int = 0,
-                 check_every: int = 0, inner_reduction: float = 0.0, stream=None, col_path: int = 0):
+                 check_every: int = 0, inner_reduction: float = 0.0, stream=None, col_path: int = 0,
+                 cluster: int = 0, joint_frac: float = 0.0):
         lib = _r.load()
         self.count = len(As)
         self._As = [np.ascontiguousarray(A, dtype=np.float64) for A in As]
@@ -456,7 +460,8 @@ class BatchSolver:
             self._alpha = np.ascontiguousarray(alpha, dtype=np.float64)
             al = self._alpha.ctypes.data_as(ctypes.c_void_p)
         opt = _r.RebkBatchOptions(tau, nrhs, max_outer, check_every, inner_reduction,
-                                  None if stream is None else ctypes.c_void_p(stream.cuda_stream), int(col_path))
+                                  None if stream is None else ctypes.c_void_p(stream.cuda_stream), int(col_path),
+                                  int(cluster), float(joint_frac))
         h = ctypes.c_void_p()
         st = lib.rebk_batch_create(ctypes.byref(h), self.count, self.m.ctypes.data_as(ctypes.c_void_p),
                                    self.n.ctypes.data_as(ctypes.c_void_p), ctypes.cast(ptrs, ctypes.c_void_p), 0,

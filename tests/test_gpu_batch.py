@@ -73,6 +73,67 @@ def test_one_pass_matches_oracle_per_system(nrhs, tau, path):
             assert np.max(np.abs(dz)) <= 1e-4 * np.max(np.abs(b[:, r])), (sid, r)
 
 
+@pytest.mark.parametrize("cluster,joint_frac,tau,path", [(2, 1e-9, 16, 0), (4, 1e-9, 16, 1), (4, 1e-9, 7, 0),
+                                                          (8, 1e-9, 64, 0), (4, 20.0, 16, 0)])
+def test_cluster_pass_matches_oracle_per_system(cluster, joint_frac, tau, path):
+    """Systems run on a whole thread-block cluster (rows and columns split over
+    its CTAs, the block products added up through distributed shared memory):
+    the same draws and the same pass as one CTA per system.  joint_frac 1e-9
+    puts every system on a cluster; 20 only the largest, the rest one per CTA."""
+    nrhs = 8
+    ps = batched_problems(9, seed=13, scale_down=8, nrhs=nrhs)
+    alphas = _alphas(ps, tau)
+    bs = BatchSolver([p.A for p in ps], nrhs=nrhs, tau=tau, alpha=alphas, max_outer=1, col_path=path,
+                     cluster=cluster, joint_frac=joint_frac)
+    B = bs.stack_rhs([p.b for p in ps], bs.m)
+    K = 100
+    out = bs.solve(B, X_ref=None, tol=0.0, max_iter=K, inner_iters=K, seed=5, record_iters=K, return_z=True)
+    st = out["stats"]
+    assert st["iterations"] == K * len(ps)
+    assert st["cluster"] == cluster
+    assert 1 <= st["joint"] <= len(ps)
+    if joint_frac < 1e-6:
+        assert st["joint"] == len(ps)
+    xs = bs.split_x(out["x"])
+    Z = out["z"].cpu().numpy()
+    idx = out["idx"].cpu().numpy()
+    for sid, p in enumerate(ps):
+        assert np.array_equal(idx[sid], oracle_draws(p.A, tau, 5, sid, K)), sid
+        ro, co = contiguous_offsets(p.m, tau), contiguous_offsets(p.n, tau)
+        lo = O.round_fp32(p.A)
+        zs = Z[bs.mrow[sid]:bs.mrow[sid + 1]]
+        b = p.b.reshape(p.m, nrhs)
+        for r in range(nrhs):
+            ref = O.refine(p.A, b[:, r], lo, ro, co, alphas[sid], seed=5, inner_iters=K, outer_max=1,
+                           stream=sid)
+            assert_close(xs[sid][:, r], ref["x"], 1e-4, str((sid, r)))
+            dz = zs[:, r] - ref["z"]
+            assert np.linalg.norm(dz) <= 1e-4 * np.linalg.norm(b[:, r]), (sid, r)
+            assert np.max(np.abs(dz)) <= 1e-4 * np.max(np.abs(b[:, r])), (sid, r)
+
+
+@pytest.mark.parametrize("cluster", [2, 4])
+def test_cluster_solves_reach_pseudoinverse_solutions(cluster):
+    """The stopping test summed over the cluster's CTAs: every RHS of every
+    system at 1e-8, and a second solve (planned from the first one's
+    iteration counts) as well."""
+    ps = batched_problems(10, seed=3, scale_down=10, nrhs=8)
+    bs = BatchSolver([p.A for p in ps], nrhs=8, tau=16, cluster=cluster, joint_frac=0.3)
+    B = bs.stack_rhs([p.b for p in ps], bs.m)
+    Xr = bs.stack_rhs([p.x_ref for p in ps], bs.n)
+    for seed in (9, 10):
+        out = bs.solve(B, X_ref=Xr, tol=1e-8, max_iter=400000, seed=seed)
+        st = out["stats"]
+        assert st["cluster"] == cluster and st["joint"] >= 1
+        assert st["converged"] == len(ps)
+        assert np.all(out["status"] == R.REBK_OK)
+        xs = bs.split_x(out["x"])
+        for sid, p in enumerate(ps):
+            for r in range(8):
+                err = np.linalg.norm(xs[sid][:, r] - p.x_ref[:, r]) / np.linalg.norm(p.x_ref[:, r])
+                assert err <= 1e-8, (sid, r, err)
+
+
 def test_batch_reaches_pseudoinverse_solutions():
     ps = batched_problems(12, seed=3, scale_down=10, nrhs=8)
     bs = BatchSolver([p.A for p in ps], nrhs=8, tau=16)
