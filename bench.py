@@ -652,7 +652,8 @@ def batch_probe(args):
     tau = --batch-tau (16 when 0), one
     pass of 2000 iterations (no stopping test), device time of the second solve
     over the iterations; next to the FP32 FMA work of an iteration at 128 FMA per
-    clock and 2.07 GHz.  --batch-probe one: only the 6000 x 2000 system, once."""
+    clock and 2.07 GHz.  --batch-probe one: only the 6000 x 2000 system, once.
+    --batch-cluster C > 1: each system on a cluster of C CTAs instead of one."""
     import torch
 
     from paper_2001_04179_gb300 import BatchSolver
@@ -668,7 +669,8 @@ def batch_probe(args):
         for (m, n) in shapes:
             rng = np.random.default_rng(m + n)
             A = rng.standard_normal((m, n))
-            bs = BatchSolver([A] * copies, nrhs=8, tau=tau, max_outer=1)
+            cl = args.batch_cluster if args.batch_cluster > 1 else 1
+            bs = BatchSolver([A] * copies, nrhs=8, tau=tau, max_outer=1, cluster=cl, joint_frac=1e-9)
             B = bs.stack_rhs([rng.standard_normal((m, 8)) for _ in range(copies)], bs.m)
             for sd in (3, 4):
                 out = bs.solve(B, X_ref=None, tol=0.0, max_iter=K, inner_iters=K, seed=sd)
@@ -677,7 +679,7 @@ def batch_probe(args):
             us = 1000.0 * st["device_ms"] / its
             fma_us = 2 * (m * tau + tau * n) * 8 / (128 * 2.07e9) * 1e6
             print(json.dumps({"probe": "batched iteration cost", "m": m, "n": n, "tau": tau, "copies": copies,
-                              "iterations": its,
+                              "cluster": st["cluster"], "systems_on_clusters": st["joint"], "iterations": its,
                               "us_per_iteration": us, "fp32_fma_us": fma_us, "fma_fraction": fma_us / us}),
                   flush=True)
             bs.close()
