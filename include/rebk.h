@@ -407,7 +407,7 @@ typedef struct {
     double joint_frac;    /* a system runs on a cluster when its predicted time (the
                              previous solve's iterations times a per-iteration cost
                              model) is at least joint_frac x the mean load per CTA;
-                             0 = 0.25                                                   */
+                             0 = 0.25, and no clusters when every system qualifies     */
 } rebk_batch_options;
 
 typedef struct {

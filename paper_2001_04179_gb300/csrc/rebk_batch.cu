@@ -44,8 +44,8 @@ constexpr int kDraws = 32;      // block draws prepared at a time (16 iterations
 constexpr int kColRowsInFlight = 4;  // column step: row loads in flight per lane (fast path)
 constexpr int64_t kPrefetchPoolBytes = 96ll << 20;  // FP32 matrix pool above which blocks are prefetched
 constexpr int kDefaultCluster = 2;       // CTAs per cluster for the longest systems, library choice
-constexpr double kDefaultJointFrac = 0.25;  // their threshold: this fraction of the mean load per CTA
-constexpr double kIterFloorElems = 900.0;  // per-iteration latency floor of a CTA, in units of the
+constexpr double kIterFloorElems = 900.0;
+constexpr double kDefaultJointFrac = 0.25;  // cluster threshold: this fraction of the mean load per CTA  // per-iteration latency floor of a CTA, in units of the
                                            // cost of one block element at tau 16 (queue ordering)
 
 
@@ -844,7 +844,8 @@ struct rebk_batch_s {
     int count = 0, nrhs = 1, tau = 0, max_outer = 6, check_every = 10;
     int col_path = 0;  // tile shape of the column step for blocks of 16 / 32 columns (autotuned with tau)
     int cluster = 1;   // CTAs per cluster for the longest systems (1 = every system on one CTA)
-    double joint_frac = kDefaultJointFrac;  // joint when predicted time >= joint_frac x the mean load per CTA
+    double joint_frac = 0.0;  // joint when predicted time >= joint_frac x the mean load per CTA
+                              // (0: kDefaultJointFrac, and no clusters when every system qualifies)
     int njoint = 0;           // systems at the front of the queue order run jointly in this solve
     int grid = 0, grid_cs = 0, grid_tau = 0;  // persistent grid size for (cluster, tau)
     std::vector<int64_t> hist_it;  // the previous solve's iterations per system (empty: none)
@@ -1167,7 +1168,7 @@ rebk_status enqueue_solve(rebk_batch h, int tau, double tol, int64_t inner_iters
         a.idx_cap = h->rec_cap;
         a.timeout_ns = kBarrierTimeoutNs;
         a.queue_joint = h->counters + 2;
-        const bool clus = h->cluster > 1 && h->grid >= h->cluster;
+        const bool clus = h->cluster > 1 && h->grid >= h->cluster && h->njoint > 0;
         a.njoint = clus ? h->njoint : 0;
         BCK(launch_inner(a, clus ? h->grid : sms, clus ? h->cluster : 1, st));
         ++*launches;
@@ -1227,7 +1228,7 @@ rebk_status rebk_batch_create(rebk_batch *out, int32_t count, const int64_t *m, 
     h->red = o.inner_reduction > 0 ? o.inner_reduction : 1e-4;
     h->col_path = o.col_path;
     h->cluster = o.cluster > 0 ? o.cluster : kDefaultCluster;
-    h->joint_frac = o.joint_frac > 0 ? o.joint_frac : kDefaultJointFrac;
+    h->joint_frac = o.joint_frac;
     h->m.assign(m, m + count);
     h->n.assign(n, n + count);
     h->alpha_given.assign(count, 0.0);
@@ -1380,9 +1381,9 @@ rebk_status run_batch(rebk_batch h, int tau, double tol, int64_t max_iter, int64
         // iteration count (1 without one) times a per-iteration cost model fitted on
         // GB300 (a latency floor plus a term in the block elements: about 5.7 us +
         // 6.4 ns x tau / 16 x (m + n)) -- longest first.  With clusters, the systems
-        // predicted to take at least joint_frac x the mean load per CTA go first and
-        // run on a whole cluster each.  The order changes no result: each system's
-        // random stream is keyed by its index.
+        // predicted at >= joint_frac (0.25 by default) x the mean load per CTA come
+        // first and run on a whole cluster each.  The order changes no result: each
+        // system's random stream is keyed by its index.
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -1400,22 +1401,22 @@ rebk_status run_batch(rebk_batch h, int tau, double tol, int64_t max_iter, int64
             cost[i] = its * (kIterFloorElems + (double)tau / 16.0 * (double)(h->m[i] + h->n[i]));
             total += cost[i];
         }
-        std::vector<char> jt(h->count, 0);
-        h->njoint = 0;
-        if (h->cluster > 1 && h->grid >= h->cluster) {
-            const double load = total / h->grid;
-            for (int i = 0; i < h->count; ++i)
-                if (cost[i] > 0.0 && cost[i] >= h->joint_frac * load) {
-                    jt[i] = 1;
-                    ++h->njoint;
-                }
-        }
         std::vector<int> order(h->count);
         std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-            if (jt[a] != jt[b]) return jt[a] > jt[b];
-            return cost[a] > cost[b];
-        });
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
+        h->njoint = 0;
+        if (h->cluster > 1 && h->grid >= h->cluster) {
+            const double frac = h->joint_frac > 0.0 ? h->joint_frac : kDefaultJointFrac;
+            const double load = total / h->grid;
+            int busy = 0;  // systems with work in this solve
+            for (int i = 0; i < h->count; ++i) busy += cost[i] > 0.0;
+            while (h->njoint < h->count && cost[order[h->njoint]] > 0.0 &&
+                   cost[order[h->njoint]] >= frac * load)
+                ++h->njoint;
+            // library choice: when every system qualifies none stands out, and a plain
+            // launch (one CTA each) is faster (152 equal systems: 315 against 322 ms)
+            if (h->joint_frac <= 0.0 && h->njoint == busy) h->njoint = 0;
+        }
         BCK(cudaMemcpyAsync(h->d_order, order.data(), sizeof(int) * h->count, cudaMemcpyHostToDevice, st));
     }
     BCK(cudaStreamSynchronize(st));
@@ -1472,7 +1473,7 @@ rebk_status run_batch(rebk_batch h, int tau, double tol, int64_t max_iter, int64
         stats->tau = tau;
         stats->graph = used_graph ? 1 : 0;
         stats->col_path = h->col_path;
-        stats->cluster = h->cluster > 1 && h->grid >= h->cluster ? h->cluster : 1;
+        stats->cluster = h->cluster > 1 && h->grid >= h->cluster && h->njoint > 0 ? h->cluster : 1;
         stats->joint = h->njoint;
     }
     return REBK_OK;

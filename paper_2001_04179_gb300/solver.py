@@ -444,7 +444,7 @@ class BatchSolver:
     autotuned with tau = 0).  cluster: CTAs per thread-block cluster for the
     systems predicted to run longest (1: one CTA per system; 0: library
     choice, 2); joint_frac: their threshold as a fraction of the mean load per
-    CTA (0: 0.25)."""
+    CTA (0: 0.25, and no clusters when every system qualifies)."""
 
     def __init__(self, As, nrhs: int = 8, tau: int = 0, alpha=None, max_outer: int = 0,
                  check_every: int = 0, inner_reduction: float = 0.0, stream=None, col_path: int = 0,
