@@ -78,6 +78,8 @@ def parse():
     ap.add_argument("--combined-systems", type=int, default=152,
                     help="combined form: batched systems of 8 held-out right-hand sides (sharing A)")
     ap.add_argument("--combined-steps", type=int, default=1500, help="combined form: network training steps")
+    ap.add_argument("--combined-batch-tau", type=int, default=0,
+                    help="combined form: block size of the timed batched solves (0 = the batch autotuner's choice)")
     ap.add_argument("--combined-target-iters", type=int, default=8000,
                     help="combined form: inner iterations per refinement pass of the target solves (2 passes)")
     ap.add_argument("--combined-stream", type=int, default=100000,
@@ -987,7 +989,10 @@ def measure_combined(args, dev, rank):
         np.concatenate([p.b[:, c0 + 8 * i:c0 + 8 * i + 8] for i in range(nbs)], axis=0))).to(dev)
     Xrb = torch.from_numpy(np.ascontiguousarray(
         np.concatenate([p.x_ref[:, c0 + 8 * i:c0 + 8 * i + 8] for i in range(nbs)], axis=0))).to(dev)
-    bsv = BatchSolver([A] * nbs, nrhs=8, tau=TAU, alpha=[alpha] * nbs, stream=stream)
+    # block size of the batched solves: the batch autotuner's (at the first solve, untimed), with
+    # its own step size 1.75 / beta_max for that partition; or a given tau at the solver's alpha
+    btau = args.combined_batch_tau
+    bsv = BatchSolver([A] * nbs, nrhs=8, tau=btau, alpha=None if btau == 0 else [alpha] * nbs, stream=stream)
     res = {}
     for mode in ("warm", "cold"):
         for rep in range(2):  # the first solve also orders the queue; the second is timed
@@ -1007,7 +1012,8 @@ def measure_combined(args, dev, rank):
         ms = ev0.elapsed_time(ev1)
         res[mode] = {"solves_per_s": nev / (ms / 1000.0), "ms": ms, "rhs": nev, "systems": nbs,
                      "rhs_reaching_1e-8": int((errs <= TOL).sum()), "rel_err_max": float(errs.max()),
-                     "iterations_mean_per_system": st_["iterations"] / nbs, "refinement_passes": st_["outer"]}
+                     "iterations_mean_per_system": st_["iterations"] / nbs, "refinement_passes": st_["outer"],
+                     "tau": st_["tau"], "col_path": st_["col_path"], "cluster": st_["cluster"]}
     bsv.close()
     # ---- plain FP64 Algorithm 1, one right-hand side at a time, on held-out right-hand sides ----
     nplain = 8
@@ -1031,7 +1037,8 @@ def measure_combined(args, dev, rank):
     sol.close()
     return {
         "workload": ("learned warm start stream: A = U diag(i^-1/2) V^T 8192x2048, b = A(Mc) + N(0,1e-3^2), "
-                     "latent 32; tau 128, alpha 1.75/beta_max, FP32 inner / FP64 refinement; "
+                     "latent 32; FP32 inner / FP64 refinement, batched tau autotuned (plain FP64 and the "
+                     "training targets at tau 128), alpha 1.75/beta_max; "
                      "MLP 8192-512-512-8192 on tcgen05 BF16 GEMMs, x0 = A^T y, z0 = b - A x0"),
         "value": warm["solves_per_s"], "unit": "solves/s",
         "speedup_vs_plain_fp64": warm["solves_per_s"] / plain["solves_per_s"],
