@@ -403,7 +403,10 @@ typedef struct {
                              rows and columns split over the CTAs, the two block
                              products added up through distributed shared memory), the
                              others on one CTA each; 1 = every system on one CTA,
-                             2 / 4 / 8, 0 = library choice (2)                        */
+                             2 / 4 / 8; 0 = library choice: clusters of 2, and the
+                             few longest systems (predicted at >= 2x the mean load
+                             per SM, at most 8) on clusters of 4 in a launch of their
+                             own beside the main one                                  */
     double joint_frac;    /* a system runs on a cluster when its predicted time (the
                              previous solve's iterations times a per-iteration cost
                              model) is at least joint_frac x the mean load per CTA;
@@ -424,8 +427,11 @@ typedef struct {
     int32_t col_path;      /* column-step tile shape for blocks of 16 / 32 columns: 0 =
                               16-byte vectors over tau/4 lanes of a row, 1 = one lane
                               per column (picked with tau by the autotuner)           */
-    int32_t cluster;       /* CTAs per cluster of the launches (1 = no clusters)      */
-    int32_t joint;         /* systems run on a whole cluster                          */
+    int32_t cluster;       /* CTAs per cluster of the main launch (1 = no clusters)   */
+    int32_t joint;         /* systems of the main launch run on a whole cluster       */
+    int32_t top_cluster;   /* CTAs per cluster of the launch of the longest systems
+                              beside the main one (library choice; 0 = none)          */
+    int32_t top_joint;     /* systems in that launch                                  */
 } rebk_batch_stats;
 
 /*

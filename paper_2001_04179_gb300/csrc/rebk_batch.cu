@@ -45,7 +45,10 @@ constexpr int kColRowsInFlight = 4;  // column step: row loads in flight per lan
 constexpr int64_t kPrefetchPoolBytes = 96ll << 20;  // FP32 matrix pool above which blocks are prefetched
 constexpr int kDefaultCluster = 2;       // CTAs per cluster for the longest systems, library choice
 constexpr double kIterFloorElems = 900.0;
-constexpr double kDefaultJointFrac = 0.25;  // cluster threshold: this fraction of the mean load per CTA  // per-iteration latency floor of a CTA, in units of the
+constexpr double kDefaultJointFrac = 0.25;  // cluster threshold: this fraction of the mean load per CTA
+constexpr int kTopCluster = 4;            // library choice: CTAs per cluster for the few longest systems
+constexpr double kTopFrac = 2.0;          // ... those predicted at >= this x the mean load per SM
+constexpr int kTopMax = 8;                // ... at most this many (their launch holds 4 x this SMs)  // per-iteration latency floor of a CTA, in units of the
                                            // cost of one block element at tau 16 (queue ordering)
 
 
@@ -844,6 +847,11 @@ struct rebk_batch_s {
     int count = 0, nrhs = 1, tau = 0, max_outer = 6, check_every = 10;
     int col_path = 0;  // tile shape of the column step for blocks of 16 / 32 columns (autotuned with tau)
     int cluster = 1;   // CTAs per cluster for the longest systems (1 = every system on one CTA)
+    bool top_tier = false;  // library choice: the few longest systems on clusters of kTopCluster,
+                            // in a launch of their own beside the main one (second stream)
+    int ntop = 0, grid_top = 0;
+    cudaStream_t stream2 = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     double joint_frac = 0.0;  // joint when predicted time >= joint_frac x the mean load per CTA
                               // (0: kDefaultJointFrac, and no clusters when every system qualifies)
     int njoint = 0;           // systems at the front of the queue order run jointly in this solve
@@ -908,6 +916,9 @@ void free_batch(rebk_batch h) {
     if (h->ev1) cudaEventDestroy(h->ev1);
     for (cudaEvent_t e : h->evs) cudaEventDestroy(e);
     if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
+    if (h->stream2) cudaStreamDestroy(h->stream2);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
     delete h;
 }
 
@@ -1038,8 +1049,8 @@ void *inner_kernel(int cpl, bool cl) {
 
 // CTAs of a persistent launch: one per SM, or for clusters of cs CTAs as many
 // whole clusters as can be resident at once (cs CTAs each).
-int inner_grid(int tau, int cs, int sms) {
-    if (cs <= 1) return sms;
+int inner_grid(int tau, int cs, int sms, int avail) {
+    if (cs <= 1) return avail;
     const int cpl = cpl_for(tau);
     const size_t smem = inner_smem(cpl, tau, cs);
     void *k = inner_kernel(cpl, true);
@@ -1061,7 +1072,7 @@ int inner_grid(int tau, int cs, int sms) {
         cudaGetLastError();
         return 0;
     }
-    return nc * cs;
+    return std::min(nc * cs, avail / cs * cs);
 }
 
 cudaError_t launch_inner(const InnerArgs &a, int grid, int cs, cudaStream_t st) {
@@ -1170,8 +1181,26 @@ rebk_status enqueue_solve(rebk_batch h, int tau, double tol, int64_t inner_iters
         a.queue_joint = h->counters + 2;
         const bool clus = h->cluster > 1 && h->grid >= h->cluster && h->njoint > 0;
         a.njoint = clus ? h->njoint : 0;
-        BCK(launch_inner(a, clus ? h->grid : sms, clus ? h->cluster : 1, st));
+        if (h->ntop > 0) {
+            // the longest systems, order[0 .. ntop), each on a cluster of kTopCluster CTAs in a
+            // launch of their own on the second stream; the main launch takes the rest
+            BCK(cudaMemsetAsync(h->counters + 3, 0, sizeof(int) * 2, st));
+            BCK(cudaEventRecord(h->ev_fork, st));
+            BCK(cudaStreamWaitEvent(h->stream2, h->ev_fork, 0));
+            InnerArgs t = a;
+            t.count = h->ntop;
+            t.njoint = h->ntop;
+            t.queue = h->counters + 4;
+            t.queue_joint = h->counters + 3;
+            BCK(launch_inner(t, h->grid_top, kTopCluster, h->stream2));
+            BCK(cudaEventRecord(h->ev_join, h->stream2));
+            ++*launches;
+            a.order = h->d_order + h->ntop;
+            a.count = h->count - h->ntop;
+        }
+        BCK(launch_inner(a, clus ? h->grid : sms - h->grid_top, clus ? h->cluster : 1, st));
         ++*launches;
+        if (h->ntop > 0) BCK(cudaStreamWaitEvent(st, h->ev_join, 0));
         // z <- z - A s, x <- x + A^T v; the FP32 duals are widened once into G and F
         // (free until the next pass) so the FP64 sweep converts nothing in its loops
         BCK(widen_f32(h->S, h->G, totn * kR, st));
@@ -1228,6 +1257,7 @@ rebk_status rebk_batch_create(rebk_batch *out, int32_t count, const int64_t *m, 
     h->red = o.inner_reduction > 0 ? o.inner_reduction : 1e-4;
     h->col_path = o.col_path;
     h->cluster = o.cluster > 0 ? o.cluster : kDefaultCluster;
+    h->top_tier = o.cluster == 0;
     h->joint_frac = o.joint_frac;
     h->m.assign(m, m + count);
     h->n.assign(n, n + count);
@@ -1298,7 +1328,7 @@ rebk_status rebk_batch_create(rebk_batch *out, int32_t count, const int64_t *m, 
     BCKH(cudaMalloc(&h->iter_cap, sizeof(int64_t) * count));
     BCKH(cudaMalloc(&h->active, sizeof(int) * count));
     BCKH(cudaMalloc(&h->status, sizeof(int) * count));
-    BCKH(cudaMalloc(&h->counters, sizeof(int) * 4));
+    BCKH(cudaMalloc(&h->counters, sizeof(int) * 8));
     BCKH(cudaMalloc(&h->thr2, sizeof(double) * count * kR));
     BCKH(cudaMalloc(&h->e2, sizeof(double) * count * kR));
     BCKH(cudaMalloc(&h->r2, sizeof(double) * count * kR));
@@ -1375,7 +1405,7 @@ rebk_status run_batch(rebk_batch h, int tau, double tol, int64_t max_iter, int64
     BCK(cudaMemcpyAsync(h->status, fours.data(), sizeof(int) * h->count, cudaMemcpyHostToDevice, st));
     std::vector<double> big(h->count * kR, 1e300);
     BCK(cudaMemcpyAsync(h->thr2, big.data(), sizeof(double) * big.size(), cudaMemcpyHostToDevice, st));
-    BCK(cudaMemsetAsync(h->counters, 0, sizeof(int) * 4, st));
+    BCK(cudaMemsetAsync(h->counters, 0, sizeof(int) * 8, st));
     {
         // Queue plan: predicted time of each system on one CTA -- the previous solve's
         // iteration count (1 without one) times a per-iteration cost model fitted on
@@ -1387,11 +1417,8 @@ rebk_status run_batch(rebk_batch h, int tau, double tol, int64_t max_iter, int64
         int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        if (h->cluster > 1 && (h->grid_cs != h->cluster || h->grid_tau != tau)) {
-            h->grid = inner_grid(tau, h->cluster, sms);
-            h->grid_cs = h->cluster;
-            h->grid_tau = tau;
-        }
+        h->ntop = 0;
+        h->grid_top = 0;
         const bool hist = (int)h->hist_it.size() == h->count;
         std::vector<double> cost(h->count, 0.0);
         double total = 0.0;
@@ -1405,17 +1432,38 @@ rebk_status run_batch(rebk_batch h, int tau, double tol, int64_t max_iter, int64
         std::iota(order.begin(), order.end(), 0);
         std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return cost[a] > cost[b]; });
         h->njoint = 0;
+        int busy = 0;  // systems with work in this solve
+        for (int i = 0; i < h->count; ++i) busy += cost[i] > 0.0;
+        // library choice: the few systems predicted at >= kTopFrac x the mean load per SM
+        // on clusters of kTopCluster, in a launch of their own beside the main one
+        if (h->top_tier && h->cluster > 1) {
+            int n1 = 0;
+            while (n1 < kTopMax && n1 < busy && cost[order[n1]] >= kTopFrac * total / sms) ++n1;
+            if (n1 > 0 && n1 < busy) {
+                const int g1 = inner_grid(tau, kTopCluster, sms, n1 * kTopCluster);
+                if (g1 >= kTopCluster) {
+                    h->ntop = g1 / kTopCluster < n1 ? g1 / kTopCluster : n1;
+                    h->grid_top = h->ntop * kTopCluster;
+                    if (!h->stream2) BCK(cudaStreamCreateWithFlags(&h->stream2, cudaStreamNonBlocking));
+                    if (!h->ev_fork) BCK(cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming));
+                    if (!h->ev_join) BCK(cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming));
+                }
+            }
+        }
+        if (h->cluster > 1) {
+            h->grid = inner_grid(tau, h->cluster, sms, sms - h->grid_top);
+            h->grid_cs = h->cluster;
+            h->grid_tau = tau;
+        }
         if (h->cluster > 1 && h->grid >= h->cluster) {
             const double frac = h->joint_frac > 0.0 ? h->joint_frac : kDefaultJointFrac;
             const double load = total / h->grid;
-            int busy = 0;  // systems with work in this solve
-            for (int i = 0; i < h->count; ++i) busy += cost[i] > 0.0;
-            while (h->njoint < h->count && cost[order[h->njoint]] > 0.0 &&
-                   cost[order[h->njoint]] >= frac * load)
+            while (h->ntop + h->njoint < h->count && cost[order[h->ntop + h->njoint]] > 0.0 &&
+                   cost[order[h->ntop + h->njoint]] >= frac * load)
                 ++h->njoint;
             // library choice: when every system qualifies none stands out, and a plain
             // launch (one CTA each) is faster (152 equal systems: 315 against 322 ms)
-            if (h->joint_frac <= 0.0 && h->njoint == busy) h->njoint = 0;
+            if (h->joint_frac <= 0.0 && h->ntop == 0 && h->njoint == busy) h->njoint = 0;
         }
         BCK(cudaMemcpyAsync(h->d_order, order.data(), sizeof(int) * h->count, cudaMemcpyHostToDevice, st));
     }
@@ -1475,6 +1523,8 @@ rebk_status run_batch(rebk_batch h, int tau, double tol, int64_t max_iter, int64
         stats->col_path = h->col_path;
         stats->cluster = h->cluster > 1 && h->grid >= h->cluster && h->njoint > 0 ? h->cluster : 1;
         stats->joint = h->njoint;
+        stats->top_cluster = h->ntop > 0 ? kTopCluster : 0;
+        stats->top_joint = h->ntop;
     }
     return REBK_OK;
 }

@@ -85,7 +85,8 @@ class RebkBatchStats(ctypes.Structure):
                 ("max_iterations", ctypes.c_int64), ("device_ms", ctypes.c_double),
                 ("inner_ms", ctypes.c_double), ("sweep_ms", ctypes.c_double), ("launches", ctypes.c_int64),
                 ("tau", ctypes.c_int32), ("graph", ctypes.c_int32), ("col_path", ctypes.c_int32),
-                ("cluster", ctypes.c_int32), ("joint", ctypes.c_int32)]
+                ("cluster", ctypes.c_int32), ("joint", ctypes.c_int32), ("top_cluster", ctypes.c_int32),
+                ("top_joint", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
         return {f: getattr(self, f) for f, _ in self._fields_}
