@@ -74,12 +74,14 @@ def test_one_pass_matches_oracle_per_system(nrhs, tau, path):
 
 
 @pytest.mark.parametrize("cluster,joint_frac,tau,path", [(2, 1e-9, 16, 0), (4, 1e-9, 16, 1), (4, 1e-9, 7, 0),
-                                                          (8, 1e-9, 64, 0), (4, 8.0, 16, 0)])
+                                                          (8, 1e-9, 64, 0), (4, 8.0, 16, 0), (0, 0.0, 16, 0)])
 def test_cluster_pass_matches_oracle_per_system(cluster, joint_frac, tau, path):
     """Systems run on a whole thread-block cluster (rows and columns split over
     its CTAs, the block products added up through distributed shared memory):
     the same draws and the same pass as one CTA per system.  joint_frac 1e-9
-    puts every system on a cluster; 8 only the largest, the rest one per CTA."""
+    puts every system on a cluster; 8 only the largest, the rest one per CTA.
+    cluster 0 (library choice): the longest systems on clusters of 4 in a launch
+    of their own beside the main one."""
     nrhs = 8
     ps = batched_problems(9, seed=13, scale_down=8, nrhs=nrhs)
     alphas = _alphas(ps, tau)
@@ -90,10 +92,13 @@ def test_cluster_pass_matches_oracle_per_system(cluster, joint_frac, tau, path):
     out = bs.solve(B, X_ref=None, tol=0.0, max_iter=K, inner_iters=K, seed=5, record_iters=K, return_z=True)
     st = out["stats"]
     assert st["iterations"] == K * len(ps)
-    assert st["cluster"] == cluster
-    assert 1 <= st["joint"] <= len(ps)
-    if joint_frac < 1e-6:
-        assert st["joint"] == len(ps)
+    if cluster == 0:
+        assert st["top_cluster"] == 4 and 1 <= st["top_joint"] < len(ps)
+    else:
+        assert st["cluster"] == cluster and st["top_joint"] == 0
+        assert 1 <= st["joint"] <= len(ps)
+        if joint_frac < 1e-6:
+            assert st["joint"] == len(ps)
     xs = bs.split_x(out["x"])
     Z = out["z"].cpu().numpy()
     idx = out["idx"].cpu().numpy()
