@@ -639,6 +639,7 @@ def run_batch_workload(args):
             "problem_gen_s": gen_s, "create_s": create_s,
             "sum_mn": int(sum(p.A.shape[0] * p.A.shape[1] for p in ps)),
             "col_path": st.get("col_path"), "cluster": st.get("cluster"), "systems_on_clusters": st.get("joint"),
+            "top_cluster": st.get("top_cluster"), "systems_on_top_clusters": st.get("top_joint"),
             "out_of_reach": {"rule": "Theorem main's rate at the batch's alpha, sigma_r^2 from device Lanczos "
                                      "(an upper estimate): iterations to 1e-8 >= log(1e-16)/log(eta) > the cap",
                              "cap": cap, "systems": len(out_idx), "rhs": 8 * len(out_idx),
