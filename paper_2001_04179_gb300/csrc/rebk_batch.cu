@@ -855,7 +855,7 @@ struct rebk_batch_s {
     double joint_frac = 0.0;  // joint when predicted time >= joint_frac x the mean load per CTA
                               // (0: kDefaultJointFrac, and no clusters when every system qualifies)
     int njoint = 0;           // systems at the front of the queue order run jointly in this solve
-    int grid = 0, grid_cs = 0, grid_tau = 0;  // persistent grid size for (cluster, tau)
+    int grid = 0;             // CTAs of the main cluster launch in this solve
     std::vector<int64_t> hist_it;  // the previous solve's iterations per system (empty: none)
     double red = 1e-4;
     std::vector<int64_t> m, n, lda, a_off, mrow, nrow;
@@ -1452,8 +1452,6 @@ rebk_status run_batch(rebk_batch h, int tau, double tol, int64_t max_iter, int64
         }
         if (h->cluster > 1) {
             h->grid = inner_grid(tau, h->cluster, sms, sms - h->grid_top);
-            h->grid_cs = h->cluster;
-            h->grid_tau = tau;
         }
         if (h->cluster > 1 && h->grid >= h->cluster) {
             const double frac = h->joint_frac > 0.0 ? h->joint_frac : kDefaultJointFrac;
