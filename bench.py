@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--residual-steps", type=int, default=2,
                     help="mixed solves timed with the residual stop rule (no known solution)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--workload", choices=["precision", "warm", "batch", "sparse", "sweep"], default="precision",
+    ap.add_argument("--workload", choices=["precision", "warm", "batch", "sparse", "sweep", "free"], default="precision",
                     help="precision: the headline solve (default); warm: the learned warm start "
                          "on the 8192 x 2048 spectrum workload (targets, training, warm vs cold)")
     ap.add_argument("--sparse-mixed", action="store_true",
@@ -689,6 +689,81 @@ def batch_probe(args):
     return 0
 
 
+def run_free_workload(args):
+    """Section 4's sampling without a partition (rebk_solve_free: tau row and tau column
+    indices drawn independently per iteration with probabilities proportional to their
+    squared norms) next to Algorithm 1 on the contiguous partition (rebk_solve), plain
+    FP64, the same block sizes and step size: the 1000 x 200 Gaussian system of the
+    plain-FP64 workload (tau 20, to 1e-10) and the 8000 x 20000 rank-2000 system (tau
+    128, to 1e-8).  Whole solves timed with CUDA events; per-iteration time from the
+    kernel events; algorithmic bytes 8 tau (m + n) per iteration (each drawn column
+    and row read once per product pass) against the measured L2 and HBM rates."""
+    import ctypes as _ct
+
+    import torch
+
+    from paper_2001_04179_gb300 import Solver
+    from paper_2001_04179_gb300 import rebk as _R
+    from workloads import gaussian_problem
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pk = _R.RebkPeaks()
+    _R.check(_R.load().rebk_device_peaks(_ct.byref(pk), None))
+    hbm_peak, _, peak_src = load_peaks()
+    cases = [("1000x200 Gaussian (full column rank, inconsistent), tau 20, to 1e-10",
+              gaussian_problem(1000, 200, seed=rank), 20, 1e-10),
+             ("8000x20000 rank 2000 (A = G1 G2, b = A x* + N(0, 0.01^2)), tau 128, to 1e-8",
+              make_problem(rank, True), 128, 1e-8)]
+    steps = max(1, args.steps)
+    out = []
+    for name, p, tau, tol in cases:
+        A = torch.from_numpy(p.A).to(dev)
+        sol = Solver(A, tau, tau, alpha=0.0, storage=())
+        del A
+        b = torch.from_numpy(p.b).to(dev)
+        xr = torch.from_numpy(p.x_ref).to(dev)
+        m, n = p.A.shape
+        res = {"workload": name, "alpha": sol.alpha}
+        for kind in ("partition", "free"):
+            def one(seed):
+                if kind == "free":
+                    r = sol.solve_free(b, tau, tau, tol=tol, max_iter=10**7, seed=seed, x_ref=xr)
+                else:
+                    r = sol.solve(b, tol=tol, max_iter=10**7, seed=seed, x_ref=xr)
+                if r["stats"]["rel_err"] > tol:
+                    raise RuntimeError(f"{kind} solve did not reach {tol}: {r['stats']}")
+                return r
+            for w in range(max(1, args.warmup)):
+                one(900 + w)
+            ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            ev0.record()
+            its, kms = 0, 0.0
+            for s_ in range(steps):
+                st = one(1000 + s_)["stats"]
+                its += st["iterations"]
+                kms += st["kernel_ms"]
+            ev1.record()
+            torch.cuda.synchronize()
+            ms = ev0.elapsed_time(ev1)
+            gbs = 8.0 * tau * (m + n) * its / (kms / 1000.0) / 1e9
+            res[kind] = {"solves_per_s": steps / (ms / 1000.0), "iterations_per_solve": its / steps,
+                         "us_per_iteration": 1000.0 * kms / its, "algorithmic_gbs": gbs,
+                         "l2_frac": gbs / pk.l2_gbs, "hbm_frac": gbs / hbm_peak}
+        res["free_over_partition_solves_per_s"] = res["free"]["solves_per_s"] / res["partition"]["solves_per_s"]
+        sol.close()
+        out.append(res)
+        torch.cuda.empty_cache()
+    if rank == 0:
+        print(json.dumps({"workload": "sampling without a partition vs Algorithm 1 on a partition (plain FP64)",
+                          "metric": "solves/s to the stated tolerance", "unit": "solves/s", "steps": steps,
+                          "cases": out, "l2_gbs_measured": pk.l2_gbs, "hbm_gbs": hbm_peak,
+                          "hbm_peak_source": peak_src}))
+    return 0
+
+
 def run_sparse_workload(args):
     """Sparse tomography-like workload: A 65536 x 16384 CSR, 96 nonzeros per row
     at uniform random columns, values U(0,1) 10^u (u ~ U(0,1) per row: row norms
@@ -1104,6 +1179,8 @@ def main():
         return run_profile_mlp(args)
     if args.workload == "sweep":
         return run_sweep(args)
+    if args.workload == "free":
+        return run_free_workload(args)
     if args.workload == "sparse":
         return run_sparse_workload(args)
     if args.workload == "warm":
