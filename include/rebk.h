@@ -198,8 +198,10 @@ rebk_status rebk_solve_refined(rebk_handle h, const double *b, double *x, double
  * the randomized extended Kaczmarz method.  Draw q (0-based) of the column set
  * of iteration k uses Philox counter (2(k-1), q, 0, 0), of the row set
  * (2(k-1)+1, q, 0, 0), key (seed, ext->stream_id), word 0 as in rebk_solve.
- * h: any handle (its FP64 copy of A; the per-row and per-column norm tables
- * are built on the first call).  alpha > 0: the step; <= 0: the handle's alpha.
+ * h: any handle (its FP64 copy of A; the per-row and per-column norm tables and
+ * an FP64 copy of A^T, n x m, from which the drawn columns are read as contiguous
+ * rows, are built on the first call and kept with the handle).  alpha > 0: the
+ * step; <= 0: the handle's alpha.
  * tau_row, tau_col in [1, 512].  ext as for rebk_solve_ex (x_ref stop rule
  * checked every check_every iterations, x0, z0, z_out, k0, stream_id), except
  * idx_out: device, (tau_col + tau_row) x max_iter int32 -- per iteration the

@@ -106,6 +106,8 @@ struct rebk_handle_s {
     int64_t fr_idx_cap = 0;  // in int32 entries
     double *fr_acc = nullptr;
     int fr_acc_w = 0;
+    double *fr_AT = nullptr;  // FP64 A^T (n rows of fr_ldt), built on the first partition-free solve
+    int64_t fr_ldt = 0;
     // several right-hand sides at once (rebk_solve_multi): one device buffer
     void *mr_buf = nullptr;
     size_t mr_bytes = 0;
@@ -117,7 +119,7 @@ void free_handle(rebk_handle h) {
     if (!h) return;
     void *ptrs[] = {h->A64, h->A32, h->A16, h->nr, h->nc, h->cdf_r, h->cdf_c, h->d_fallback, h->acc,
                     h->d_row_off, h->d_col_off, h->fr_rn, h->fr_cn, h->fr_cdf_r, h->fr_cdf_c,
-                    h->fr_idx, h->fr_acc, h->mr_buf,
+                    h->fr_idx, h->fr_acc, h->fr_AT, h->mr_buf,
                     h->coef_r64, h->coef_c64, h->coef_r32, h->coef_c32,
                     h->ws, h->zbuf, h->f, h->g, h->ym, h->yn, h->dz, h->dx, h->sd, h->vd,
                     h->idxbuf};
@@ -1256,6 +1258,14 @@ rebk_status rebk_solve_free(rebk_handle h, int64_t tau_row, int64_t tau_col, dou
         cudaFree(fb);
         CK(ce);
     }
+    // the drawn columns are read as rows of a transposed FP64 copy (contiguous), built once
+    if (!h->fr_AT) {
+        const int64_t ldt = round_up(h->m, 32);
+        CK(cudaMalloc(&h->fr_AT, sizeof(double) * (size_t)h->n * ldt));
+        h->fr_ldt = ldt;
+        CK(cudaMemsetAsync(h->fr_AT, 0, sizeof(double) * (size_t)h->n * ldt, st));
+        LK(h, transpose_f64(h->A64, h->lda, h->m, h->n, h->fr_AT, ldt, st));
+    }
     const int acc_w = (int)round_up(W + 1, 32);
     if (acc_w > h->fr_acc_w) {
         if (h->fr_acc) cudaFree(h->fr_acc);
@@ -1303,6 +1313,8 @@ rebk_status rebk_solve_free(rebk_handle h, int64_t tau_row, int64_t tau_col, dou
     FreeArgs a;
     memset(&a, 0, sizeof(a));
     a.A = h->A64;
+    a.AT = h->fr_AT;
+    a.ldt = h->fr_ldt;
     a.lda = h->lda;
     a.m = h->m;
     a.n = h->n;

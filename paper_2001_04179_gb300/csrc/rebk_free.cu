@@ -17,10 +17,12 @@
 // x entries); no CTA reads another's z or x.  One device-wide barrier per
 // iteration: round t applies x^{t-1} (needs r^{t-1}) and z^t (needs w^t) on
 // the owned slices, then adds its partials of r^t = A_{I_t} x^{t-1} - b_I +
-// z^t_I and of w^{t+1} = A_{J_{t+1}}^T z^t, and arrives.  The gathered
-// columns A_{:,J} are strided in the row-major copy: each lane loads single
-// elements (the partition kernel's 16-byte tiles do not apply to a scattered
-// set).  Partials meet in FP64 atomics on three rotating accumulator sets.
+// z^t_I and of w^{t+1} = A_{J_{t+1}}^T z^t, and arrives.  The drawn rows
+// are read from the row-major copy, the drawn columns from a transposed FP64
+// copy A^T (built on the first partition-free solve), where each is one
+// contiguous row: in the row-major copy a set of scattered columns costs one
+// 32-byte sector, from anywhere in the matrix, per 8-byte element.  Partials
+// meet in FP64 atomics on three rotating accumulator sets.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -32,6 +34,9 @@ namespace {
 
 constexpr int kFreeThreads = 256;
 constexpr int kFreeWarps = kFreeThreads / 32;
+constexpr int kCU = 4;             // owned rows / columns per lane in flight (the updates)
+constexpr int kRU = 4;             // rows per warp in flight (row-wise products)
+constexpr int kXCols = 32 * kCU;   // owned columns per pass of the x update
 
 __global__ void free_sample_kernel(uint64_t seed, uint64_t stream, int64_t k0, int64_t K,
                                    const double *__restrict__ cdf_r, int m, const double *__restrict__ cdf_c, int n,
@@ -51,9 +56,10 @@ __global__ void free_sample_kernel(uint64_t seed, uint64_t stream, int64_t k0, i
 }
 
 // Shared memory: the draws of two consecutive iterations (J and I, by parity),
-// w and r of the current round, and reduction scratch.
+// w and r of the current round, reduction scratch, and the per-warp partial
+// sums of the updates whose warps split a sum ([kFreeWarps][kXCols]).
 struct FreeSmem {
-    size_t jset, iset, w, r, red, total;
+    size_t jset, iset, w, r, red, part, total;
 };
 
 __host__ __device__ inline FreeSmem free_layout(int tau_r, int tau_c) {
@@ -65,6 +71,7 @@ __host__ __device__ inline FreeSmem free_layout(int tau_r, int tau_c) {
     L.w = o;    o = al(o + sizeof(double) * (size_t)tau_c);
     L.r = o;    o = al(o + sizeof(double) * (size_t)tau_r);
     L.red = o;  o = al(o + sizeof(double) * (kFreeWarps + 4));
+    L.part = o; o = al(o + sizeof(double) * kFreeWarps * (size_t)kXCols);
     L.total = o;
     return L;
 }
@@ -77,14 +84,17 @@ __global__ void __launch_bounds__(kFreeThreads, 1) rebk_free_kernel(const FreeAr
     double *sw = reinterpret_cast<double *>(fsm + L.w);
     double *sr = reinterpret_cast<double *>(fsm + L.r);
     double *red = reinterpret_cast<double *>(fsm + L.red);
+    double *part = reinterpret_cast<double *>(fsm + L.part);
     __shared__ int s_flag, s_test, s_bad_r, s_bad_w;  // one flag per decision of a round
 
     const int G = gridDim.x, cta = blockIdx.x, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double *__restrict__ A = a.A;
-    const int64_t m = a.m, n = a.n, lda = a.lda;
+    const double *__restrict__ AT = a.AT;  // n rows of ldt: A^T
+    const int64_t m = a.m, n = a.n, lda = a.lda, ldt = a.ldt;
     const int64_t r0 = m * cta / G, r1 = m * (cta + 1) / G;  // owned rows (z)
     const int64_t c0 = n * cta / G, c1 = n * (cta + 1) / G;  // owned columns (x)
     const int tr = a.tau_r, tc = a.tau_c, W = tr + tc;
+    constexpr int pw = kXCols;  // row stride of part
     const int64_t K = a.iters;
     const int aw = a.acc_w;
     const int64_t clr0 = (int64_t)aw * cta / G, clr1 = (int64_t)aw * (cta + 1) / G;  // this CTA's share
@@ -101,14 +111,31 @@ __global__ void __launch_bounds__(kFreeThreads, 1) rebk_free_kernel(const FreeAr
             else sI[(t & 1) * tr + (q - tc)] = v;
         }
     };
-    // partial of w^{t} = A_{R_c, J_t}^T z on the owned rows, into set `dst`
+    // partial of w^{t} = A_{R_c, J_t}^T z on the owned rows, into set `dst`: warps over
+    // the drawn columns (kRU in flight), each a row of A^T, lanes over the owned rows
     auto partial_w = [&](int64_t t, double *dst) {
         const int *J = sJ + (t & 1) * tc;
-        for (int q = tid; q < tc; q += kFreeThreads) {
-            const int64_t j = J[q];
-            double s = 0.0;
-            for (int64_t r = r0; r < r1; ++r) s = fma(__ldg(A + r * lda + j), z[r], s);
-            if (r1 > r0) atomicAdd(dst + tr + q, s);
+        for (int qb = warp; qb < tc; qb += kFreeWarps * kRU) {
+            double s[kRU];
+            int64_t ju[kRU];
+#pragma unroll
+            for (int u = 0; u < kRU; ++u) {
+                const int q = qb + u * kFreeWarps;
+                ju[u] = q < tc ? J[q] : -1;
+                s[u] = 0.0;
+            }
+            for (int64_t r = r0 + lane; r < r1; r += 32) {
+                const double zr = z[r];
+#pragma unroll
+                for (int u = 0; u < kRU; ++u)
+                    if (ju[u] >= 0) s[u] = fma(__ldg(AT + ju[u] * ldt + r), zr, s[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < kRU; ++u) {
+                const double v = warp_sum(s[u]);
+                const int q = qb + u * kFreeWarps;
+                if (lane == 0 && q < tc && r1 > r0) atomicAdd(dst + tr + q, v);
+            }
         }
     };
 
@@ -156,10 +183,34 @@ __global__ void __launch_bounds__(kFreeThreads, 1) rebk_free_kernel(const FreeAr
                 break;
             }
             const double cI = red[kFreeWarps];
-            for (int64_t c = c0 + tid; c < c1; c += kFreeThreads) {
-                double s = 0.0;
-                for (int q = 0; q < tr; ++q) s = fma(__ldg(A + (int64_t)I[q] * lda + c), sr[q], s);
-                x[c] -= cI * s;
+            // lanes over kXCols owned columns (coalesced), warps over the drawn rows, the
+            // warps' sums added in warp order
+            for (int64_t cb = c0; cb < c1; cb += kXCols) {
+                double acc[kCU];
+#pragma unroll
+                for (int u = 0; u < kCU; ++u) acc[u] = 0.0;
+#pragma unroll 2
+                for (int q = warp; q < tr; q += kFreeWarps) {
+                    const double *Ai = A + (int64_t)I[q] * lda;
+                    const double rq = sr[q];
+#pragma unroll
+                    for (int u = 0; u < kCU; ++u) {
+                        const int64_t c = cb + lane + 32 * u;
+                        if (c < c1) acc[u] = fma(__ldg(Ai + c), rq, acc[u]);
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kCU; ++u) part[warp * pw + lane + 32 * u] = acc[u];
+                __syncthreads();
+                for (int e = tid; e < kXCols; e += kFreeThreads) {
+                    const int64_t c = cb + e;
+                    if (c < c1) {
+                        double s = 0.0;
+                        for (int w2 = 0; w2 < kFreeWarps; ++w2) s += part[w2 * pw + e];
+                        x[c] -= cI * s;
+                    }
+                }
+                __syncthreads();
             }
         }
         if (t == K + 1) break;
@@ -182,11 +233,34 @@ __global__ void __launch_bounds__(kFreeThreads, 1) rebk_free_kernel(const FreeAr
             break;
         }
         const double cJ = red[kFreeWarps + 1];
-        for (int64_t r = r0 + warp; r < r1; r += kFreeWarps) {
-            double s = 0.0;
-            for (int q = lane; q < tc; q += 32) s = fma(__ldg(A + r * lda + J[q]), sw[q], s);
-            s = warp_sum(s);
-            if (lane == 0) z[r] -= cJ * s;
+        // lanes over kXCols owned rows (coalesced in A^T), warps over the drawn columns,
+        // the warps' sums added in warp order
+        for (int64_t rb = r0; rb < r1; rb += kXCols) {
+            double acc[kCU];
+#pragma unroll
+            for (int u = 0; u < kCU; ++u) acc[u] = 0.0;
+#pragma unroll 2
+            for (int q = warp; q < tc; q += kFreeWarps) {
+                const double *Aq = AT + (int64_t)J[q] * ldt;
+                const double wq = sw[q];
+#pragma unroll
+                for (int u = 0; u < kCU; ++u) {
+                    const int64_t r = rb + lane + 32 * u;
+                    if (r < r1) acc[u] = fma(__ldg(Aq + r), wq, acc[u]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kCU; ++u) part[warp * pw + lane + 32 * u] = acc[u];
+            __syncthreads();
+            for (int e = tid; e < kXCols; e += kFreeThreads) {
+                const int64_t r = rb + e;
+                if (r < r1) {
+                    double s = 0.0;
+                    for (int w2 = 0; w2 < kFreeWarps; ++w2) s += part[w2 * pw + e];
+                    z[r] -= cJ * s;
+                }
+            }
+            __syncthreads();
         }
         if (t + 1 <= K) load_draws(t + 1);  // J_{t+1}, I_{t+1} into the other slot
         __syncthreads();
@@ -194,14 +268,32 @@ __global__ void __launch_bounds__(kFreeThreads, 1) rebk_free_kernel(const FreeAr
         double *accT = a.acc + (t % 3) * aw;
         {
             const int *I = sI + (t & 1) * tr;
-            for (int q = warp; q < tr; q += kFreeWarps) {  // r^t: A_{i_q, C_c} x^{t-1} (+ z^t_i - b_i if owned)
-                const int64_t i = I[q];
-                double s = 0.0;
-                for (int64_t c = c0 + lane; c < c1; c += 32) s = fma(__ldg(A + i * lda + c), x[c], s);
-                s = warp_sum(s);
-                if (lane == 0) {
-                    if (i >= r0 && i < r1) s += z[i] - a.b[i];
-                    if (c1 > c0 || (i >= r0 && i < r1)) atomicAdd(accT + q, s);
+            // r^t: A_{i_q, C_c} x^{t-1} (+ z^t_i - b_i if owned); warps over the drawn rows
+            // (kRU in flight), lanes over the owned columns
+            for (int qb = warp; qb < tr; qb += kFreeWarps * kRU) {
+                double s[kRU];
+                int64_t iu[kRU];
+#pragma unroll
+                for (int u = 0; u < kRU; ++u) {
+                    const int q = qb + u * kFreeWarps;
+                    iu[u] = q < tr ? I[q] : -1;
+                    s[u] = 0.0;
+                }
+                for (int64_t c = c0 + lane; c < c1; c += 32) {
+                    const double xc = x[c];
+#pragma unroll
+                    for (int u = 0; u < kRU; ++u)
+                        if (iu[u] >= 0) s[u] = fma(__ldg(A + iu[u] * lda + c), xc, s[u]);
+                }
+#pragma unroll
+                for (int u = 0; u < kRU; ++u) {
+                    double v = warp_sum(s[u]);
+                    const int q = qb + u * kFreeWarps;
+                    if (lane == 0 && q < tr) {
+                        const int64_t i = iu[u];
+                        if (i >= r0 && i < r1) v += z[i] - a.b[i];
+                        if (c1 > c0 || (i >= r0 && i < r1)) atomicAdd(accT + q, v);
+                    }
                 }
             }
         }
@@ -233,6 +325,34 @@ __global__ void __launch_bounds__(kFreeThreads, 1) rebk_free_kernel(const FreeAr
 }  // namespace
 
 size_t free_smem_bytes(int tau_r, int tau_c) { return free_layout(tau_r, tau_c).total; }
+
+namespace {
+// AT[j * ldt + i] = A[i * lda + j] for i < m, j < n, through 32 x 32 shared-memory
+// tiles (both sides coalesced).
+__global__ void transpose_f64_kernel(const double *__restrict__ A, int64_t lda, int64_t m, int64_t n,
+                                     double *__restrict__ AT, int64_t ldt) {
+    __shared__ double tile[32][33];
+    const int64_t i0 = (int64_t)blockIdx.y * 32, j0 = (int64_t)blockIdx.x * 32;
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t i = i0 + r, j = j0 + threadIdx.x;
+        tile[r][threadIdx.x] = (i < m && j < n) ? A[i * lda + j] : 0.0;
+    }
+    __syncthreads();
+    for (int r = threadIdx.y; r < 32; r += blockDim.y) {
+        const int64_t j = j0 + r, i = i0 + threadIdx.x;
+        if (j < n && i < m) AT[j * ldt + i] = tile[threadIdx.x][r];
+    }
+}
+}  // namespace
+
+cudaError_t transpose_f64(const double *A, int64_t lda, int64_t m, int64_t n, double *AT, int64_t ldt,
+                          cudaStream_t st) {
+    if (m <= 0 || n <= 0) return cudaSuccess;
+    const dim3 grid((unsigned)((n + 31) / 32), (unsigned)((m + 31) / 32));
+    if (grid.y > 65535u) return cudaErrorInvalidValue;
+    transpose_f64_kernel<<<grid, dim3(32, 8), 0, st>>>(A, lda, m, n, AT, ldt);
+    return cudaGetLastError();
+}
 
 cudaError_t free_sample(uint64_t seed, uint64_t stream, int64_t k0, int64_t K, const double *cdf_r, int64_t m,
                         const double *cdf_c, int64_t n, int tau_r, int tau_c, int fb_r, int fb_c, int32_t *idx,

@@ -201,6 +201,8 @@ cudaError_t lanczos_extremes(const double *A, int64_t lda, int64_t m, int64_t n,
 // index sets drawn independently per row / column (plain FP64).
 struct FreeArgs {
     const double *A;        // FP64 copy, row-major, leading dimension lda
+    const double *AT;       // FP64 copy of A^T, n rows of leading dimension ldt
+    int64_t ldt;
     int64_t lda, m, n;
     int tau_r, tau_c;       // rows and columns drawn per iteration
     const double *rn, *cn;  // squared row / column norms
@@ -225,6 +227,9 @@ cudaError_t free_sample(uint64_t seed, uint64_t stream, int64_t k0, int64_t K, c
                         const double *cdf_c, int64_t n, int tau_r, int tau_c, int fb_r, int fb_c, int32_t *idx,
                         cudaStream_t st);
 cudaError_t launch_free(const FreeArgs &a, int G, cudaStream_t st);
+// AT (n rows of ldt) = A^T (A: m rows of lda), FP64.
+cudaError_t transpose_f64(const double *A, int64_t lda, int64_t m, int64_t n, double *AT, int64_t ldt,
+                          cudaStream_t st);
 size_t free_smem_bytes(int tau_r, int tau_c);
 int free_max_ctas(int tau_r, int tau_c);
 
