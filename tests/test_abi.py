@@ -190,3 +190,30 @@ def test_multi_right_hand_side_entry_points_reject_bad_arguments_on_the_host():
     assert "NULL" in lib.rebk_last_error().decode()
     g = ctypes.c_int32(0)
     assert lib.rebk_multi_group(None, R.REBK_FP32, ctypes.byref(g)) == R.REBK_EINVAL
+
+
+def test_batch_cluster_options_are_checked_on_the_host():
+    """rebk_batch_create rejects a cluster size other than 0, 1, 2, 4, 8 and a
+    negative joint_frac before any CUDA call."""
+    import ctypes
+    from paper_2001_04179_gb300 import rebk as R
+    lib = R.load()
+    m = (ctypes.c_int64 * 1)(4)
+    n = (ctypes.c_int64 * 1)(3)
+    A = (ctypes.c_double * 12)()
+    ptrs = (ctypes.c_void_p * 1)(ctypes.cast(A, ctypes.c_void_p).value)
+    h = ctypes.c_void_p()
+
+    def create(cluster, joint_frac):
+        opt = R.RebkBatchOptions(16, 8, 0, 0, 0.0, None, 0, cluster, joint_frac)
+        return lib.rebk_batch_create(ctypes.byref(h), 1, ctypes.cast(m, ctypes.c_void_p),
+                                     ctypes.cast(n, ctypes.c_void_p), ctypes.cast(ptrs, ctypes.c_void_p), 0, None,
+                                     ctypes.byref(opt))
+
+    assert create(3, 0.0) == R.REBK_EINVAL
+    assert "cluster" in lib.rebk_last_error().decode()
+    assert create(16, 0.0) == R.REBK_EINVAL
+    assert create(2, -1.0) == R.REBK_EINVAL
+    assert "joint_frac" in lib.rebk_last_error().decode()
+    assert create(2, float("nan")) == R.REBK_EINVAL
+    assert not h.value
